@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 mapping path on the RGG 2^20 workload.
+
+One step = one complete multilevel mapping (GPU-IM, Section 4.2): label-
+propagation coarsening with sort-based contraction down to < 8k vertices,
+initial mapping, then Alg. 6 refinement (label propagation + rebalancing +
+J evaluation) on every level from the coarsest to the input graph.
+
+Workload: random geometric graph, n = 2^20 points uniform in the unit square,
+radius for mean degree 12 (about 6.28M undirected edges), edge weights uniform
+in 1..10, unit vertex weights, hierarchy 4:8:8 (k = 256), distances 1:10:100,
+eps = 0.03, seed 0x5EED0002.
+
+Metric: refinement edge throughput of the whole job, in edges/s: every
+refinement round (Alg. 6 iteration) on a level with m undirected edges
+processes m edges; value = sum over the job's rounds of m / job time, so the
+coarsening, contraction, initial mapping and projection time is included in
+the denominator.  The end-to-end map time is ``ms_per_step``; J is bit-equal
+to the CPU oracle (tests).  ``e2e`` measures the same metric through the C
+ABI with host buffers (graph upload, validation, mapping, download of P).
+
+``--impl reference`` times the CPU oracle (plain serial C, one core) on the
+same workload and prints its line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edges/s per refine round, end-to-end map time at equal J, % HBM peak"
+UNIT = "edges/s"
+L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes per algorithmic byte of the reported kernel from an ncu capture,
+# valid only for the kernel source it was measured on (see profiles/).
+TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(log2n):
+    from paper_2510_12196_gb300 import inputs as I
+    return I.workload_rgg(log2n)
+
+
+def config_of(w, extra=None):
+    g, t = w.graph, w.topo
+    cfg = {"workload": f"rgg2d n=2^{int(np.log2(g.n))} mean-degree-12 edge-weights-1..10 "
+                       f"H={':'.join(map(str, t.hier))} D={':'.join(map(str, t.dist))} eps={t.eps} full-multilevel",
+           "n": g.n, "m_undirected": g.m, "m_dir": g.m_dir, "k": t.k, "seed": w.seed,
+           "l2": "flushed between timed steps (512 MiB write); the CSR (~112 MB) is below the 129 MB L2",
+           "parallelism": "replicas"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def edge_rounds(stats_levels, n_list, m_dir_list, iters_list):
+    return int(sum(it * (m // 2) for m, it in zip(m_dir_list, iters_list)))
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["index", "pci.bus_id", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        rows = [[x.strip() for x in l.split(",")] for l in self.lines if l.count(",") >= len(self.FIELDS) - 1]
+        if self.bus_id:
+            mine = [r for r in rows if r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[6:10]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("refine.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2510_12196_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_run(w, samples):
+    import oracle as O
+    g, t = w.graph, w.topo
+    prm = O.default_params(w.seed)
+    times, last = [], None
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        pi, J, st = O.map_run(g, t.hier, t.dist, t.eps, prm)
+        times.append(time.perf_counter() - t0)
+        last = (J, st)
+    J, st = last
+    er = edge_rounds(st.levels, [st.n[i] for i in range(st.levels)], [st.m_dir[i] for i in range(st.levels)],
+                     [st.iters[i] for i in range(st.levels)])
+    return times, er, J
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    w = workload(args.log2n)
+    for _ in range(max(0, args.warmup)):
+        oracle_run(w, 1)
+    times, er, J = oracle_run(w, max(1, args.steps))
+    tot = sum(times)
+    val = er * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": config_of(w), "J": J,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "the full workload per step (complete multilevel run)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+    import ctypes as C
+    from paper_2510_12196_gb300 import gpumap as G
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    w = workload(args.log2n)
+    g, t = w.graph, w.topo
+    stream = torch.cuda.current_stream(dev)
+    d_in = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adj, g.adjw, g.vw)]
+    cfg = G.map_config_default(w.seed)
+    ctx = G.map_create(*d_in, g.n, t.hier, t.dist, t.eps, cfg, stream=stream, inputs_on_device=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    Js = []
+    for _ in range(max(0, args.warmup)):
+        Js.append(G.map_run(ctx))
+    st = G.map_stats(ctx)
+    levels = st.levels
+    er = edge_rounds(levels, [st.n[i] for i in range(levels)], [st.m_dir[i] for i in range(levels)],
+                     [st.iters[i] for i in range(levels)])
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(getattr(props, "pci_bus_id", None))
+    sampler.start()
+    time.sleep(0.3)
+    G.map_profile_enable(ctx, 1)
+    launches0 = G.lib().map_launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i)  # evict L2 between timed steps (outside the events)
+        evs[i][0].record(stream)
+        Js.append(G.map_run(ctx))
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    launches = G.lib().map_launch_count() - launches0 - 0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    prof = {}
+    names = {0: "lp_gain", 1: "lp_after", 2: "eval_J", 3: "cluster", 4: "radix_sort"}
+    for kid, nm in names.items():
+        l, ms, by = C.c_int64(), C.c_double(), C.c_int64()
+        G.lib().map_profile_read(ctx, kid, C.byref(l), C.byref(ms), C.byref(by))
+        prof[nm] = {"launches": l.value, "ms": ms.value, "bytes": by.value}
+    G.map_profile_enable(ctx, 0)
+    assert len(set(Js)) == 1, f"nondeterministic J: {set(Js)}"
+    if pg:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = er * args.steps * ws / (total_ms / 1000.0)
+
+    # roofline of the dominant profiled kernel (largest device time)
+    peak, peak_kind = measured_peak()
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    tn, tv = top
+    achieved = tv["bytes"] / (tv["ms"] / 1000.0) / 1e9 if tv["ms"] > 0 else 0.0
+    tr = TRAFFIC.get(tn)
+    traffic = None
+    if tr and tr.get("kernel_hash") == kernel_hash() and tv["launches"]:
+        traffic = tr["dram_per_alg_byte"] * tv["bytes"] / tv["launches"]
+    roof = {"bound": "hbm", "kernel": tn, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+            "bytes_per_launch": tv["bytes"] / max(1, tv["launches"]), "launches": tv["launches"],
+            "avg_launch_us": 1000 * tv["ms"] / max(1, tv["launches"])}
+
+    # end to end through the C ABI with host buffers (pinned), P read back
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        h = [torch.from_numpy(a).pin_memory() for a in (g.xadj, g.adj, g.adjw, g.vw)]
+        out = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        hbytes = sum(x.numel() * x.element_size() for x in h)
+        e2e_t = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2 = G.map_create(*[x.data_ptr() for x in h], g.n, t.hier, t.dist, t.eps, cfg, stream=stream)
+            J2 = G.lib().map_run(c2, C.c_void_p(out.data_ptr()), None)
+            G.map_sync(c2)
+            dt = time.perf_counter() - t0
+            G.map_destroy(c2)
+            assert J2 == 0
+            if i > 0:  # first one warms the allocator
+                e2e_t.append(dt)
+        e2e_s = sum(e2e_t)
+        if pg:
+            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": er * len(e2e_t) * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": hbytes,
+               "d2h_bytes_per_step": g.n * 4, "ms_per_step": 1000 * e2e_s / len(e2e_t),
+               "path": "map_create(host CSR) + map_run + download of P + map_destroy"}
+
+    G.map_destroy(ctx)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        times, er_c, Jc = oracle_run(w, args.cpu_samples)
+        assert er_c == er and Jc == Js[0], "oracle and GPU disagree on the bench workload"
+        cpu = {"value": er * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the full workload, {len(times)} complete runs (serial C oracle)",
+               "ms_per_run": 1000 * sum(times) / len(times)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": config_of(w, {"levels": levels, "refine_rounds": [st.iters[i] for i in range(levels)],
+                                        "edge_rounds_per_step": er}),
+                "J": Js[0], "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": int(launches), "kernels": prof,
+                "phase_ms": {"coarsen": st.ms_coarsen, "initial": st.ms_initial, "refine": st.ms_refine,
+                             "project": st.ms_project}}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,242 @@
+/*
+ * gpumap: GB300 (sm_103a) library for the integrated multilevel process
+ * mapping method (GPU-IM, Section 4.2 of "GPU-Accelerated Algorithms for
+ * Process Mapping", Samoldekin, Schulz & Woydt).
+ *
+ * The task graph G = (V, E) with vertex weights c and edge weights w is mapped
+ * onto the k = a_1 * ... * a_l processing elements (PEs) of a hierarchical
+ * machine H = a_1:...:a_l with distances D = d_1:...:d_l (Section 2).  The
+ * library minimises the communication cost
+ *     J(P) = sum over ordered pairs (u, v) in E of w(u, v) * D(P(u), P(v))
+ * (Section 2; every undirected edge counts twice) under the balance bound
+ *     c(V_b) <= L_max = ceil((1 + eps) c(V) / k)     for every PE b.
+ * D(p, q) = 0 for p = q, else d_i for the smallest level i whose group holds
+ * both; PE p lies in level-i group floor(p / (a_1 ... a_i)), so PEs p and p+1
+ * share a processor when a_1 > 1.
+ *
+ * Conventions shared by every call:
+ *  - Graphs are CSR: xadj int64[n+1], adjncy int32[m], adjwgt int32[m],
+ *    vwgt int32[n].  Both directions of every edge are stored with equal
+ *    weight, each row is strictly ascending (no duplicates), no self-loops,
+ *    all weights >= 1, sum of vwgt < 2^31 and sum of adjwgt < 2^31.
+ *  - Mappings are int32 PE ids in [0, k), one per vertex.
+ *  - Host pointers unless stated otherwise.  The caller keeps ownership of
+ *    every buffer it passes; map_create copies its inputs.  The library owns
+ *    all device memory of a context and frees it in map_destroy.
+ *  - Work is enqueued on the CUDA stream given to map_create.  Calls that
+ *    return host data synchronise that stream before returning.
+ *  - Every call returns a map_status; on error map_last_error gives a text.
+ *    No C++ exception crosses this interface.
+ *  - Results are deterministic: the same inputs and seed give bit-identical
+ *    mappings and objectives on every run, whatever the launch schedule.
+ */
+#ifndef GPUMAP_H
+#define GPUMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GPUMAP_API __attribute__((visibility("default")))
+#else
+#define GPUMAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct map_ctx map_ctx;
+
+typedef enum {
+  MAP_OK = 0,
+  MAP_E_INVALID = 1,   /* malformed argument or graph (see map_last_error) */
+  MAP_E_OOM = 2,       /* device allocation failed */
+  MAP_E_CUDA = 3,      /* a CUDA call failed */
+  MAP_E_OVERFLOW = 4,  /* weight sums exceed the int32 contract */
+  MAP_E_TIMEOUT = 5,   /* a bounded device wait gave up */
+  MAP_E_STATE = 6,     /* call made in the wrong state (e.g. level not built) */
+  MAP_E_INTERNAL = 7   /* a device-side consistency check failed */
+} map_status;
+
+/* Optional device allocator: alloc returns device memory usable on `stream`
+ * (NULL on failure); free releases it.  Used for every device buffer of a
+ * context when both are set, else cudaMallocAsync / cudaFreeAsync are used. */
+typedef void* (*map_alloc_fn)(size_t bytes, void* user, void* stream);
+typedef void (*map_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
+
+/* Tunable constants.  Defaults (map_config_default) are the paper's:
+ * patience 12, weak_max 2, phi = 999/1000 (Alg. 6), sigma_gap 100 (Section
+ * 4.2, rebalancing threshold sigma = L_max - 100), coarsest_factor 8
+ * (coarsen until fewer than 8k vertices, Section 4.2, initial partitioning);
+ * cluster_iters 5, cluster_cap_div 4, max_levels 64 and stall 9/10 belong to
+ * the label-propagation clustering coarsener. */
+typedef struct {
+  uint64_t seed;
+  int32_t patience;
+  int32_t weak_max;
+  int32_t phi_num, phi_den;
+  int32_t sigma_gap;
+  int32_t coarsest_factor;
+  int32_t cluster_iters;
+  int32_t cluster_cap_div;
+  int32_t max_levels;
+  int32_t stall_num, stall_den;
+  map_alloc_fn alloc;
+  map_free_fn free;
+  void* alloc_user;
+} map_config;
+
+typedef struct {
+  int32_t levels;          /* graphs in the hierarchy (1 = not coarsened) */
+  int32_t n[65];           /* vertices per level */
+  int64_t m_dir[65];       /* CSR entries per level */
+  int64_t J[65];           /* objective after refining each level (map_run) */
+  int32_t iters[65];       /* Alg. 6 iterations per level (map_run) */
+  double ms_coarsen, ms_initial, ms_refine, ms_project;  /* host wall time per phase */
+  int64_t device_bytes;    /* device memory held by the context */
+} map_stats_t;
+
+/* Fills *cfg with the defaults listed above (seed 0x5EED0000, no allocator). */
+GPUMAP_API void map_config_default(map_config* cfg);
+
+/* Human-readable name of a status. */
+GPUMAP_API const char* map_status_string(map_status s);
+
+/* Creates a context for one graph and one hierarchy (Section 2).
+ *  xadj, adjncy, adjwgt, vwgt: CSR as above; adjwgt / vwgt may be NULL
+ *    (unit weights).  With inputs_on_device != 0 they are device pointers.
+ *  n >= 1 vertices.
+ *  hier[levels], dist[levels]: a_1..a_l (each >= 1) and d_1..d_l (each >= 0),
+ *    1 <= levels <= 16; the PE code space prod 2^ceil(log2 a_i) must not
+ *    exceed 16384 (k <= 16384 for power-of-two hierarchies).
+ *  eps: imbalance, 0 <= eps < 1, quantised to parts per million.
+ *  cfg: NULL for defaults.  stream: a cudaStream_t (NULL = legacy stream).
+ * The graph is validated on the device (MAP_E_INVALID / MAP_E_OVERFLOW).
+ * The initial mapping is all vertices on PE 0 until map_set_mapping or
+ * map_initial / map_run set one.  *out receives the context. */
+GPUMAP_API map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t* adjwgt,
+                      const int32_t* vwgt, int32_t n, const int32_t* hier, const int32_t* dist,
+                      int32_t levels, double eps, const map_config* cfg, void* stream,
+                      int32_t inputs_on_device, map_ctx** out);
+
+/* Frees all device memory of the context (after draining its stream). */
+GPUMAP_API void map_destroy(map_ctx* ctx);
+
+/* Text of the last error of this context (empty if none).  With ctx = NULL:
+ * the error of the last failed map_create on the calling thread. */
+GPUMAP_API const char* map_last_error(const map_ctx* ctx);
+
+/* Waits for all work of the context. */
+GPUMAP_API map_status map_sync(map_ctx* ctx);
+
+/* Number of PEs k and balance bound L_max of the context. */
+GPUMAP_API map_status map_info(const map_ctx* ctx, int32_t* out_k, int64_t* out_lmax, int64_t* out_total_weight);
+
+/* Sets / reads the mapping of hierarchy level `level` (0 = input graph):
+ * pi is host int32[n_level] of PE ids in [0, k). */
+GPUMAP_API map_status map_set_mapping(map_ctx* ctx, int32_t level, const int32_t* pi);
+GPUMAP_API map_status map_get_mapping(map_ctx* ctx, int32_t level, int32_t* pi);
+
+/* Objective J (Section 2, int64) and the maximum block weight (maxImb of
+ * Alg. 6) of the current mapping of `level`.  Either output may be NULL. */
+GPUMAP_API map_status map_objective(map_ctx* ctx, int32_t level, int64_t* out_J, int64_t* out_max_block_weight);
+
+/* Block weights c(V_b), host int64[k], of the current mapping of `level`. */
+GPUMAP_API map_status map_block_weights(map_ctx* ctx, int32_t level, int64_t* out_W);
+
+/* One step of unconstrained label propagation (Alg. 4) on `level`:
+ * gains by Eq. 1 over the neighbouring PEs, best target (lowest PE id on
+ * ties), non-negative filter, recomputed gain under the ord approximation,
+ * simultaneous move of the vertices that stay non-negative, and locking of
+ * the moved vertices for the next label-propagation step (Section 4.2).
+ * *out_moved (may be NULL) receives |M|. */
+GPUMAP_API map_status map_lp_step(map_ctx* ctx, int32_t level, int32_t* out_moved);
+
+/* The per-vertex results of the last map_lp_step on `level` (host arrays of
+ * n_level entries, any may be NULL): target PE P'(v) (P(v) outside X),
+ * gain g(v) (0 outside X), membership in X, and the lock (= moved) flags. */
+GPUMAP_API map_status map_get_lp_state(map_ctx* ctx, int32_t level, int32_t* pi_prime, int64_t* gain,
+                            uint8_t* in_x, uint8_t* moved);
+
+/* Sets the lock flags (host uint8[n_level]) used by the next map_lp_step. */
+GPUMAP_API map_status map_set_lock(map_ctx* ctx, int32_t level, const uint8_t* lock);
+
+/* One weak (Alg. 5) or strong rebalancing step on `level` with edge-cut
+ * loss (Section 4.2).  t is the iteration number that seeds the "random
+ * block" fallback.  *out_moved (may be NULL) receives the moved count. */
+GPUMAP_API map_status map_rebalance_step(map_ctx* ctx, int32_t level, int32_t strong, int32_t t, int32_t* out_moved);
+
+/* Overall refinement (Alg. 6) of the current mapping of `level`.  rounds < 0
+ * uses the patience rule (12 / 2 / phi); rounds >= 0 runs exactly that many
+ * iterations.  The best mapping found is kept.  Outputs may be NULL. */
+GPUMAP_API map_status map_refine(map_ctx* ctx, int32_t level, int32_t rounds, int64_t* out_J,
+                      int64_t* out_max_block_weight, int32_t* out_iters);
+
+/* Per-iteration record of the last map_refine (host arrays of `cap`
+ * entries, any may be NULL): step kind (0 label propagation, 1 weak,
+ * 2 strong), J and max block weight after the step. *out_count = iterations. */
+GPUMAP_API map_status map_get_refine_trace(map_ctx* ctx, int32_t cap, int32_t* kind, int64_t* J,
+                                int64_t* max_block_weight, int32_t* out_count);
+
+/* Builds the coarse hierarchy (Section 4.2: coarsen until fewer than
+ * coarsest_factor * k vertices) by label-propagation clustering and
+ * contraction (summed vertex weights, fused parallel edges, dropped
+ * self-loops; Section 2.1, Alg. 3).  Replaces any previous hierarchy. */
+GPUMAP_API map_status map_coarsen(map_ctx* ctx, int32_t* out_levels);
+
+/* Sizes of hierarchy level `level`. */
+GPUMAP_API map_status map_level_info(map_ctx* ctx, int32_t level, int32_t* out_n, int64_t* out_m_dir);
+
+/* Copies level `level` of the hierarchy to host arrays (any may be NULL):
+ * CSR (xadj[n+1], adjncy[m], adjwgt[m], vwgt[n]) and the map M[n] of its
+ * vertices to the next coarser level (undefined for the coarsest level). */
+GPUMAP_API map_status map_get_level_graph(map_ctx* ctx, int32_t level, int64_t* xadj, int32_t* adjncy,
+                               int32_t* adjwgt, int32_t* vwgt, int32_t* M);
+
+/* Initial mapping of the coarsest level (breadth-first order cut into k
+ * consecutive weight chunks; Section 4.2 leaves this partitioner open). */
+GPUMAP_API map_status map_initial(map_ctx* ctx);
+
+/* Uncontraction (Section 4.2): P_level(v) = P_{level+1}(M(v)). */
+GPUMAP_API map_status map_project(map_ctx* ctx, int32_t level);
+
+/* The whole GPU-IM pipeline: coarsen, initial mapping, Alg. 6 on the
+ * coarsest level, then project and refine level by level.  out_pi (host
+ * int32[n], may be NULL) receives the final mapping, *out_J its objective. */
+GPUMAP_API map_status map_run(map_ctx* ctx, int32_t* out_pi, int64_t* out_J);
+
+/* Statistics of the hierarchy and of the last map_run. */
+GPUMAP_API map_status map_stats(map_ctx* ctx, map_stats_t* out);
+
+/* Kernel classes of the optional profiler. */
+enum {
+  MAP_K_LP_GAIN = 0,   /* Alg. 4 step 1 (gains, low-degree path) */
+  MAP_K_LP_AFTER = 1,  /* Alg. 4 step 2 (recomputed gains, low-degree path) */
+  MAP_K_EVAL = 2,      /* objective J (low-degree path) */
+  MAP_K_CLUSTER = 3,   /* clustering rating (low-degree path) */
+  MAP_K_SORT = 4,      /* radix-sort scatter passes */
+  MAP_K_COUNT = 5
+};
+
+/* Enables (1) or disables (0) CUDA-event timing of the kernel classes above
+ * on the context's stream.  Timing adds two event records per timed launch
+ * and no synchronisation. */
+GPUMAP_API map_status map_profile_enable(map_ctx* ctx, int32_t enable);
+
+/* Totals since the last read for kernel class `which`: timed launches,
+ * device time in ms (sum of event intervals) and the algorithmic bytes those
+ * launches move by the library's byte model (compulsory CSR and per-vertex
+ * streams; each neighbour gather counted once as 4 bytes).  Synchronises the
+ * stream; resets the class.  Outputs may be NULL. */
+GPUMAP_API map_status map_profile_read(map_ctx* ctx, int32_t which, int64_t* launches, double* total_ms,
+                                       int64_t* bytes);
+
+/* Number of kernels this library has launched in this process so far. */
+GPUMAP_API long long map_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPUMAP_H */

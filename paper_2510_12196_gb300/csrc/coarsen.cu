@@ -1,0 +1,841 @@
+// Coarsening engine: graph validation, label-propagation clustering,
+// contraction by sort + segmented reduce, projection (uncontraction) and the
+// initial mapping of the coarsest graph.
+//
+// Clustering (the clustering alternative named in Sections 2.1 and 4.2):
+// clusters start as singletons; in each of two sub-rounds per iteration the
+// active half of the vertices (a hash bit) rates the neighbouring clusters by
+// edge weight (own cluster included), ties to the smaller tie-hash, then the
+// smaller label; requests into a cluster are admitted in (hash, id) order
+// while it stays within the weight cap.  Only over-subscribed clusters need
+// that order, so only their requests are sorted.  Every decision is a
+// function of values, never of thread timing, which keeps the result
+// bit-identical to a serial evaluation.
+//
+// Contraction (Section 2.1 semantics, replacing the CAS hashing of Alg. 3):
+// keys (M(u), M(v)) of the non-self-loop edges are radix-sorted, equal keys
+// are reduced by a prefix sum of the weights, and the coarse CSR rows follow
+// from the sorted unique keys, so adjacency order is deterministic.
+#include <algorithm>
+#include <chrono>
+
+#include "engine.h"
+
+namespace gm {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHiThreads = 256;
+
+struct GraphView {
+  int32_t n;
+  const int64_t* __restrict__ xadj;
+  const int32_t* __restrict__ adj;
+  const int32_t* __restrict__ adjw;
+  const int32_t* __restrict__ vw;
+};
+inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+
+inline unsigned grid_for(const Ctx& c, int64_t items_per_block, int64_t n) {
+  int64_t g = (n + items_per_block - 1) / items_per_block;
+  int64_t cap = (int64_t)c.num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------
+// validation of the input graph
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_validate(GraphView g, int64_t m, uint32_t* err, unsigned long long* sums) {
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  uint32_t e_local = 0;
+  unsigned long long sw = 0, sv = 0;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
+    if (beg < 0 || end < beg || end > m) {
+      e_local |= ERR_XADJ;
+      continue;
+    }
+    if (lane == 0) {
+      if (g.vw[v] < 1) e_local |= ERR_WEIGHT;
+      else sv += (unsigned long long)g.vw[v];
+    }
+    for (int64_t e = beg + lane; e < end; e += kSubWarp) {
+      const int32_t u = g.adj[e];
+      const int32_t w = g.adjw[e];
+      if (u < 0 || u >= g.n) {
+        e_local |= ERR_RANGE;
+        continue;
+      }
+      if (u == v) e_local |= ERR_SELFLOOP;
+      if (e > beg && g.adj[e - 1] >= u) e_local |= ERR_UNSORTED;
+      if (w < 1) e_local |= ERR_WEIGHT;
+      else sw += (unsigned long long)w;
+      int64_t lo = g.xadj[u], hi = g.xadj[u + 1];
+      lo = lo < 0 ? 0 : (lo > m ? m : lo);
+      hi = hi < lo ? lo : (hi > m ? m : hi);
+      while (lo < hi) {  // first entry >= v in row u
+        const int64_t mid = (lo + hi) >> 1;
+        if (g.adj[mid] < v) lo = mid + 1;
+        else hi = mid;
+      }
+      const int64_t rend = g.xadj[u + 1] > m ? m : g.xadj[u + 1];
+      if (lo >= rend || g.adj[lo] != v || g.adjw[lo] != w) e_local |= ERR_ASYM;
+    }
+  }
+  if (e_local) atomicOr(err, e_local);
+  if (sw) atomicAdd(&sums[1], sw);
+  if (sv) atomicAdd(&sums[0], sv);
+}
+
+__global__ void k_iota(int32_t* a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// clustering
+// ---------------------------------------------------------------------------
+struct Cand {
+  int32_t score;
+  int32_t t;
+  uint64_t h;
+};
+// a better than b: larger score, then smaller tie-hash, then smaller label
+__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
+  if (a.t < 0) return false;
+  if (b.t < 0) return true;
+  if (a.score != b.score) return a.score > b.score;
+  if (a.h != b.h) return a.h < b.h;
+  return a.t < b.t;
+}
+
+struct ClusterArgs {
+  const int32_t* C;      // labels (snapshot)
+  const int32_t* Wc;     // cluster weights (snapshot)
+  int32_t* ReqW;         // requested weight per target
+  int32_t* req;          // requested target per vertex (-1 none)
+  int64_t wcap;
+  uint64_t seed;
+  int32_t level;
+  int32_t it;
+  int32_t round;
+};
+
+__device__ __forceinline__ bool cluster_active(const ClusterArgs& a, int32_t v, int64_t deg) {
+  return deg > 0 && (int32_t)((h_active(a.seed, a.level, v) >> a.it) & 1ULL) == a.round;
+}
+
+__device__ __forceinline__ void cluster_request(const ClusterArgs& a, int32_t v, int32_t own, int32_t best,
+                                                int32_t cv) {
+  if (best != own && (int64_t)a.Wc[best] + cv <= a.wcap) {
+    a.req[v] = best;
+    atomicAdd(&a.ReqW[best], cv);
+  } else {
+    a.req[v] = -1;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cluster_low(GraphView g, ClusterArgs a) {
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  for (int64_t vv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; vv < g.n; vv += nsw) {
+    const int32_t v = (int32_t)vv;
+    const int64_t beg = g.xadj[v];
+    const int deg = (int)(g.xadj[v + 1] - beg);
+    if (deg > kLowDeg) continue;
+    if (!cluster_active(a, v, deg)) {
+      if (lane == 0) a.req[v] = -1;
+      continue;
+    }
+    const int32_t own = a.C[v];
+    int32_t t[kSlots], w[kSlots];
+    int32_t so = 0;
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) {
+      const int idx = lane + kSubWarp * r;
+      if (idx < deg) {
+        t[r] = a.C[g.adj[beg + idx]];
+        w[r] = g.adjw[beg + idx];
+      } else {
+        t[r] = -1;
+        w[r] = 0;
+      }
+      if (t[r] == own) so += w[r];
+    }
+#pragma unroll
+    for (int o = kSubWarp / 2; o > 0; o >>= 1) so += tile.shfl_xor(so, o);
+    int32_t sc[kSlots] = {0, 0, 0, 0};
+    const int rows = (deg + kSubWarp - 1) / kSubWarp;
+    for (int rr = 0; rr < rows; rr++) {
+      int32_t trr = t[0], wrr = w[0];
+#pragma unroll
+      for (int i = 1; i < kSlots; i++)
+        if (rr == i) {
+          trr = t[i];
+          wrr = w[i];
+        }
+      for (int j = 0; j < kSubWarp; j++) {
+        const int32_t ts = tile.shfl(trr, j);
+        const int32_t ws = tile.shfl(wrr, j);
+#pragma unroll
+        for (int r = 0; r < kSlots; r++) sc[r] += (t[r] == ts) ? ws : 0;
+      }
+    }
+    Cand best{so, own, h_tie(a.seed, a.level, own)};
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) {
+      if (t[r] < 0 || t[r] == own) continue;
+      Cand x{sc[r], t[r], h_tie(a.seed, a.level, t[r])};
+      if (better(x, best)) best = x;
+    }
+#pragma unroll
+    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+      Cand x{tile.shfl_xor(best.score, o), tile.shfl_xor(best.t, o), tile.shfl_xor(best.h, o)};
+      if (better(x, best)) best = x;
+    }
+    if (lane == 0) cluster_request(a, v, own, best.t, g.vw[v]);
+  }
+}
+
+// one CTA per high-degree vertex, open-addressing table in global memory
+__device__ __forceinline__ uint32_t slot_hash(int32_t t) {
+  uint32_t x = (uint32_t)t * 0x9E3779B1u;
+  return x ^ (x >> 15);
+}
+
+__global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                             const int64_t* __restrict__ hoff, int32_t* hkey,
+                                                             int32_t* hval, ClusterArgs a, uint32_t* err) {
+  __shared__ Cand sb[32];
+  for (int32_t idx = blockIdx.x; idx < n_hi; idx += gridDim.x) {
+    const int32_t v = hi[idx];
+    const int64_t deg = g.xadj[v + 1] - g.xadj[v];
+    if (!cluster_active(a, v, deg)) {
+      if (threadIdx.x == 0) a.req[v] = -1;
+      continue;
+    }
+    const int64_t base = hoff[idx];
+    const int32_t size = (int32_t)(hoff[idx + 1] - base);
+    const uint32_t mask = (uint32_t)size - 1u;
+    int32_t* K = hkey + base;
+    int32_t* V = hval + base;
+    for (int32_t s = threadIdx.x; s < size; s += blockDim.x) {
+      K[s] = -1;
+      V[s] = 0;
+    }
+    __syncthreads();
+    const int32_t own = a.C[v];
+    const int64_t beg = g.xadj[v];
+    for (int64_t e = beg - 1 + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x) {
+      const int32_t t = (e < beg) ? own : a.C[g.adj[e]];
+      const int32_t w = (e < beg) ? 0 : g.adjw[e];
+      uint32_t h = slot_hash(t) & mask;
+      bool placed = false;
+      for (int32_t probe = 0; probe < size; probe++) {
+        const int32_t prev = atomicCAS(&K[h], -1, t);
+        if (prev == -1 || prev == t) {
+          atomicAdd(&V[h], w);
+          placed = true;
+          break;
+        }
+        h = (h + 1) & mask;
+      }
+      if (!placed) atomicOr(err, ERR_CAPACITY);
+    }
+    __syncthreads();
+    Cand best{0, -1, 0};
+    for (int32_t s = threadIdx.x; s < size; s += blockDim.x) {
+      const int32_t t = K[s];
+      if (t < 0) continue;
+      Cand x{V[s], t, h_tie(a.seed, a.level, t)};
+      if (better(x, best)) best = x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      Cand x{__shfl_xor_sync(0xffffffffu, best.score, o), __shfl_xor_sync(0xffffffffu, best.t, o),
+             __shfl_xor_sync(0xffffffffu, best.h, o)};
+      if (better(x, best)) best = x;
+    }
+    if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+        if (better(sb[w], best)) best = sb[w];
+      cluster_request(a, v, own, best.t, g.vw[v]);
+    }
+    __syncthreads();
+  }
+}
+
+// 1: admitted without ordering (the whole demand fits), 2: contested
+__global__ void k_cluster_classify(int32_t n, const int32_t* __restrict__ req, const int32_t* __restrict__ Wc,
+                                   const int32_t* __restrict__ ReqW, int64_t wcap, uint8_t* flag) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = req[v];
+    uint8_t f = 0;
+    if (t >= 0) f = ((int64_t)Wc[t] + ReqW[t] <= wcap) ? 1 : 2;
+    flag[v] = f;
+  }
+}
+
+struct LoadContested {
+  const uint8_t* flag;
+  __device__ int64_t operator()(int64_t i) const { return flag[i] == 2 ? 1 : 0; }
+};
+struct StoreContested {
+  const int32_t* req;
+  uint64_t seed;
+  int32_t level;
+  uint64_t* key;
+  int32_t* val;
+  __device__ void operator()(int64_t i, int64_t e, int64_t x) const {
+    if (x) {
+      const uint32_t hk = (uint32_t)(h_active(seed, level, (int32_t)i) >> 32);
+      key[e] = ((uint64_t)(uint32_t)req[i] << 32) | hk;
+      val[e] = (int32_t)i;
+    }
+  }
+};
+struct LoadSortedVw {
+  const int32_t* val;
+  const int32_t* vw;
+  __device__ int64_t operator()(int64_t i) const { return vw[val[i]]; }
+};
+
+__global__ void k_cluster_heads(const uint64_t* __restrict__ key, const int64_t* __restrict__ P, const int64_t* d_n,
+                                int64_t max_n, int64_t* headP) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = key[i] >> 32;
+    if (i == 0 || (key[i - 1] >> 32) != t) headP[t] = P[i];
+  }
+}
+
+__global__ void k_cluster_admit(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                                const int64_t* __restrict__ P, const int64_t* __restrict__ headP, const int64_t* d_n,
+                                int64_t max_n, const int32_t* __restrict__ Wc, const int32_t* __restrict__ vw,
+                                int64_t wcap, uint8_t* flag) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = (int32_t)(key[i] >> 32);
+    const int32_t v = val[i];
+    const int64_t inc = P[i] + vw[v] - headP[t];
+    flag[v] = ((int64_t)Wc[t] + inc <= wcap) ? 1 : 0;
+  }
+}
+
+__global__ void k_cluster_apply(int32_t n, const int32_t* __restrict__ req, const uint8_t* __restrict__ flag,
+                                int32_t* C, int32_t* Wc, int32_t* ReqW, const int32_t* __restrict__ vw,
+                                int64_t* moved) {
+  int32_t mine = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = req[v];
+    if (t < 0) continue;
+    ReqW[t] = 0;
+    if (flag[v] != 1) continue;
+    const int32_t cv = vw[v];
+    atomicAdd(&Wc[C[v]], -cv);
+    atomicAdd(&Wc[t], cv);
+    C[v] = t;
+    mine++;
+  }
+  if (mine) atomicAdd((unsigned long long*)moved, (unsigned long long)mine);
+}
+
+// isolated vertices: chunks of weight <= cap in id order, labelled n + chunk
+struct LoadIsolated {
+  const int64_t* xadj;
+  const int32_t* vw;
+  __device__ int64_t operator()(int64_t v) const { return xadj[v + 1] == xadj[v] ? vw[v] : 0; }
+};
+struct StoreIsolated {
+  int32_t* C;
+  const int32_t* vw;
+  int32_t n;
+  int64_t wcap;
+  __device__ void operator()(int64_t v, int64_t s, int64_t x) const {
+    if (!x) return;
+    const int64_t first = s / wcap, last = (s + vw[v] - 1) / wcap;
+    if (first == last) C[v] = (int32_t)(n + first);
+  }
+};
+
+__global__ void k_mark_used(int32_t n, const int32_t* __restrict__ C, int32_t* used) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    used[C[v]] = 1;
+}
+struct LoadI32 {
+  const int32_t* a;
+  __device__ int64_t operator()(int64_t i) const { return a[i]; }
+};
+struct StoreRankI32 {
+  int32_t* out;
+  __device__ void operator()(int64_t i, int64_t e, int64_t) const { out[i] = (int32_t)e; }
+};
+__global__ void k_apply_rank(int32_t n, const int32_t* __restrict__ C, const int32_t* __restrict__ rank, int32_t* M) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    M[v] = rank[C[v]];
+}
+
+// ---------------------------------------------------------------------------
+// contraction
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_vw(int32_t n, const int32_t* __restrict__ M, const int32_t* __restrict__ vw, int32_t* vwc) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&vwc[M[v]], vw[v]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_contract_keys(GraphView g, const int32_t* __restrict__ M, int bits,
+                                                            uint64_t* key, int32_t* val, int64_t* valid) {
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  const uint64_t sentinel = (bits >= 32 ? ~0ULL : ((1ULL << (2 * bits)) - 1ULL));
+  int64_t mine = 0;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    const int32_t mv = M[v];
+    for (int64_t e = g.xadj[v] + lane; e < g.xadj[v + 1]; e += kSubWarp) {
+      const int32_t mu = M[g.adj[e]];
+      if (mu != mv) {
+        key[e] = ((uint64_t)(uint32_t)mv << bits) | (uint32_t)mu;
+        mine++;
+      } else {
+        key[e] = sentinel;
+      }
+      val[e] = g.adjw[e];
+    }
+  }
+  mine = warp_sum(mine);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd((unsigned long long*)valid, (unsigned long long)mine);
+}
+
+struct LoadHead {
+  const uint64_t* key;
+  const int64_t* d_valid;
+  __device__ int64_t operator()(int64_t i) const {
+    if (i >= *d_valid) return 0;
+    return (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+  }
+};
+struct StoreHead {
+  const uint64_t* key;
+  uint64_t* ukey;
+  int64_t* hstart;
+  __device__ void operator()(int64_t i, int64_t e, int64_t x) const {
+    if (x) {
+      ukey[e] = key[i];
+      hstart[e] = i;
+    }
+  }
+};
+struct LoadValid32 {
+  const int32_t* val;
+  const int64_t* d_valid;
+  __device__ int64_t operator()(int64_t i) const { return i < *d_valid ? val[i] : 0; }
+};
+
+__global__ void k_put_total(const int64_t* total, const int64_t* d_idx, int64_t* P) { P[*d_idx] = *total; }
+
+__global__ void k_contract_fill(int64_t mc, const uint64_t* __restrict__ ukey, const int64_t* __restrict__ hstart,
+                                const int64_t* __restrict__ P, const int64_t* d_valid, int bits, int32_t* adjc,
+                                int32_t* adjwc) {
+  const uint64_t mask = (1ULL << bits) - 1ULL;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < mc; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = hstart[u];
+    const int64_t e = (u + 1 < mc) ? hstart[u + 1] : *d_valid;
+    adjc[u] = (int32_t)(ukey[u] & mask);
+    adjwc[u] = (int32_t)(P[e] - P[s]);
+  }
+}
+
+__global__ void k_contract_xadj(int32_t nc, int64_t mc, const uint64_t* __restrict__ ukey, int bits, int64_t* xadjc) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= nc; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t target = (uint64_t)r << bits;
+    int64_t lo = 0, hi = mc;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ukey[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    xadjc[r] = lo;
+  }
+}
+
+__global__ void k_project(int32_t n, const int32_t* __restrict__ M, const int32_t* __restrict__ pic, int32_t* pi) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    pi[v] = pic[M[v]];
+}
+
+// ---------------------------------------------------------------------------
+// initial mapping: breadth-first order in one CTA, cut into k weight chunks
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_initial(GraphView g, int32_t* order, int32_t* claim, int32_t* seen,
+                                                  const int32_t* __restrict__ code_of_pe, int64_t k, int64_t cV,
+                                                  int32_t* pi, uint32_t* err) {
+  __shared__ int64_t sm[33];
+  __shared__ int32_t s_tail, s_head, s_next;
+  const int32_t n = g.n;
+  for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+    seen[v] = 0;
+    claim[v] = INT32_MAX;
+  }
+  if (threadIdx.x == 0) {
+    s_tail = 0;
+    s_head = 0;
+    s_next = 0;
+  }
+  __syncthreads();
+  int64_t guard = 0;
+  while (true) {
+    const int32_t tail = s_tail;
+    const int32_t head = s_head;
+    if (tail >= n) break;
+    if (++guard > 2 * (int64_t)n + 4) {  // cannot happen; bounded for safety
+      if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+      break;
+    }
+    __syncthreads();
+    if (head == tail) {  // next component: lowest unvisited id
+      if (threadIdx.x == 0) {
+        int32_t s = s_next;
+        while (seen[s]) s++;
+        s_next = s + 1;
+        order[tail] = s;
+        seen[s] = 1;
+        s_tail = tail + 1;
+      }
+      __syncthreads();
+      continue;
+    }
+    // one level: frontier [head, tail); children claimed by the earliest parent
+    for (int32_t i = head + threadIdx.x; i < tail; i += blockDim.x) {
+      const int32_t v = order[i];
+      for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; e++) {
+        const int32_t u = g.adj[e];
+        if (!seen[u]) atomicMin(&claim[u], i);
+      }
+    }
+    __syncthreads();
+    int64_t carry = 0;
+    for (int32_t base = head; base < tail; base += blockDim.x) {
+      const int32_t i = base + threadIdx.x;
+      int64_t cnt = 0;
+      if (i < tail) {
+        const int32_t v = order[i];
+        for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; e++) {
+          const int32_t u = g.adj[e];
+          if (!seen[u] && claim[u] == i) cnt++;
+        }
+      }
+      int64_t total;
+      const int64_t ex = block_exclusive_scan(cnt, sm, &total);
+      if (i < tail && cnt) {
+        int64_t pos = tail + carry + ex;
+        const int32_t v = order[i];
+        for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; e++) {
+          const int32_t u = g.adj[e];
+          if (!seen[u] && claim[u] == i) order[pos++] = u;
+        }
+      }
+      carry += total;
+    }
+    __syncthreads();
+    for (int64_t j = tail + threadIdx.x; j < tail + carry; j += blockDim.x) {
+      const int32_t u = order[j];
+      seen[u] = 1;
+      claim[u] = INT32_MAX;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_head = tail;
+      s_tail = (int32_t)(tail + carry);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  // PE of the vertex whose preceding weight in breadth-first order is s
+  int64_t carry = 0;
+  for (int32_t base = 0; base < n; base += blockDim.x) {
+    const int32_t i = base + threadIdx.x;
+    const int64_t cv = (i < n) ? g.vw[order[i]] : 0;
+    int64_t total;
+    const int64_t ex = block_exclusive_scan(cv, sm, &total);
+    if (i < n) pi[order[i]] = code_of_pe[((carry + ex) * k) / cV];
+    carry += total;
+  }
+}
+
+// high-degree hash-table sizes: next power of two >= 2 (deg + 1), at least 64
+struct LoadTableSize {
+  const int32_t* hi;
+  const int64_t* xadj;
+  __device__ int64_t operator()(int64_t i) const {
+    const int32_t v = hi[i];
+    const int64_t want = 2 * (xadj[v + 1] - xadj[v] + 1);
+    int64_t s = 64;
+    while (s < want) s <<= 1;
+    return s;
+  }
+};
+
+int64_t read_i64(Ctx& c, const int64_t* d) {
+  int64_t h = 0;
+  GM_CUDA(cudaMemcpyAsync(&h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  return h;
+}
+
+int bits_for(int64_t x) {  // smallest b with x < 2^b
+  int b = 0;
+  while (b < 62 && (1LL << b) <= x) b++;
+  return b;
+}
+
+void check_err(Ctx& c) {
+  uint32_t e = 0;
+  GM_CUDA(cudaMemcpyAsync(&e, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  if (e & ERR_TIMEOUT) throw ApiError(MAP_E_TIMEOUT, "a bounded device loop gave up");
+  if (e) throw ApiError(MAP_E_INTERNAL, "device consistency check failed (flags " + std::to_string(e) + ")");
+}
+
+// Clusters level `lvl`; returns n_c, fills L.M.
+int32_t cluster_level(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  const int32_t n = L.n;
+  const unsigned gv = grid_for(c, kThreads, n);
+  const unsigned gl = grid_for(c, kThreads / kSubWarp, n);
+  int64_t wcap = c.lmax / c.cfg.cluster_cap_div;
+  if (wcap < L.max_vw) wcap = L.max_vw;
+  if (wcap < 1) wcap = 1;
+  k_iota<<<gv, kThreads, 0, c.st>>>(c.C, n); count_launch();
+  GM_CUDA(cudaMemcpyAsync(c.Wc, L.vw, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
+  GM_CUDA(cudaMemsetAsync(c.ReqW, 0, (size_t)n * sizeof(int32_t), c.st));
+  // hash tables for the high-degree vertices
+  if (L.n_hi) {
+    if (!L.hi_off) L.hi_off = c.mem.make<int64_t>((size_t)L.n_hi + 1);
+    scan(LoadTableSize{L.hi, L.xadj}, StoreExcl{L.hi_off}, L.n_hi, nullptr, c.scan, c.st);
+    const int64_t tiles = std::max<int64_t>(1, scan_tiles(L.n_hi));
+    GM_CUDA(cudaMemcpyAsync(L.hi_off + L.n_hi, c.scan.tile_sums + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                            c.st));
+    L.hi_slots = read_i64(c, L.hi_off + L.n_hi);
+    if (L.hi_slots > c.hcap) {
+      if (c.hkey) c.mem.put(c.hkey);
+      if (c.hval) c.mem.put(c.hval);
+      c.hcap = L.hi_slots;
+      c.hkey = c.mem.make<int32_t>((size_t)c.hcap);
+      c.hval = c.mem.make<int32_t>((size_t)c.hcap);
+    }
+  }
+  uint8_t* flag = c.elig;
+  int64_t* moved = c.counters + 5;
+  int64_t* d_cont = c.counters + 6;
+  const int kbits = bits_for(n) + 32;
+  for (int32_t it = 0; it < c.cfg.cluster_iters; it++) {
+    GM_CUDA(cudaMemsetAsync(moved, 0, sizeof(int64_t), c.st));
+    for (int32_t r = 0; r < 2; r++) {
+      ClusterArgs a{c.C, c.Wc, c.ReqW, c.req, wcap, c.cfg.seed, lvl, it, r};
+      cudaEvent_t ev = c.prof_begin();
+      k_cluster_low<<<gl, kThreads, 0, c.st>>>(view(L), a); count_launch();
+      // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
+      c.prof_end(ev, PK_CLUSTER, 16 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+      if (L.n_hi)
+        k_cluster_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
+            view(L), L.hi, L.n_hi, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
+      k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag); count_launch();
+      scan(LoadContested{flag}, StoreContested{c.req, c.cfg.seed, lvl, c.sort.key[0], c.sort.val[0]}, n, nullptr,
+           c.scan, c.st);
+      GM_CUDA(cudaMemcpyAsync(d_cont, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), sizeof(int64_t),
+                              cudaMemcpyDeviceToDevice, c.st));
+      const int cur = radix_sort_pairs(c.sort, n, d_cont, kbits, c.st);
+      scan(LoadSortedVw{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_cont, c.scan, c.st);
+      k_cluster_heads<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_cont, n, c.headP); count_launch();
+      k_cluster_admit<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_cont, n, c.Wc,
+                                                 L.vw, wcap, flag); count_launch();
+      k_cluster_apply<<<gv, kThreads, 0, c.st>>>(n, c.req, flag, c.C, c.Wc, c.ReqW, L.vw, moved); count_launch();
+    }
+    GM_CUDA(cudaGetLastError());
+    const int64_t mv = read_i64(c, moved);
+    if (mv * 100 < (int64_t)n) break;
+  }
+  // isolated vertices, then number the clusters by ascending label
+  scan(LoadIsolated{L.xadj, L.vw}, StoreIsolated{c.C, L.vw, n, wcap}, n, nullptr, c.scan, c.st);
+  const int64_t nlab = 2 * (int64_t)n + 1;
+  GM_CUDA(cudaMemsetAsync(c.rank, 0, (size_t)nlab * sizeof(int32_t), c.st));
+  k_mark_used<<<gv, kThreads, 0, c.st>>>(n, c.C, c.rank); count_launch();
+  scan(LoadI32{c.rank}, StoreRankI32{c.rank}, nlab, nullptr, c.scan, c.st);
+  const int64_t nc = read_i64(c, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(nlab)));
+  if (!L.M) L.M = c.mem.make<int32_t>((size_t)std::max(1, n));
+  k_apply_rank<<<gv, kThreads, 0, c.st>>>(n, c.C, c.rank, L.M); count_launch();
+  GM_CUDA(cudaGetLastError());
+  check_err(c);
+  return (int32_t)nc;
+}
+
+// Builds level lvl + 1 from level lvl and its M.
+void contract_level(Ctx& c, int lvl, int32_t nc) {
+  Level& F = c.lv[lvl];
+  Level C;
+  C.n = nc;
+  const int64_t m = F.m;
+  const unsigned gv = grid_for(c, kThreads, F.n);
+  C.vw = c.mem.make<int32_t>((size_t)std::max(1, nc));
+  GM_CUDA(cudaMemsetAsync(C.vw, 0, (size_t)std::max(1, nc) * sizeof(int32_t), c.st));
+  k_coarse_vw<<<gv, kThreads, 0, c.st>>>(F.n, F.M, F.vw, C.vw); count_launch();
+  const int bits = bits_for(nc);  // ids < 2^bits - 1, so the all-ones key is free
+  int64_t* d_valid = c.counters + 7;
+  GM_CUDA(cudaMemsetAsync(d_valid, 0, sizeof(int64_t), c.st));
+  int64_t mc = 0;
+  C.xadj = c.mem.make<int64_t>((size_t)nc + 1);
+  if (m > 0) {
+    k_contract_keys<<<grid_for(c, kThreads / kSubWarp, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
+                                                                                   c.sort.val[0], d_valid); count_launch();
+    cudaEvent_t ev = c.prof_begin();
+    const int cur = radix_sort_pairs(c.sort, m, nullptr, 2 * bits, c.st);
+    // per 8-bit pass: keys read twice (histogram, scatter), key + value read and written once
+    c.prof_end(ev, PK_SORT, (int64_t)((2 * bits + 7) / 8) * m * (8 + 12 + 12));
+    uint64_t* skey = c.sort.key[cur];
+    int32_t* sval = c.sort.val[cur];
+    uint64_t* ukey = c.sort.key[cur ^ 1];
+    scan(LoadHead{skey, d_valid}, StoreHead{skey, ukey, c.P64b}, m, nullptr, c.scan, c.st);
+    mc = read_i64(c, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(m)));
+    scan(LoadValid32{sval, d_valid}, StoreExcl{c.P64}, m, nullptr, c.scan, c.st);
+    // P64[valid] = total weight of the valid entries
+    k_put_total<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(m)), d_valid, c.P64); count_launch();
+    C.adj = c.mem.make<int32_t>((size_t)std::max<int64_t>(1, mc));
+    C.adjw = c.mem.make<int32_t>((size_t)std::max<int64_t>(1, mc));
+    if (mc > 0)
+      k_contract_fill<<<grid_for(c, kThreads, mc), kThreads, 0, c.st>>>(mc, ukey, c.P64b, c.P64, d_valid, bits, C.adj,
+                                                                       C.adjw); count_launch();
+    k_contract_xadj<<<grid_for(c, kThreads, nc + 1), kThreads, 0, c.st>>>(nc, mc, ukey, bits, C.xadj); count_launch();
+  } else {
+    C.adj = c.mem.make<int32_t>(1);
+    C.adjw = c.mem.make<int32_t>(1);
+    GM_CUDA(cudaMemsetAsync(C.xadj, 0, ((size_t)nc + 1) * sizeof(int64_t), c.st));
+  }
+  C.m = mc;
+  C.pi = c.mem.make<int32_t>((size_t)std::max(1, nc));
+  GM_CUDA(cudaMemsetAsync(C.pi, 0, (size_t)std::max(1, nc) * sizeof(int32_t), c.st));
+  GM_CUDA(cudaGetLastError());
+  c.lv.push_back(C);
+}
+
+__global__ void k_max_i32(int32_t n, const int32_t* __restrict__ a, int32_t* out) {
+  int32_t m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = a[i] > m ? a[i] : m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+int32_t device_max_vw(Ctx& c, const Level& L) {
+  int32_t* d = reinterpret_cast<int32_t*>(c.counters + 4);
+  GM_CUDA(cudaMemsetAsync(d, 0, sizeof(int64_t), c.st));
+  k_max_i32<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.vw, d); count_launch();
+  int32_t h = 0;
+  GM_CUDA(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  return h;
+}
+
+void free_level(Ctx& c, Level& L) {
+  for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
+                  (void*)L.hi_off})
+    if (p) c.mem.put(p);
+  L = Level{};
+}
+
+}  // namespace
+
+void coarsen_alloc(Ctx& c) {
+  const size_t n = (size_t)std::max(1, c.n0);
+  c.C = c.mem.make<int32_t>(n);
+  c.Wc = c.mem.make<int32_t>(n);
+  c.ReqW = c.mem.make<int32_t>(n);
+  c.req = c.mem.make<int32_t>(n);
+  c.rank = c.mem.make<int32_t>(2 * n + 2);
+}
+
+void validate_graph(Ctx& c) {
+  Level& L = c.lv[0];
+  unsigned long long* sums = reinterpret_cast<unsigned long long*>(c.counters);
+  GM_CUDA(cudaMemsetAsync(c.errword, 0, sizeof(uint32_t), c.st));
+  GM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), c.st));
+  k_validate<<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.m, c.errword, sums); count_launch();
+  GM_CUDA(cudaGetLastError());
+  uint32_t e = 0;
+  unsigned long long h[2] = {0, 0};
+  GM_CUDA(cudaMemcpyAsync(&e, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  GM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), c.st));
+  if (e) {
+    std::string m = "invalid graph:";
+    if (e & ERR_XADJ) m += " xadj not monotone or out of range;";
+    if (e & ERR_RANGE) m += " adjacency index out of range;";
+    if (e & ERR_SELFLOOP) m += " self-loop;";
+    if (e & ERR_UNSORTED) m += " row not strictly ascending (duplicate edge?);";
+    if (e & ERR_ASYM) m += " missing or differently weighted reverse edge;";
+    if (e & ERR_WEIGHT) m += " weight < 1;";
+    throw ApiError(MAP_E_INVALID, m);
+  }
+  if (h[0] >= (1ULL << 31) || h[1] >= (1ULL << 31))
+    throw ApiError(MAP_E_OVERFLOW, "sum of vertex weights and sum of edge weights must be < 2^31");
+  c.cV = (int64_t)h[0];
+  L.max_vw = device_max_vw(c, L);
+}
+
+int32_t coarsen(Ctx& c) {
+  while (c.lv.size() > 1) {
+    free_level(c, c.lv.back());
+    c.lv.pop_back();
+  }
+  if (c.lv[0].M) {
+    c.mem.put(c.lv[0].M);
+    c.lv[0].M = nullptr;
+  }
+  while ((int32_t)c.lv.size() < c.cfg.max_levels &&
+         (int64_t)c.lv.back().n >= (int64_t)c.cfg.coarsest_factor * c.k) {
+    const int lvl = (int)c.lv.size() - 1;
+    const int32_t nc = cluster_level(c, lvl);
+    Level& F = c.lv[lvl];
+    if ((int64_t)nc * c.cfg.stall_den > (int64_t)c.cfg.stall_num * F.n) {
+      c.mem.put(F.M);
+      F.M = nullptr;
+      break;
+    }
+    contract_level(c, lvl, nc);
+    Level& N = c.lv.back();
+    classify_degrees(c, (int)c.lv.size() - 1);
+    N.max_vw = device_max_vw(c, N);
+  }
+  return (int32_t)c.lv.size();
+}
+
+void initial_map(Ctx& c) {
+  Level& L = c.lv.back();
+  k_initial<<<1, 1024, 0, c.st>>>(view(L), c.C, c.req, c.Wc, c.d_code_of_pe, c.k, c.cV, L.pi, c.errword); count_launch();
+  GM_CUDA(cudaGetLastError());
+  check_err(c);
+}
+
+void project(Ctx& c, int lvl) {
+  Level& F = c.lv[lvl];
+  const Level& C = c.lv[lvl + 1];
+  k_project<<<grid_for(c, kThreads, F.n), kThreads, 0, c.st>>>(F.n, F.M, C.pi, F.pi); count_launch();
+  GM_CUDA(cudaGetLastError());
+}
+
+}  // namespace gm

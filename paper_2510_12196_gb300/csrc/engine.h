@@ -1,0 +1,187 @@
+// Host-side engine state of one mapping context (one task graph, one machine
+// hierarchy) and the entry points of the refinement and coarsening engines.
+#pragma once
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/gpumap.h"
+#include "common.cuh"
+#include "prim.cuh"
+
+namespace gm {
+
+struct CudaError : std::runtime_error {
+  cudaError_t code;
+  CudaError(cudaError_t c, const char* what, const char* file, int line)
+      : std::runtime_error(std::string(cudaGetErrorString(c)) + " at " + file + ":" + std::to_string(line) +
+                           " (" + what + ")"),
+        code(c) {}
+};
+struct ApiError : std::runtime_error {
+  map_status status;
+  ApiError(map_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+// Step kinds of the Alg. 6 state machine.
+enum : int32_t { KIND_LP = 0, KIND_WEAK = 1, KIND_STRONG = 2, KIND_NONE = 3 };
+
+// Device-resident state of one Alg. 6 run.
+struct RefineState {
+  int64_t J;           // objective of the current mapping P'
+  int64_t maxw;        // max block weight of P'
+  int64_t best_J;      // objective of the best mapping P
+  int64_t best_maxw;
+  int32_t i;           // patience counter
+  int32_t iw;          // consecutive weak rebalancing steps
+  int32_t t;           // iterations started
+  int32_t kind;        // step of the current iteration
+  int32_t done;
+  int32_t copy_best;   // the iteration just finished produced a new best
+  int32_t rounds;      // >= 0: fixed number of iterations
+  int32_t level;
+  int32_t moved;       // vertices moved by the last step
+  int32_t pad;
+};
+
+// Kernel classes timed by the optional CUDA-event profiler.
+enum : int32_t { PK_LP_GAIN = 0, PK_LP_AFTER = 1, PK_EVAL = 2, PK_CLUSTER = 3, PK_SORT = 4, PK_COUNT = 5 };
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int32_t kind;
+  int64_t bytes;
+};
+
+struct Level {
+  int32_t n = 0;
+  int64_t m = 0;
+  int64_t* xadj = nullptr;
+  int32_t* adj = nullptr;
+  int32_t* adjw = nullptr;
+  int32_t* vw = nullptr;
+  int32_t* M = nullptr;        // fine -> coarse map (to level + 1)
+  int32_t* pi = nullptr;       // mapping as PE codes
+  int32_t* hi = nullptr;       // vertices of degree > kLowDeg, ascending
+  int32_t n_hi = 0;
+  int64_t m_hi = 0;            // CSR entries of the high-degree vertices
+  int64_t* hi_off = nullptr;   // hash-table offsets of the high-degree vertices (n_hi + 1)
+  int64_t hi_slots = 0;
+  int32_t max_vw = 0;
+};
+
+struct DevMem {
+  map_alloc_fn afn = nullptr;
+  map_free_fn ffn = nullptr;
+  void* user = nullptr;
+  cudaStream_t st = nullptr;
+  struct Block {
+    void* p;
+    size_t bytes;
+  };
+  std::vector<Block> blocks;
+  size_t total = 0;
+  void* get(size_t bytes);
+  void put(void* p);
+  void release_all();
+  template <class T>
+  T* make(size_t count) {
+    return static_cast<T*>(get(count * sizeof(T)));
+  }
+};
+
+struct Ctx {
+  cudaStream_t st = nullptr;
+  map_config cfg{};
+  Topo topo{};
+  int32_t k = 0;
+  int64_t cV = 0;
+  int64_t lmax = 0;
+  double eps = 0;
+  std::vector<int32_t> code_of_pe, pe_of_code;
+  int32_t* d_code_of_pe = nullptr;
+  int32_t* d_pe_of_code = nullptr;
+  std::vector<Level> lv;       // lv[0] = input graph
+  int32_t n0 = 0;
+  int64_t m0 = 0;
+  DevMem mem;
+  std::string err;
+  int dev = 0;
+  int num_sms = 0;
+  size_t max_smem = 0;
+
+  // refinement scratch (sized for level 0)
+  int32_t* pp = nullptr;        // P'
+  int64_t* gain = nullptr;
+  uint8_t* inx = nullptr;
+  uint8_t* lock = nullptr;      // moved by the last label-propagation step
+  int32_t* pi_best = nullptr;
+  int32_t* dest = nullptr;
+  uint8_t* elig = nullptr;
+  uint8_t* sel = nullptr;
+  uint8_t* acc = nullptr;
+  int64_t* sarr = nullptr;      // per-vertex prefix weights
+  int64_t* W = nullptr;         // block weights [kc]
+  int64_t* accepted = nullptr;  // [kc]
+  int64_t* headP = nullptr;     // [kc]
+  int64_t* Rb = nullptr;        // [kc + 1]
+  int32_t* U = nullptr;         // [kc]
+  int64_t* counters = nullptr;  // small device counters
+  int64_t* Jacc = nullptr;
+  RefineState* state = nullptr;
+  RefineState* h_state = nullptr;  // pinned mirror
+  int32_t* trace_kind = nullptr;
+  int64_t* trace_J = nullptr;
+  int64_t* trace_maxw = nullptr;
+  int32_t trace_cap = 4096;
+  int32_t last_iters = 0;
+
+  // sort / scan scratch
+  SortBufs sort;
+  ScanTmp scan;
+  int64_t* P64 = nullptr;       // per-element prefix (max(m0, n0) + 1)
+  int64_t* P64b = nullptr;
+
+  // coarsening scratch
+  int32_t* C = nullptr;         // cluster labels (int32, < 2 n0)
+  int32_t* Wc = nullptr;        // cluster weights [n0]
+  int32_t* ReqW = nullptr;      // requested weight per target [n0]
+  int32_t* req = nullptr;       // requested target per vertex [n0]
+  int32_t* rank = nullptr;      // label -> coarse id [2 n0 + 2]
+  int32_t* hkey = nullptr;      // hash tables of high-degree vertices
+  int32_t* hval = nullptr;
+  int64_t hcap = 0;
+  uint32_t* errword = nullptr;
+
+  // profiler
+  bool prof = false;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  cudaEvent_t prof_begin();
+  void prof_end(cudaEvent_t a, int32_t kind, int64_t bytes);
+
+  // stats
+  double ms_coarsen = 0, ms_initial = 0, ms_refine = 0, ms_project = 0;
+  int32_t iters[65] = {0};
+  int64_t Jlev[65] = {0};
+};
+
+// refine.cu
+void refine_alloc(Ctx& c);
+void compute_block_weights(Ctx& c, int lvl);
+void objective(Ctx& c, int lvl, int64_t* J, int64_t* maxw);
+int32_t lp_step(Ctx& c, int lvl);
+int32_t rebalance_step(Ctx& c, int lvl, bool strong, int32_t t);
+void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters);
+void classify_degrees(Ctx& c, int lvl);
+
+// coarsen.cu
+void coarsen_alloc(Ctx& c);
+int32_t coarsen(Ctx& c);
+void initial_map(Ctx& c);
+void project(Ctx& c, int lvl);
+void validate_graph(Ctx& c);
+
+}  // namespace gm

@@ -1,0 +1,120 @@
+// Non-template parts of the device primitives (see prim.cuh).
+#include <atomic>
+
+#include "prim.cuh"
+
+namespace gm {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(int64_t* tile_sums, int64_t ntiles) {
+  __shared__ int64_t sm[33];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = (i < ntiles) ? tile_sums[i] : 0;
+    int64_t total;
+    int64_t e = block_exclusive_scan(v, sm, &total);
+    if (i < ntiles) tile_sums[i] = carry + e;
+    carry += total;
+  }
+  if (threadIdx.x == 0) tile_sums[ntiles] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ keys, int64_t max_n,
+                                                            const int64_t* d_n, int shift,
+                                                            int64_t* __restrict__ hist, int64_t max_tiles) {
+  __shared__ int32_t cnt[256];
+  const int64_t n = load_count(d_n, max_n);
+  for (int i = threadIdx.x; i < 256; i += kSortThreads) cnt[i] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base < n) {
+    for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
+      int64_t idx = base + i;
+      if (idx < n) atomicAdd(&cnt[(int)((keys[idx] >> shift) & 255u)], 1);
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += kSortThreads) hist[(int64_t)d * max_tiles + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter: within a tile, items are ordered (warp, item, lane), which is
+// the global index order; ranks among equal digits follow that order.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* __restrict__ kin,
+                                                               const int32_t* __restrict__ vin,
+                                                               uint64_t* __restrict__ kout,
+                                                               int32_t* __restrict__ vout, int64_t max_n,
+                                                               const int64_t* d_n, int shift,
+                                                               const int64_t* __restrict__ hist_off,
+                                                               int64_t max_tiles) {
+  __shared__ int32_t wcnt[kSortWarps][256];
+  __shared__ int64_t goff[256];
+  const int64_t n = load_count(d_n, max_n);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+  for (int d = threadIdx.x; d < 256; d += kSortThreads) goff[d] = hist_off[(int64_t)d * max_tiles + blockIdx.x];
+  __syncthreads();
+
+  uint64_t k[kSortItems];
+  int32_t v[kSortItems];
+  int32_t rank[kSortItems];
+  const unsigned lt = (1u << l) - 1u;
+  const int64_t wbase = base + (int64_t)w * 32 * kSortItems;
+#pragma unroll
+  for (int j = 0; j < kSortItems; j++) {
+    int64_t idx = wbase + j * 32 + l;
+    bool valid = idx < n;
+    k[j] = valid ? kin[idx] : 0;
+    v[j] = valid ? vin[idx] : 0;
+    int d = valid ? (int)((k[j] >> shift) & 255u) : 256 + l;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int r = 0;
+    if (valid) r = wcnt[w][d] + __popc(peers & lt);
+    __syncwarp();
+    if (valid && (peers & lt) == 0) wcnt[w][d] += __popc(peers);
+    __syncwarp();
+    rank[j] = valid ? r : -1;
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+    int32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ww++) {
+      int32_t t = wcnt[ww][d];
+      wcnt[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kSortItems; j++) {
+    if (rank[j] >= 0) {
+      int d = (int)((k[j] >> shift) & 255u);
+      int64_t pos = goff[d] + wcnt[w][d] + rank[j];
+      kout[pos] = k[j];
+      vout[pos] = v[j];
+    }
+  }
+}
+
+int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st) {
+  if (max_n <= 0 || bits <= 0) return 0;
+  const int64_t tiles = sort_tiles(max_n);
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], max_n, d_n, shift, b.hist, tiles); count_launch();
+    scan(LoadI64{b.hist}, StoreExcl{b.hist_off}, 256 * tiles, nullptr, b.scan, st);
+    k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], b.val[cur], b.key[cur ^ 1],
+                                                             b.val[cur ^ 1], max_n, d_n, shift, b.hist_off,
+                                                             tiles); count_launch();
+    cur ^= 1;
+  }
+  return cur;
+}
+
+}  // namespace gm

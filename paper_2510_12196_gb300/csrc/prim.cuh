@@ -1,0 +1,189 @@
+// Deterministic device primitives: block reductions, a three-phase exclusive
+// scan over int64 values produced by a functor, and a stable LSD radix sort of
+// (uint64 key, int32 value) pairs.  Element counts may live in device memory
+// (``d_n``) so that data-dependent sizes need no host round trip; grids are
+// sized for the host-known upper bound ``max_n`` and tiles past the count
+// exit at once.  These are the building blocks of the contraction (sort +
+// segmented reduce), cluster admission and rebalancing selection.
+#pragma once
+
+#include "common.cuh"
+
+namespace gm {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__device__ __forceinline__ int64_t load_count(const int64_t* d_n, int64_t max_n) {
+  return d_n ? *d_n : max_n;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide helpers (blockDim.x multiple of 32, <= 1024)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class T>
+__device__ T block_sum(T v, T* sm /* >= 32 */) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (w == 0) {
+    r = (l < (int)(blockDim.x >> 5)) ? sm[l] : T(0);
+    r = warp_sum(r);
+    if (l == 0) sm[0] = r;
+  }
+  __syncthreads();
+  r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive block scan of one value per thread; returns the exclusive prefix
+// and writes the block total to *total.
+template <class T>
+__device__ T block_exclusive_scan(T v, T* sm /* >= 33 */, T* total) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (l >= o) x += y;
+  }
+  __syncthreads();
+  if (l == 31) sm[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    T s = (l < nw) ? sm[l] : T(0);
+    T t = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += y;
+    }
+    if (l < nw) sm[l] = t - s;
+    if (l == 31) sm[32] = t;
+  }
+  __syncthreads();
+  T r = sm[w] + x - v;
+  *total = sm[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// scan: out(i, exclusive prefix, value) for i < n, plus total
+// ---------------------------------------------------------------------------
+template <class Load>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load load, int64_t max_n, const int64_t* d_n,
+                                                              int64_t* tile_sums) {
+  __shared__ int64_t sm[33];
+  const int64_t n = load_count(d_n, max_n);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+  if (base < n) {
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+      int64_t idx = base + i;
+      if (idx < n) s += load(idx);
+    }
+  }
+  s = block_sum(s, sm);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = (base < n) ? s : 0;
+}
+
+// single block: exclusive scan of tile sums in place, total to tile_sums[ntiles]
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(int64_t* tile_sums, int64_t ntiles);
+
+template <class Load, class Store>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Load load, Store store, int64_t max_n,
+                                                             const int64_t* d_n, const int64_t* tile_off) {
+  __shared__ int64_t sm[33];
+  const int64_t n = load_count(d_n, max_n);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (base >= n) return;
+  int64_t vals[kScanItems];
+  int64_t local = 0;
+  const int64_t first = base + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    int64_t idx = first + j;
+    vals[j] = (idx < n) ? load(idx) : 0;
+    local += vals[j];
+  }
+  int64_t total;
+  int64_t run = block_exclusive_scan(local, sm, &total) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    int64_t idx = first + j;
+    if (idx < n) store(idx, run, vals[j]);
+    run += vals[j];
+  }
+}
+
+struct ScanTmp {
+  int64_t* tile_sums = nullptr;  // >= tiles(max_n) + 1
+};
+
+__host__ inline int64_t scan_tiles(int64_t max_n) { return (max_n + kScanTile - 1) / kScanTile; }
+
+// Exclusive scan; the total lands in tmp.tile_sums[tiles] (device).
+template <class Load, class Store>
+void scan(Load load, Store store, int64_t max_n, const int64_t* d_n, ScanTmp tmp, cudaStream_t st) {
+  int64_t tiles = scan_tiles(max_n);
+  if (tiles == 0) tiles = 1;
+  k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, st>>>(load, max_n, d_n, tmp.tile_sums); count_launch();
+  k_scan_tile_sums<<<1, 1024, 0, st>>>(tmp.tile_sums, tiles); count_launch();
+  k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(load, store, max_n, d_n, tmp.tile_sums); count_launch();
+}
+
+// common functors
+struct LoadI64 {
+  const int64_t* a;
+  __device__ int64_t operator()(int64_t i) const { return a[i]; }
+};
+struct StoreExcl {
+  int64_t* out;
+  __device__ void operator()(int64_t i, int64_t e, int64_t) const { out[i] = e; }
+};
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits
+// ---------------------------------------------------------------------------
+struct SortBufs {
+  uint64_t* key[2] = {nullptr, nullptr};
+  int32_t* val[2] = {nullptr, nullptr};
+  int64_t* hist = nullptr;      // 256 * max_tiles
+  int64_t* hist_off = nullptr;  // 256 * max_tiles
+  ScanTmp scan;                 // for 256 * max_tiles elements
+  int64_t capacity = 0;         // elements
+};
+
+__host__ inline int64_t sort_tiles(int64_t max_n) { return (max_n + kSortTile - 1) / kSortTile; }
+
+__global__ void k_sort_hist(const uint64_t* __restrict__ keys, int64_t max_n, const int64_t* d_n, int shift,
+                            int64_t* __restrict__ hist, int64_t max_tiles);
+__global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                               uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t max_n,
+                               const int64_t* d_n, int shift, const int64_t* __restrict__ hist_off,
+                               int64_t max_tiles);
+
+// Sorts buffer 0 (n elements, count on device or max_n) by key bits [0, bits).
+// Returns the buffer index (0 or 1) that holds the sorted result.
+int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st);
+
+}  // namespace gm

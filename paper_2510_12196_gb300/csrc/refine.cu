@@ -1,0 +1,1178 @@
+// Refinement engine: objective J, block weights, unconstrained label
+// propagation (Alg. 4), weak / strong rebalancing (Alg. 5 and its strong
+// variant, edge-cut loss) and the overall refinement driver (Alg. 6) with its
+// state machine on the device.
+//
+// Work split by degree.  A vertex of degree <= 32 is handled by an 8-lane
+// sub-warp that keeps its (up to 32) neighbour PEs and edge weights in
+// registers; gains of every neighbouring PE are evaluated by shuffles, so the
+// per-vertex connectivity table of Section 4.2 never leaves registers.  A
+// higher-degree vertex gets a whole CTA with a dense shared-memory
+// connectivity array over the PE code space; per-level group sums of that
+// array give the gain of every candidate PE in O(levels).
+#include <algorithm>
+
+#include "engine.h"
+
+namespace gm {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHiThreads = 256;
+
+struct GraphView {
+  int32_t n;
+  const int64_t* __restrict__ xadj;
+  const int32_t* __restrict__ adj;
+  const int32_t* __restrict__ adjw;
+  const int32_t* __restrict__ vw;
+};
+
+inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+
+__device__ __forceinline__ bool kind_is(const RefineState* st, int mask) {
+  return (mask >> st->kind) & 1;
+}
+
+// Register-array element r (r uniform across the tile; avoids local memory).
+__device__ __forceinline__ int32_t pick(const int32_t (&a)[kSlots], int r) {
+  int32_t x = a[0];
+#pragma unroll
+  for (int i = 1; i < kSlots; i++)
+    if (r == i) x = a[i];
+  return x;
+}
+
+template <class Tile>
+__device__ __forceinline__ int64_t tile_sum64(Tile& t, int64_t v) {
+#pragma unroll
+  for (int o = kSubWarp / 2; o > 0; o >>= 1) v += t.shfl_xor(v, o);
+  return v;
+}
+template <class Tile>
+__device__ __forceinline__ int32_t tile_sum32(Tile& t, int32_t v) {
+#pragma unroll
+  for (int o = kSubWarp / 2; o > 0; o >>= 1) v += t.shfl_xor(v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// block weights and J
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_block_weights(int32_t n, const int32_t* __restrict__ pi,
+                                                            const int32_t* __restrict__ vw, int32_t kc,
+                                                            int64_t* __restrict__ W) {
+  extern __shared__ int32_t hist[];
+  for (int b = threadIdx.x; b < kc; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hist[pi[v]], vw[v]);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kc; b += blockDim.x)
+    if (hist[b]) atomicAdd((unsigned long long*)&W[b], (unsigned long long)(int64_t)hist[b]);
+}
+
+// J contribution of the low-degree vertices.
+__global__ void __launch_bounds__(kThreads) k_eval_low(GraphView g, const int32_t* __restrict__ pi, Topo topo,
+                                                       int64_t* Jacc) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  load_sdist(sdist, topo);
+  __syncthreads();
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  int64_t acc = 0;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
+    if (end - beg > kLowDeg) continue;
+    const int32_t p = pi[v];
+    for (int64_t e = beg + lane; e < end; e += kSubWarp) acc += (int64_t)g.adjw[e] * dcode(sdist, p, pi[g.adj[e]]);
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
+}
+
+// J contribution of the high-degree vertices (one CTA per vertex).
+__global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                          const int32_t* __restrict__ pi, Topo topo, int64_t* Jacc) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  load_sdist(sdist, topo);
+  __syncthreads();
+  int64_t acc = 0;
+  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
+    const int32_t v = hi[i];
+    const int32_t p = pi[v];
+    for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
+      acc += (int64_t)g.adjw[e] * dcode(sdist, p, pi[g.adj[e]]);
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 4 step 1: best target per vertex by Eq. 1, non-negative filter
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_lp_gain_low(GraphView g, const int32_t* __restrict__ pi,
+                                                          uint8_t* __restrict__ lock, int32_t* __restrict__ pp,
+                                                          int64_t* __restrict__ gain, uint8_t* __restrict__ inx,
+                                                          Topo topo, const RefineState* st) {
+  __shared__ int32_t sdist[32];
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    const int64_t beg = g.xadj[v];
+    const int deg = (int)(g.xadj[v + 1] - beg);
+    if (deg > kLowDeg) continue;
+    const int32_t p = pi[v];
+    int32_t c[kSlots], w[kSlots];
+    bool cand = false;
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) {
+      const int idx = lane + kSubWarp * r;
+      if (idx < deg) {
+        c[r] = pi[g.adj[beg + idx]];
+        w[r] = g.adjw[beg + idx];
+      } else {
+        c[r] = p;  // padding: same block, zero weight, never a candidate
+        w[r] = 0;
+      }
+      cand |= (c[r] != p);
+    }
+    const bool locked = lock[v] != 0;
+    cand = tile.any(cand);
+    if (locked || !cand) {
+      if (lane == 0) {
+        inx[v] = 0;
+        pp[v] = p;
+        gain[v] = 0;
+        if (locked) lock[v] = 0;
+      }
+      continue;
+    }
+    // T(x) = sum over neighbours of w * D(x, P(u)); G_q(v) = T(P(v)) - T(q).
+    int64_t Tp = 0;
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) Tp += (int64_t)w[r] * dcode(sdist, p, c[r]);
+    Tp = tile_sum64(tile, Tp);
+    int64_t T[kSlots];
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) T[r] = 0;
+    const int rows = (deg + kSubWarp - 1) / kSubWarp;
+    for (int rr = 0; rr < rows; rr++) {
+      const int32_t crr = pick(c, rr);
+      const int32_t wrr = pick(w, rr);
+      for (int j = 0; j < kSubWarp; j++) {
+        const int32_t cs = tile.shfl(crr, j);
+        const int32_t ws = tile.shfl(wrr, j);
+#pragma unroll
+        for (int r = 0; r < kSlots; r++) T[r] += (int64_t)ws * dcode(sdist, c[r], cs);
+      }
+    }
+    int64_t bt = INT64_MAX;
+    int32_t bc = INT32_MAX;
+#pragma unroll
+    for (int r = 0; r < kSlots; r++)
+      if (c[r] != p && (T[r] < bt || (T[r] == bt && c[r] < bc))) {
+        bt = T[r];
+        bc = c[r];
+      }
+#pragma unroll
+    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+      const int64_t ot = tile.shfl_xor(bt, o);
+      const int32_t oc = tile.shfl_xor(bc, o);
+      if (ot < bt || (ot == bt && oc < bc)) {
+        bt = ot;
+        bc = oc;
+      }
+    }
+    if (lane == 0) {
+      const int64_t G = Tp - bt;
+      if (G >= 0) {
+        inx[v] = 1;
+        pp[v] = bc;
+        gain[v] = G;
+      } else {
+        inx[v] = 0;
+        pp[v] = p;
+        gain[v] = 0;
+      }
+    }
+  }
+}
+
+// Shared-memory layout of the dense connectivity array and its group sums.
+struct GroupLayout {
+  int32_t off[kMaxLevels + 1];  // off[0] = 0 (conn itself), off[i] = start of level-i group sums
+  int32_t total;
+};
+__host__ inline GroupLayout group_layout(const Topo& t) {
+  GroupLayout gl{};
+  int32_t o = t.kc;
+  gl.off[0] = 0;
+  for (int i = 1; i <= t.levels; i++) {
+    gl.off[i] = o;
+    o += t.kc >> t.s[i];
+  }
+  gl.total = o;
+  return gl;
+}
+
+// Fills conn[0, kc) (already zeroed) with the edge weights of v per neighbour
+// PE and the level group sums after it.  Returns T(P(v)) summed over the block.
+__device__ void conn_build(const GraphView& g, int32_t v, const int32_t* __restrict__ pi, const Topo& topo,
+                           const GroupLayout& gl, int32_t* tab) {
+  for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
+    atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
+  __syncthreads();
+  for (int i = 1; i <= topo.levels; i++) {
+    const int32_t cnt = topo.kc >> topo.s[i];
+    const int32_t sh = topo.s[i] - topo.s[i - 1];
+    const int32_t* prev = tab + gl.off[i - 1];
+    int32_t* cur = tab + gl.off[i];
+    for (int32_t gidx = threadIdx.x; gidx < cnt; gidx += blockDim.x) {
+      int32_t s = 0;
+      for (int32_t j = 0; j < (1 << sh); j++) s += prev[(gidx << sh) + j];
+      cur[gidx] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// sum_b conn(b) D(q, b) from the group sums (Eq. 1 regrouped by level).
+__device__ __forceinline__ int64_t conn_T(const int32_t* tab, const Topo& topo, const GroupLayout& gl, int32_t q) {
+  int64_t T = 0;
+  int32_t prev = tab[q];
+  for (int i = 1; i <= topo.levels; i++) {
+    const int32_t cur = tab[gl.off[i] + (q >> topo.s[i])];
+    T += (int64_t)topo.dist[i - 1] * (cur - prev);
+    prev = cur;
+  }
+  return T;
+}
+
+__global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                             const int32_t* __restrict__ pi, uint8_t* lock,
+                                                             int32_t* pp, int64_t* gain, uint8_t* inx, Topo topo,
+                                                             GroupLayout gl, const RefineState* st) {
+  extern __shared__ int32_t tab[];
+  __shared__ int64_t sbt[32];
+  __shared__ int32_t sbc[32];
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
+    const int32_t v = hi[i];
+    const int32_t p = pi[v];
+    if (lock[v]) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        inx[v] = 0;
+        pp[v] = p;
+        gain[v] = 0;
+        lock[v] = 0;
+      }
+      continue;
+    }
+    for (int32_t b = threadIdx.x; b < gl.total; b += blockDim.x) tab[b] = 0;
+    __syncthreads();
+    conn_build(g, v, pi, topo, gl, tab);
+    int64_t bt = INT64_MAX;
+    int32_t bc = INT32_MAX;
+    for (int32_t q = threadIdx.x; q < topo.kc; q += blockDim.x) {
+      if (q == p || tab[q] == 0) continue;
+      const int64_t T = conn_T(tab, topo, gl, q);
+      if (T < bt || (T == bt && q < bc)) {
+        bt = T;
+        bc = q;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ot < bt || (ot == bt && oc < bc)) {
+        bt = ot;
+        bc = oc;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sbt[threadIdx.x >> 5] = bt;
+      sbc[threadIdx.x >> 5] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+        if (sbt[w] < bt || (sbt[w] == bt && sbc[w] < bc)) {
+          bt = sbt[w];
+          bc = sbc[w];
+        }
+      const int64_t Tp = conn_T(tab, topo, gl, p);
+      const int64_t G = Tp - bt;
+      if (bc != INT32_MAX && G >= 0) {
+        inx[v] = 1;
+        pp[v] = bc;
+        gain[v] = G;
+      } else {
+        inx[v] = 0;
+        pp[v] = p;
+        gain[v] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 4 step 2: gain under the approximate future state given by ord
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t future_block(int32_t u, int32_t v, int64_t gv, const int32_t* __restrict__ pi,
+                                                const int32_t* __restrict__ pp, const int64_t* __restrict__ gain,
+                                                const uint8_t* __restrict__ inx) {
+  if (inx[u]) {
+    const int64_t gu = gain[u];
+    if (gu > gv || (gu == gv && u < v)) return pp[u];
+  }
+  return pi[u];
+}
+
+__global__ void __launch_bounds__(kThreads) k_lp_after_low(GraphView g, const int32_t* __restrict__ pi,
+                                                           const int32_t* __restrict__ pp,
+                                                           const int64_t* __restrict__ gain,
+                                                           const uint8_t* __restrict__ inx, uint8_t* lock, Topo topo,
+                                                           const RefineState* st) {
+  __shared__ int32_t sdist[32];
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    if (!inx[v]) continue;
+    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
+    if (end - beg > kLowDeg) continue;
+    const int32_t p = pi[v], q = pp[v];
+    const int64_t gv = gain[v];
+    int64_t s = 0;
+    for (int64_t e = beg + lane; e < end; e += kSubWarp) {
+      const int32_t b = future_block(g.adj[e], (int32_t)v, gv, pi, pp, gain, inx);
+      s += (int64_t)g.adjw[e] * (dcode(sdist, p, b) - dcode(sdist, q, b));
+    }
+    s = tile_sum64(tile, s);
+    if (lane == 0 && s >= 0) lock[v] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kHiThreads) k_lp_after_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                              const int32_t* __restrict__ pi,
+                                                              const int32_t* __restrict__ pp,
+                                                              const int64_t* __restrict__ gain,
+                                                              const uint8_t* __restrict__ inx, uint8_t* lock,
+                                                              Topo topo, const RefineState* st) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
+    const int32_t v = hi[i];
+    if (!inx[v]) continue;
+    const int32_t p = pi[v], q = pp[v];
+    const int64_t gv = gain[v];
+    int64_t s = 0;
+    for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x) {
+      const int32_t b = future_block(g.adj[e], v, gv, pi, pp, gain, inx);
+      s += (int64_t)g.adjw[e] * (dcode(sdist, p, b) - dcode(sdist, q, b));
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0 && s >= 0) lock[v] = 1;
+  }
+}
+
+// Alg. 4 step 3: simultaneous move of M (lock = moved), block weights.
+__global__ void __launch_bounds__(kThreads) k_lp_apply(int32_t n, int32_t* __restrict__ pi,
+                                                       const int32_t* __restrict__ pp,
+                                                       const uint8_t* __restrict__ lock,
+                                                       const int32_t* __restrict__ vw, int64_t* W,
+                                                       RefineState* st) {
+  __shared__ int32_t cnt;
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int32_t mine = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (!lock[v]) continue;
+    const int32_t p = pi[v], q = pp[v];
+    const int64_t c = vw[v];
+    pi[v] = q;
+    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
+    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    mine++;
+  }
+  if (mine) atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0 && cnt) atomicAdd(&st->moved, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// rebalancing (Alg. 5, edge-cut loss; strong variant)
+// ---------------------------------------------------------------------------
+enum { CNT_NU = 0, CNT_SIGMA = 1, CNT_ELIG = 2, CNT_SEL = 3, CNT_TMP = 4, CNT_N = 8 };
+
+// sigma, the fallback destination list U (ascending codes of valid PEs with
+// weight <= sigma), and resets of the per-step counters.
+__global__ void __launch_bounds__(1024) k_reb_prep(const int64_t* __restrict__ W, const int32_t* __restrict__ pe_of_code,
+                                                   Topo topo, int64_t lmax, int64_t cV, int32_t sigma_gap,
+                                                   int32_t* U, int64_t* cnt, int64_t* accepted,
+                                                   const RefineState* st) {
+  __shared__ int64_t sm[33];
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  const bool strong = st->kind == KIND_STRONG;
+  int64_t sigma;
+  if (strong) {
+    sigma = lmax;
+  } else {
+    const int64_t avg = (cV + topo.k - 1) / topo.k;
+    sigma = lmax - sigma_gap;
+    if (sigma < avg) sigma = avg;
+  }
+  int64_t carry = 0;
+  for (int32_t base = 0; base < topo.kc; base += blockDim.x) {
+    const int32_t b = base + threadIdx.x;
+    const int64_t ok = (b < topo.kc && pe_of_code[b] >= 0 && W[b] <= sigma) ? 1 : 0;
+    int64_t tot;
+    const int64_t e = block_exclusive_scan(ok, sm, &tot);
+    if (ok) U[carry + e] = b;
+    carry += tot;
+  }
+  for (int32_t b = threadIdx.x; b < topo.kc; b += blockDim.x) accepted[b] = 0;
+  if (threadIdx.x == 0) {
+    cnt[CNT_NU] = carry;
+    cnt[CNT_SIGMA] = sigma;
+  }
+}
+
+struct RebArgs {
+  const int64_t* W;
+  const int32_t* U;
+  const int64_t* cnt;
+  int64_t lmax;
+  int64_t cV;
+  int32_t k;
+  uint64_t seed;
+};
+
+__device__ __forceinline__ bool reb_eligible(const RebArgs& a, int32_t A, int32_t cv) {
+  const int64_t WA = a.W[A];
+  if (WA <= a.lmax) return false;
+  // heavy: c(v) > 1.5 (c(A) - c(V)/k), in integers: 2k c(v) > 3 (k c(A) - c(V))
+  return !(2 * (int64_t)a.k * cv > 3 * ((int64_t)a.k * WA - a.cV));
+}
+
+__global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const int32_t* __restrict__ pi, RebArgs a,
+                                                             int32_t* __restrict__ dest, uint8_t* __restrict__ bkt,
+                                                             uint8_t* __restrict__ elig, const RefineState* st) {
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
+  const int lane = tile.thread_rank();
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  const int64_t sigma = a.cnt[CNT_SIGMA];
+  const int64_t nU = a.cnt[CNT_NU];
+  const int32_t level = st->level, t = st->t;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    const int64_t beg = g.xadj[v];
+    const int deg = (int)(g.xadj[v + 1] - beg);
+    if (deg > kLowDeg) continue;
+    const int32_t A = pi[v];
+    if (!reb_eligible(a, A, g.vw[v])) {
+      if (lane == 0) elig[v] = 0;
+      continue;
+    }
+    int32_t c[kSlots], w[kSlots];
+    int32_t connA = 0;
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) {
+      const int idx = lane + kSubWarp * r;
+      if (idx < deg) {
+        c[r] = pi[g.adj[beg + idx]];
+        w[r] = g.adjw[beg + idx];
+      } else {
+        c[r] = A;
+        w[r] = 0;
+      }
+      if (c[r] == A) connA += w[r];
+    }
+    connA = tile_sum32(tile, connA);
+    // conn of each slot's block (only destinations below sigma are candidates)
+    int32_t cc[kSlots];
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) cc[r] = 0;
+    const int rows = (deg + kSubWarp - 1) / kSubWarp;
+    for (int rr = 0; rr < rows; rr++) {
+      const int32_t crr = pick(c, rr);
+      const int32_t wrr = pick(w, rr);
+      for (int j = 0; j < kSubWarp; j++) {
+        const int32_t cs = tile.shfl(crr, j);
+        const int32_t ws = tile.shfl(wrr, j);
+#pragma unroll
+        for (int r = 0; r < kSlots; r++) cc[r] += (c[r] == cs) ? ws : 0;
+      }
+    }
+    int32_t bconn = -1, bc = INT32_MAX;
+#pragma unroll
+    for (int r = 0; r < kSlots; r++) {
+      if (c[r] == A || a.W[c[r]] > sigma) continue;
+      if (cc[r] > bconn || (cc[r] == bconn && c[r] < bc)) {
+        bconn = cc[r];
+        bc = c[r];
+      }
+    }
+#pragma unroll
+    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+      const int32_t ob = tile.shfl_xor(bconn, o);
+      const int32_t oc = tile.shfl_xor(bc, o);
+      if (ob > bconn || (ob == bconn && oc < bc)) {
+        bconn = ob;
+        bc = oc;
+      }
+    }
+    if (lane == 0) {
+      int64_t gcut;
+      if (bconn >= 0) {
+        gcut = (int64_t)bconn - connA;
+      } else if (nU > 0) {
+        bc = a.U[h_rebalance(a.seed, level, t, (int32_t)v) % (uint64_t)nU];
+        gcut = -(int64_t)connA;
+      } else {
+        elig[v] = 0;
+        continue;
+      }
+      dest[v] = bc;
+      bkt[v] = (uint8_t)loss_bucket(gcut);
+      elig[v] = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                                const int32_t* __restrict__ pi, RebArgs a, int32_t kc,
+                                                                int32_t* dest, uint8_t* bkt, uint8_t* elig,
+                                                                const RefineState* st) {
+  extern __shared__ int32_t tab[];
+  __shared__ int32_t sbb[32], sbc[32];
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  const int64_t sigma = a.cnt[CNT_SIGMA];
+  const int64_t nU = a.cnt[CNT_NU];
+  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
+    const int32_t v = hi[i];
+    const int32_t A = pi[v];
+    if (!reb_eligible(a, A, g.vw[v])) {
+      if (threadIdx.x == 0) elig[v] = 0;
+      continue;
+    }
+    for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) tab[b] = 0;
+    __syncthreads();
+    for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
+      atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
+    __syncthreads();
+    int32_t bconn = -1, bc = INT32_MAX;
+    for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) {
+      const int32_t x = tab[b];
+      if (x == 0 || b == A || a.W[b] > sigma) continue;
+      if (x > bconn || (x == bconn && b < bc)) {
+        bconn = x;
+        bc = b;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int32_t ob = __shfl_xor_sync(0xffffffffu, bconn, o);
+      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ob > bconn || (ob == bconn && oc < bc)) {
+        bconn = ob;
+        bc = oc;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sbb[threadIdx.x >> 5] = bconn;
+      sbc[threadIdx.x >> 5] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+        if (sbb[w] > bconn || (sbb[w] == bconn && sbc[w] < bc)) {
+          bconn = sbb[w];
+          bc = sbc[w];
+        }
+      const int64_t connA = tab[A];
+      int64_t gcut = 0;
+      bool ok = true;
+      if (bconn >= 0) {
+        gcut = (int64_t)bconn - connA;
+      } else if (nU > 0) {
+        bc = a.U[h_rebalance(a.seed, st->level, st->t, v) % (uint64_t)nU];
+        gcut = -connA;
+      } else {
+        ok = false;
+      }
+      if (ok) {
+        dest[v] = bc;
+        bkt[v] = (uint8_t)loss_bucket(gcut);
+      }
+      elig[v] = ok ? 1 : 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Compaction stores for the sort inputs.
+struct LoadFlag {
+  const uint8_t* f;
+  __device__ int64_t operator()(int64_t i) const { return f[i] ? 1 : 0; }
+};
+struct LoadFlag2 {
+  const uint8_t* a;
+  const uint8_t* b;
+  __device__ int64_t operator()(int64_t i) const { return (a[i] && b[i]) ? 1 : 0; }
+};
+struct StoreKeyed {
+  const int32_t* keysrc;  // block code (pi) or destination
+  const uint8_t* bkt;
+  uint64_t* key;
+  int32_t* val;
+  __device__ void operator()(int64_t i, int64_t e, int64_t x) const {
+    if (x) {
+      key[e] = ((uint64_t)(uint32_t)keysrc[i] << kBucketBits) | bkt[i];
+      val[e] = (int32_t)i;
+    }
+  }
+};
+struct LoadSortedWeight {
+  const int32_t* val;
+  const int32_t* vw;
+  __device__ int64_t operator()(int64_t i) const { return vw[val[i]]; }
+};
+struct LoadRejected {
+  const uint8_t* elig;
+  const uint8_t* sel;
+  const uint8_t* acc;
+  const int32_t* vw;
+  __device__ int64_t operator()(int64_t i) const { return (elig[i] && sel[i] && !acc[i]) ? vw[i] : 0; }
+};
+struct StoreIfPositive {
+  int64_t* out;
+  __device__ void operator()(int64_t i, int64_t e, int64_t x) const {
+    if (x) out[i] = e;
+  }
+};
+
+__global__ void k_copy_count(const int64_t* src, int64_t* dst) { *dst = *src; }
+
+// Segment heads of a sorted (group << 6 | bucket) list: headP[group] = P[i].
+__global__ void k_heads(const uint64_t* __restrict__ key, const int64_t* __restrict__ P, const int64_t* d_n,
+                        int64_t max_n, int64_t* headP) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t grp = key[i] >> kBucketBits;
+    if (i == 0 || (key[i - 1] >> kBucketBits) != grp) headP[grp] = P[i];
+  }
+}
+
+// weight strictly before v within its source block < c(A) - L_max
+__global__ void k_reb_mark(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                           const int64_t* __restrict__ P, const int64_t* __restrict__ headP, const int64_t* d_n,
+                           int64_t max_n, const int64_t* __restrict__ W, int64_t lmax, uint8_t* sel) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t A = (int32_t)(key[i] >> kBucketBits);
+    sel[val[i]] = (P[i] - headP[A] < W[A] - lmax) ? 1 : 0;
+  }
+}
+
+__global__ void k_reb_apply_weak(const int32_t* __restrict__ val, const int64_t* d_n, int64_t max_n,
+                                 const uint8_t* __restrict__ sel, const int32_t* __restrict__ dest, int32_t* pi,
+                                 const int32_t* __restrict__ vw, int64_t* W, RefineState* st) {
+  if (st->kind != KIND_WEAK) return;
+  const int64_t n = *d_n;
+  int32_t mine = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = val[i];
+    if (!sel[v]) continue;
+    const int32_t p = pi[v], q = dest[v];
+    const int64_t c = vw[v];
+    pi[v] = q;
+    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
+    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    mine++;
+  }
+  if (mine) atomicAdd(&st->moved, mine);
+}
+
+// strong: movers grouped by destination are accepted while it stays <= L_max
+__global__ void k_reb_accept(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                             const int64_t* __restrict__ P, const int64_t* __restrict__ headP, const int64_t* d_n,
+                             int64_t max_n, const int64_t* __restrict__ W, int64_t lmax,
+                             const int32_t* __restrict__ vw, uint8_t* acc, int64_t* accepted) {
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = (int32_t)(key[i] >> kBucketBits);
+    const int32_t v = val[i];
+    const int64_t inc = P[i] + vw[v] - headP[d];
+    const bool ok = W[d] + inc <= lmax;
+    acc[v] = ok ? 1 : 0;
+    if (ok) atomicAdd((unsigned long long*)&accepted[d], (unsigned long long)(int64_t)vw[v]);
+  }
+}
+
+// residual room of the non-overloaded blocks in code order, prefix Rb
+__global__ void __launch_bounds__(1024) k_reb_residual(const int64_t* __restrict__ W, const int64_t* __restrict__ accepted,
+                                                       const int32_t* __restrict__ pe_of_code, int32_t kc,
+                                                       int64_t lmax, int64_t* Rb) {
+  __shared__ int64_t sm[33];
+  int64_t carry = 0;
+  for (int32_t base = 0; base < kc; base += blockDim.x) {
+    const int32_t b = base + threadIdx.x;
+    int64_t r = 0;
+    if (b < kc && pe_of_code[b] >= 0 && W[b] <= lmax) {
+      r = lmax - W[b] - accepted[b];
+      if (r < 0) r = 0;
+    }
+    int64_t tot;
+    const int64_t e = block_exclusive_scan(r, sm, &tot);
+    if (b < kc) Rb[b] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) Rb[kc] = carry;
+}
+
+__global__ void k_reb_apply_strong(const uint64_t* __restrict__ key, const int32_t* __restrict__ val, const int64_t* d_n,
+                                   int64_t max_n, const uint8_t* __restrict__ acc, const int64_t* __restrict__ sarr,
+                                   const int64_t* __restrict__ Rb, int32_t kc, int32_t* pi,
+                                   const int32_t* __restrict__ vw, int64_t* W, RefineState* st) {
+  const int64_t n = *d_n;
+  int32_t mine = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = val[i];
+    const int64_t c = vw[v];
+    int32_t q = -1;
+    if (acc[v]) {
+      q = (int32_t)(key[i] >> kBucketBits);
+    } else {
+      // the room interval [Rb[b], Rb[b+1]) holding s: last b with Rb[b] <= s
+      const int64_t s = sarr[v];
+      int32_t lo = 0, hi = kc + 1;  // upper_bound over Rb[0..kc]
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (Rb[mid] <= s) lo = mid + 1;
+        else hi = mid;
+      }
+      const int32_t b = lo - 1;
+      if (b >= 0 && b < kc && s + c <= Rb[b + 1]) q = b;
+    }
+    if (q < 0) continue;
+    const int32_t p = pi[v];
+    pi[v] = q;
+    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
+    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    mine++;
+  }
+  if (mine) atomicAdd(&st->moved, mine);
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 6 controller (one CTA): best-state tracking, patience, next step kind
+// ---------------------------------------------------------------------------
+struct CtlArgs {
+  int64_t lmax;
+  int32_t kc;
+  int32_t patience, weak_max, phi_num, phi_den;
+  int32_t* tk;
+  int64_t* tJ;
+  int64_t* tW;
+  int32_t tcap;
+};
+
+__global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* __restrict__ W, int64_t* Jacc,
+                                                 CtlArgs a, int phase) {
+  __shared__ int64_t smax[32];
+  int64_t mx = 0;
+  for (int32_t b = threadIdx.x; b < a.kc; b += blockDim.x) mx = W[b] > mx ? W[b] : mx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = smax[w] > mx ? smax[w] : mx;
+  if (phase == 1 && s->done) return;
+  const int64_t J = *Jacc;
+  *Jacc = 0;
+  s->copy_best = 0;
+  s->J = J;
+  s->maxw = mx;
+  if (phase == 0) {
+    s->best_J = J;
+    s->best_maxw = mx;
+    s->i = 0;
+    s->iw = 0;
+    s->t = 0;
+    s->done = 0;
+  } else {
+    const int32_t t = s->t;
+    if (t - 1 < a.tcap) {
+      a.tk[t - 1] = s->kind;
+      a.tJ[t - 1] = J;
+      a.tW[t - 1] = mx;
+    }
+    if (mx <= a.lmax) {
+      if (s->best_maxw > a.lmax) {  // a feasible mapping replaces an infeasible best
+        s->best_J = J;
+        s->best_maxw = mx;
+        s->copy_best = 1;
+        s->i = 0;
+      } else {
+        // both tests compare with the best J before it is replaced
+        const bool reset = (__int128)a.phi_den * J < (__int128)a.phi_num * s->best_J;
+        if (J < s->best_J) {
+          s->best_J = J;
+          s->best_maxw = mx;
+          s->copy_best = 1;
+        }
+        if (reset) s->i = 0;
+      }
+    } else if (mx < s->best_maxw) {
+      s->best_J = J;
+      s->best_maxw = mx;
+      s->copy_best = 1;
+      s->i = 0;
+    }
+  }
+  const bool stop = s->rounds >= 0 ? (s->t >= s->rounds) : (s->i >= a.patience);
+  s->moved = 0;
+  if (stop) {
+    s->done = 1;
+    s->kind = KIND_NONE;
+    return;
+  }
+  s->i++;
+  s->t++;
+  if (mx <= a.lmax) {
+    s->kind = KIND_LP;
+    s->iw = 0;
+  } else if (s->iw < a.weak_max) {
+    s->kind = KIND_WEAK;
+    s->iw++;
+  } else {
+    s->kind = KIND_STRONG;
+    s->iw = 0;
+  }
+}
+
+__global__ void k_copy_best(const RefineState* s, const int32_t* __restrict__ pi, int32_t* __restrict__ best, int32_t n) {
+  if (!s->copy_best) return;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    best[v] = pi[v];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+inline unsigned grid_for(const Ctx& c, int64_t items_per_block, int64_t n) {
+  int64_t g = (n + items_per_block - 1) / items_per_block;
+  int64_t cap = (int64_t)c.num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+size_t conn_smem(const Ctx& c) { return (size_t)group_layout(c.topo).total * sizeof(int32_t); }
+
+void launch_eval(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  cudaEvent_t ev = c.prof_begin();
+  k_eval_low<<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc); count_launch();
+  // xadj (8) + P(v) (4) per vertex; adjacency (4) + weight (4) + gathered P(u) (4) per entry
+  c.prof_end(ev, PK_EVAL, 12 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+  if (L.n_hi)
+    k_eval_high<<<std::min(L.n_hi, c.num_sms * 8), kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc); count_launch();
+}
+
+void launch_lp(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  const unsigned gl = grid_for(c, kThreads / kSubWarp, L.n);
+  const unsigned gh = std::max(1, std::min(L.n_hi, c.num_sms * 8));
+  cudaEvent_t ev = c.prof_begin();
+  k_lp_gain_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, c.state); count_launch();
+  // per vertex: xadj 8, P 4, lock 1, X 1, P' 4, g 8; per entry: adjacency 4, weight 4, gathered P(u) 4
+  c.prof_end(ev, PK_LP_GAIN, 26 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+  if (L.n_hi)
+    k_lp_gain_high<<<gh, kHiThreads, conn_smem(c), c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.lock, c.pp, c.gain, c.inx,
+                                                          c.topo, group_layout(c.topo), c.state); count_launch();
+  ev = c.prof_begin();
+  k_lp_after_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.pp, c.gain, c.inx, c.lock, c.topo, c.state); count_launch();
+  // the X flag of every vertex (the work on X itself is data dependent)
+  c.prof_end(ev, PK_LP_AFTER, (int64_t)(L.n - L.n_hi));
+  if (L.n_hi)
+    k_lp_after_high<<<gh, kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.pp, c.gain, c.inx, c.lock, c.topo,
+                                                 c.state); count_launch();
+  k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.state); count_launch();
+}
+
+void launch_rebalance(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  const int64_t n = L.n;
+  k_reb_prep<<<1, 1024, 0, c.st>>>(c.W, c.d_pe_of_code, c.topo, c.lmax, c.cV, c.cfg.sigma_gap, c.U, c.counters,
+                                   c.accepted, c.state); count_launch();
+  RebArgs a{c.W, c.U, c.counters, c.lmax, c.cV, c.k, c.cfg.seed};
+  // per vertex: destination (c.dest), loss bucket (c.sel), eligibility (c.elig)
+  k_reb_select_low<<<grid_for(c, kThreads / kSubWarp, n), kThreads, 0, c.st>>>(view(L), L.pi, a, c.dest, c.sel, c.elig,
+                                                                                 c.state); count_launch();
+  if (L.n_hi)
+    k_reb_select_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, (size_t)c.topo.kc * sizeof(int32_t),
+                        c.st>>>(view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, c.dest, c.sel, c.elig, c.state); count_launch();
+  // eligible vertices in id order -> (source block, bucket, id) order
+  int64_t* d_elig = c.counters + CNT_ELIG;
+  scan(LoadFlag{c.elig}, StoreKeyed{L.pi, c.sel, c.sort.key[0], c.sort.val[0]}, n, nullptr, c.scan, c.st);
+  k_copy_count<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_elig); count_launch();
+  const int bits = c.topo.code_bits + kBucketBits;
+  int cur = radix_sort_pairs(c.sort, n, d_elig, bits, c.st);
+  scan(LoadSortedWeight{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_elig, c.scan, c.st);
+  const unsigned g = grid_for(c, kThreads, n);
+  k_heads<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_elig, n, c.headP); count_launch();
+  // The bucket array (c.sel) is consumed by the scan above; the selection
+  // flags go to c.inx (free during rebalancing).
+  uint8_t* selflag = c.inx;
+  k_reb_mark<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_elig, n, c.W, c.lmax,
+                                       selflag); count_launch();
+  k_reb_apply_weak<<<g, kThreads, 0, c.st>>>(c.sort.val[cur], d_elig, n, selflag, c.dest, L.pi, L.vw, c.W, c.state); count_launch();
+}
+
+__global__ void k_strong_gate(const RefineState* st, int64_t* d_sel) {
+  if (st->kind != KIND_STRONG) *d_sel = 0;
+}
+
+}  // namespace
+
+// The strong variant continues from the selection made by launch_rebalance:
+// selected movers in id order -> (destination, bucket, id) order -> accept
+// while the destination stays within L_max -> water-fill the rejected ones.
+static void launch_rebalance_strong_tail(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  const int64_t n = L.n;
+  uint8_t* selflag = c.inx;
+  int64_t* d_sel = c.counters + CNT_SEL;
+  scan(LoadFlag2{c.elig, selflag}, StoreKeyed{c.dest, c.sel, c.sort.key[0], c.sort.val[0]}, n, nullptr, c.scan, c.st);
+  k_copy_count<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_sel); count_launch();
+  k_strong_gate<<<1, 1, 0, c.st>>>(c.state, d_sel); count_launch();
+  const int bits = c.topo.code_bits + kBucketBits;
+  int cur = radix_sort_pairs(c.sort, n, d_sel, bits, c.st);
+  scan(LoadSortedWeight{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_sel, c.scan, c.st);
+  const unsigned g = grid_for(c, kThreads, n);
+  k_heads<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_sel, n, c.headP); count_launch();
+  k_reb_accept<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_sel, n, c.W, c.lmax, L.vw,
+                                         c.acc, c.accepted); count_launch();
+  // rejected movers (selected, not accepted) in id order: prefix weights
+  // (only for vertices in the selected list; acc is meaningful there)
+  scan(LoadRejected{c.elig, selflag, c.acc, L.vw}, StoreIfPositive{c.sarr}, n, nullptr, c.scan, c.st);
+  k_reb_residual<<<1, 1024, 0, c.st>>>(c.W, c.accepted, c.d_pe_of_code, c.topo.kc, c.lmax, c.Rb); count_launch();
+  k_reb_apply_strong<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], d_sel, n, c.acc, c.sarr, c.Rb,
+                                               c.topo.kc, L.pi, L.vw, c.W, c.state); count_launch();
+}
+
+namespace {
+CtlArgs ctl_args(Ctx& c) {
+  return CtlArgs{c.lmax, c.topo.kc, c.cfg.patience, c.cfg.weak_max, c.cfg.phi_num, c.cfg.phi_den,
+                 c.trace_kind, c.trace_J, c.trace_maxw, c.trace_cap};
+}
+}  // namespace
+
+void refine_alloc(Ctx& c) {
+  const size_t n = (size_t)std::max(1, c.n0);
+  const size_t kc = (size_t)c.topo.kc;
+  c.pp = c.mem.make<int32_t>(n);
+  c.gain = c.mem.make<int64_t>(n);
+  c.inx = c.mem.make<uint8_t>(n);
+  c.lock = c.mem.make<uint8_t>(n);
+  c.pi_best = c.mem.make<int32_t>(n);
+  c.dest = c.mem.make<int32_t>(n);
+  c.elig = c.mem.make<uint8_t>(n);
+  c.sel = c.mem.make<uint8_t>(n);
+  c.acc = c.mem.make<uint8_t>(n);
+  c.sarr = c.mem.make<int64_t>(n);
+  c.W = c.mem.make<int64_t>(kc);
+  c.accepted = c.mem.make<int64_t>(kc);
+  c.headP = c.mem.make<int64_t>(std::max(kc, n));
+  c.Rb = c.mem.make<int64_t>(kc + 1);
+  c.U = c.mem.make<int32_t>(kc);
+  c.counters = c.mem.make<int64_t>(CNT_N);
+  c.Jacc = c.mem.make<int64_t>(1);
+  c.state = c.mem.make<RefineState>(1);
+  c.trace_kind = c.mem.make<int32_t>(c.trace_cap);
+  c.trace_J = c.mem.make<int64_t>(c.trace_cap);
+  c.trace_maxw = c.mem.make<int64_t>(c.trace_cap);
+  GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), c.st));
+  GM_CUDA(cudaMemsetAsync(c.lock, 0, n, c.st));
+  GM_CUDA(cudaMemsetAsync(c.counters, 0, CNT_N * sizeof(int64_t), c.st));
+  GM_CUDA(cudaMemsetAsync(c.state, 0, sizeof(RefineState), c.st));
+  if (!c.h_state) GM_CUDA(cudaMallocHost(&c.h_state, sizeof(RefineState)));
+  const size_t smem = conn_smem(c);
+  if (smem > 48 * 1024) {
+    GM_CUDA(cudaFuncSetAttribute(k_lp_gain_high, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  if (kc * sizeof(int32_t) > 48 * 1024) {
+    GM_CUDA(cudaFuncSetAttribute(k_reb_select_high, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kc * sizeof(int32_t))));
+    GM_CUDA(cudaFuncSetAttribute(k_block_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kc * sizeof(int32_t))));
+  }
+}
+
+void compute_block_weights(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  GM_CUDA(cudaMemsetAsync(c.W, 0, (size_t)c.topo.kc * sizeof(int64_t), c.st));
+  k_block_weights<<<grid_for(c, kThreads * 16, L.n), kThreads, (size_t)c.topo.kc * sizeof(int32_t), c.st>>>(
+      L.n, L.pi, L.vw, c.topo.kc, c.W); count_launch();
+  GM_CUDA(cudaGetLastError());
+}
+
+void objective(Ctx& c, int lvl, int64_t* J, int64_t* maxw) {
+  compute_block_weights(c, lvl);
+  GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), c.st));
+  launch_eval(c, lvl);
+  GM_CUDA(cudaGetLastError());
+  std::vector<int64_t> W(c.topo.kc);
+  int64_t hJ = 0;
+  GM_CUDA(cudaMemcpyAsync(&hJ, c.Jacc, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(W.data(), c.W, W.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  if (J) *J = hJ;
+  if (maxw) *maxw = W.empty() ? 0 : *std::max_element(W.begin(), W.end());
+}
+
+static void set_state(Ctx& c, int32_t kind, int32_t t, int32_t level) {
+  RefineState s{};
+  s.kind = kind;
+  s.t = t;
+  s.level = level;
+  s.rounds = -1;
+  *c.h_state = s;
+  GM_CUDA(cudaMemcpyAsync(c.state, c.h_state, sizeof(RefineState), cudaMemcpyHostToDevice, c.st));
+}
+
+static int32_t read_moved(Ctx& c) {
+  GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  return c.h_state->moved;
+}
+
+int32_t lp_step(Ctx& c, int lvl) {
+  compute_block_weights(c, lvl);
+  set_state(c, KIND_LP, 0, lvl);
+  launch_lp(c, lvl);
+  GM_CUDA(cudaGetLastError());
+  return read_moved(c);
+}
+
+int32_t rebalance_step(Ctx& c, int lvl, bool strong, int32_t t) {
+  compute_block_weights(c, lvl);
+  set_state(c, strong ? KIND_STRONG : KIND_WEAK, t, lvl);
+  launch_rebalance(c, lvl);
+  launch_rebalance_strong_tail(c, lvl);
+  GM_CUDA(cudaGetLastError());
+  return read_moved(c);
+}
+
+void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
+  Level& L = c.lv[lvl];
+  compute_block_weights(c, lvl);
+  GM_CUDA(cudaMemsetAsync(c.lock, 0, (size_t)std::max(1, L.n), c.st));
+  GM_CUDA(cudaMemcpyAsync(c.pi_best, L.pi, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
+  RefineState s{};
+  s.rounds = rounds;
+  s.level = lvl;
+  *c.h_state = s;
+  GM_CUDA(cudaMemcpyAsync(c.state, c.h_state, sizeof(RefineState), cudaMemcpyHostToDevice, c.st));
+  GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), c.st));
+  launch_eval(c, lvl);
+  const CtlArgs ca = ctl_args(c);
+  k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 0); count_launch();
+  const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
+  while (true) {
+    GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+    const RefineState h = *c.h_state;
+    if (h.done) break;
+    if (h.kind == KIND_LP) {
+      launch_lp(c, lvl);
+    } else {
+      launch_rebalance(c, lvl);
+      if (h.kind == KIND_STRONG) launch_rebalance_strong_tail(c, lvl);
+    }
+    launch_eval(c, lvl);
+    k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 1); count_launch();
+    k_copy_best<<<gcopy, kThreads, 0, c.st>>>(c.state, L.pi, c.pi_best, L.n); count_launch();
+    GM_CUDA(cudaGetLastError());
+  }
+  GM_CUDA(cudaMemcpyAsync(L.pi, c.pi_best, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
+  const RefineState h = *c.h_state;
+  c.last_iters = h.t;
+  if (J) *J = h.best_J;
+  if (maxw) *maxw = h.best_maxw;
+  if (iters) *iters = h.t;
+}
+
+// high-degree vertex list of a level (ascending ids)
+namespace {
+struct LoadHigh {
+  const int64_t* xadj;
+  __device__ int64_t operator()(int64_t v) const { return (xadj[v + 1] - xadj[v] > kLowDeg) ? 1 : 0; }
+};
+struct LoadHighDeg {
+  const int64_t* xadj;
+  __device__ int64_t operator()(int64_t v) const {
+    const int64_t d = xadj[v + 1] - xadj[v];
+    return d > kLowDeg ? d : 0;
+  }
+};
+struct StoreNothing {
+  __device__ void operator()(int64_t, int64_t, int64_t) const {}
+};
+struct StoreHigh {
+  int32_t* out;
+  __device__ void operator()(int64_t v, int64_t e, int64_t x) const {
+    if (x) out[e] = (int32_t)v;
+  }
+};
+}  // namespace
+
+void classify_degrees(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  if (!L.hi) L.hi = c.mem.make<int32_t>((size_t)std::max(1, L.n));
+  scan(LoadHigh{L.xadj}, StoreHigh{L.hi}, L.n, nullptr, c.scan, c.st);
+  int64_t cnt = 0;
+  GM_CUDA(cudaMemcpyAsync(&cnt, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  L.n_hi = (int32_t)cnt;
+  L.m_hi = 0;
+  if (cnt) {
+    scan(LoadHighDeg{L.xadj}, StoreNothing{}, L.n, nullptr, c.scan, c.st);
+    GM_CUDA(cudaMemcpyAsync(&L.m_hi, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+  }
+}
+
+}  // namespace gm

@@ -1,0 +1,343 @@
+"""ctypes binding of the CUDA mapping library ``libgpumap.so``.
+
+Function names match the C ABI in ``include/gpumap.h``; this module only
+marshals arguments (numpy arrays for host data, torch CUDA tensors or raw
+device pointers for device data) and turns non-OK statuses into
+``MapError``.  Every step of the mapping path runs in the library's kernels.
+There is no CPU fallback: without the built library (and a CUDA device) every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+
+class MapError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+STATUS = {0: "MAP_OK", 1: "MAP_E_INVALID", 2: "MAP_E_OOM", 3: "MAP_E_CUDA", 4: "MAP_E_OVERFLOW",
+          5: "MAP_E_TIMEOUT", 6: "MAP_E_STATE", 7: "MAP_E_INTERNAL"}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class MapConfig(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("patience", C.c_int32), ("weak_max", C.c_int32),
+                ("phi_num", C.c_int32), ("phi_den", C.c_int32), ("sigma_gap", C.c_int32),
+                ("coarsest_factor", C.c_int32), ("cluster_iters", C.c_int32),
+                ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
+                ("stall_num", C.c_int32), ("stall_den", C.c_int32),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class MapStats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("n", C.c_int32 * 65), ("m_dir", C.c_int64 * 65),
+                ("J", C.c_int64 * 65), ("iters", C.c_int32 * 65), ("ms_coarsen", C.c_double),
+                ("ms_initial", C.c_double), ("ms_refine", C.c_double), ("ms_project", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "map_config_default": (None, [_P]),
+    "map_status_string": (C.c_char_p, [C.c_int]),
+    "map_create": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, C.c_int32, C.c_double, _P, _P, C.c_int32, _P]),
+    "map_destroy": (None, [_P]),
+    "map_last_error": (C.c_char_p, [_P]),
+    "map_sync": (C.c_int, [_P]),
+    "map_info": (C.c_int, [_P, _P, _P, _P]),
+    "map_set_mapping": (C.c_int, [_P, C.c_int32, _P]),
+    "map_get_mapping": (C.c_int, [_P, C.c_int32, _P]),
+    "map_objective": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "map_block_weights": (C.c_int, [_P, C.c_int32, _P]),
+    "map_lp_step": (C.c_int, [_P, C.c_int32, _P]),
+    "map_get_lp_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "map_set_lock": (C.c_int, [_P, C.c_int32, _P]),
+    "map_rebalance_step": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P]),
+    "map_refine": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
+    "map_get_refine_trace": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "map_coarsen": (C.c_int, [_P, _P]),
+    "map_level_info": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "map_get_level_graph": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    "map_initial": (C.c_int, [_P]),
+    "map_project": (C.c_int, [_P, C.c_int32]),
+    "map_run": (C.c_int, [_P, _P, _P]),
+    "map_stats": (C.c_int, [_P, _P]),
+}
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libgpumap.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is None:
+        path = _build.OUT
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _check(ctx, st: int, where: str):
+    if st != 0:
+        msg = lib().map_last_error(ctx)
+        raise MapError(st, where, msg.decode() if msg else "")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def map_config_default(seed: Optional[int] = None) -> MapConfig:
+    cfg = MapConfig()
+    lib().map_config_default(C.byref(cfg))
+    if seed is not None:
+        cfg.seed = seed
+    return cfg
+
+
+def torch_allocator(cfg: MapConfig) -> tuple:
+    """Routes the context's device allocations through torch's caching
+    allocator.  Returns the callback objects, which must outlive the context."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, user, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, user, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    cfg.alloc, cfg.free = a, f
+    return (a, f)
+
+
+def map_create(xadj, adjncy, adjwgt, vwgt, n: int, hier: Sequence[int], dist: Sequence[int], eps: float,
+               cfg: Optional[MapConfig] = None, stream=None, inputs_on_device: bool = False):
+    h = np.ascontiguousarray(hier, dtype=np.int32)
+    d = np.ascontiguousarray(dist, dtype=np.int32)
+    out = C.c_void_p()
+    st = lib().map_create(_ptr(xadj), _ptr(adjncy), _ptr(adjwgt), _ptr(vwgt), int(n), _ptr(h), _ptr(d), len(h),
+                          float(eps), C.byref(cfg) if cfg is not None else None, _stream_handle(stream),
+                          int(bool(inputs_on_device)), C.byref(out))
+    if st != 0:
+        msg = lib().map_last_error(None)
+        raise MapError(st, "map_create", msg.decode() if msg else "")
+    return out.value
+
+
+def map_destroy(ctx) -> None:
+    lib().map_destroy(ctx)
+
+
+def map_last_error(ctx) -> str:
+    m = lib().map_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def map_sync(ctx) -> None:
+    _check(ctx, lib().map_sync(ctx), "map_sync")
+
+
+def map_info(ctx):
+    k, lm, tw = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(ctx, lib().map_info(ctx, C.byref(k), C.byref(lm), C.byref(tw)), "map_info")
+    return k.value, lm.value, tw.value
+
+
+def map_level_info(ctx, level: int = 0):
+    n, m = C.c_int32(), C.c_int64()
+    _check(ctx, lib().map_level_info(ctx, level, C.byref(n), C.byref(m)), "map_level_info")
+    return n.value, m.value
+
+
+def map_set_mapping(ctx, level: int, pi) -> None:
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    _check(ctx, lib().map_set_mapping(ctx, level, _ptr(pi)), "map_set_mapping")
+
+
+def map_get_mapping(ctx, level: int = 0) -> np.ndarray:
+    n, _ = map_level_info(ctx, level)
+    pi = np.zeros(n, np.int32)
+    _check(ctx, lib().map_get_mapping(ctx, level, _ptr(pi)), "map_get_mapping")
+    return pi
+
+
+def map_objective(ctx, level: int = 0):
+    J, mw = C.c_int64(), C.c_int64()
+    _check(ctx, lib().map_objective(ctx, level, C.byref(J), C.byref(mw)), "map_objective")
+    return J.value, mw.value
+
+
+def map_block_weights(ctx, level: int = 0) -> np.ndarray:
+    k, _, _ = map_info(ctx)
+    W = np.zeros(k, np.int64)
+    _check(ctx, lib().map_block_weights(ctx, level, _ptr(W)), "map_block_weights")
+    return W
+
+
+def map_lp_step(ctx, level: int = 0) -> int:
+    mv = C.c_int32()
+    _check(ctx, lib().map_lp_step(ctx, level, C.byref(mv)), "map_lp_step")
+    return mv.value
+
+
+def map_get_lp_state(ctx, level: int = 0):
+    n, _ = map_level_info(ctx, level)
+    pp = np.zeros(n, np.int32)
+    g = np.zeros(n, np.int64)
+    inx = np.zeros(n, np.uint8)
+    mv = np.zeros(n, np.uint8)
+    _check(ctx, lib().map_get_lp_state(ctx, level, _ptr(pp), _ptr(g), _ptr(inx), _ptr(mv)), "map_get_lp_state")
+    return pp, g, inx, mv
+
+
+def map_set_lock(ctx, level: int, lock) -> None:
+    lock = np.ascontiguousarray(lock, dtype=np.uint8)
+    _check(ctx, lib().map_set_lock(ctx, level, _ptr(lock)), "map_set_lock")
+
+
+def map_rebalance_step(ctx, level: int, strong: bool, t: int = 1) -> int:
+    mv = C.c_int32()
+    _check(ctx, lib().map_rebalance_step(ctx, level, int(bool(strong)), int(t), C.byref(mv)), "map_rebalance_step")
+    return mv.value
+
+
+def map_refine(ctx, level: int = 0, rounds: int = -1):
+    J, mw, it = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(ctx, lib().map_refine(ctx, level, rounds, C.byref(J), C.byref(mw), C.byref(it)), "map_refine")
+    return J.value, mw.value, it.value
+
+
+def map_get_refine_trace(ctx, cap: int = 4096):
+    kind = np.zeros(cap, np.int32)
+    J = np.zeros(cap, np.int64)
+    W = np.zeros(cap, np.int64)
+    cnt = C.c_int32()
+    _check(ctx, lib().map_get_refine_trace(ctx, cap, _ptr(kind), _ptr(J), _ptr(W), C.byref(cnt)),
+           "map_get_refine_trace")
+    m = min(cnt.value, cap)
+    return kind[:m], J[:m], W[:m], cnt.value
+
+
+def map_coarsen(ctx) -> int:
+    lv = C.c_int32()
+    _check(ctx, lib().map_coarsen(ctx, C.byref(lv)), "map_coarsen")
+    return lv.value
+
+
+def map_get_level_graph(ctx, level: int, with_M: bool = True):
+    n, m = map_level_info(ctx, level)
+    xadj = np.zeros(n + 1, np.int64)
+    adj = np.zeros(max(m, 1), np.int32)
+    w = np.zeros(max(m, 1), np.int32)
+    vw = np.zeros(n, np.int32)
+    M = np.zeros(n, np.int32) if with_M else None
+    _check(ctx, lib().map_get_level_graph(ctx, level, _ptr(xadj), _ptr(adj), _ptr(w), _ptr(vw), _ptr(M)),
+           "map_get_level_graph")
+    return xadj, adj[:m], w[:m], vw, M
+
+
+def map_initial(ctx) -> None:
+    _check(ctx, lib().map_initial(ctx), "map_initial")
+
+
+def map_project(ctx, level: int) -> None:
+    _check(ctx, lib().map_project(ctx, level), "map_project")
+
+
+def map_run(ctx, out_pi=None):
+    J = C.c_int64()
+    _check(ctx, lib().map_run(ctx, _ptr(out_pi), C.byref(J)), "map_run")
+    return J.value
+
+
+def map_stats(ctx) -> MapStats:
+    s = MapStats()
+    _check(ctx, lib().map_stats(ctx, C.byref(s)), "map_stats")
+    return s
+
+
+class Mapper:
+    """Owns one context; convenience wrapper over the functions above."""
+
+    def __init__(self, graph, hier, dist, eps=0.03, seed=None, cfg=None, stream=None, device_inputs=None,
+                 torch_alloc=False):
+        self._keep = None
+        cfg = cfg or map_config_default(seed)
+        if torch_alloc:
+            self._keep = torch_allocator(cfg)
+        if device_inputs is not None:
+            xadj, adj, w, vw = device_inputs
+            self.ctx = map_create(xadj, adj, w, vw, graph.n, hier, dist, eps, cfg, stream, True)
+        else:
+            self.ctx = map_create(graph.xadj, graph.adj if graph.m_dir else None, graph.adjw if graph.m_dir else None,
+                                  graph.vw, graph.n, hier, dist, eps, cfg, stream, False)
+        self.n = graph.n
+
+    def close(self):
+        if self.ctx:
+            map_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

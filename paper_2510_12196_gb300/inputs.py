@@ -37,11 +37,12 @@ _U64 = np.uint64
 
 def splitmix64(seed: int, counter) -> np.ndarray:
     """SplitMix64 output for state ``seed ^ counter`` (vectorised, uint64)."""
-    z = np.asarray(counter, dtype=np.uint64) ^ _U64(seed & 0xFFFFFFFFFFFFFFFF)
-    z = z + _GAMMA
-    z = (z ^ (z >> _U64(30))) * _M1
-    z = (z ^ (z >> _U64(27))) * _M2
-    return z ^ (z >> _U64(31))
+    with np.errstate(over="ignore"):
+        z = np.asarray(counter, dtype=np.uint64) ^ _U64(seed & 0xFFFFFFFFFFFFFFFF)
+        z = z + _GAMMA
+        z = (z ^ (z >> _U64(30))) * _M1
+        z = (z ^ (z >> _U64(27))) * _M2
+        return z ^ (z >> _U64(31))
 
 
 def uniform01(seed: int, counter) -> np.ndarray:

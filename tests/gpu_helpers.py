@@ -1,0 +1,47 @@
+"""Shared helpers of the GPU parity tests: build a context from a seeded graph
+and compare the CUDA library with the CPU oracle on the same inputs."""
+import numpy as np
+
+import oracle as O
+from paper_2510_12196_gb300 import gpumap as G
+from paper_2510_12196_gb300 import inputs as I
+
+
+def make_ctx(g, hier, dist, eps=0.03, seed=0x5EED0000, **cfg_over):
+    cfg = G.map_config_default(seed)
+    for k, v in cfg_over.items():
+        setattr(cfg, k, v)
+    return G.map_create(g.xadj, g.adj if g.m_dir else None, g.adjw if g.m_dir else None, g.vw, g.n,
+                        hier, dist, eps, cfg)
+
+
+def oracle_params(seed=0x5EED0000, **over):
+    p = O.default_params(seed)
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def graph_zoo():
+    """Small graphs covering the degree classes and structure of the paper's
+    workload families, plus degenerate cases."""
+    zoo = [
+        I.grid2d(16, 12),
+        I.grid3d(6, 5, 4),
+        I.rgg2d(3000, I.rgg_radius(3000, 12), 11, wmax=10),
+        I.erdos_renyi(60, 0.7, 5, wmax=9, vwmax=4),      # degrees ~40: CTA-per-vertex path
+        I.rmat(11, 8, 0.57, 0.19, 0.19, 3),               # hubs + isolated vertices
+        I.erdos_renyi(40, 0.05, 8, wmax=3, vwmax=5),      # sparse, isolated vertices
+    ]
+    # a star: one vertex of degree 299 plus leaves
+    n = 300
+    zoo.append(I.csr_from_pairs(n, np.zeros(n - 1, np.int64), np.arange(1, n), name="star300"))
+    return zoo
+
+
+TOPOS = [((4, 8), (1, 10)), ((4, 8, 6), (1, 10, 100)), ((2, 3), (3, 7)), ((3,), (5,)),
+         ((1, 4, 2), (2, 9, 40)), ((2, 4, 16, 8), (1, 10, 100, 1000))]
+
+
+def g_graph_from_level(xadj, adj, w, vw):
+    return I.Graph(len(vw), xadj, adj, w, vw)

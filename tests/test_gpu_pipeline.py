@@ -1,0 +1,216 @@
+"""GPU parity of the multilevel pipeline (clustering, contraction, initial
+mapping, projection, full map_run) against the CPU oracle, the full-size
+RGG workload, determinism, edge cases and input validation."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_12196_gb300 import gpumap as G
+from paper_2510_12196_gb300 import inputs as I
+
+from gpu_helpers import make_ctx, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_levels(g, k, lmax, prm, max_levels=64):
+    """Coarsening chain computed by the oracle: list of (graph, M)."""
+    out = []
+    cur = g
+    while len(out) + 1 < max_levels and cur.n >= prm.coarsest_factor * k:
+        wcap = max(lmax // prm.cluster_cap_div, int(cur.vw.max()))
+        M, nc = O.cluster(cur, wcap, prm, level=len(out))
+        if nc * prm.stall_den > prm.stall_num * cur.n:
+            break
+        xc, ac, wc, vc = O.contract(cur, M, nc)
+        out.append((cur, M))
+        cur = I.Graph(nc, xc, ac, wc, vc)
+    out.append((cur, None))
+    return out
+
+
+def _check_coarsening(g, hier, dist, seed=0x5EED0000, **over):
+    k = O.num_pes(hier)
+    prm = oracle_params(seed, **over)
+    lmax = O.lmax(int(g.vw.sum()), k, 0.03)
+    chain = _oracle_levels(g, k, lmax, prm)
+    ctx = make_ctx(g, hier, dist, seed=seed, **over)
+    try:
+        nl = G.map_coarsen(ctx)
+        assert nl == len(chain)
+        for lvl, (og, oM) in enumerate(chain):
+            xadj, adj, w, vw, M = G.map_get_level_graph(ctx, lvl, with_M=oM is not None)
+            assert np.array_equal(xadj, og.xadj), lvl
+            assert np.array_equal(adj, og.adj), lvl
+            assert np.array_equal(w, og.adjw), lvl
+            assert np.array_equal(vw, og.vw), lvl
+            if oM is not None:
+                assert np.array_equal(M, oM), lvl
+        # initial mapping of the coarsest level
+        G.map_initial(ctx)
+        top = chain[-1][0]
+        assert np.array_equal(G.map_get_mapping(ctx, nl - 1), O.initial(top, k))
+        # projection
+        if nl > 1:
+            pc = I.random_mapping(chain[-1][0].n, k, 5)
+            G.map_set_mapping(ctx, nl - 1, pc)
+            G.map_project(ctx, nl - 2)
+            assert np.array_equal(G.map_get_mapping(ctx, nl - 2), pc[chain[-2][1]])
+    finally:
+        G.map_destroy(ctx)
+    return chain
+
+
+def test_coarsen_rgg16():
+    g = I.rgg2d(1 << 16, I.rgg_radius(1 << 16, 12), 7, wmax=10)
+    chain = _check_coarsening(g, (4, 8, 8), (1, 10, 100))
+    assert len(chain) >= 3
+
+
+def test_coarsen_rmat_hubs():
+    g = I.rmat(14, 16, 0.57, 0.19, 0.19, 9)
+    _check_coarsening(g, (4, 8), (1, 10))
+
+
+def test_coarsen_grid3d_and_weights():
+    g = I.grid3d(32, 16, 16)
+    _check_coarsening(g, (4, 16), (1, 10), coarsest_factor=2, cluster_cap_div=2)
+    g2 = I.erdos_renyi(700, 0.02, 4, wmax=7, vwmax=5)
+    _check_coarsening(g2, (2, 4), (1, 10), coarsest_factor=4)
+
+
+def _map_run_compare(g, hier, dist, eps=0.03, seed=0x5EED0000, **over):
+    ctx = make_ctx(g, hier, dist, eps=eps, seed=seed, **over)
+    try:
+        pi = np.zeros(g.n, np.int32)
+        J = G.map_run(ctx, pi)
+        st = G.map_stats(ctx)
+    finally:
+        G.map_destroy(ctx)
+    opi, oJ, ost = O.map_run(g, hier, dist, eps, oracle_params(seed, **over))
+    assert st.levels == ost.levels
+    assert [st.n[i] for i in range(st.levels)] == [ost.n[i] for i in range(ost.levels)]
+    assert [st.iters[i] for i in range(st.levels)] == [ost.iters[i] for i in range(ost.levels)]
+    assert [st.J[i] for i in range(st.levels)] == [ost.J[i] for i in range(ost.levels)]
+    assert J == oJ
+    assert np.array_equal(pi, opi)
+    return J
+
+
+@pytest.mark.parametrize("case", ["rgg15", "grid3d", "rmat13", "er", "shuffled"])
+def test_map_run_parity(case):
+    if case == "rgg15":
+        g, h, d = I.rgg2d(1 << 15, I.rgg_radius(1 << 15, 12), 3, wmax=10), (4, 8, 8), (1, 10, 100)
+    elif case == "grid3d":
+        g, h, d = I.grid3d(32, 32, 16), (4, 16, 8), (1, 10, 100)
+    elif case == "rmat13":
+        g, h, d = I.rmat(13, 16, 0.57, 0.19, 0.19, 5), (4, 16), (1, 10)
+    elif case == "er":
+        g, h, d = I.erdos_renyi(900, 0.01, 6, wmax=9, vwmax=3), (2, 4, 16), (1, 10, 100)
+    else:
+        g, h, d = I.rgg2d(1 << 14, I.rgg_radius(1 << 14, 12), 4, wmax=10, shuffled=True), (4, 8, 6), (1, 10, 100)
+    _map_run_compare(g, h, d)
+
+
+def test_map_run_rgg_2_20_full_size():
+    """RGG 2^20, mean degree 12, weights 1..10, 4:8:8 / 1:10:100, eps 0.03:
+    the complete pipeline bit-identical to the oracle."""
+    w = I.workload_rgg(20)
+    _map_run_compare(w.graph, w.topo.hier, w.topo.dist, w.topo.eps, seed=w.seed)
+
+
+def test_determinism_repeat_and_streams():
+    import torch
+    g = I.rgg2d(1 << 15, I.rgg_radius(1 << 15, 12), 8, wmax=10)
+    outs = []
+    for rep in range(3):
+        s = torch.cuda.Stream() if rep == 2 else None
+        cfg = G.map_config_default()
+        ctx = G.map_create(g.xadj, g.adj, g.adjw, g.vw, g.n, (4, 8, 8), (1, 10, 100), 0.03, cfg, stream=s)
+        pi = np.zeros(g.n, np.int32)
+        J = G.map_run(ctx, pi)
+        G.map_destroy(ctx)
+        outs.append((J, pi))
+    for J, pi in outs[1:]:
+        assert J == outs[0][0] and np.array_equal(pi, outs[0][1])
+
+
+def test_device_inputs_and_torch_allocator():
+    import torch
+    g = I.rgg2d(5000, I.rgg_radius(5000, 12), 12, wmax=10)
+    dev = [torch.from_numpy(a).cuda() for a in (g.xadj, g.adj, g.adjw, g.vw)]
+    m = G.Mapper(g, (4, 8), (1, 10), device_inputs=dev, torch_alloc=True)
+    try:
+        pi = np.zeros(g.n, np.int32)
+        J = G.map_run(m.ctx, pi)
+    finally:
+        m.close()
+    opi, oJ, _ = O.map_run(g, (4, 8), (1, 10), 0.03, oracle_params())
+    assert J == oJ and np.array_equal(pi, opi)
+
+
+# ----------------------------------------------------------------------------
+# edge cases
+# ----------------------------------------------------------------------------
+
+def test_single_vertex_and_edgeless():
+    g1 = I.csr_from_pairs(1, np.zeros(0), np.zeros(0))
+    _map_run_compare(g1, (4, 8), (1, 10))
+    g0 = I.csr_from_pairs(500, np.zeros(0), np.zeros(0), vw=np.arange(1, 501) % 7 + 1)
+    _map_run_compare(g0, (2, 2), (1, 10), coarsest_factor=2)
+
+
+def test_one_pe_and_unit_levels():
+    g = I.rgg2d(3000, I.rgg_radius(3000, 10), 2, wmax=10)
+    assert _map_run_compare(g, (1,), (5,)) == 0
+    _map_run_compare(g, (1, 8, 1), (3, 10, 100))
+
+
+def test_zero_imbalance_and_heavy_vertices():
+    g = I.erdos_renyi(300, 0.03, 13, wmax=5, vwmax=60)
+    _map_run_compare(g, (2, 4), (1, 10), eps=0.0, coarsest_factor=4)
+
+
+def test_max_hierarchy_code_space():
+    g = I.rgg2d(1 << 15, I.rgg_radius(1 << 15, 12), 21, wmax=10)
+    k = 16384
+    pi = I.random_mapping(g.n, k, 3)
+    ctx = make_ctx(g, (4, 16, 16, 16), (1, 10, 100, 1000))
+    try:
+        G.map_set_mapping(ctx, 0, pi)
+        assert G.map_objective(ctx, 0) == O.objective(g, (4, 16, 16, 16), (1, 10, 100, 1000), pi)[:2]
+        G.map_lp_step(ctx, 0)
+        opi = O.lp_step(g, (4, 16, 16, 16), (1, 10, 100, 1000), pi, np.zeros(g.n, np.uint8))[0]
+        assert np.array_equal(G.map_get_mapping(ctx, 0), opi)
+    finally:
+        G.map_destroy(ctx)
+
+
+def _expect_status(status, **kw):
+    g = kw.pop("g")
+    with pytest.raises(G.MapError) as ei:
+        ctx = G.map_create(g.xadj, g.adj, g.adjw, g.vw, g.n, kw.get("hier", (4, 8)), kw.get("dist", (1, 10)),
+                           kw.get("eps", 0.03))
+        G.map_destroy(ctx)
+    assert ei.value.status == status, str(ei.value)
+
+
+def test_validation_errors():
+    g = I.grid2d(8, 8)
+    bad = I.Graph(g.n, g.xadj.copy(), g.adj.copy(), g.adjw.copy(), g.vw.copy())
+    bad.adjw[3] += 1  # asymmetric weight
+    _expect_status(1, g=bad)
+    bad = I.Graph(g.n, g.xadj.copy(), g.adj.copy(), g.adjw.copy(), g.vw.copy())
+    bad.adj[0] = 0  # self-loop at vertex 0
+    _expect_status(1, g=bad)
+    bad = I.Graph(g.n, g.xadj.copy(), g.adj.copy(), g.adjw.copy(), g.vw.copy())
+    bad.adj[5] = 1000  # out of range
+    _expect_status(1, g=bad)
+    bad = I.Graph(g.n, g.xadj.copy(), g.adj.copy(), g.adjw.copy(), g.vw.copy())
+    bad.vw[0] = 0
+    _expect_status(1, g=bad)
+    big = I.Graph(g.n, g.xadj.copy(), g.adj.copy(), g.adjw.copy(), np.full(g.n, 1 << 26, np.int32))
+    _expect_status(4, g=big)
+    _expect_status(1, g=g, hier=(4, 0), dist=(1, 10))
+    _expect_status(1, g=g, hier=(256, 256), dist=(1, 10))
+    _expect_status(1, g=g, eps=1.5)
