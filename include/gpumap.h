@@ -224,16 +224,18 @@ enum {
  * and no synchronisation. */
 GPUMAP_API map_status map_profile_enable(map_ctx* ctx, int32_t enable);
 
-/* Totals since the last read for kernel class `which`: timed launches,
- * device time in ms (sum of event intervals) and the algorithmic bytes those
- * launches move by the library's byte model (compulsory CSR and per-vertex
- * streams; each neighbour gather counted once as 4 bytes).  Synchronises the
- * stream; resets the class.  Outputs may be NULL. */
-GPUMAP_API map_status map_profile_read(map_ctx* ctx, int32_t which, int64_t* launches, double* total_ms,
-                                       int64_t* bytes);
+/* Totals since the last read for kernel class `which` on hierarchy level
+ * `level` (-1: all levels): timed launches, device time in ms (sum of event
+ * intervals) and the algorithmic bytes those launches move by the library's
+ * byte model (compulsory CSR and per-vertex streams; each neighbour gather
+ * counted once as 4 bytes).  Synchronises the stream; the records read are
+ * removed.  Outputs may be NULL. */
+GPUMAP_API map_status map_profile_read(map_ctx* ctx, int32_t which, int32_t level, int64_t* launches,
+                                       double* total_ms, int64_t* bytes);
 
 /* Number of kernels this library has launched in this process so far. */
 GPUMAP_API long long map_launch_count(void);
+
 
 #ifdef __cplusplus
 }

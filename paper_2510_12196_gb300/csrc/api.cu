@@ -75,7 +75,7 @@ void Ctx::prof_end(cudaEvent_t a, int32_t kind, int64_t bytes) {
   if (!prof || !a) return;
   cudaEvent_t b = ev_pool[ev_used++];
   GM_CUDA(cudaEventRecord(b, st));
-  prof_recs.push_back(ProfRec{a, b, kind, bytes});
+  prof_recs.push_back(ProfRec{a, b, kind, prof_level, bytes});
 }
 
 namespace {
@@ -576,7 +576,8 @@ map_status map_profile_enable(map_ctx* ctx, int32_t enable) {
   });
 }
 
-map_status map_profile_read(map_ctx* ctx, int32_t which, int64_t* launches, double* total_ms, int64_t* bytes) {
+map_status map_profile_read(map_ctx* ctx, int32_t which, int32_t level, int64_t* launches, double* total_ms,
+                            int64_t* bytes) {
   return guarded(ctx, [&](Ctx& c) {
     if (which < 0 || which >= PK_COUNT) throw ApiError(MAP_E_INVALID, "unknown kernel class");
     sync(c);
@@ -584,7 +585,7 @@ map_status map_profile_read(map_ctx* ctx, int32_t which, int64_t* launches, doub
     double ms = 0;
     std::vector<ProfRec> keep;
     for (const ProfRec& r : c.prof_recs) {
-      if (r.kind != which) {
+      if (r.kind != which || (level >= 0 && r.level != level)) {
         keep.push_back(r);
         continue;
       }

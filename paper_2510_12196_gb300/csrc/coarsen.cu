@@ -643,6 +643,7 @@ int32_t cluster_level(Ctx& c, int lvl) {
     GM_CUDA(cudaMemsetAsync(moved, 0, sizeof(int64_t), c.st));
     for (int32_t r = 0; r < 2; r++) {
       ClusterArgs a{c.C, c.Wc, c.ReqW, c.req, wcap, c.cfg.seed, lvl, it, r};
+      c.prof_level = lvl;
       cudaEvent_t ev = c.prof_begin();
       k_cluster_low<<<gl, kThreads, 0, c.st>>>(view(L), a); count_launch();
       // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
@@ -698,6 +699,7 @@ void contract_level(Ctx& c, int lvl, int32_t nc) {
   if (m > 0) {
     k_contract_keys<<<grid_for(c, kThreads / kSubWarp, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
                                                                                    c.sort.val[0], d_valid); count_launch();
+    c.prof_level = lvl;
     cudaEvent_t ev = c.prof_begin();
     const int cur = radix_sort_pairs(c.sort, m, nullptr, 2 * bits, c.st);
     // per 8-bit pass: keys read twice (histogram, scatter), key + value read and written once

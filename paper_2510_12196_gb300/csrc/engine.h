@@ -51,6 +51,7 @@ enum : int32_t { PK_LP_GAIN = 0, PK_LP_AFTER = 1, PK_EVAL = 2, PK_CLUSTER = 3, P
 struct ProfRec {
   cudaEvent_t a, b;
   int32_t kind;
+  int32_t level;
   int64_t bytes;
 };
 
@@ -160,6 +161,7 @@ struct Ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   cudaEvent_t prof_begin();
+  int32_t prof_level = 0;     // level of the launches being recorded
   void prof_end(cudaEvent_t a, int32_t kind, int64_t bytes);
 
   // stats

@@ -25,9 +25,11 @@ __global__ void __launch_bounds__(1024) k_scan_tile_sums(int64_t* tile_sums, int
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __restrict__ keys, int64_t max_n,
                                                             const int64_t* d_n, int shift,
-                                                            int64_t* __restrict__ hist, int64_t max_tiles) {
+                                                            int64_t* __restrict__ hist, int64_t max_tiles,
+                                                            int64_t skip_upto) {
   __shared__ int32_t cnt[256];
-  const int64_t n = load_count(d_n, max_n);
+  int64_t n = load_count(d_n, max_n);
+  if (n <= skip_upto) n = 0;  // the single-CTA sort handles it
   for (int i = threadIdx.x; i < 256; i += kSortThreads) cnt[i] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -49,10 +51,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                int32_t* __restrict__ vout, int64_t max_n,
                                                                const int64_t* d_n, int shift,
                                                                const int64_t* __restrict__ hist_off,
-                                                               int64_t max_tiles) {
+                                                               int64_t max_tiles, int64_t skip_upto) {
   __shared__ int32_t wcnt[kSortWarps][256];
   __shared__ int64_t goff[256];
   const int64_t n = load_count(d_n, max_n);
+  if (n <= skip_upto) return;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -102,16 +105,124 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
   }
 }
 
+// Single CTA: stable LSD radix sort of n <= kSmallSort pairs in shared memory.
+// Items of warp w are [w * items, (w + 1) * items) in lane-strided order, so
+// (warp, item, lane) order is index order and equal digits keep it.
+__global__ void __launch_bounds__(kSmallThreads) k_sort_small(const uint64_t* __restrict__ kin,
+                                                              const int32_t* __restrict__ vin,
+                                                              uint64_t* __restrict__ kout,
+                                                              int32_t* __restrict__ vout, const int64_t* d_n,
+                                                              int64_t max_n, int bits) {
+  constexpr int kW = kSmallThreads / 32;
+  constexpr int kItems = kSmallSort / kSmallThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* ks = reinterpret_cast<uint64_t*>(smem_raw);                  // [2][kSmallSort]
+  int32_t* vs = reinterpret_cast<int32_t*>(ks + 2 * kSmallSort);          // [2][kSmallSort]
+  int32_t* wcnt = vs + 2 * kSmallSort;                                    // [kW][256]
+  __shared__ int32_t dbase[257];
+  __shared__ int64_t sm[33];
+  const int64_t n64 = load_count(d_n, max_n);
+  if (n64 > kSmallSort || n64 <= 0) return;
+  const int n = (int)n64;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const unsigned lt = (1u << l) - 1u;
+  for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+    ks[i] = kin[i];
+    vs[i] = vin[i];
+  }
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    const uint64_t* kc = ks + cur * kSmallSort;
+    const int32_t* vc = vs + cur * kSmallSort;
+    uint64_t* kn = ks + (cur ^ 1) * kSmallSort;
+    int32_t* vn = vs + (cur ^ 1) * kSmallSort;
+    for (int i = threadIdx.x; i < kW * 256; i += kSmallThreads) wcnt[i] = 0;
+    __syncthreads();
+    int rank[kItems], dig[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+      const int idx = w * 32 * kItems + j * 32 + l;
+      const bool valid = idx < n;
+      const int d = valid ? (int)((kc[idx] >> shift) & 255u) : 256 + l;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      int r = 0;
+      if (valid) r = wcnt[w * 256 + d] + __popc(peers & lt);
+      __syncwarp();
+      if (valid && (peers & lt) == 0) wcnt[w * 256 + d] += __popc(peers);
+      __syncwarp();
+      rank[j] = valid ? r : -1;
+      dig[j] = d;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, digit totals -> digit bases
+    int64_t tot = 0;
+    if (threadIdx.x < 256) {
+      int32_t run = 0;
+      for (int ww = 0; ww < kW; ww++) {
+        const int32_t t = wcnt[ww * 256 + threadIdx.x];
+        wcnt[ww * 256 + threadIdx.x] = run;
+        run += t;
+      }
+      tot = run;
+    }
+    int64_t all;
+    const int64_t ex = block_exclusive_scan(tot, sm, &all);
+    if (threadIdx.x < 256) dbase[threadIdx.x] = (int32_t)ex;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+      if (rank[j] < 0) continue;
+      const int idx = w * 32 * kItems + j * 32 + l;
+      const int pos = dbase[dig[j]] + wcnt[w * 256 + dig[j]] + rank[j];
+      kn[pos] = kc[idx];
+      vn[pos] = vc[idx];
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+    kout[i] = ks[cur * kSmallSort + i];
+    vout[i] = vs[cur * kSmallSort + i];
+  }
+}
+
+void sort_init() {
+  static std::atomic<unsigned long long> done{0};  // one bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ULL << (dev & 63);
+  if (done.load() & bit) return;
+  cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_sort_smem());
+  done.fetch_or(bit);
+}
+
 int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st) {
   if (max_n <= 0 || bits <= 0) return 0;
   const int64_t tiles = sort_tiles(max_n);
+  const int passes = (bits + 7) / 8;
+  const int out = passes & 1;  // buffer holding the result after `passes` swaps
+  // device-counted sets: the single-CTA kernel takes counts <= kSmallSort and
+  // writes into the result buffer; the multi-CTA passes skip those counts
+  int64_t skip = -1;
+  if (d_n) {
+    sort_init();
+    k_sort_small<<<1, kSmallThreads, small_sort_smem(), st>>>(b.key[0], b.val[0], b.key[out], b.val[out], d_n,
+                                                              max_n, bits); count_launch();
+    skip = kSmallSort;
+  }
+  if (!d_n && max_n <= kSmallSort) {
+    sort_init();
+    k_sort_small<<<1, kSmallThreads, small_sort_smem(), st>>>(b.key[0], b.val[0], b.key[out], b.val[out], nullptr,
+                                                              max_n, bits); count_launch();
+    return out;
+  }
   int cur = 0;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], max_n, d_n, shift, b.hist, tiles); count_launch();
+    k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], max_n, d_n, shift, b.hist, tiles, skip); count_launch();
     scan(LoadI64{b.hist}, StoreExcl{b.hist_off}, 256 * tiles, nullptr, b.scan, st);
     k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], b.val[cur], b.key[cur ^ 1],
                                                              b.val[cur ^ 1], max_n, d_n, shift, b.hist_off,
-                                                             tiles); count_launch();
+                                                             tiles, skip); count_launch();
     cur ^= 1;
   }
   return cur;

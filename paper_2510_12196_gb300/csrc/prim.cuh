@@ -175,12 +175,26 @@ struct SortBufs {
 
 __host__ inline int64_t sort_tiles(int64_t max_n) { return (max_n + kSortTile - 1) / kSortTile; }
 
+// Single-CTA sort of device-counted sets of at most kSmallSort elements
+// (stable LSD radix sort in shared memory); larger sets take the multi-CTA
+// passes, whose kernels return at once when the count is small.
+constexpr int kSmallSort = 4096;
+constexpr int kSmallThreads = 1024;
+__host__ inline size_t small_sort_smem() {
+  return (size_t)2 * kSmallSort * (sizeof(uint64_t) + sizeof(int32_t)) +
+         (size_t)(kSmallThreads / 32) * 256 * sizeof(int32_t);
+}
+
 __global__ void k_sort_hist(const uint64_t* __restrict__ keys, int64_t max_n, const int64_t* d_n, int shift,
-                            int64_t* __restrict__ hist, int64_t max_tiles);
+                            int64_t* __restrict__ hist, int64_t max_tiles, int64_t skip_upto);
 __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                                uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t max_n,
                                const int64_t* d_n, int shift, const int64_t* __restrict__ hist_off,
-                               int64_t max_tiles);
+                               int64_t max_tiles, int64_t skip_upto);
+__global__ void k_sort_small(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                             uint64_t* __restrict__ kout, int32_t* __restrict__ vout, const int64_t* d_n,
+                             int64_t max_n, int bits);
+void sort_init();
 
 // Sorts buffer 0 (n elements, count on device or max_n) by key bits [0, bits).
 // Returns the buffer index (0 or 1) that holds the sorted result.

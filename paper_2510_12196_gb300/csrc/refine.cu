@@ -901,6 +901,7 @@ size_t conn_smem(const Ctx& c) { return (size_t)group_layout(c.topo).total * siz
 
 void launch_eval(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
+  c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
   k_eval_low<<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc); count_launch();
   // xadj (8) + P(v) (4) per vertex; adjacency (4) + weight (4) + gathered P(u) (4) per entry
@@ -913,6 +914,7 @@ void launch_lp(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
   const unsigned gl = grid_for(c, kThreads / kSubWarp, L.n);
   const unsigned gh = std::max(1, std::min(L.n_hi, c.num_sms * 8));
+  c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
   k_lp_gain_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, c.state); count_launch();
   // per vertex: xadj 8, P 4, lock 1, X 1, P' 4, g 8; per entry: adjacency 4, weight 4, gathered P(u) 4

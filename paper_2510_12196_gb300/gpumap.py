@@ -75,6 +75,9 @@ _SIGS = {
     "map_project": (C.c_int, [_P, C.c_int32]),
     "map_run": (C.c_int, [_P, _P, _P]),
     "map_stats": (C.c_int, [_P, _P]),
+    "map_profile_enable": (C.c_int, [_P, C.c_int32]),
+    "map_profile_read": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
+    "map_launch_count": (C.c_longlong, []),
 }
 
 
@@ -306,6 +309,26 @@ def map_stats(ctx) -> MapStats:
     s = MapStats()
     _check(ctx, lib().map_stats(ctx, C.byref(s)), "map_stats")
     return s
+
+
+KERNEL_CLASSES = {0: "lp_gain", 1: "lp_after", 2: "eval_J", 3: "cluster", 4: "radix_sort"}
+
+
+def map_profile_enable(ctx, enable: bool = True) -> None:
+    _check(ctx, lib().map_profile_enable(ctx, int(bool(enable))), "map_profile_enable")
+
+
+def map_profile_read(ctx, which: int, level: int = -1):
+    """(launches, total ms, algorithmic bytes) of one kernel class since the last
+    read, on one hierarchy level (-1: all levels)."""
+    l, ms, by = C.c_int64(), C.c_double(), C.c_int64()
+    _check(ctx, lib().map_profile_read(ctx, which, level, C.byref(l), C.byref(ms), C.byref(by)),
+           "map_profile_read")
+    return l.value, ms.value, by.value
+
+
+def map_launch_count() -> int:
+    return int(lib().map_launch_count())
 
 
 class Mapper:
