@@ -124,7 +124,8 @@ GPUMAP_API map_status map_create(const int64_t* xadj, const int32_t* adjncy, con
 GPUMAP_API void map_destroy(map_ctx* ctx);
 
 /* Text of the last error of this context (empty if none).  With ctx = NULL:
- * the error of the last failed map_create on the calling thread. */
+ * the error of the last failed map_create or map_objective_noalloc on the
+ * calling thread. */
 GPUMAP_API const char* map_last_error(const map_ctx* ctx);
 
 /* Waits for all work of the context. */
@@ -236,6 +237,30 @@ GPUMAP_API map_status map_profile_read(map_ctx* ctx, int32_t which, int32_t leve
 /* Number of kernels this library has launched in this process so far. */
 GPUMAP_API long long map_launch_count(void);
 
+/* The paper has no counterpart to this call.  It returns what map_objective
+ * returns (J and the maximum block weight) for callers that cannot or must
+ * not allocate device memory: cudaMalloc / cudaFree may synchronise the whole
+ * device and stall unrelated streams, and some callers run under a fixed
+ * device-memory budget owned by their own pool, or just want the cost of a
+ * mapping they already hold in device memory without creating a context.
+ * It allocates nothing: no context, no cudaMalloc / cudaFree, no allocating
+ * library routine.
+ *  xadj, adjncy, adjwgt, vwgt, pi: DEVICE pointers (CSR as above, adjwgt may
+ *    be NULL for unit weights; pi int32[n] PE ids in [0, k); entries out of
+ *    range are skipped, not reported).  n >= 1.
+ *  hier[levels], dist[levels]: HOST arrays as in map_create; the PE code
+ *    space must not exceed 16384 (else MAP_E_INVALID, see map_last_error(NULL)).
+ *  out: DEVICE int64[2], receives {J, maximum block weight}.
+ *  stream: cudaStream_t; the work is enqueued on it and not waited for.
+ * Scratch: one file-scope device array of about 192 KiB per device, held until
+ * the process exits.  Every call shares it and it keeps the last call's
+ * contents; each call clears what must start at zero.  Calls that overlap on
+ * the GPU (several streams or host threads) race on it: serialise them.  The
+ * first call on a device looks up the array's address with that device
+ * current; make that first call before any stream capture on the device. */
+GPUMAP_API map_status map_objective_noalloc(const int64_t* xadj, const int32_t* adjncy, const int32_t* adjwgt,
+                                            const int32_t* vwgt, int32_t n, const int32_t* pi, const int32_t* hier,
+                                            const int32_t* dist, int32_t levels, int64_t* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,11 @@ void Ctx::prof_end(cudaEvent_t a, int32_t kind, int64_t bytes) {
   prof_recs.push_back(ProfRec{a, b, kind, prof_level, bytes});
 }
 
+std::string& last_create_error() {
+  static thread_local std::string s;
+  return s;
+}
+
 namespace {
 
 void build_topology(Ctx& c, const int32_t* hier, const int32_t* dist, int32_t levels) {
@@ -176,11 +181,6 @@ map_status guarded(map_ctx* ctx, F&& f) {
 }
 
 void sync(Ctx& c) { GM_CUDA(cudaStreamSynchronize(c.st)); }
-
-std::string& last_create_error() {
-  static thread_local std::string s;
-  return s;
-}
 
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();

@@ -170,6 +170,9 @@ struct Ctx {
   int64_t Jlev[65] = {0};
 };
 
+// api.cu: error text of the last failed context-free call on this thread
+std::string& last_create_error();
+
 // refine.cu
 void refine_alloc(Ctx& c);
 void compute_block_weights(Ctx& c, int lvl);

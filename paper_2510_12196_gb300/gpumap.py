@@ -78,6 +78,7 @@ _SIGS = {
     "map_profile_enable": (C.c_int, [_P, C.c_int32]),
     "map_profile_read": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
     "map_launch_count": (C.c_longlong, []),
+    "map_objective_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, C.c_int32, _P, _P]),
 }
 
 
@@ -329,6 +330,19 @@ def map_profile_read(ctx, which: int, level: int = -1):
 
 def map_launch_count() -> int:
     return int(lib().map_launch_count())
+
+
+def map_objective_noalloc(xadj, adjncy, adjwgt, vwgt, n: int, pi, hier, dist, out, stream=None) -> None:
+    """J and max block weight into the device int64[2] ``out`` without any
+    device allocation (all graph / mapping / output arguments are device
+    tensors or pointers; see include/gpumap.h)."""
+    h = np.ascontiguousarray(hier, dtype=np.int32)
+    d = np.ascontiguousarray(dist, dtype=np.int32)
+    st = lib().map_objective_noalloc(_ptr(xadj), _ptr(adjncy), _ptr(adjwgt), _ptr(vwgt), int(n), _ptr(pi),
+                                     _ptr(h), _ptr(d), len(h), _ptr(out), _stream_handle(stream))
+    if st != 0:
+        msg = lib().map_last_error(None)
+        raise MapError(st, "map_objective_noalloc", msg.decode() if msg else "")
 
 
 class Mapper:
