@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=2)
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps re-run with per-kernel CUDA events after the timed region")
     ap.add_argument("--probe", action="store_true",
                     help="one map_run, then one label-propagation step and one J evaluation on the input "
                          "graph inside the NVTX range 'probe' (for ncu captures of single launches)")
@@ -233,7 +235,6 @@ def run_ours(args, ws, rank, local):
     sampler = ClockSampler(getattr(props, "pci_bus_id", None))
     sampler.start()
     time.sleep(0.3)
-    G.map_profile_enable(ctx, 1)
     launches0 = G.map_launch_count()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -253,6 +254,13 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
+    # Per-kernel CUDA-event timing cannot see inside the refinement graphs, so
+    # the same steps run again with stream launches and events around the
+    # profiled kernels (same kernels, same work, same results).
+    G.map_profile_enable(ctx, 1)
+    for i in range(args.profile_steps):
+        flush.fill_(i)
+        Js.append(G.map_run(ctx))
     prof = {}
     for kid, nm in G.KERNEL_CLASSES.items():
         l0, ms0, by0 = G.map_profile_read(ctx, kid, 0)      # input-graph level
@@ -277,7 +285,9 @@ def run_ours(args, ws, rank, local):
     traffic = None
     if tr and tr.get("kernel_hash") == kernel_hash() and tv["launches"]:
         traffic = tr["dram_per_alg_byte"] * tv["bytes"] / tv["launches"]
-    roof = {"bound": "hbm", "kernel": tn, "scope": "launches on the input graph (level 0)",
+    roof = {"bound": "hbm", "kernel": tn,
+            "scope": "launches on the input graph (level 0), CUDA events on the library stream during "
+                     f"{args.profile_steps} profiled steps that follow the timed region",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
             "bytes_per_launch": tv["bytes"] / max(1, tv["launches"]), "launches": tv["launches"],

@@ -243,6 +243,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       throw ApiError(MAP_E_INVALID, "map_config field out of range");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
+    for (auto& cs : c.cap.s) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    sort_init();
     GM_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.dev));
     c.mem.st = c.st;
     c.mem.afn = c.cfg.alloc;
@@ -311,7 +313,11 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       ctx->c.mem.release_all();
       if (ctx->c.h_state) cudaFreeHost(ctx->c.h_state);
       ctx->c.h_state = nullptr;
+      if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
+      ctx->c.h_cstate = nullptr;
       cudaStreamSynchronize(ctx->c.st);
+      for (auto& cs : ctx->c.cap.s)
+        if (cs) cudaStreamDestroy(cs);
     } catch (...) {
     }
     last_create_error() = ctx->c.err;
@@ -330,7 +336,14 @@ void map_destroy(map_ctx* ctx) {
     ctx->c.mem.release_all();
     cudaStreamSynchronize(ctx->c.st);
     if (ctx->c.h_state) cudaFreeHost(ctx->c.h_state);
+    if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
     for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
+    for (auto& L : ctx->c.lv) {
+      drop_graph(L);
+      if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
+    }
+    for (auto& cs : ctx->c.cap.s)
+      if (cs) cudaStreamDestroy(cs);
   } catch (...) {
   }
   delete ctx;

@@ -121,13 +121,13 @@ struct ClusterArgs {
   int32_t* req;          // requested target per vertex (-1 none)
   int64_t wcap;
   uint64_t seed;
+  const ClusterState* cs;  // current iteration
   int32_t level;
-  int32_t it;
   int32_t round;
 };
 
 __device__ __forceinline__ bool cluster_active(const ClusterArgs& a, int32_t v, int64_t deg) {
-  return deg > 0 && (int32_t)((h_active(a.seed, a.level, v) >> a.it) & 1ULL) == a.round;
+  return deg > 0 && (int32_t)((h_active(a.seed, a.level, v) >> a.cs->it) & 1ULL) == a.round;
 }
 
 __device__ __forceinline__ void cluster_request(const ClusterArgs& a, int32_t v, int32_t own, int32_t best,
@@ -350,6 +350,25 @@ __global__ void k_cluster_apply(int32_t n, const int32_t* __restrict__ req, cons
   if (mine) atomicAdd((unsigned long long*)moved, (unsigned long long)mine);
 }
 
+// Iteration control of the clustering loop: stop after cluster_iters
+// iterations or once fewer than 1 % of the vertices moved in one.
+__global__ void k_cl_init(ClusterState* cs, int32_t iters, cudaGraphConditionalHandle h, int use_h) {
+  cs->it = 0;
+  cs->done = iters <= 0;
+  cs->moved = 0;
+  cs->kernels = 0;
+  if (use_h) cudaGraphSetConditional(h, iters > 0 ? 1u : 0u);
+}
+__global__ void k_cl_begin(ClusterState* cs) { cs->moved = 0; }
+__global__ void k_cl_end(ClusterState* cs, int32_t n, int32_t iters, cudaGraphConditionalHandle h, int use_h,
+                         unsigned long long body_kernels) {
+  cs->kernels += body_kernels;
+  const bool stop = cs->moved * 100 < (int64_t)n || cs->it + 1 >= iters;
+  cs->it += 1;
+  cs->done = stop ? 1 : 0;
+  if (use_h) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
 // isolated vertices: chunks of weight <= cap in id order, labelled n + chunk
 struct LoadIsolated {
   const int64_t* xadj;
@@ -441,6 +460,8 @@ struct LoadValid32 {
   const int64_t* d_valid;
   __device__ int64_t operator()(int64_t i) const { return i < *d_valid ? val[i] : 0; }
 };
+
+__global__ void k_copy_i64(const int64_t* src, int64_t* dst) { *dst = *src; }
 
 __global__ void k_put_total(const int64_t* total, const int64_t* d_idx, int64_t* P) { P[*d_idx] = *total; }
 
@@ -607,6 +628,88 @@ void check_err(Ctx& c) {
   if (e) throw ApiError(MAP_E_INTERNAL, "device consistency check failed (flags " + std::to_string(e) + ")");
 }
 
+// One clustering sub-round: ratings and requests, classification, ordered
+// admission of the contested requests, moves.
+void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
+  Level& L = c.lv[lvl];
+  const int32_t n = L.n;
+  const unsigned gv = grid_for(c, kThreads, n);
+  const unsigned gl = grid_for(c, kThreads / kSubWarp, n);
+  uint8_t* flag = c.elig;
+  int64_t* d_cont = c.counters + 6;
+  const int kbits = bits_for(n) + 32;
+  ClusterArgs a{c.C, c.Wc, c.ReqW, c.req, wcap, c.cfg.seed, c.cstate, lvl, r};
+  c.prof_level = lvl;
+  cudaEvent_t ev = c.prof_begin();
+  k_cluster_low<<<gl, kThreads, 0, c.st>>>(view(L), a); count_launch();
+  // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
+  c.prof_end(ev, PK_CLUSTER, 16 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+  if (L.n_hi)
+    k_cluster_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
+        view(L), L.hi, L.n_hi, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
+  k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag); count_launch();
+  scan(LoadContested{flag}, StoreContested{c.req, c.cfg.seed, lvl, c.sort.key[0], c.sort.val[0]}, n, nullptr,
+       c.scan, c.st);
+  k_copy_i64<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_cont); count_launch();
+  const int cur = radix_sort_pairs(c.sort, n, d_cont, kbits, c.st, &c.cap, &c.cstate->kernels);
+  scan(LoadSortedVw{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_cont, c.scan, c.st);
+  k_cluster_heads<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_cont, n, c.headP); count_launch();
+  k_cluster_admit<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_cont, n, c.Wc,
+                                             L.vw, wcap, flag); count_launch();
+  k_cluster_apply<<<gv, kThreads, 0, c.st>>>(n, c.req, flag, c.C, c.Wc, c.ReqW, L.vw, &c.cstate->moved); count_launch();
+}
+
+// Captures the clustering loop of one level: init; WHILE(continue) {
+// sub-round 0; sub-round 1; stop test }.
+void build_cluster_graph(Ctx& c, int lvl, int64_t wcap) {
+  Level& L = c.lv[lvl];
+  if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
+  L.cgexec = nullptr;
+  const int32_t n = L.n;
+  const unsigned gv = grid_for(c, kThreads, n);
+  cudaStream_t saved = c.st;
+  cudaStream_t cs = c.cap.s[0];
+  long long root = 0, body = 0;
+  long long* outer = set_capture_counter(&root);
+  GM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  c.cap.depth = 0;
+  c.st = cs;
+  try {
+    k_iota<<<gv, kThreads, 0, cs>>>(c.C, n); count_launch();
+    GM_CUDA(cudaMemcpyAsync(c.Wc, L.vw, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, cs));
+    GM_CUDA(cudaMemsetAsync(c.ReqW, 0, (size_t)n * sizeof(int32_t), cs));
+    cudaGraphConditionalHandle h = cap_handle(cs, 0);
+    k_cl_init<<<1, 1, 0, cs>>>(c.cstate, c.cfg.cluster_iters, h, 1); count_launch();
+    cap_cond(c.cap, cs, h, cudaGraphCondTypeWhile, [&](cudaStream_t bs) {
+      c.st = bs;
+      set_capture_counter(&body);
+      k_cl_begin<<<1, 1, 0, bs>>>(c.cstate); count_launch();
+      launch_subround(c, lvl, 0, wcap);
+      launch_subround(c, lvl, 1, wcap);
+      k_cl_end<<<1, 1, 0, bs>>>(c.cstate, n, c.cfg.cluster_iters, h, 1, (unsigned long long)body + 1); count_launch();
+      set_capture_counter(&root);
+    });
+    cudaGraph_t g = nullptr;
+    GM_CUDA(cudaStreamEndCapture(cs, &g));
+    c.cap.depth = -1;
+    c.st = saved;
+    set_capture_counter(outer);
+    cudaError_t e = cudaGraphInstantiate(&L.cgexec, g, 0);
+    cudaGraphDestroy(g);
+    GM_CUDA(e);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c.cap.depth = -1;
+    c.st = saved;
+    set_capture_counter(outer);
+    throw;
+  }
+  L.cg_root = root;
+}
+
 // Clusters level `lvl`; returns n_c, fills L.M.
 int32_t cluster_level(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
@@ -616,12 +719,9 @@ int32_t cluster_level(Ctx& c, int lvl) {
   int64_t wcap = c.lmax / c.cfg.cluster_cap_div;
   if (wcap < L.max_vw) wcap = L.max_vw;
   if (wcap < 1) wcap = 1;
-  k_iota<<<gv, kThreads, 0, c.st>>>(c.C, n); count_launch();
-  GM_CUDA(cudaMemcpyAsync(c.Wc, L.vw, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
-  GM_CUDA(cudaMemsetAsync(c.ReqW, 0, (size_t)n * sizeof(int32_t), c.st));
   // hash tables for the high-degree vertices
   if (L.n_hi) {
-    if (!L.hi_off) L.hi_off = c.mem.make<int64_t>((size_t)L.n_hi + 1);
+    if (!L.hi_off) L.hi_off = c.mem.make<int64_t>((size_t)L.n + 1);
     scan(LoadTableSize{L.hi, L.xadj}, StoreExcl{L.hi_off}, L.n_hi, nullptr, c.scan, c.st);
     const int64_t tiles = std::max<int64_t>(1, scan_tiles(L.n_hi));
     GM_CUDA(cudaMemcpyAsync(L.hi_off + L.n_hi, c.scan.tile_sums + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice,
@@ -635,37 +735,33 @@ int32_t cluster_level(Ctx& c, int lvl) {
       c.hval = c.mem.make<int32_t>((size_t)c.hcap);
     }
   }
-  uint8_t* flag = c.elig;
-  int64_t* moved = c.counters + 5;
-  int64_t* d_cont = c.counters + 6;
-  const int kbits = bits_for(n) + 32;
-  for (int32_t it = 0; it < c.cfg.cluster_iters; it++) {
-    GM_CUDA(cudaMemsetAsync(moved, 0, sizeof(int64_t), c.st));
-    for (int32_t r = 0; r < 2; r++) {
-      ClusterArgs a{c.C, c.Wc, c.ReqW, c.req, wcap, c.cfg.seed, lvl, it, r};
-      c.prof_level = lvl;
-      cudaEvent_t ev = c.prof_begin();
-      k_cluster_low<<<gl, kThreads, 0, c.st>>>(view(L), a); count_launch();
-      // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
-      c.prof_end(ev, PK_CLUSTER, 16 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
-      if (L.n_hi)
-        k_cluster_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
-            view(L), L.hi, L.n_hi, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
-      k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag); count_launch();
-      scan(LoadContested{flag}, StoreContested{c.req, c.cfg.seed, lvl, c.sort.key[0], c.sort.val[0]}, n, nullptr,
-           c.scan, c.st);
-      GM_CUDA(cudaMemcpyAsync(d_cont, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), sizeof(int64_t),
-                              cudaMemcpyDeviceToDevice, c.st));
-      const int cur = radix_sort_pairs(c.sort, n, d_cont, kbits, c.st);
-      scan(LoadSortedVw{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_cont, c.scan, c.st);
-      k_cluster_heads<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_cont, n, c.headP); count_launch();
-      k_cluster_admit<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_cont, n, c.Wc,
-                                                 L.vw, wcap, flag); count_launch();
-      k_cluster_apply<<<gv, kThreads, 0, c.st>>>(n, c.req, flag, c.C, c.Wc, c.ReqW, L.vw, moved); count_launch();
+  ClusterState* cs = c.cstate;
+  if (c.use_graphs && !c.prof) {
+    const int64_t key[6] = {(int64_t)L.n, L.m, (int64_t)L.n_hi, L.hi_slots, wcap, (int64_t)(intptr_t)c.hkey};
+    bool same = L.cgexec != nullptr;
+    for (int i = 0; i < 6 && same; i++) same = L.cg_key[i] == key[i];
+    if (!same) {
+      build_cluster_graph(c, lvl, wcap);
+      for (int i = 0; i < 6; i++) L.cg_key[i] = key[i];
     }
-    GM_CUDA(cudaGetLastError());
-    const int64_t mv = read_i64(c, moved);
-    if (mv * 100 < (int64_t)n) break;
+    GM_CUDA(cudaGraphLaunch(L.cgexec, c.st));
+    GM_CUDA(cudaMemcpyAsync(c.h_cstate, cs, sizeof(ClusterState), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+    add_launches(L.cg_root + (long long)c.h_cstate->kernels);
+  } else {
+    k_iota<<<gv, kThreads, 0, c.st>>>(c.C, n); count_launch();
+    GM_CUDA(cudaMemcpyAsync(c.Wc, L.vw, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
+    GM_CUDA(cudaMemsetAsync(c.ReqW, 0, (size_t)n * sizeof(int32_t), c.st));
+    k_cl_init<<<1, 1, 0, c.st>>>(cs, c.cfg.cluster_iters, 0, 0); count_launch();
+    for (int32_t it = 0; it < c.cfg.cluster_iters; it++) {
+      k_cl_begin<<<1, 1, 0, c.st>>>(cs); count_launch();
+      launch_subround(c, lvl, 0, wcap);
+      launch_subround(c, lvl, 1, wcap);
+      k_cl_end<<<1, 1, 0, c.st>>>(cs, n, c.cfg.cluster_iters, 0, 0, 0); count_launch();
+      GM_CUDA(cudaMemcpyAsync(c.h_cstate, cs, sizeof(ClusterState), cudaMemcpyDeviceToHost, c.st));
+      GM_CUDA(cudaStreamSynchronize(c.st));
+      if (c.h_cstate->done) break;
+    }
   }
   // isolated vertices, then number the clusters by ascending label
   scan(LoadIsolated{L.xadj, L.vw}, StoreIsolated{c.C, L.vw, n, wcap}, n, nullptr, c.scan, c.st);
@@ -682,20 +778,41 @@ int32_t cluster_level(Ctx& c, int lvl) {
 }
 
 // Builds level lvl + 1 from level lvl and its M.
-void contract_level(Ctx& c, int lvl, int32_t nc) {
+void free_level(Ctx& c, Level& L) {
+  drop_graph(L);
+  if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
+  L.cgexec = nullptr;
+  for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
+                  (void*)L.hi_off, (void*)L.M})
+    if (p) c.mem.put(p);
+  L = Level{};
+}
+
+// Builds level lvl + 1 from level lvl and its M.  `spare` is the level that
+// held this index before (repeated runs): its buffers are reused when the
+// sizes match, which also keeps its instantiated refinement graph valid.
+void contract_level(Ctx& c, int lvl, int32_t nc, Level* spare) {
   Level& F = c.lv[lvl];
   Level C;
+  const bool reuse_n = spare && spare->n == nc;
+  if (reuse_n) {
+    C = *spare;
+    *spare = Level{};
+  } else if (spare) {
+    free_level(c, *spare);
+  }
   C.n = nc;
   const int64_t m = F.m;
   const unsigned gv = grid_for(c, kThreads, F.n);
-  C.vw = c.mem.make<int32_t>((size_t)std::max(1, nc));
+  if (!reuse_n) C.vw = c.mem.make<int32_t>((size_t)std::max(1, nc));
   GM_CUDA(cudaMemsetAsync(C.vw, 0, (size_t)std::max(1, nc) * sizeof(int32_t), c.st));
   k_coarse_vw<<<gv, kThreads, 0, c.st>>>(F.n, F.M, F.vw, C.vw); count_launch();
   const int bits = bits_for(nc);  // ids < 2^bits - 1, so the all-ones key is free
   int64_t* d_valid = c.counters + 7;
   GM_CUDA(cudaMemsetAsync(d_valid, 0, sizeof(int64_t), c.st));
   int64_t mc = 0;
-  C.xadj = c.mem.make<int64_t>((size_t)nc + 1);
+  if (!reuse_n) C.xadj = c.mem.make<int64_t>((size_t)nc + 1);
+  const int64_t old_m = reuse_n ? C.m : -1;
   if (m > 0) {
     k_contract_keys<<<grid_for(c, kThreads / kSubWarp, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
                                                                                    c.sort.val[0], d_valid); count_launch();
@@ -712,19 +829,25 @@ void contract_level(Ctx& c, int lvl, int32_t nc) {
     scan(LoadValid32{sval, d_valid}, StoreExcl{c.P64}, m, nullptr, c.scan, c.st);
     // P64[valid] = total weight of the valid entries
     k_put_total<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(m)), d_valid, c.P64); count_launch();
-    C.adj = c.mem.make<int32_t>((size_t)std::max<int64_t>(1, mc));
-    C.adjw = c.mem.make<int32_t>((size_t)std::max<int64_t>(1, mc));
+    if (old_m != mc) {
+      if (C.adj) c.mem.put(C.adj);
+      if (C.adjw) c.mem.put(C.adjw);
+      drop_graph(C);
+      C.adj = c.mem.make<int32_t>((size_t)std::max<int64_t>(1, mc));
+      C.adjw = c.mem.make<int32_t>((size_t)std::max<int64_t>(1, mc));
+    }
     if (mc > 0)
       k_contract_fill<<<grid_for(c, kThreads, mc), kThreads, 0, c.st>>>(mc, ukey, c.P64b, c.P64, d_valid, bits, C.adj,
                                                                        C.adjw); count_launch();
     k_contract_xadj<<<grid_for(c, kThreads, nc + 1), kThreads, 0, c.st>>>(nc, mc, ukey, bits, C.xadj); count_launch();
   } else {
-    C.adj = c.mem.make<int32_t>(1);
-    C.adjw = c.mem.make<int32_t>(1);
+    if (!C.adj) C.adj = c.mem.make<int32_t>(1);
+    if (!C.adjw) C.adjw = c.mem.make<int32_t>(1);
+    if (old_m != 0) drop_graph(C);
     GM_CUDA(cudaMemsetAsync(C.xadj, 0, ((size_t)nc + 1) * sizeof(int64_t), c.st));
   }
   C.m = mc;
-  C.pi = c.mem.make<int32_t>((size_t)std::max(1, nc));
+  if (!reuse_n) C.pi = c.mem.make<int32_t>((size_t)std::max(1, nc));
   GM_CUDA(cudaMemsetAsync(C.pi, 0, (size_t)std::max(1, nc) * sizeof(int32_t), c.st));
   GM_CUDA(cudaGetLastError());
   c.lv.push_back(C);
@@ -752,17 +875,13 @@ int32_t device_max_vw(Ctx& c, const Level& L) {
   return h;
 }
 
-void free_level(Ctx& c, Level& L) {
-  for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
-                  (void*)L.hi_off})
-    if (p) c.mem.put(p);
-  L = Level{};
-}
 
 }  // namespace
 
 void coarsen_alloc(Ctx& c) {
   const size_t n = (size_t)std::max(1, c.n0);
+  c.cstate = c.mem.make<ClusterState>(1);
+  if (!c.h_cstate) GM_CUDA(cudaMallocHost(&c.h_cstate, sizeof(ClusterState)));
   c.C = c.mem.make<int32_t>(n);
   c.Wc = c.mem.make<int32_t>(n);
   c.ReqW = c.mem.make<int32_t>(n);
@@ -800,14 +919,10 @@ void validate_graph(Ctx& c) {
 }
 
 int32_t coarsen(Ctx& c) {
-  while (c.lv.size() > 1) {
-    free_level(c, c.lv.back());
-    c.lv.pop_back();
-  }
-  if (c.lv[0].M) {
-    c.mem.put(c.lv[0].M);
-    c.lv[0].M = nullptr;
-  }
+  // previous coarse levels are kept as spares: repeated runs on the same
+  // graph rebuild identical levels into the same buffers
+  std::vector<Level> spare(c.lv.begin() + 1, c.lv.end());
+  c.lv.resize(1);
   while ((int32_t)c.lv.size() < c.cfg.max_levels &&
          (int64_t)c.lv.back().n >= (int64_t)c.cfg.coarsest_factor * c.k) {
     const int lvl = (int)c.lv.size() - 1;
@@ -818,11 +933,12 @@ int32_t coarsen(Ctx& c) {
       F.M = nullptr;
       break;
     }
-    contract_level(c, lvl, nc);
+    contract_level(c, lvl, nc, lvl < (int)spare.size() ? &spare[lvl] : nullptr);
     Level& N = c.lv.back();
     classify_degrees(c, (int)c.lv.size() - 1);
     N.max_vw = device_max_vw(c, N);
   }
+  for (Level& L : spare) free_level(c, L);
   return (int32_t)c.lv.size();
 }
 

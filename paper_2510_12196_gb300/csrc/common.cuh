@@ -87,9 +87,13 @@ enum : uint32_t {
   ERR_TIMEOUT = 128u,   // a bounded device wait gave up
 };
 
-// Process-wide count of kernels launched by this library (host side).
+// Process-wide count of kernels launched by this library (host side).  Graph
+// executions are added after they complete (add_launches); while a graph is
+// captured, count_launch counts into the capture counter that is set.
 void count_launch();
 long long launch_count();
+void add_launches(long long n);
+long long* set_capture_counter(long long* p);
 
 }  // namespace gm
 

@@ -24,6 +24,8 @@ struct ApiError : std::runtime_error {
   ApiError(map_status s, const std::string& m) : std::runtime_error(m), status(s) {}
 };
 
+constexpr int32_t kMaxRefineIters = (1 << 20) - 1;
+
 // Step kinds of the Alg. 6 state machine.
 enum : int32_t { KIND_LP = 0, KIND_WEAK = 1, KIND_STRONG = 2, KIND_NONE = 3 };
 
@@ -42,7 +44,18 @@ struct RefineState {
   int32_t rounds;      // >= 0: fixed number of iterations
   int32_t level;
   int32_t moved;       // vertices moved by the last step
-  int32_t pad;
+  int32_t last_kind;   // kind of the iteration k_control just closed
+  int32_t capped;      // the iteration cap ended the run
+  int32_t pad2;
+  unsigned long long kernels;  // kernels run by conditional graph bodies
+};
+
+// Device-resident state of the clustering loop of one level.
+struct ClusterState {
+  int32_t it;          // current iteration
+  int32_t done;
+  int64_t moved;       // vertices moved in the current iteration
+  unsigned long long kernels;  // kernels run by conditional graph bodies
 };
 
 // Kernel classes timed by the optional CUDA-event profiler.
@@ -70,6 +83,15 @@ struct Level {
   int64_t* hi_off = nullptr;   // hash-table offsets of the high-degree vertices (n_hi + 1)
   int64_t hi_slots = 0;
   int32_t max_vw = 0;
+  // instantiated Alg. 6 graph of this level and what it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  int32_t g_rounds = -2;
+  int32_t g_nhi = -1;
+  long long g_root = 0;  // kernel nodes outside the conditional bodies
+  // instantiated clustering graph of this level and its key
+  cudaGraphExec_t cgexec = nullptr;
+  int64_t cg_key[6] = {0, 0, 0, 0, 0, 0};
+  long long cg_root = 0;
 };
 
 struct DevMem {
@@ -107,6 +129,8 @@ struct Ctx {
   int32_t n0 = 0;
   int64_t m0 = 0;
   DevMem mem;
+  Capture cap;
+  bool use_graphs = true;
   std::string err;
   int dev = 0;
   int num_sms = 0;
@@ -154,6 +178,8 @@ struct Ctx {
   int32_t* hval = nullptr;
   int64_t hcap = 0;
   uint32_t* errword = nullptr;
+  ClusterState* cstate = nullptr;
+  ClusterState* h_cstate = nullptr;  // pinned mirror
 
   // profiler
   bool prof = false;
@@ -181,6 +207,7 @@ int32_t lp_step(Ctx& c, int lvl);
 int32_t rebalance_step(Ctx& c, int lvl, bool strong, int32_t t);
 void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters);
 void classify_degrees(Ctx& c, int lvl);
+void drop_graph(Level& L);
 
 // coarsen.cu
 void coarsen_alloc(Ctx& c);

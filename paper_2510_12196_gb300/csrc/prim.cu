@@ -6,8 +6,20 @@
 namespace gm {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long* t_capture_counter = nullptr;
+// While a graph is being captured, launches are counted into the capture's
+// counter instead: they run later, as graph nodes, and are added then.
+void count_launch() {
+  if (t_capture_counter) ++*t_capture_counter;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long* set_capture_counter(long long* p) {
+  long long* old = t_capture_counter;
+  t_capture_counter = p;
+  return old;
+}
 
 __global__ void __launch_bounds__(1024) k_scan_tile_sums(int64_t* tile_sums, int64_t ntiles) {
   __shared__ int64_t sm[33];
@@ -196,26 +208,27 @@ void sort_init() {
   done.fetch_or(bit);
 }
 
-int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st) {
-  if (max_n <= 0 || bits <= 0) return 0;
+cudaGraphConditionalHandle cap_handle(cudaStream_t st, unsigned int default_value) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamGetCaptureInfo(st, &status, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+      status != cudaStreamCaptureStatusActive)
+    throw std::runtime_error("cap_handle: stream is not capturing");
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, default_value, cudaGraphCondAssignDefault) != cudaSuccess)
+    throw std::runtime_error("cap_handle: cudaGraphConditionalHandleCreate failed");
+  return h;
+}
+
+__global__ void k_sort_gate(const int64_t* d_n, cudaGraphConditionalHandle h, unsigned long long* kcount,
+                            unsigned long long body_kernels) {
+  const bool big = *d_n > kSmallSort;
+  cudaGraphSetConditional(h, big ? 1u : 0u);
+  if (big && kcount) atomicAdd(kcount, body_kernels);
+}
+
+static void sort_passes(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, int64_t skip, cudaStream_t st) {
   const int64_t tiles = sort_tiles(max_n);
-  const int passes = (bits + 7) / 8;
-  const int out = passes & 1;  // buffer holding the result after `passes` swaps
-  // device-counted sets: the single-CTA kernel takes counts <= kSmallSort and
-  // writes into the result buffer; the multi-CTA passes skip those counts
-  int64_t skip = -1;
-  if (d_n) {
-    sort_init();
-    k_sort_small<<<1, kSmallThreads, small_sort_smem(), st>>>(b.key[0], b.val[0], b.key[out], b.val[out], d_n,
-                                                              max_n, bits); count_launch();
-    skip = kSmallSort;
-  }
-  if (!d_n && max_n <= kSmallSort) {
-    sort_init();
-    k_sort_small<<<1, kSmallThreads, small_sort_smem(), st>>>(b.key[0], b.val[0], b.key[out], b.val[out], nullptr,
-                                                              max_n, bits); count_launch();
-    return out;
-  }
   int cur = 0;
   for (int shift = 0; shift < bits; shift += 8) {
     k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], max_n, d_n, shift, b.hist, tiles, skip); count_launch();
@@ -225,7 +238,41 @@ int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, c
                                                              tiles, skip); count_launch();
     cur ^= 1;
   }
-  return cur;
+}
+
+int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st, Capture* cap,
+                     unsigned long long* kcount) {
+  if (max_n <= 0 || bits <= 0) return 0;
+  const int passes = (bits + 7) / 8;
+  const int out = passes & 1;  // buffer holding the result after `passes` swaps
+  sort_init();
+  if (!d_n) {
+    if (max_n <= kSmallSort) {
+      k_sort_small<<<1, kSmallThreads, small_sort_smem(), st>>>(b.key[0], b.val[0], b.key[out], b.val[out], nullptr,
+                                                                max_n, bits); count_launch();
+    } else {
+      sort_passes(b, max_n, nullptr, bits, -1, st);
+    }
+    return out;
+  }
+  // device-counted: the single-CTA kernel takes counts <= kSmallSort and
+  // writes into the result buffer; the multi-CTA passes skip those counts
+  k_sort_small<<<1, kSmallThreads, small_sort_smem(), st>>>(b.key[0], b.val[0], b.key[out], b.val[out], d_n, max_n,
+                                                            bits); count_launch();
+  if (max_n <= kSmallSort) return out;
+  if (cap && cap->on()) {
+    cudaGraphConditionalHandle h = cap_handle(st, 0);
+    k_sort_gate<<<1, 1, 0, st>>>(d_n, h, kcount, (unsigned long long)passes * 5); count_launch();
+    long long body = 0;
+    long long* outer = set_capture_counter(&body);
+    cap_cond(*cap, st, h, cudaGraphCondTypeIf,
+             [&](cudaStream_t bs) { sort_passes(b, max_n, d_n, bits, kSmallSort, bs); });
+    set_capture_counter(outer);
+    if (body != (long long)passes * 5) throw std::runtime_error("radix_sort_pairs: unexpected pass kernel count");
+  } else {
+    sort_passes(b, max_n, d_n, bits, kSmallSort, st);
+  }
+  return out;
 }
 
 }  // namespace gm

@@ -7,6 +7,8 @@
 // segmented reduce), cluster admission and rebalancing selection.
 #pragma once
 
+#include <stdexcept>
+
 #include "common.cuh"
 
 namespace gm {
@@ -196,8 +198,59 @@ __global__ void k_sort_small(const uint64_t* __restrict__ kin, const int32_t* __
                              int64_t max_n, int bits);
 void sort_init();
 
+// ---------------------------------------------------------------------------
+// stream capture into graphs with conditional nodes
+// ---------------------------------------------------------------------------
+// s[d] captures at nesting depth d (0: the root graph); depth < 0: no capture.
+struct Capture {
+  cudaStream_t s[6] = {};
+  int depth = -1;
+  bool on() const { return depth >= 0; }
+};
+
+// A conditional handle on the graph currently captured by `st`.
+cudaGraphConditionalHandle cap_handle(cudaStream_t st, unsigned int default_value);
+
+// Appends a conditional node (IF / WHILE on handle h) to the graph captured by
+// `st` and captures `body(stream)` into its body graph.
+template <class F>
+void cap_cond(Capture& cap, cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+              F&& body) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, &ed, &nd) != cudaSuccess ||
+      status != cudaStreamCaptureStatusActive)
+    throw std::runtime_error("cap_cond: stream is not capturing");
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, ed, nd, &p) != cudaSuccess)
+    throw std::runtime_error("cap_cond: cudaGraphAddNode failed");
+  if (cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    throw std::runtime_error("cap_cond: cudaStreamUpdateCaptureDependencies failed");
+  cudaGraph_t bg = p.conditional.phGraph_out[0];
+  const int d = ++cap.depth;
+  cudaStream_t bs = cap.s[d];
+  if (cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    throw std::runtime_error("cap_cond: cudaStreamBeginCaptureToGraph failed");
+  body(bs);
+  if (cudaStreamEndCapture(bs, &bg) != cudaSuccess) throw std::runtime_error("cap_cond: cudaStreamEndCapture failed");
+  --cap.depth;
+}
+
 // Sorts buffer 0 (n elements, count on device or max_n) by key bits [0, bits).
-// Returns the buffer index (0 or 1) that holds the sorted result.
-int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st);
+// Returns the buffer index (0 or 1) that holds the sorted result.  While
+// `cap` is capturing, the multi-CTA passes sit in a conditional node that
+// runs only for device counts above kSmallSort.
+// kcount (device, may be NULL) accumulates the kernels run by the
+// conditional passes, so that graph executions can be counted.
+int radix_sort_pairs(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits, cudaStream_t st,
+                     Capture* cap = nullptr, unsigned long long* kcount = nullptr);
 
 }  // namespace gm

@@ -803,7 +803,8 @@ struct CtlArgs {
 };
 
 __global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* __restrict__ W, int64_t* Jacc,
-                                                 CtlArgs a, int phase) {
+                                                 CtlArgs a, int phase, cudaGraphConditionalHandle h_loop,
+                                                 int use_handle) {
   __shared__ int64_t smax[32];
   int64_t mx = 0;
   for (int32_t b = threadIdx.x; b < a.kc; b += blockDim.x) mx = W[b] > mx ? W[b] : mx;
@@ -816,12 +817,16 @@ __global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* 
   __syncthreads();
   if (threadIdx.x != 0) return;
   for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = smax[w] > mx ? smax[w] : mx;
-  if (phase == 1 && s->done) return;
+  if (phase == 1 && s->done) {
+    if (use_handle) cudaGraphSetConditional(h_loop, 0u);
+    return;
+  }
   const int64_t J = *Jacc;
   *Jacc = 0;
   s->copy_best = 0;
   s->J = J;
   s->maxw = mx;
+  s->last_kind = s->kind;
   if (phase == 0) {
     s->best_J = J;
     s->best_maxw = mx;
@@ -859,8 +864,14 @@ __global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* 
       s->i = 0;
     }
   }
-  const bool stop = s->rounds >= 0 ? (s->t >= s->rounds) : (s->i >= a.patience);
+  // Alg. 6 terminates (each patience reset needs a 0.1 % better J or a lower
+  // maximum block weight); the cap on t only bounds the loop by construction
+  // and also keeps t inside the 20 bits of the rebalancing hash.
+  const bool capped = s->t >= kMaxRefineIters;
+  if (capped && s->rounds < 0) s->capped = 1;
+  const bool stop = capped || (s->rounds >= 0 ? (s->t >= s->rounds) : (s->i >= a.patience));
   s->moved = 0;
+  if (use_handle) cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
   if (stop) {
     s->done = 1;
     s->kind = KIND_NONE;
@@ -880,7 +891,35 @@ __global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* 
   }
 }
 
-__global__ void k_copy_best(const RefineState* s, const int32_t* __restrict__ pi, int32_t* __restrict__ best, int32_t n) {
+// Graph mode: the start of one Alg. 6 iteration selects the step bodies.
+__global__ void k_decide(const RefineState* s, cudaGraphConditionalHandle h_lp, cudaGraphConditionalHandle h_reb,
+                         cudaGraphConditionalHandle h_strong) {
+  const int32_t kind = s->kind;
+  cudaGraphSetConditional(h_lp, kind == KIND_LP ? 1u : 0u);
+  cudaGraphSetConditional(h_reb, (kind == KIND_WEAK || kind == KIND_STRONG) ? 1u : 0u);
+  cudaGraphSetConditional(h_strong, kind == KIND_STRONG ? 1u : 0u);
+}
+
+// Kernels run by one graph iteration: the fixed nodes plus the body of the
+// step that ran (the kind is recorded by k_control before it moves on).
+struct IterCounts {
+  unsigned long long fixed, lp, reb, strong;
+};
+
+__global__ void k_state_init(RefineState* s, int32_t rounds, int32_t level) {
+  RefineState z{};
+  z.rounds = rounds;
+  z.level = level;
+  *s = z;
+}
+
+__global__ void k_copy_best(RefineState* s, const int32_t* __restrict__ pi, int32_t* __restrict__ best, int32_t n,
+                            IterCounts ic) {
+  if (ic.fixed && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int32_t k = s->last_kind;
+    s->kernels += ic.fixed + (k == KIND_LP ? ic.lp : 0) + ((k == KIND_WEAK || k == KIND_STRONG) ? ic.reb : 0) +
+                  (k == KIND_STRONG ? ic.strong : 0);
+  }
   if (!s->copy_best) return;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
     best[v] = pi[v];
@@ -949,7 +988,7 @@ void launch_rebalance(Ctx& c, int lvl) {
   scan(LoadFlag{c.elig}, StoreKeyed{L.pi, c.sel, c.sort.key[0], c.sort.val[0]}, n, nullptr, c.scan, c.st);
   k_copy_count<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_elig); count_launch();
   const int bits = c.topo.code_bits + kBucketBits;
-  int cur = radix_sort_pairs(c.sort, n, d_elig, bits, c.st);
+  int cur = radix_sort_pairs(c.sort, n, d_elig, bits, c.st, &c.cap, &c.state->kernels);
   scan(LoadSortedWeight{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_elig, c.scan, c.st);
   const unsigned g = grid_for(c, kThreads, n);
   k_heads<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_elig, n, c.headP); count_launch();
@@ -979,7 +1018,7 @@ static void launch_rebalance_strong_tail(Ctx& c, int lvl) {
   k_copy_count<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_sel); count_launch();
   k_strong_gate<<<1, 1, 0, c.st>>>(c.state, d_sel); count_launch();
   const int bits = c.topo.code_bits + kBucketBits;
-  int cur = radix_sort_pairs(c.sort, n, d_sel, bits, c.st);
+  int cur = radix_sort_pairs(c.sort, n, d_sel, bits, c.st, &c.cap, &c.state->kernels);
   scan(LoadSortedWeight{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_sel, c.scan, c.st);
   const unsigned g = grid_for(c, kThreads, n);
   k_heads<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_sel, n, c.headP); count_launch();
@@ -1096,7 +1135,7 @@ int32_t rebalance_step(Ctx& c, int lvl, bool strong, int32_t t) {
   return read_moved(c);
 }
 
-void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
+static void refine_stream(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
   Level& L = c.lv[lvl];
   compute_block_weights(c, lvl);
   GM_CUDA(cudaMemsetAsync(c.lock, 0, (size_t)std::max(1, L.n), c.st));
@@ -1109,7 +1148,7 @@ void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t*
   GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), c.st));
   launch_eval(c, lvl);
   const CtlArgs ca = ctl_args(c);
-  k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 0); count_launch();
+  k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 0, 0, 0); count_launch();
   const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
   while (true) {
     GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
@@ -1123,16 +1162,127 @@ void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t*
       if (h.kind == KIND_STRONG) launch_rebalance_strong_tail(c, lvl);
     }
     launch_eval(c, lvl);
-    k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 1); count_launch();
-    k_copy_best<<<gcopy, kThreads, 0, c.st>>>(c.state, L.pi, c.pi_best, L.n); count_launch();
+    k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 1, 0, 0); count_launch();
+    k_copy_best<<<gcopy, kThreads, 0, c.st>>>(c.state, L.pi, c.pi_best, L.n, IterCounts{0, 0, 0, 0}); count_launch();
     GM_CUDA(cudaGetLastError());
   }
   GM_CUDA(cudaMemcpyAsync(L.pi, c.pi_best, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
   const RefineState h = *c.h_state;
+  if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
   c.last_iters = h.t;
   if (J) *J = h.best_J;
   if (maxw) *maxw = h.best_maxw;
   if (iters) *iters = h.t;
+}
+
+void drop_graph(Level& L) {
+  if (L.gexec) cudaGraphExecDestroy(L.gexec);
+  L.gexec = nullptr;
+  L.g_rounds = -2;
+  L.g_nhi = -1;
+}
+
+// Captures one level's whole Alg. 6 run as a graph: initial J / weights, then
+// WHILE(not done) { decide; IF(LP){Alg. 4}; IF(weak or strong){Alg. 5};
+// IF(strong){strong tail}; J; control; copy best }, then best -> P.
+static void build_refine_graph(Ctx& c, int lvl, int32_t rounds) {
+  Level& L = c.lv[lvl];
+  drop_graph(L);
+  cudaStream_t saved = c.st;
+  cudaStream_t cs = c.cap.s[0];
+  const CtlArgs ca = ctl_args(c);
+  const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
+  long long root = 0, n_fixed = 0, n_lp = 0, n_reb = 0, n_strong = 0;
+  long long* outer = set_capture_counter(&root);
+  GM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  c.cap.depth = 0;
+  c.st = cs;
+  try {
+    GM_CUDA(cudaMemsetAsync(c.W, 0, (size_t)c.topo.kc * sizeof(int64_t), cs));
+    k_block_weights<<<grid_for(c, kThreads * 16, L.n), kThreads, (size_t)c.topo.kc * sizeof(int32_t), cs>>>(
+        L.n, L.pi, L.vw, c.topo.kc, c.W); count_launch();
+    GM_CUDA(cudaMemsetAsync(c.lock, 0, (size_t)std::max(1, L.n), cs));
+    GM_CUDA(cudaMemcpyAsync(c.pi_best, L.pi, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, cs));
+    k_state_init<<<1, 1, 0, cs>>>(c.state, rounds, lvl); count_launch();
+    GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), cs));
+    launch_eval(c, lvl);
+    cudaGraphConditionalHandle h_loop = cap_handle(cs, 0);
+    k_control<<<1, 256, 0, cs>>>(c.state, c.W, c.Jacc, ca, 0, h_loop, 1); count_launch();
+    cap_cond(c.cap, cs, h_loop, cudaGraphCondTypeWhile, [&](cudaStream_t bs) {
+      c.st = bs;
+      set_capture_counter(&n_fixed);
+      cudaGraphConditionalHandle h_lp = cap_handle(bs, 0), h_reb = cap_handle(bs, 0), h_strong = cap_handle(bs, 0);
+      // counts of the bodies are known only after they are captured: the
+      // decide node reads them from this iteration's parameters below
+      k_decide<<<1, 1, 0, bs>>>(c.state, h_lp, h_reb, h_strong); count_launch();
+      set_capture_counter(&n_lp);
+      cap_cond(c.cap, bs, h_lp, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
+        c.st = s2;
+        launch_lp(c, lvl);
+      });
+      set_capture_counter(&n_reb);
+      cap_cond(c.cap, bs, h_reb, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
+        c.st = s2;
+        launch_rebalance(c, lvl);
+      });
+      set_capture_counter(&n_strong);
+      cap_cond(c.cap, bs, h_strong, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
+        c.st = s2;
+        launch_rebalance_strong_tail(c, lvl);
+      });
+      set_capture_counter(&n_fixed);
+      c.st = bs;
+      launch_eval(c, lvl);
+      k_control<<<1, 256, 0, bs>>>(c.state, c.W, c.Jacc, ca, 1, h_loop, 1); count_launch();
+      // this node is the iteration's last: all body counts are known now
+      const IterCounts ic{(unsigned long long)n_fixed + 1, (unsigned long long)n_lp, (unsigned long long)n_reb,
+                          (unsigned long long)n_strong};
+      k_copy_best<<<gcopy, kThreads, 0, bs>>>(c.state, L.pi, c.pi_best, L.n, ic); count_launch();
+      set_capture_counter(&root);
+    });
+    c.st = cs;
+    GM_CUDA(cudaMemcpyAsync(L.pi, c.pi_best, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, cs));
+    cudaGraph_t g = nullptr;
+    GM_CUDA(cudaStreamEndCapture(cs, &g));
+    c.cap.depth = -1;
+    c.st = saved;
+    set_capture_counter(outer);
+    cudaError_t e = cudaGraphInstantiate(&L.gexec, g, 0);
+    cudaGraphDestroy(g);
+    GM_CUDA(e);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c.cap.depth = -1;
+    c.st = saved;
+    set_capture_counter(outer);
+    throw;
+  }
+  L.g_rounds = rounds;
+  L.g_nhi = L.n_hi;
+  L.g_root = root;
+}
+
+static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
+  Level& L = c.lv[lvl];
+  if (!L.gexec || L.g_rounds != rounds || L.g_nhi != L.n_hi) build_refine_graph(c, lvl, rounds);
+  GM_CUDA(cudaGraphLaunch(L.gexec, c.st));
+  GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  const RefineState h = *c.h_state;
+  add_launches(L.g_root + (long long)h.kernels);
+  if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
+  c.last_iters = h.t;
+  if (J) *J = h.best_J;
+  if (maxw) *maxw = h.best_maxw;
+  if (iters) *iters = h.t;
+}
+
+void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
+  if (c.use_graphs && !c.prof) refine_graph(c, lvl, rounds, J, maxw, iters);
+  else refine_stream(c, lvl, rounds, J, maxw, iters);
 }
 
 // high-degree vertex list of a level (ascending ids)

@@ -214,3 +214,32 @@ def test_validation_errors():
     _expect_status(1, g=g, hier=(4, 0), dist=(1, 10))
     _expect_status(1, g=g, hier=(256, 256), dist=(1, 10))
     _expect_status(1, g=g, eps=1.5)
+
+
+def test_graph_and_stream_paths_agree():
+    """The refinement runs as captured graphs (conditional nodes) by default
+    and as host-driven stream launches while profiling: same results, also
+    when the cached graphs are replayed."""
+    g = I.rgg2d(1 << 15, I.rgg_radius(1 << 15, 12), 31, wmax=10)
+    res = []
+    for prof in (False, True, False):
+        ctx = make_ctx(g, (4, 8, 8), (1, 10, 100))
+        try:
+            if prof:
+                G.map_profile_enable(ctx, True)
+            for rep in range(2):  # second run replays the cached graphs
+                pi = np.zeros(g.n, np.int32)
+                J = G.map_run(ctx, pi)
+                st = G.map_stats(ctx)
+                res.append((J, pi, [st.iters[i] for i in range(st.levels)]))
+            w = I.random_mapping(g.n, 256, 4)
+            G.map_set_mapping(ctx, 0, w)
+            res.append(G.map_refine(ctx, 0, 7) + (G.map_get_refine_trace(ctx)[1].tolist(),))
+        finally:
+            G.map_destroy(ctx)
+    base = res[0]
+    for r in res[1:]:
+        if len(r) == 3 and isinstance(r[1], np.ndarray):
+            assert r[0] == base[0] and np.array_equal(r[1], base[1]) and r[2] == base[2]
+    fixed = [r for r in res if not isinstance(r[1], np.ndarray)]
+    assert all(f == fixed[0] for f in fixed)
