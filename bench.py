@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=2)
+    ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1],
+                    help="0: refinement / clustering loops as CUDA graphs; 1: stream launches")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="steps re-run with per-kernel CUDA events after the timed region")
     ap.add_argument("--probe", action="store_true",
@@ -222,6 +224,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     d_in = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adj, g.adjw, g.vw)]
     cfg = G.map_config_default(w.seed)
+    cfg.launch_mode = args.launch_mode
     ctx = G.map_create(*d_in, g.n, t.hier, t.dist, t.eps, cfg, stream=stream, inputs_on_device=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     Js = []
@@ -352,7 +355,15 @@ def run_probe(args, local):
     torch.cuda.set_device(local)
     w = workload(args.log2n)
     g, t = w.graph, w.topo
-    ctx = G.map_create(g.xadj, g.adj, g.adjw, g.vw, g.n, t.hier, t.dist, t.eps, G.map_config_default(w.seed))
+    cfg = G.map_config_default(w.seed)
+    cfg.launch_mode = 1  # stream launches: a profiler sees every kernel
+    ctx = G.map_create(g.xadj, g.adj, g.adjw, g.vw, g.n, t.hier, t.dist, t.eps, cfg)
+    J = G.map_run(ctx)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("probe_coarsen")
+    G.map_coarsen(ctx)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     J = G.map_run(ctx)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("probe")
@@ -361,7 +372,8 @@ def run_probe(args, local):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     G.map_destroy(ctx)
-    print(json.dumps({"probe": "lp_step+objective on level 0 after map_run", "J_map": J, "moved": moved,
+    print(json.dumps({"probe": "coarsening (range probe_coarsen); lp_step + objective on level 0 after "
+                               "map_run (range probe)", "J_map": J, "moved": moved,
                       "J_after_step": J2, "n": g.n, "m_dir": g.m_dir}))
     return 0
 

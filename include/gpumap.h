@@ -85,6 +85,7 @@ typedef struct {
   map_alloc_fn alloc;
   map_free_fn free;
   void* alloc_user;
+  int32_t launch_mode;   /* 0: refinement and clustering loops as CUDA graphs (default); 1: stream launches */
 } map_config;
 
 typedef struct {

@@ -241,6 +241,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
         c.cfg.coarsest_factor < 1 || c.cfg.cluster_iters < 0 || c.cfg.cluster_cap_div < 1 || c.cfg.max_levels < 1 ||
         c.cfg.max_levels > 64 || c.cfg.stall_den < 1)
       throw ApiError(MAP_E_INVALID, "map_config field out of range");
+    if (c.cfg.launch_mode < 0 || c.cfg.launch_mode > 1) throw ApiError(MAP_E_INVALID, "launch_mode must be 0 or 1");
+    c.use_graphs = c.cfg.launch_mode == 0;
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     for (auto& cs : c.cap.s) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

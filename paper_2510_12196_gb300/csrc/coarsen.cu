@@ -20,6 +20,7 @@
 #include <chrono>
 
 #include "engine.h"
+#include "tile.cuh"
 
 namespace gm {
 
@@ -36,6 +37,16 @@ struct GraphView {
   const int32_t* __restrict__ vw;
 };
 inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+
+// Persistent grid of a warp-tile kernel: one wave of resident blocks.
+inline unsigned tile_grid(Ctx& c, const void* fn, int64_t n) {
+  const int64_t tiles = (n + kTileV - 1) / kTileV;
+  int64_t g = (tiles + kTileWarps - 1) / kTileWarps;
+  const int64_t cap = (int64_t)c.num_sms * c.resident_blocks(fn, kTileThreads, 0);
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
 
 inline unsigned grid_for(const Ctx& c, int64_t items_per_block, int64_t n) {
   int64_t g = (n + items_per_block - 1) / items_per_block;
@@ -140,66 +151,128 @@ __device__ __forceinline__ void cluster_request(const ClusterArgs& a, int32_t v,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_cluster_low(GraphView g, ClusterArgs a) {
-  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
-  const int lane = tile.thread_rank();
-  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
-  for (int64_t vv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; vv < g.n; vv += nsw) {
-    const int32_t v = (int32_t)vv;
-    const int64_t beg = g.xadj[v];
-    const int deg = (int)(g.xadj[v + 1] - beg);
-    if (deg > kLowDeg) continue;
-    if (!cluster_active(a, v, deg)) {
-      if (lane == 0) a.req[v] = -1;
+struct GatherLabel {
+  const int32_t* __restrict__ C;
+  __device__ __forceinline__ int32_t operator()(int32_t u) const { return C[u]; }
+};
+
+// Best cluster of one vertex: the largest edge weight into a neighbouring
+// cluster or its own, ties to the smaller tie-hash, then the smaller label.
+// Hashes are computed only when scores tie (same total order).
+template <class Row>
+__device__ __forceinline__ int32_t best_cluster(const Row& r, int deg, int32_t own, const ClusterArgs& a) {
+  int32_t so = 0;
+  for (int j = 0; j < deg; j++) so += (r.code(j) == own) ? r.weight(j) : 0;
+  int32_t bt = own, bs = so;
+  uint64_t bh = 0;
+  bool bh_known = false;
+  for (int j = 0; j < deg; j++) {
+    const int32_t t = r.code(j);
+    if (t == own) continue;
+    bool seen = false;
+    for (int l = 0; l < j; l++)
+      if (r.code(l) == t) {
+        seen = true;
+        break;
+      }
+    if (seen) continue;
+    int32_t sc = 0;
+    for (int l = j; l < deg; l++) sc += (r.code(l) == t) ? r.weight(l) : 0;
+    if (sc < bs) continue;
+    if (sc > bs) {
+      bs = sc;
+      bt = t;
+      bh_known = false;
       continue;
     }
-    const int32_t own = a.C[v];
-    int32_t t[kSlots], w[kSlots];
-    int32_t so = 0;
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) {
-      const int idx = lane + kSubWarp * r;
-      if (idx < deg) {
-        t[r] = a.C[g.adj[beg + idx]];
-        w[r] = g.adjw[beg + idx];
-      } else {
-        t[r] = -1;
-        w[r] = 0;
-      }
-      if (t[r] == own) so += w[r];
+    if (!bh_known) {
+      bh = h_tie(a.seed, a.level, bt);
+      bh_known = true;
     }
-#pragma unroll
-    for (int o = kSubWarp / 2; o > 0; o >>= 1) so += tile.shfl_xor(so, o);
-    int32_t sc[kSlots] = {0, 0, 0, 0};
-    const int rows = (deg + kSubWarp - 1) / kSubWarp;
-    for (int rr = 0; rr < rows; rr++) {
-      int32_t trr = t[0], wrr = w[0];
-#pragma unroll
-      for (int i = 1; i < kSlots; i++)
-        if (rr == i) {
-          trr = t[i];
-          wrr = w[i];
+    const uint64_t h = h_tie(a.seed, a.level, t);
+    if (h < bh || (h == bh && t < bt)) {
+      bt = t;
+      bh = h;
+    }
+  }
+  return bt;
+}
+
+// a better than b under (score desc, tie-hash asc, label asc); hashes are
+// computed only for equal scores
+__device__ __forceinline__ bool better_lazy(int32_t as, int32_t at, int32_t bs, int32_t bt, const ClusterArgs& a) {
+  if (at < 0) return false;
+  if (bt < 0) return true;
+  if (as != bs) return as > bs;
+  if (at == bt) return false;
+  const uint64_t ha = h_tie(a.seed, a.level, at), hb = h_tie(a.seed, a.level, bt);
+  if (ha != hb) return ha < hb;
+  return at < bt;
+}
+
+// Clustering ratings for the low-degree vertices.  Warp tiles stage the
+// neighbour labels; the active vertices of a tile are then rated four at a
+// time by 8-lane sub-warps reading the staged entries from shared memory.
+__global__ void __launch_bounds__(kTileThreads) k_cluster_tile(GraphView g, ClusterArgs a) {
+  __shared__ int32_t sc[kTileWarps][kTileE];
+  __shared__ int32_t sw[kTileWarps][kTileE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane >> 3, sl = lane & 7;
+  const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
+  const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
+  for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
+    const TileLane t = stage_tile(tg, tile * kTileV, lane, sc[warp], sw[warp], GatherLabel{a.C});
+    const int deg = (int)(t.e - t.b);
+    const bool low = t.v < g.n && deg <= kLowDeg;
+    const bool active = low && cluster_active(a, (int32_t)t.v, deg);
+    int32_t own = active ? a.C[t.v] : -1;
+    if (low && !active) a.req[t.v] = -1;
+    if (active && !t.staged) {  // oversized tile: this lane alone, from global memory
+      const int32_t best =
+          best_cluster(GlobalRow<GatherLabel>{g.adj + t.b, g.adjw + t.b, GatherLabel{a.C}}, deg, own, a);
+      cluster_request(a, (int32_t)t.v, own, best, g.vw[t.v]);
+    }
+    const unsigned work = __ballot_sync(0xffffffffu, active && t.staged);
+    const int rounds = (__popc(work) + 3) / 4;
+    for (int r = 0; r < rounds; r++) {
+      const int src = tile_worker(work, r, sub);
+      const int s2 = src < 0 ? 0 : src;
+      const int off = (int)(__shfl_sync(0xffffffffu, t.b, s2) - t.E0);
+      const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - __shfl_sync(0xffffffffu, t.b, s2));
+      const int32_t ow = __shfl_sync(0xffffffffu, own, s2);
+      const int32_t* c = sc[warp] + off;
+      const int32_t* w = sw[warp] + off;
+      int32_t bs = 0, bt = -1, so = 0;
+      if (src >= 0) {
+        for (int j = sl; j < dg; j += kSubWarp) {
+          const int32_t cj = c[j];
+          so += (cj == ow) ? w[j] : 0;
+          if (cj == ow) continue;
+          int32_t scj = 0;
+          for (int l = 0; l < dg; l++) scj += (c[l] == cj) ? w[l] : 0;
+          if (better_lazy(scj, cj, bs, bt, a)) {
+            bs = scj;
+            bt = cj;
+          }
         }
-      for (int j = 0; j < kSubWarp; j++) {
-        const int32_t ts = tile.shfl(trr, j);
-        const int32_t ws = tile.shfl(wrr, j);
+      }
 #pragma unroll
-        for (int r = 0; r < kSlots; r++) sc[r] += (t[r] == ts) ? ws : 0;
+      for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+        so += __shfl_xor_sync(0xffffffffu, so, o);
+        const int32_t os = __shfl_xor_sync(0xffffffffu, bs, o);
+        const int32_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        if (better_lazy(os, ot, bs, bt, a)) {
+          bs = os;
+          bt = ot;
+        }
+      }
+      if (src >= 0 && sl == 0) {
+        const int32_t v = (int32_t)(tile * kTileV + src);
+        const int32_t best = better_lazy(bs, bt, so, ow, a) ? bt : ow;
+        cluster_request(a, v, ow, best, g.vw[v]);
       }
     }
-    Cand best{so, own, h_tie(a.seed, a.level, own)};
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) {
-      if (t[r] < 0 || t[r] == own) continue;
-      Cand x{sc[r], t[r], h_tie(a.seed, a.level, t[r])};
-      if (better(x, best)) best = x;
-    }
-#pragma unroll
-    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-      Cand x{tile.shfl_xor(best.score, o), tile.shfl_xor(best.t, o), tile.shfl_xor(best.h, o)};
-      if (better(x, best)) best = x;
-    }
-    if (lane == 0) cluster_request(a, v, own, best.t, g.vw[v]);
+    __syncwarp();
   }
 }
 
@@ -641,7 +714,7 @@ void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
   ClusterArgs a{c.C, c.Wc, c.ReqW, c.req, wcap, c.cfg.seed, c.cstate, lvl, r};
   c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
-  k_cluster_low<<<gl, kThreads, 0, c.st>>>(view(L), a); count_launch();
+  k_cluster_tile<<<tile_grid(c, (const void*)k_cluster_tile, n), kTileThreads, 0, c.st>>>(view(L), a); count_launch();
   // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
   c.prof_end(ev, PK_CLUSTER, 16 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
   if (L.n_hi)

@@ -4,6 +4,7 @@
 
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/gpumap.h"
@@ -152,8 +153,12 @@ struct Ctx {
   int64_t* headP = nullptr;     // [kc]
   int64_t* Rb = nullptr;        // [kc + 1]
   int32_t* U = nullptr;         // [kc]
+  int64_t* tab = nullptr;       // [kc * kBuckets] eligible weight per (block, bucket), zero between steps
+  int32_t* bcut = nullptr;      // [kc] cut bucket per overloaded block
+  int64_t* rem = nullptr;       // [kc] weight still to move inside the cut bucket
   int64_t* counters = nullptr;  // small device counters
   int64_t* Jacc = nullptr;
+  unsigned int* evctr = nullptr;  // blocks finished in a fused J evaluation
   RefineState* state = nullptr;
   RefineState* h_state = nullptr;  // pinned mirror
   int32_t* trace_kind = nullptr;
@@ -180,6 +185,20 @@ struct Ctx {
   uint32_t* errword = nullptr;
   ClusterState* cstate = nullptr;
   ClusterState* h_cstate = nullptr;  // pinned mirror
+
+  // resident blocks per SM of a kernel (occupancy API, cached)
+  std::unordered_map<const void*, int> occ;
+  int resident_blocks(const void* fn, int threads, size_t smem) {
+    auto it = occ.find(fn);
+    if (it != occ.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+      cudaGetLastError();
+      nb = 1;
+    }
+    occ[fn] = nb;
+    return nb;
+  }
 
   // profiler
   bool prof = false;

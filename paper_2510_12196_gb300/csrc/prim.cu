@@ -125,8 +125,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(const uint64_t* __
                                                               uint64_t* __restrict__ kout,
                                                               int32_t* __restrict__ vout, const int64_t* d_n,
                                                               int64_t max_n, int bits) {
-  constexpr int kW = kSmallThreads / 32;
-  constexpr int kItems = kSmallSort / kSmallThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* ks = reinterpret_cast<uint64_t*>(smem_raw);                  // [2][kSmallSort]
   int32_t* vs = reinterpret_cast<int32_t*>(ks + 2 * kSmallSort);          // [2][kSmallSort]
@@ -136,62 +134,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(const uint64_t* __
   const int64_t n64 = load_count(d_n, max_n);
   if (n64 > kSmallSort || n64 <= 0) return;
   const int n = (int)n64;
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const unsigned lt = (1u << l) - 1u;
   for (int i = threadIdx.x; i < n; i += kSmallThreads) {
     ks[i] = kin[i];
     vs[i] = vin[i];
   }
-  int cur = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
-    const uint64_t* kc = ks + cur * kSmallSort;
-    const int32_t* vc = vs + cur * kSmallSort;
-    uint64_t* kn = ks + (cur ^ 1) * kSmallSort;
-    int32_t* vn = vs + (cur ^ 1) * kSmallSort;
-    for (int i = threadIdx.x; i < kW * 256; i += kSmallThreads) wcnt[i] = 0;
-    __syncthreads();
-    int rank[kItems], dig[kItems];
-#pragma unroll
-    for (int j = 0; j < kItems; j++) {
-      const int idx = w * 32 * kItems + j * 32 + l;
-      const bool valid = idx < n;
-      const int d = valid ? (int)((kc[idx] >> shift) & 255u) : 256 + l;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      int r = 0;
-      if (valid) r = wcnt[w * 256 + d] + __popc(peers & lt);
-      __syncwarp();
-      if (valid && (peers & lt) == 0) wcnt[w * 256 + d] += __popc(peers);
-      __syncwarp();
-      rank[j] = valid ? r : -1;
-      dig[j] = d;
-    }
-    __syncthreads();
-    // per digit: exclusive prefix over warps, digit totals -> digit bases
-    int64_t tot = 0;
-    if (threadIdx.x < 256) {
-      int32_t run = 0;
-      for (int ww = 0; ww < kW; ww++) {
-        const int32_t t = wcnt[ww * 256 + threadIdx.x];
-        wcnt[ww * 256 + threadIdx.x] = run;
-        run += t;
-      }
-      tot = run;
-    }
-    int64_t all;
-    const int64_t ex = block_exclusive_scan(tot, sm, &all);
-    if (threadIdx.x < 256) dbase[threadIdx.x] = (int32_t)ex;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kItems; j++) {
-      if (rank[j] < 0) continue;
-      const int idx = w * 32 * kItems + j * 32 + l;
-      const int pos = dbase[dig[j]] + wcnt[w * 256 + dig[j]] + rank[j];
-      kn[pos] = kc[idx];
-      vn[pos] = vc[idx];
-    }
-    __syncthreads();
-    cur ^= 1;
-  }
+  const int cur = cta_sort_small(ks, vs, wcnt, dbase, sm, n, bits);
   for (int i = threadIdx.x; i < n; i += kSmallThreads) {
     kout[i] = ks[cur * kSmallSort + i];
     vout[i] = vs[cur * kSmallSort + i];

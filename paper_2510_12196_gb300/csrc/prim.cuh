@@ -193,6 +193,71 @@ __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* 
                                uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t max_n,
                                const int64_t* d_n, int shift, const int64_t* __restrict__ hist_off,
                                int64_t max_tiles, int64_t skip_upto);
+// Stable LSD radix sort of n <= kSmallSort (key, value) pairs held in the
+// double buffers ks[2][kSmallSort], vs[2][kSmallSort] of shared memory, by
+// key bits [0, bits), by one CTA of kSmallThreads threads.  wcnt holds
+// (kSmallThreads / 32) * 256 counters, dbase 257, sm 33.  Returns the buffer
+// index holding the result.  Items of warp w are [w * items, (w + 1) * items)
+// in lane-strided order, so (warp, item, lane) order is index order and equal
+// digits keep it.
+__device__ __forceinline__ int cta_sort_small(uint64_t* ks, int32_t* vs, int32_t* wcnt, int32_t* dbase, int64_t* sm,
+                                              int n, int bits) {
+  constexpr int kW = kSmallThreads / 32;
+  constexpr int kItems = kSmallSort / kSmallThreads;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const unsigned lt = (1u << l) - 1u;
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    const uint64_t* kc = ks + cur * kSmallSort;
+    const int32_t* vc = vs + cur * kSmallSort;
+    uint64_t* kn = ks + (cur ^ 1) * kSmallSort;
+    int32_t* vn = vs + (cur ^ 1) * kSmallSort;
+    for (int i = threadIdx.x; i < kW * 256; i += kSmallThreads) wcnt[i] = 0;
+    __syncthreads();
+    int rank[kItems], dig[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+      const int idx = w * 32 * kItems + j * 32 + l;
+      const bool valid = idx < n;
+      const int d = valid ? (int)((kc[idx] >> shift) & 255u) : 256 + l;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      int r = 0;
+      if (valid) r = wcnt[w * 256 + d] + __popc(peers & lt);
+      __syncwarp();
+      if (valid && (peers & lt) == 0) wcnt[w * 256 + d] += __popc(peers);
+      __syncwarp();
+      rank[j] = valid ? r : -1;
+      dig[j] = d;
+    }
+    __syncthreads();
+    int64_t tot = 0;
+    if (threadIdx.x < 256) {
+      int32_t run = 0;
+      for (int ww = 0; ww < kW; ww++) {
+        const int32_t t = wcnt[ww * 256 + threadIdx.x];
+        wcnt[ww * 256 + threadIdx.x] = run;
+        run += t;
+      }
+      tot = run;
+    }
+    int64_t all;
+    const int64_t ex = block_exclusive_scan(tot, sm, &all);
+    if (threadIdx.x < 256) dbase[threadIdx.x] = (int32_t)ex;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+      if (rank[j] < 0) continue;
+      const int idx = w * 32 * kItems + j * 32 + l;
+      const int pos = dbase[dig[j]] + wcnt[w * 256 + dig[j]] + rank[j];
+      kn[pos] = kc[idx];
+      vn[pos] = vc[idx];
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  return cur;
+}
+
 __global__ void k_sort_small(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                              uint64_t* __restrict__ kout, int32_t* __restrict__ vout, const int64_t* d_n,
                              int64_t max_n, int bits);

@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "engine.h"
+#include "tile.cuh"
 
 namespace gm {
 
@@ -30,6 +31,12 @@ struct GraphView {
 };
 
 inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+
+inline int bits_for_n(int64_t x) {  // smallest b with x <= 2^b
+  int b = 0;
+  while (b < 62 && (1LL << b) < x) b++;
+  return b;
+}
 
 __device__ __forceinline__ bool kind_is(const RefineState* st, int mask) {
   return (mask >> st->kind) & 1;
@@ -73,25 +80,79 @@ __global__ void __launch_bounds__(kThreads) k_block_weights(int32_t n, const int
     if (hist[b]) atomicAdd((unsigned long long*)&W[b], (unsigned long long)(int64_t)hist[b]);
 }
 
-// J contribution of the low-degree vertices.
-__global__ void __launch_bounds__(kThreads) k_eval_low(GraphView g, const int32_t* __restrict__ pi, Topo topo,
-                                                       int64_t* Jacc) {
+struct GatherPi {
+  const int32_t* __restrict__ pi;
+  __device__ __forceinline__ int32_t operator()(int32_t u) const { return pi[u]; }
+};
+
+// Persistent grid of a warp-tile kernel: one wave of resident blocks.
+inline unsigned tile_grid(Ctx& c, const void* fn, int64_t n) {
+  const int64_t tiles = (n + kTileV - 1) / kTileV;
+  int64_t g = (tiles + kTileWarps - 1) / kTileWarps;
+  const int64_t cap = (int64_t)c.num_sms * c.resident_blocks(fn, kTileThreads, 0);
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// sum_j w_j D(x, c_j) over one neighbourhood
+template <class Row>
+__device__ __forceinline__ int64_t row_cost(const Row& r, int deg, const int32_t* sdist, int32_t x) {
+  int64_t T = 0;
+  for (int j = 0; j < deg; j++) T += (int64_t)r.weight(j) * dcode(sdist, x, r.code(j));
+  return T;
+}
+
+struct CtlArgs {
+  int64_t lmax;
+  int32_t kc;
+  int32_t patience, weak_max, phi_num, phi_den;
+  int32_t* tk;
+  int64_t* tJ;
+  int64_t* tW;
+  int32_t tcap;
+};
+
+// Controller attached to a J evaluation (s == nullptr: J only).
+struct EvalCtl {
+  RefineState* s;
+  unsigned int* ctr;  // blocks finished (zero between launches)
+  const int64_t* W;
+  CtlArgs a;
+  int phase;
+  cudaGraphConditionalHandle h;
+  int use_h;
+};
+__device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec);
+
+// J contribution of the low-degree vertices (warp tiles, one lane per vertex).
+// With a controller attached, the last block to finish runs the Alg. 6
+// decision on the complete J (the high-degree part is added before).
+__global__ void __launch_bounds__(kTileThreads) k_eval_tile(GraphView g, const int32_t* __restrict__ pi, Topo topo,
+                                                            int64_t* Jacc, EvalCtl ec) {
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
+  __shared__ int32_t sc[kTileWarps][kTileE];
+  __shared__ int32_t sw[kTileWarps][kTileE];
   load_sdist(sdist, topo);
   __syncthreads();
-  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
-  const int lane = tile.thread_rank();
-  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
+  const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
   int64_t acc = 0;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
-    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
-    if (end - beg > kLowDeg) continue;
-    const int32_t p = pi[v];
-    for (int64_t e = beg + lane; e < end; e += kSubWarp) acc += (int64_t)g.adjw[e] * dcode(sdist, p, pi[g.adj[e]]);
+  for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
+    const TileLane t = stage_tile(tg, tile * kTileV, lane, sc[warp], sw[warp], GatherPi{pi});
+    const int deg = (int)(t.e - t.b);
+    if (t.v < g.n && deg <= kLowDeg) {
+      const int32_t p = pi[t.v];
+      if (t.staged) acc += row_cost(StagedRow{sc[warp] + (t.b - t.E0), sw[warp] + (t.b - t.E0)}, deg, sdist, p);
+      else acc += row_cost(GlobalRow<GatherPi>{g.adj + t.b, g.adjw + t.b, GatherPi{pi}}, deg, sdist, p);
+    }
+    __syncwarp();
   }
   acc = block_sum(acc, sm);
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
+  eval_finish(Jacc, ec);
 }
 
 // J contribution of the high-degree vertices (one CTA per vertex).
@@ -115,95 +176,136 @@ __global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int
 // ---------------------------------------------------------------------------
 // Alg. 4 step 1: best target per vertex by Eq. 1, non-negative filter
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_lp_gain_low(GraphView g, const int32_t* __restrict__ pi,
-                                                          uint8_t* __restrict__ lock, int32_t* __restrict__ pp,
-                                                          int64_t* __restrict__ gain, uint8_t* __restrict__ inx,
-                                                          Topo topo, const RefineState* st) {
+// Best target of one vertex: argmin over the neighbouring PEs q != p of
+// T(q) = sum_j w_j D(q, c_j) (ties: lowest code), i.e. argmax of Eq. 1's
+// G_q(v) = T(p) - T(q).  Returns false if no neighbour lies outside p.
+template <class Row>
+__device__ __forceinline__ bool best_target(const Row& r, int deg, int32_t p, const int32_t* sdist, int32_t& best_c,
+                                            int64_t& best_T) {
+  best_c = INT32_MAX;
+  best_T = INT64_MAX;
+  bool any = false;
+  for (int j = 0; j < deg; j++) {
+    const int32_t q = r.code(j);
+    if (q == p) continue;
+    bool seen = false;
+    for (int l = 0; l < j; l++)
+      if (r.code(l) == q) {
+        seen = true;
+        break;
+      }
+    if (seen) continue;
+    any = true;
+    const int64_t T = row_cost(r, deg, sdist, q);
+    if (T < best_T || (T == best_T && q < best_c)) {
+      best_T = T;
+      best_c = q;
+    }
+  }
+  return any;
+}
+
+// Alg. 4 step 1 for the low-degree vertices.  Warp tiles stage the
+// neighbour PEs; each lane checks its own vertex (T(P(v)), any neighbour
+// outside P(v)); the vertices with candidates are then evaluated four at a
+// time by 8-lane sub-warps from the staged entries.
+__global__ void __launch_bounds__(kTileThreads) k_lp_gain_tile(GraphView g, const int32_t* __restrict__ pi,
+                                                               uint8_t* __restrict__ lock, int32_t* __restrict__ pp,
+                                                               int64_t* __restrict__ gain, uint8_t* __restrict__ inx,
+                                                               Topo topo, const RefineState* st) {
   __shared__ int32_t sdist[32];
+  __shared__ int32_t sc[kTileWarps][kTileE];
+  __shared__ int32_t sw[kTileWarps][kTileE];
   if (!kind_is(st, 1 << KIND_LP)) return;
   load_sdist(sdist, topo);
   __syncthreads();
-  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
-  const int lane = tile.thread_rank();
-  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
-    const int64_t beg = g.xadj[v];
-    const int deg = (int)(g.xadj[v + 1] - beg);
-    if (deg > kLowDeg) continue;
-    const int32_t p = pi[v];
-    int32_t c[kSlots], w[kSlots];
-    bool cand = false;
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) {
-      const int idx = lane + kSubWarp * r;
-      if (idx < deg) {
-        c[r] = pi[g.adj[beg + idx]];
-        w[r] = g.adjw[beg + idx];
-      } else {
-        c[r] = p;  // padding: same block, zero weight, never a candidate
-        w[r] = 0;
-      }
-      cand |= (c[r] != p);
-    }
-    const bool locked = lock[v] != 0;
-    cand = tile.any(cand);
-    if (locked || !cand) {
-      if (lane == 0) {
-        inx[v] = 0;
-        pp[v] = p;
-        gain[v] = 0;
-        if (locked) lock[v] = 0;
-      }
-      continue;
-    }
-    // T(x) = sum over neighbours of w * D(x, P(u)); G_q(v) = T(P(v)) - T(q).
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane >> 3, sl = lane & 7;
+  const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
+  const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
+  for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
+    const TileLane t = stage_tile(tg, tile * kTileV, lane, sc[warp], sw[warp], GatherPi{pi});
+    const int deg = (int)(t.e - t.b);
+    const bool low = t.v < g.n && deg <= kLowDeg;
+    int32_t p = -1;
     int64_t Tp = 0;
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) Tp += (int64_t)w[r] * dcode(sdist, p, c[r]);
-    Tp = tile_sum64(tile, Tp);
-    int64_t T[kSlots];
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) T[r] = 0;
-    const int rows = (deg + kSubWarp - 1) / kSubWarp;
-    for (int rr = 0; rr < rows; rr++) {
-      const int32_t crr = pick(c, rr);
-      const int32_t wrr = pick(w, rr);
-      for (int j = 0; j < kSubWarp; j++) {
-        const int32_t cs = tile.shfl(crr, j);
-        const int32_t ws = tile.shfl(wrr, j);
-#pragma unroll
-        for (int r = 0; r < kSlots; r++) T[r] += (int64_t)ws * dcode(sdist, c[r], cs);
+    bool cand = false;
+    if (low) {
+      p = pi[t.v];
+      if (lock[t.v]) {
+        lock[t.v] = 0;
+      } else if (t.staged) {
+        const int32_t* c = sc[warp] + (t.b - t.E0);
+        const int32_t* w = sw[warp] + (t.b - t.E0);
+        for (int j = 0; j < deg; j++) {
+          Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
+          cand |= c[j] != p;
+        }
+      } else {  // oversized tile: this lane alone, from global memory
+        const GlobalRow<GatherPi> r{g.adj + t.b, g.adjw + t.b, GatherPi{pi}};
+        int32_t bc;
+        int64_t bt;
+        if (best_target(r, deg, p, sdist, bc, bt)) {
+          const int64_t G = row_cost(r, deg, sdist, p) - bt;
+          if (G >= 0) {
+            inx[t.v] = 1;
+            pp[t.v] = bc;
+            gain[t.v] = G;
+            goto done_lane;
+          }
+        }
+      }
+      if (!cand) {  // locked, no neighbour outside P(v), or the global path found no move
+        inx[t.v] = 0;
+        pp[t.v] = p;
+        gain[t.v] = 0;
       }
     }
-    int64_t bt = INT64_MAX;
-    int32_t bc = INT32_MAX;
-#pragma unroll
-    for (int r = 0; r < kSlots; r++)
-      if (c[r] != p && (T[r] < bt || (T[r] == bt && c[r] < bc))) {
-        bt = T[r];
-        bc = c[r];
+  done_lane:
+    const unsigned work = __ballot_sync(0xffffffffu, cand);
+    const int rounds = (__popc(work) + 3) / 4;
+    for (int r = 0; r < rounds; r++) {
+      const int src = tile_worker(work, r, sub);
+      const int s2 = src < 0 ? 0 : src;
+      const int64_t vb = __shfl_sync(0xffffffffu, t.b, s2);
+      const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - vb);
+      const int32_t pv = __shfl_sync(0xffffffffu, p, s2);
+      const int64_t tp = __shfl_sync(0xffffffffu, Tp, s2);
+      const int32_t* c = sc[warp] + (vb - t.E0);
+      const int32_t* w = sw[warp] + (vb - t.E0);
+      int64_t bt = INT64_MAX;
+      int32_t bc = INT32_MAX;
+      if (src >= 0) {
+        for (int j = sl; j < dg; j += kSubWarp) {
+          const int32_t q = c[j];
+          if (q == pv) continue;
+          int64_t T = 0;
+          for (int l = 0; l < dg; l++) T += (int64_t)w[l] * dcode(sdist, q, c[l]);
+          if (T < bt || (T == bt && q < bc)) {
+            bt = T;
+            bc = q;
+          }
+        }
       }
 #pragma unroll
-    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-      const int64_t ot = tile.shfl_xor(bt, o);
-      const int32_t oc = tile.shfl_xor(bc, o);
-      if (ot < bt || (ot == bt && oc < bc)) {
-        bt = ot;
-        bc = oc;
+      for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+        const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        if (ot < bt || (ot == bt && oc < bc)) {
+          bt = ot;
+          bc = oc;
+        }
+      }
+      if (src >= 0 && sl == 0) {
+        const int64_t v = tile * kTileV + src;
+        const int64_t G = tp - bt;
+        const bool in = G >= 0;
+        inx[v] = in ? 1 : 0;
+        pp[v] = in ? bc : pv;
+        gain[v] = in ? G : 0;
       }
     }
-    if (lane == 0) {
-      const int64_t G = Tp - bt;
-      if (G >= 0) {
-        inx[v] = 1;
-        pp[v] = bc;
-        gain[v] = G;
-      } else {
-        inx[v] = 0;
-        pp[v] = p;
-        gain[v] = 0;
-      }
-    }
+    __syncwarp();
   }
 }
 
@@ -424,43 +526,70 @@ __global__ void __launch_bounds__(kThreads) k_lp_apply(int32_t n, int32_t* __res
 // ---------------------------------------------------------------------------
 enum { CNT_NU = 0, CNT_SIGMA = 1, CNT_ELIG = 2, CNT_SEL = 3, CNT_TMP = 4, CNT_N = 8 };
 
+struct RebPrepArgs {
+  const int64_t* W;
+  const int32_t* pe_of_code;
+  Topo topo;
+  int64_t lmax;
+  int64_t cV;
+  int32_t sigma_gap;
+  int32_t* U;
+  int64_t* cnt;
+  int64_t* accepted;
+};
+
 // sigma, the fallback destination list U (ascending codes of valid PEs with
-// weight <= sigma), and resets of the per-step counters.
-__global__ void __launch_bounds__(1024) k_reb_prep(const int64_t* __restrict__ W, const int32_t* __restrict__ pe_of_code,
-                                                   Topo topo, int64_t lmax, int64_t cV, int32_t sigma_gap,
-                                                   int32_t* U, int64_t* cnt, int64_t* accepted,
-                                                   const RefineState* st) {
+// weight <= sigma), and resets of the per-step counters (all threads).
+__device__ void reb_prep_body(const RebPrepArgs& p, bool strong) {
   __shared__ int64_t sm[33];
-  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
-  const bool strong = st->kind == KIND_STRONG;
   int64_t sigma;
   if (strong) {
-    sigma = lmax;
+    sigma = p.lmax;
   } else {
-    const int64_t avg = (cV + topo.k - 1) / topo.k;
-    sigma = lmax - sigma_gap;
+    const int64_t avg = (p.cV + p.topo.k - 1) / p.topo.k;
+    sigma = p.lmax - p.sigma_gap;
     if (sigma < avg) sigma = avg;
   }
   int64_t carry = 0;
-  for (int32_t base = 0; base < topo.kc; base += blockDim.x) {
+  for (int32_t base = 0; base < p.topo.kc; base += blockDim.x) {
     const int32_t b = base + threadIdx.x;
-    const int64_t ok = (b < topo.kc && pe_of_code[b] >= 0 && W[b] <= sigma) ? 1 : 0;
+    const int64_t ok = (b < p.topo.kc && p.pe_of_code[b] >= 0 && p.W[b] <= sigma) ? 1 : 0;
     int64_t tot;
     const int64_t e = block_exclusive_scan(ok, sm, &tot);
-    if (ok) U[carry + e] = b;
+    if (ok) p.U[carry + e] = b;
     carry += tot;
   }
-  for (int32_t b = threadIdx.x; b < topo.kc; b += blockDim.x) accepted[b] = 0;
+  for (int32_t b = threadIdx.x; b < p.topo.kc; b += blockDim.x) p.accepted[b] = 0;
   if (threadIdx.x == 0) {
-    cnt[CNT_NU] = carry;
-    cnt[CNT_SIGMA] = sigma;
+    p.cnt[CNT_NU] = carry;
+    p.cnt[CNT_SIGMA] = sigma;
   }
+}
+
+__global__ void __launch_bounds__(1024) k_reb_prep(RebPrepArgs p, const RefineState* st) {
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  reb_prep_body(p, st->kind == KIND_STRONG);
+}
+
+// Graph mode: the start of one Alg. 6 iteration selects the step bodies and,
+// for a rebalancing step, prepares it.
+__global__ void __launch_bounds__(1024) k_decide_prep(const RefineState* s, cudaGraphConditionalHandle h_lp,
+                                                      cudaGraphConditionalHandle h_reb,
+                                                      cudaGraphConditionalHandle h_strong, RebPrepArgs p) {
+  const int32_t kind = s->kind;
+  if (threadIdx.x == 0) {
+    cudaGraphSetConditional(h_lp, kind == KIND_LP ? 1u : 0u);
+    cudaGraphSetConditional(h_reb, (kind == KIND_WEAK || kind == KIND_STRONG) ? 1u : 0u);
+    cudaGraphSetConditional(h_strong, kind == KIND_STRONG ? 1u : 0u);
+  }
+  if (kind == KIND_WEAK || kind == KIND_STRONG) reb_prep_body(p, kind == KIND_STRONG);
 }
 
 struct RebArgs {
   const int64_t* W;
   const int32_t* U;
   const int64_t* cnt;
+  int64_t* tab;  // eligible weight per (source block, loss bucket)
   int64_t lmax;
   int64_t cV;
   int32_t k;
@@ -552,9 +681,11 @@ __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const 
         elig[v] = 0;
         continue;
       }
+      const int32_t bk = loss_bucket(gcut);
       dest[v] = bc;
-      bkt[v] = (uint8_t)loss_bucket(gcut);
+      bkt[v] = (uint8_t)bk;
       elig[v] = 1;
+      atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
     }
   }
 }
@@ -621,8 +752,10 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
         ok = false;
       }
       if (ok) {
+        const int32_t bk = loss_bucket(gcut);
         dest[v] = bc;
-        bkt[v] = (uint8_t)loss_bucket(gcut);
+        bkt[v] = (uint8_t)bk;
+        atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
       }
       elig[v] = ok ? 1 : 0;
     }
@@ -631,10 +764,6 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
 }
 
 // Compaction stores for the sort inputs.
-struct LoadFlag {
-  const uint8_t* f;
-  __device__ int64_t operator()(int64_t i) const { return f[i] ? 1 : 0; }
-};
 struct LoadFlag2 {
   const uint8_t* a;
   const uint8_t* b;
@@ -673,6 +802,160 @@ struct StoreIfPositive {
 
 __global__ void k_copy_count(const int64_t* src, int64_t* dst) { *dst = *src; }
 
+// Alg. 5 selection without sorting whole blocks.  In source block A the
+// eligible vertices are ordered by (bucket, id) and v moves iff the weight
+// before it is < E = c(A) - L_max.  With T_b the eligible weight of bucket b
+// and C_b = T_0 + ... + T_{b-1}: buckets with C_b + T_b <= E move entirely,
+// buckets with C_b >= E not at all, and in the one bucket with
+// C_b < E < C_b + T_b a vertex moves iff the weight of the lower ids of that
+// bucket is < rem = E - C_b.  Only that bucket needs an id order.
+__global__ void __launch_bounds__(1024) k_reb_cut(const int64_t* __restrict__ W, int32_t kc, int64_t lmax,
+                                                  int64_t* tab, int32_t* bcut, int64_t* rem, int64_t* cnt,
+                                                  const RefineState* st) {
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  for (int32_t A = threadIdx.x; A < kc; A += blockDim.x) {
+    if (W[A] <= lmax) continue;  // only overloaded blocks have eligible vertices
+    const int64_t E = W[A] - lmax;
+    int64_t cum = 0, r = 0;
+    int32_t cut = kBuckets;
+    for (int b = 0; b < kBuckets; b++) {
+      const int64_t t = tab[(int64_t)A * kBuckets + b];
+      tab[(int64_t)A * kBuckets + b] = 0;  // the table is zero between steps
+      if (cut == kBuckets) {
+        if (cum + t <= E) {
+          cum += t;
+        } else {
+          cut = b;
+          r = E - cum;
+        }
+      }
+    }
+    bcut[A] = cut;
+    rem[A] = r;
+  }
+  if (threadIdx.x == 0) cnt[CNT_ELIG] = 0;
+}
+
+// Buckets below the cut move, above it stay; the cut bucket's vertices go to
+// a list keyed (block, id) whose order does not depend on the append order.
+__global__ void k_reb_classify(int32_t n, const int32_t* __restrict__ pi, const uint8_t* __restrict__ elig,
+                               const uint8_t* __restrict__ bkt, const int32_t* __restrict__ bcut,
+                               const int64_t* __restrict__ rem, int idbits, uint8_t* sel, uint64_t* key,
+                               int32_t* val, int64_t* cnt, const RefineState* st) {
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (!elig[v]) continue;
+    const int32_t A = pi[v];
+    const int32_t b = bkt[v], cut = bcut[A];
+    if (b != cut) {
+      sel[v] = b < cut ? 1 : 0;
+      continue;
+    }
+    sel[v] = 0;
+    if (rem[A] > 0) {
+      const unsigned long long i = atomicAdd((unsigned long long*)&cnt[CNT_ELIG], 1ULL);
+      key[i] = ((uint64_t)(uint32_t)A << idbits) | (uint64_t)v;
+      val[i] = (int32_t)v;
+    }
+  }
+}
+
+// The cut-bucket list, when it has at most kSmallSort entries: one CTA sorts
+// it by (block, id) in shared memory and selects by the per-block prefix.
+__global__ void __launch_bounds__(kSmallThreads) k_reb_resolve(const uint64_t* __restrict__ kin,
+                                                               const int32_t* __restrict__ vin,
+                                                               const int64_t* __restrict__ cnt, int bits, int idbits,
+                                                               const int32_t* __restrict__ vw,
+                                                               const int64_t* __restrict__ rem, int64_t* headP,
+                                                               uint8_t* sel, const RefineState* st,
+                                                               cudaGraphConditionalHandle h_big, int use_h) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* ks = reinterpret_cast<uint64_t*>(smem_raw);
+  int32_t* vs = reinterpret_cast<int32_t*>(ks + 2 * kSmallSort);
+  int32_t* wcnt = vs + 2 * kSmallSort;
+  __shared__ int32_t dbase[257];
+  __shared__ int64_t sm[33];
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  const int64_t n64 = cnt[CNT_ELIG];
+  if (use_h && threadIdx.x == 0) cudaGraphSetConditional(h_big, n64 > kSmallSort ? 1u : 0u);
+  if (n64 <= 0 || n64 > kSmallSort) return;
+  const int n = (int)n64;
+  for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+    ks[i] = kin[i];
+    vs[i] = vin[i];
+  }
+  const int cur = cta_sort_small(ks, vs, wcnt, dbase, sm, n, bits);
+  const uint64_t* k = ks + cur * kSmallSort;
+  const int32_t* v = vs + cur * kSmallSort;
+  constexpr int kItems = kSmallSort / kSmallThreads;
+  const int first = threadIdx.x * kItems;
+  int64_t c[kItems], local = 0;
+#pragma unroll
+  for (int j = 0; j < kItems; j++) {
+    c[j] = (first + j < n) ? vw[v[first + j]] : 0;
+    local += c[j];
+  }
+  int64_t total;
+  int64_t run = block_exclusive_scan(local, sm, &total);
+  int64_t P[kItems];
+#pragma unroll
+  for (int j = 0; j < kItems; j++) {
+    P[j] = run;
+    run += c[j];
+    const int i = first + j;
+    if (i < n && (i == 0 || (k[i] >> idbits) != (k[i - 1] >> idbits))) headP[k[i] >> idbits] = P[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kItems; j++) {
+    const int i = first + j;
+    if (i >= n) continue;
+    const int32_t A = (int32_t)(k[i] >> idbits);
+    sel[v[i]] = (P[j] - headP[A] < rem[A]) ? 1 : 0;
+  }
+}
+
+// Larger cut-bucket lists: after a multi-CTA sort by (block, id).
+__global__ void k_heads_shift(const uint64_t* __restrict__ key, const int64_t* __restrict__ P,
+                              const int64_t* __restrict__ cnt, int shift, int64_t* headP) {
+  const int64_t n = cnt[CNT_ELIG];
+  if (n <= kSmallSort) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t grp = key[i] >> shift;
+    if (i == 0 || (key[i - 1] >> shift) != grp) headP[grp] = P[i];
+  }
+}
+__global__ void k_reb_mark_cut(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                               const int64_t* __restrict__ P, const int64_t* __restrict__ headP,
+                               const int64_t* __restrict__ cnt, int shift, const int64_t* __restrict__ rem,
+                               uint8_t* sel, unsigned long long* kcount, unsigned long long body) {
+  const int64_t n = cnt[CNT_ELIG];
+  if (kcount && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(kcount, body);
+  if (n <= kSmallSort) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t A = (int32_t)(key[i] >> shift);
+    sel[val[i]] = (P[i] - headP[A] < rem[A]) ? 1 : 0;
+  }
+}
+
+__global__ void k_reb_apply_sel(int32_t n, const uint8_t* __restrict__ elig, const uint8_t* __restrict__ sel,
+                                const int32_t* __restrict__ dest, int32_t* pi, const int32_t* __restrict__ vw,
+                                int64_t* W, RefineState* st) {
+  if (st->kind != KIND_WEAK) return;
+  int32_t mine = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (!elig[v] || !sel[v]) continue;
+    const int32_t p = pi[v], q = dest[v];
+    const int64_t c = vw[v];
+    pi[v] = q;
+    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
+    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    mine++;
+  }
+  mine = warp_sum(mine);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&st->moved, mine);
+}
+
 // Segment heads of a sorted (group << 6 | bucket) list: headP[group] = P[i].
 __global__ void k_heads(const uint64_t* __restrict__ key, const int64_t* __restrict__ P, const int64_t* d_n,
                         int64_t max_n, int64_t* headP) {
@@ -682,38 +965,6 @@ __global__ void k_heads(const uint64_t* __restrict__ key, const int64_t* __restr
     const uint64_t grp = key[i] >> kBucketBits;
     if (i == 0 || (key[i - 1] >> kBucketBits) != grp) headP[grp] = P[i];
   }
-}
-
-// weight strictly before v within its source block < c(A) - L_max
-__global__ void k_reb_mark(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
-                           const int64_t* __restrict__ P, const int64_t* __restrict__ headP, const int64_t* d_n,
-                           int64_t max_n, const int64_t* __restrict__ W, int64_t lmax, uint8_t* sel) {
-  const int64_t n = *d_n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t A = (int32_t)(key[i] >> kBucketBits);
-    sel[val[i]] = (P[i] - headP[A] < W[A] - lmax) ? 1 : 0;
-  }
-}
-
-__global__ void k_reb_apply_weak(const int32_t* __restrict__ val, const int64_t* d_n, int64_t max_n,
-                                 const uint8_t* __restrict__ sel, const int32_t* __restrict__ dest, int32_t* pi,
-                                 const int32_t* __restrict__ vw, int64_t* W, RefineState* st) {
-  if (st->kind != KIND_WEAK) return;
-  const int64_t n = *d_n;
-  int32_t mine = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = val[i];
-    if (!sel[v]) continue;
-    const int32_t p = pi[v], q = dest[v];
-    const int64_t c = vw[v];
-    pi[v] = q;
-    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
-    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
-    mine++;
-  }
-  if (mine) atomicAdd(&st->moved, mine);
 }
 
 // strong: movers grouped by destination are accepted while it stays <= L_max
@@ -792,22 +1043,13 @@ __global__ void k_reb_apply_strong(const uint64_t* __restrict__ key, const int32
 // ---------------------------------------------------------------------------
 // Alg. 6 controller (one CTA): best-state tracking, patience, next step kind
 // ---------------------------------------------------------------------------
-struct CtlArgs {
-  int64_t lmax;
-  int32_t kc;
-  int32_t patience, weak_max, phi_num, phi_den;
-  int32_t* tk;
-  int64_t* tJ;
-  int64_t* tW;
-  int32_t tcap;
-};
 
-__global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* __restrict__ W, int64_t* Jacc,
-                                                 CtlArgs a, int phase, cudaGraphConditionalHandle h_loop,
-                                                 int use_handle) {
-  __shared__ int64_t smax[32];
+
+// Maximum block weight over the code space (all threads of the block call
+// it; thread 0 gets the result).
+__device__ __forceinline__ int64_t block_max_w(const int64_t* __restrict__ W, int32_t kc, int64_t* smax) {
   int64_t mx = 0;
-  for (int32_t b = threadIdx.x; b < a.kc; b += blockDim.x) mx = W[b] > mx ? W[b] : mx;
+  for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) mx = W[b] > mx ? W[b] : mx;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const int64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
@@ -815,14 +1057,19 @@ __global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* 
   }
   if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = smax[w] > mx ? smax[w] : mx;
+  if (threadIdx.x == 0)
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = smax[w] > mx ? smax[w] : mx;
+  return mx;
+}
+
+// One Alg. 6 decision (thread 0): lines 16-21 on J and the maximum block
+// weight of P', the patience test, and the kind of the next step.
+__device__ void control_step(RefineState* s, int64_t mx, int64_t J, const CtlArgs& a, int phase,
+                             cudaGraphConditionalHandle h_loop, int use_handle) {
   if (phase == 1 && s->done) {
     if (use_handle) cudaGraphSetConditional(h_loop, 0u);
     return;
   }
-  const int64_t J = *Jacc;
-  *Jacc = 0;
   s->copy_best = 0;
   s->J = J;
   s->maxw = mx;
@@ -891,14 +1138,29 @@ __global__ void __launch_bounds__(256) k_control(RefineState* s, const int64_t* 
   }
 }
 
-// Graph mode: the start of one Alg. 6 iteration selects the step bodies.
-__global__ void k_decide(const RefineState* s, cudaGraphConditionalHandle h_lp, cudaGraphConditionalHandle h_reb,
-                         cudaGraphConditionalHandle h_strong) {
-  const int32_t kind = s->kind;
-  cudaGraphSetConditional(h_lp, kind == KIND_LP ? 1u : 0u);
-  cudaGraphSetConditional(h_reb, (kind == KIND_WEAK || kind == KIND_STRONG) ? 1u : 0u);
-  cudaGraphSetConditional(h_strong, kind == KIND_STRONG ? 1u : 0u);
+// Last block of a fused J evaluation: the Alg. 6 decision on the complete J.
+__device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec) {
+  __shared__ unsigned int last;
+  __shared__ int64_t smax[32];
+  if (!ec.s) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ec.ctr, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t mx = block_max_w(ec.W, ec.a.kc, smax);
+  if (threadIdx.x == 0) {
+    const int64_t J = (int64_t)atomicAdd((unsigned long long*)Jacc, 0ULL);
+    *Jacc = 0;
+    *ec.ctr = 0;
+    control_step(ec.s, mx, J, ec.a, ec.phase, ec.h, ec.use_h);
+  }
 }
+
+
 
 // Kernels run by one graph iteration: the fixed nodes plus the body of the
 // step that ran (the kind is recorded by k_control before it moves on).
@@ -938,15 +1200,20 @@ inline unsigned grid_for(const Ctx& c, int64_t items_per_block, int64_t n) {
 
 size_t conn_smem(const Ctx& c) { return (size_t)group_layout(c.topo).total * sizeof(int32_t); }
 
-void launch_eval(Ctx& c, int lvl) {
+// J of the current mapping of a level; with `ec`, the last block of the
+// low-degree pass also takes the Alg. 6 decision (the high-degree pass runs
+// first so that J is complete then).
+void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr) {
   Level& L = c.lv[lvl];
   c.prof_level = lvl;
-  cudaEvent_t ev = c.prof_begin();
-  k_eval_low<<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc); count_launch();
-  // xadj (8) + P(v) (4) per vertex; adjacency (4) + weight (4) + gathered P(u) (4) per entry
-  c.prof_end(ev, PK_EVAL, 12 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
   if (L.n_hi)
     k_eval_high<<<std::min(L.n_hi, c.num_sms * 8), kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc); count_launch();
+  cudaEvent_t ev = c.prof_begin();
+  const EvalCtl none{nullptr, nullptr, nullptr, CtlArgs{}, 0, 0, 0};
+  k_eval_tile<<<tile_grid(c, (const void*)k_eval_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc,
+                                                                                       ec ? *ec : none); count_launch();
+  // xadj (8) + P(v) (4) per vertex; adjacency (4) + weight (4) + gathered P(u) (4) per entry
+  c.prof_end(ev, PK_EVAL, 12 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
 }
 
 void launch_lp(Ctx& c, int lvl) {
@@ -955,7 +1222,8 @@ void launch_lp(Ctx& c, int lvl) {
   const unsigned gh = std::max(1, std::min(L.n_hi, c.num_sms * 8));
   c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
-  k_lp_gain_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, c.state); count_launch();
+  k_lp_gain_tile<<<tile_grid(c, (const void*)k_lp_gain_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.lock, c.pp, c.gain, c.inx, c.topo,
+                                                                c.state); count_launch();
   // per vertex: xadj 8, P 4, lock 1, X 1, P' 4, g 8; per entry: adjacency 4, weight 4, gathered P(u) 4
   c.prof_end(ev, PK_LP_GAIN, 26 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
   if (L.n_hi)
@@ -971,33 +1239,55 @@ void launch_lp(Ctx& c, int lvl) {
   k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.state); count_launch();
 }
 
-void launch_rebalance(Ctx& c, int lvl) {
+RebPrepArgs reb_prep_args(const Ctx& c) {
+  return RebPrepArgs{c.W, c.d_pe_of_code, c.topo, c.lmax, c.cV, c.cfg.sigma_gap, c.U, c.counters, c.accepted};
+}
+
+void launch_rebalance(Ctx& c, int lvl, bool prep_done = false) {
   Level& L = c.lv[lvl];
   const int64_t n = L.n;
-  k_reb_prep<<<1, 1024, 0, c.st>>>(c.W, c.d_pe_of_code, c.topo, c.lmax, c.cV, c.cfg.sigma_gap, c.U, c.counters,
-                                   c.accepted, c.state); count_launch();
-  RebArgs a{c.W, c.U, c.counters, c.lmax, c.cV, c.k, c.cfg.seed};
-  // per vertex: destination (c.dest), loss bucket (c.sel), eligibility (c.elig)
-  k_reb_select_low<<<grid_for(c, kThreads / kSubWarp, n), kThreads, 0, c.st>>>(view(L), L.pi, a, c.dest, c.sel, c.elig,
-                                                                                 c.state); count_launch();
+  uint8_t* bucket = c.sel;    // loss bucket per eligible vertex
+  uint8_t* selected = c.inx;  // selection flag per eligible vertex (X is free while rebalancing)
+  if (!prep_done) {
+    k_reb_prep<<<1, 1024, 0, c.st>>>(reb_prep_args(c), c.state); count_launch();
+  }
+  RebArgs a{c.W, c.U, c.counters, c.tab, c.lmax, c.cV, c.k, c.cfg.seed};
+  k_reb_select_low<<<grid_for(c, kThreads / kSubWarp, n), kThreads, 0, c.st>>>(view(L), L.pi, a, c.dest, bucket,
+                                                                                 c.elig, c.state); count_launch();
   if (L.n_hi)
     k_reb_select_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, (size_t)c.topo.kc * sizeof(int32_t),
-                        c.st>>>(view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, c.dest, c.sel, c.elig, c.state); count_launch();
-  // eligible vertices in id order -> (source block, bucket, id) order
-  int64_t* d_elig = c.counters + CNT_ELIG;
-  scan(LoadFlag{c.elig}, StoreKeyed{L.pi, c.sel, c.sort.key[0], c.sort.val[0]}, n, nullptr, c.scan, c.st);
-  k_copy_count<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_elig); count_launch();
-  const int bits = c.topo.code_bits + kBucketBits;
-  int cur = radix_sort_pairs(c.sort, n, d_elig, bits, c.st, &c.cap, &c.state->kernels);
-  scan(LoadSortedWeight{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_elig, c.scan, c.st);
+                        c.st>>>(view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, c.dest, bucket, c.elig, c.state); count_launch();
+  k_reb_cut<<<1, 1024, 0, c.st>>>(c.W, c.topo.kc, c.lmax, c.tab, c.bcut, c.rem, c.counters, c.state); count_launch();
+  const int idbits = bits_for_n(n);
+  const int bits = c.topo.code_bits + idbits;
   const unsigned g = grid_for(c, kThreads, n);
-  k_heads<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_elig, n, c.headP); count_launch();
-  // The bucket array (c.sel) is consumed by the scan above; the selection
-  // flags go to c.inx (free during rebalancing).
-  uint8_t* selflag = c.inx;
-  k_reb_mark<<<g, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_elig, n, c.W, c.lmax,
-                                       selflag); count_launch();
-  k_reb_apply_weak<<<g, kThreads, 0, c.st>>>(c.sort.val[cur], d_elig, n, selflag, c.dest, L.pi, L.vw, c.W, c.state); count_launch();
+  k_reb_classify<<<g, kThreads, 0, c.st>>>(L.n, L.pi, c.elig, bucket, c.bcut, c.rem, idbits, selected, c.sort.key[0],
+                                           c.sort.val[0], c.counters, c.state); count_launch();
+  cudaGraphConditionalHandle h = c.cap.on() ? cap_handle(c.st, 0) : 0;
+  k_reb_resolve<<<1, kSmallThreads, small_sort_smem(), c.st>>>(c.sort.key[0], c.sort.val[0], c.counters, bits, idbits,
+                                                               L.vw, c.rem, c.headP, selected, c.state, h,
+                                                               c.cap.on() ? 1 : 0); count_launch();
+  int64_t* d_list = c.counters + CNT_ELIG;
+  auto big = [&](cudaStream_t bs, unsigned long long* kcount, long long* body) {
+    cudaStream_t saved = c.st;
+    c.st = bs;
+    const int cur = radix_sort_pairs(c.sort, n, d_list, bits, bs);
+    scan(LoadSortedWeight{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_list, c.scan, bs);
+    k_heads_shift<<<g, kThreads, 0, bs>>>(c.sort.key[cur], c.P64, c.counters, idbits, c.headP); count_launch();
+    const unsigned long long bk = body ? (unsigned long long)(*body + 1) : 0ULL;
+    k_reb_mark_cut<<<g, kThreads, 0, bs>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, c.counters, idbits, c.rem,
+                                          selected, kcount, bk); count_launch();
+    c.st = saved;
+  };
+  if (c.cap.on()) {
+    long long body = 0;
+    long long* outer = set_capture_counter(&body);
+    cap_cond(c.cap, c.st, h, cudaGraphCondTypeIf, [&](cudaStream_t bs) { big(bs, &c.state->kernels, &body); });
+    set_capture_counter(outer);
+  } else {
+    big(c.st, nullptr, nullptr);
+  }
+  k_reb_apply_sel<<<g, kThreads, 0, c.st>>>(L.n, c.elig, selected, c.dest, L.pi, L.vw, c.W, c.state); count_launch();
 }
 
 __global__ void k_strong_gate(const RefineState* st, int64_t* d_sel) {
@@ -1057,8 +1347,14 @@ void refine_alloc(Ctx& c) {
   c.headP = c.mem.make<int64_t>(std::max(kc, n));
   c.Rb = c.mem.make<int64_t>(kc + 1);
   c.U = c.mem.make<int32_t>(kc);
+  c.tab = c.mem.make<int64_t>(kc * kBuckets);
+  c.bcut = c.mem.make<int32_t>(kc);
+  c.rem = c.mem.make<int64_t>(kc);
+  GM_CUDA(cudaMemsetAsync(c.tab, 0, kc * kBuckets * sizeof(int64_t), c.st));
   c.counters = c.mem.make<int64_t>(CNT_N);
   c.Jacc = c.mem.make<int64_t>(1);
+  c.evctr = reinterpret_cast<unsigned int*>(c.mem.make<int64_t>(1));
+  GM_CUDA(cudaMemsetAsync(c.evctr, 0, sizeof(int64_t), c.st));
   c.state = c.mem.make<RefineState>(1);
   c.trace_kind = c.mem.make<int32_t>(c.trace_cap);
   c.trace_J = c.mem.make<int64_t>(c.trace_cap);
@@ -1072,6 +1368,7 @@ void refine_alloc(Ctx& c) {
   if (smem > 48 * 1024) {
     GM_CUDA(cudaFuncSetAttribute(k_lp_gain_high, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
+  GM_CUDA(cudaFuncSetAttribute(k_reb_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_sort_smem()));
   if (kc * sizeof(int32_t) > 48 * 1024) {
     GM_CUDA(cudaFuncSetAttribute(k_reb_select_high, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kc * sizeof(int32_t))));
@@ -1146,9 +1443,9 @@ static void refine_stream(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* 
   *c.h_state = s;
   GM_CUDA(cudaMemcpyAsync(c.state, c.h_state, sizeof(RefineState), cudaMemcpyHostToDevice, c.st));
   GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), c.st));
-  launch_eval(c, lvl);
-  const CtlArgs ca = ctl_args(c);
-  k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 0, 0, 0); count_launch();
+  const EvalCtl ec0{c.state, c.evctr, c.W, ctl_args(c), 0, 0, 0};
+  const EvalCtl ec1{c.state, c.evctr, c.W, ctl_args(c), 1, 0, 0};
+  launch_eval(c, lvl, &ec0);
   const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
   while (true) {
     GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
@@ -1161,8 +1458,7 @@ static void refine_stream(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* 
       launch_rebalance(c, lvl);
       if (h.kind == KIND_STRONG) launch_rebalance_strong_tail(c, lvl);
     }
-    launch_eval(c, lvl);
-    k_control<<<1, 256, 0, c.st>>>(c.state, c.W, c.Jacc, ca, 1, 0, 0); count_launch();
+    launch_eval(c, lvl, &ec1);
     k_copy_best<<<gcopy, kThreads, 0, c.st>>>(c.state, L.pi, c.pi_best, L.n, IterCounts{0, 0, 0, 0}); count_launch();
     GM_CUDA(cudaGetLastError());
   }
@@ -1205,16 +1501,17 @@ static void build_refine_graph(Ctx& c, int lvl, int32_t rounds) {
     GM_CUDA(cudaMemcpyAsync(c.pi_best, L.pi, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, cs));
     k_state_init<<<1, 1, 0, cs>>>(c.state, rounds, lvl); count_launch();
     GM_CUDA(cudaMemsetAsync(c.Jacc, 0, sizeof(int64_t), cs));
-    launch_eval(c, lvl);
     cudaGraphConditionalHandle h_loop = cap_handle(cs, 0);
-    k_control<<<1, 256, 0, cs>>>(c.state, c.W, c.Jacc, ca, 0, h_loop, 1); count_launch();
+    const EvalCtl ec0{c.state, c.evctr, c.W, ca, 0, h_loop, 1};
+    const EvalCtl ec1{c.state, c.evctr, c.W, ca, 1, h_loop, 1};
+    launch_eval(c, lvl, &ec0);
     cap_cond(c.cap, cs, h_loop, cudaGraphCondTypeWhile, [&](cudaStream_t bs) {
       c.st = bs;
       set_capture_counter(&n_fixed);
       cudaGraphConditionalHandle h_lp = cap_handle(bs, 0), h_reb = cap_handle(bs, 0), h_strong = cap_handle(bs, 0);
       // counts of the bodies are known only after they are captured: the
       // decide node reads them from this iteration's parameters below
-      k_decide<<<1, 1, 0, bs>>>(c.state, h_lp, h_reb, h_strong); count_launch();
+      k_decide_prep<<<1, 1024, 0, bs>>>(c.state, h_lp, h_reb, h_strong, reb_prep_args(c)); count_launch();
       set_capture_counter(&n_lp);
       cap_cond(c.cap, bs, h_lp, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
         c.st = s2;
@@ -1223,7 +1520,7 @@ static void build_refine_graph(Ctx& c, int lvl, int32_t rounds) {
       set_capture_counter(&n_reb);
       cap_cond(c.cap, bs, h_reb, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
         c.st = s2;
-        launch_rebalance(c, lvl);
+        launch_rebalance(c, lvl, /*prep_done=*/true);
       });
       set_capture_counter(&n_strong);
       cap_cond(c.cap, bs, h_strong, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
@@ -1232,8 +1529,7 @@ static void build_refine_graph(Ctx& c, int lvl, int32_t rounds) {
       });
       set_capture_counter(&n_fixed);
       c.st = bs;
-      launch_eval(c, lvl);
-      k_control<<<1, 256, 0, bs>>>(c.state, c.W, c.Jacc, ca, 1, h_loop, 1); count_launch();
+      launch_eval(c, lvl, &ec1);
       // this node is the iteration's last: all body counts are known now
       const IterCounts ic{(unsigned long long)n_fixed + 1, (unsigned long long)n_lp, (unsigned long long)n_reb,
                           (unsigned long long)n_strong};
