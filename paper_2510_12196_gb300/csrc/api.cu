@@ -339,6 +339,7 @@ void map_destroy(map_ctx* ctx) {
     cudaStreamSynchronize(ctx->c.st);
     if (ctx->c.h_state) cudaFreeHost(ctx->c.h_state);
     if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
+    if (ctx->c.h_eng_job) cudaFreeHost(ctx->c.h_eng_job);
     for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
     for (auto& L : ctx->c.lv) {
       drop_graph(L);

@@ -186,6 +186,11 @@ struct Ctx {
   ClusterState* cstate = nullptr;
   ClusterState* h_cstate = nullptr;  // pinned mirror
 
+  // fused small-level engine
+  int eng_max_cluster = 0;
+  void* eng_job = nullptr;    // device job descriptor
+  void* h_eng_job = nullptr;  // pinned staging
+
   // resident blocks per SM of a kernel (occupancy API, cached)
   std::unordered_map<const void*, int> occ;
   int resident_blocks(const void* fn, int threads, size_t smem) {

@@ -32,7 +32,7 @@ struct GraphView {
 
 inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
 
-inline int bits_for_n(int64_t x) {  // smallest b with x <= 2^b
+__host__ __device__ inline int bits_for_n(int64_t x) {  // smallest b with x <= 2^b
   int b = 0;
   while (b < 62 && (1LL << b) < x) b++;
   return b;
@@ -1294,6 +1294,493 @@ __global__ void k_strong_gate(const RefineState* st, int64_t* d_sel) {
   if (st->kind != KIND_STRONG) *d_sel = 0;
 }
 
+// ---------------------------------------------------------------------------
+// Fused engine: the whole Alg. 6 run of one small level (or of every graph
+// of a batch, one cluster each) in a single launch of thread-block clusters.
+// The phases of an iteration are separated by cluster barriers instead of
+// kernel boundaries; one thread per vertex walks its row (rows have at most
+// kLowDeg entries here); the serial steps (sorts, cut, strong tail, the
+// controller) run in the cluster's first CTA.  Arrays written inside the
+// launch are read through plain pointers (no read-only path), and the
+// barriers order the phases across the cluster's SMs.
+// ---------------------------------------------------------------------------
+constexpr int kEngThreads = 1024;
+constexpr int kEngMaxN = 1 << 15;  // vertices handled by the fused engine
+constexpr int kEngMaxCluster = 16;
+
+struct EngineJob {
+  GraphView g;
+  int32_t* pi;
+  int32_t* pp;
+  int64_t* gain;
+  uint8_t* inx;
+  uint8_t* lock;
+  int32_t* best;
+  int32_t* dest;
+  uint8_t* elig;
+  uint8_t* bkt;
+  uint8_t* sel;
+  uint8_t* acc;
+  int64_t* sarr;
+  int64_t* P;  // [n + 1]
+  int64_t* W;
+  int64_t* accepted;
+  int32_t* U;
+  int64_t* tab;
+  int32_t* bcut;
+  int64_t* rem;
+  int64_t* headP;
+  int64_t* Rb;
+  uint64_t* key0;
+  int32_t* val0;
+  uint64_t* key1;
+  int32_t* val1;
+  int64_t* cnt;
+  int64_t* Jacc;
+  RefineState* s;
+  const int32_t* pe_of_code;
+  Topo topo;
+  CtlArgs ctl;
+  int64_t lmax;
+  int64_t cV;
+  uint64_t seed;
+  int32_t k;
+  int32_t sigma_gap;
+  int32_t level;
+  int32_t rounds;
+};
+
+struct PlainRow {  // neighbour PEs through plain loads (the mapping changes inside the launch)
+  const int32_t* __restrict__ adj;
+  const int32_t* __restrict__ adjw;
+  const int32_t* pi;
+  __device__ __forceinline__ int32_t code(int j) const { return pi[adj[j]]; }
+  __device__ __forceinline__ int32_t weight(int j) const { return adjw[j]; }
+};
+
+__device__ __forceinline__ void eng_sync() { cg::this_cluster().sync(); }
+
+// block-wide exclusive scan over chunks of blockDim values: f(i) for i < n,
+// out(i, exclusive, value); returns the total (all threads)
+template <class F, class O>
+__device__ int64_t cta_scan(int64_t n, F f, O out, int64_t* sm) {
+  int64_t carry = 0;
+  for (int64_t base = 0; base < n; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t x = i < n ? f(i) : 0;
+    int64_t tot;
+    const int64_t e = block_exclusive_scan(x, sm, &tot);
+    if (i < n) out(i, carry + e, x);
+    carry += tot;
+  }
+  return carry;
+}
+
+struct EngSmem {
+  int32_t hist[256];
+  int32_t ctot[256];
+  int32_t wcnt[32 * 256];
+  int64_t sm[33];
+  int32_t sdist[32];
+  int64_t smax[32];
+};
+
+// Stable LSD radix sort (8-bit digits) of n pairs by one CTA through global
+// buffers: per pass a digit histogram, then chunks of blockDim elements in
+// index order, ranked within the chunk by warp matching.  Returns 0 or 1,
+// the buffer holding the result.
+__device__ int cta_sort_global(uint64_t* k0, int32_t* v0, uint64_t* k1, int32_t* v1, int n, int bits, EngSmem& S) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const unsigned lt = (1u << l) - 1u;
+  const int nw = blockDim.x >> 5;
+  uint64_t* K[2] = {k0, k1};
+  int32_t* V[2] = {v0, v1};
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) S.hist[d] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&S.hist[(int)((K[cur][i] >> shift) & 255u)], 1);
+    __syncthreads();
+    {
+      const int64_t x = threadIdx.x < 256 ? S.hist[threadIdx.x] : 0;
+      int64_t tot;
+      const int64_t e = block_exclusive_scan(x, S.sm, &tot);
+      if (threadIdx.x < 256) S.hist[threadIdx.x] = (int32_t)e;  // running offset of each digit
+    }
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+      for (int i = threadIdx.x; i < nw * 256; i += blockDim.x) S.wcnt[i] = 0;
+      __syncthreads();
+      const int i = base + threadIdx.x;
+      const bool valid = i < n;
+      const uint64_t key = valid ? K[cur][i] : 0;
+      const int32_t val = valid ? V[cur][i] : 0;
+      const int d = valid ? (int)((key >> shift) & 255u) : 256 + l;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int r = __popc(peers & lt);
+      if (valid && (peers & lt) == 0) S.wcnt[w * 256 + d] = __popc(peers);
+      __syncthreads();
+      if (threadIdx.x < 256) {
+        int32_t run = 0;
+        for (int ww = 0; ww < nw; ww++) {
+          const int32_t t = S.wcnt[ww * 256 + threadIdx.x];
+          S.wcnt[ww * 256 + threadIdx.x] = run;
+          run += t;
+        }
+        S.ctot[threadIdx.x] = run;
+      }
+      __syncthreads();
+      if (valid) {
+        const int pos = S.hist[d] + S.wcnt[w * 256 + d] + r;
+        K[cur ^ 1][pos] = key;
+        V[cur ^ 1][pos] = val;
+      }
+      __syncthreads();
+      if (threadIdx.x < 256) S.hist[threadIdx.x] += S.ctot[threadIdx.x];
+      __syncthreads();
+    }
+    cur ^= 1;
+  }
+  return cur;
+}
+
+// Alg. 5 destination of one vertex (thread level): edge-cut gain, lowest id
+// on ties, the random-block fallback; returns false if the vertex cannot move.
+__device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int64_t nU, int32_t t, int32_t& dst,
+                               int32_t& bucket) {
+  const GraphView& g = J.g;
+  const int32_t A = J.pi[v];
+  const int64_t WA = J.W[A];
+  if (WA <= J.lmax) return false;
+  if (2 * (int64_t)J.k * g.vw[v] > 3 * ((int64_t)J.k * WA - J.cV)) return false;
+  const int64_t b = g.xadj[v], e = g.xadj[v + 1];
+  int32_t connA = 0, bconn = -1, bc = INT32_MAX;
+  for (int64_t x = b; x < e; x++) {
+    const int32_t c = J.pi[g.adj[x]];
+    if (c == A) {
+      connA += g.adjw[x];
+      continue;
+    }
+    if (J.W[c] > sigma) continue;
+    bool seen = false;
+    for (int64_t y = b; y < x; y++)
+      if (J.pi[g.adj[y]] == c) {
+        seen = true;
+        break;
+      }
+    if (seen) continue;
+    int32_t cc = 0;
+    for (int64_t y = x; y < e; y++) cc += (J.pi[g.adj[y]] == c) ? g.adjw[y] : 0;
+    if (cc > bconn || (cc == bconn && c < bc)) {
+      bconn = cc;
+      bc = c;
+    }
+  }
+  int64_t gcut;
+  if (bconn >= 0) {
+    gcut = (int64_t)bconn - connA;
+  } else if (nU > 0) {
+    bc = J.U[h_rebalance(J.seed, J.level, t, v) % (uint64_t)nU];
+    gcut = -(int64_t)connA;
+  } else {
+    return false;
+  }
+  dst = bc;
+  bucket = loss_bucket(gcut);
+  return true;
+}
+
+__global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __restrict__ jobs) {
+  __shared__ EngSmem S;
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const EngineJob& J = jobs[blockIdx.x / csize];
+  const GraphView& g = J.g;
+  const int32_t n = g.n;
+  const int64_t gt = (int64_t)crank * blockDim.x + threadIdx.x;
+  const int64_t GT = (int64_t)csize * blockDim.x;
+  const bool lead = crank == 0;
+  RefineState* s = J.s;
+  load_sdist(S.sdist, J.topo);
+  __syncthreads();
+
+  // --- initial state: block weights, locks, best copy, J, controller ---
+  if (lead)
+    for (int32_t b = threadIdx.x; b < J.topo.kc; b += blockDim.x) J.W[b] = 0;
+  if (lead && threadIdx.x == 0) {
+    RefineState z{};
+    z.rounds = J.rounds;
+    z.level = J.level;
+    *s = z;
+    *J.Jacc = 0;
+  }
+  eng_sync();
+  for (int64_t v = gt; v < n; v += GT) {
+    atomicAdd((unsigned long long*)&J.W[J.pi[v]], (unsigned long long)(int64_t)g.vw[v]);
+    J.lock[v] = 0;
+    J.best[v] = J.pi[v];
+  }
+  int phase = 0;
+  while (true) {
+    // J of the current mapping, then the Alg. 6 decision
+    int64_t acc = 0;
+    for (int64_t v = gt; v < n; v += GT) {
+      const int64_t b = g.xadj[v];
+      acc += row_cost(PlainRow{g.adj + b, g.adjw + b, J.pi}, (int)(g.xadj[v + 1] - b), S.sdist, J.pi[v]);
+    }
+    acc = block_sum(acc, S.sm);
+    if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
+    eng_sync();
+    if (lead) {
+      const int64_t mx = block_max_w(J.W, J.topo.kc, S.smax);
+      if (threadIdx.x == 0) {
+        const int64_t Jv = *(volatile int64_t*)J.Jacc;
+        *J.Jacc = 0;
+        control_step(s, mx, Jv, J.ctl, phase, 0, 0);
+      }
+    }
+    eng_sync();
+    const int32_t done = *(volatile int32_t*)&s->done;
+    const int32_t kind = *(volatile int32_t*)&s->kind;
+    const int32_t copy = *(volatile int32_t*)&s->copy_best;
+    if (copy)
+      for (int64_t v = gt; v < n; v += GT) J.best[v] = J.pi[v];
+    if (done) break;
+    phase = 1;
+    if (kind == KIND_LP) {
+      // Alg. 4 step 1
+      for (int64_t v = gt; v < n; v += GT) {
+        const int32_t p = J.pi[v];
+        bool in = false;
+        int32_t bc = p;
+        int64_t G = 0;
+        if (J.lock[v]) {
+          J.lock[v] = 0;
+        } else {
+          const int64_t b = g.xadj[v];
+          const int deg = (int)(g.xadj[v + 1] - b);
+          const PlainRow r{g.adj + b, g.adjw + b, J.pi};
+          int64_t bt;
+          if (best_target(r, deg, p, S.sdist, bc, bt)) {
+            G = row_cost(r, deg, S.sdist, p) - bt;
+            in = G >= 0;
+          }
+        }
+        J.inx[v] = in ? 1 : 0;
+        J.pp[v] = in ? bc : p;
+        J.gain[v] = in ? G : 0;
+      }
+      eng_sync();
+      // step 2: recomputed gain under ord
+      for (int64_t v = gt; v < n; v += GT) {
+        if (!J.inx[v]) continue;
+        const int32_t p = J.pi[v], q = J.pp[v];
+        const int64_t gv = J.gain[v];
+        int64_t sum = 0;
+        for (int64_t x = g.xadj[v]; x < g.xadj[v + 1]; x++) {
+          const int32_t u = g.adj[x];
+          int32_t bu = J.pi[u];
+          if (J.inx[u]) {
+            const int64_t gu = J.gain[u];
+            if (gu > gv || (gu == gv && u < v)) bu = J.pp[u];
+          }
+          sum += (int64_t)g.adjw[x] * (dcode(S.sdist, p, bu) - dcode(S.sdist, q, bu));
+        }
+        if (sum >= 0) J.lock[v] = 1;
+      }
+      eng_sync();
+      // step 3: simultaneous move of M
+      for (int64_t v = gt; v < n; v += GT) {
+        if (!J.lock[v]) continue;
+        const int32_t p = J.pi[v], q = J.pp[v];
+        const int64_t c = g.vw[v];
+        J.pi[v] = q;
+        atomicAdd((unsigned long long*)&J.W[p], (unsigned long long)(-c));
+        atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
+      }
+      eng_sync();
+      continue;
+    }
+    // --- weak / strong rebalancing ---
+    const bool strong = kind == KIND_STRONG;
+    const int32_t t = *(volatile int32_t*)&s->t;
+    if (lead) {
+      const RebPrepArgs pa{J.W, J.pe_of_code, J.topo, J.lmax, J.cV, J.sigma_gap, J.U, J.cnt, J.accepted};
+      reb_prep_body(pa, strong);
+    }
+    eng_sync();
+    const int64_t sigma = *(volatile int64_t*)&J.cnt[CNT_SIGMA];
+    const int64_t nU = *(volatile int64_t*)&J.cnt[CNT_NU];
+    for (int64_t v = gt; v < n; v += GT) {
+      int32_t dst, bk;
+      const bool ok = eng_reb_select(J, (int32_t)v, sigma, nU, t, dst, bk);
+      J.elig[v] = ok ? 1 : 0;
+      if (ok) {
+        J.dest[v] = dst;
+        J.bkt[v] = (uint8_t)bk;
+        atomicAdd((unsigned long long*)&J.tab[(int64_t)J.pi[v] * kBuckets + bk],
+                  (unsigned long long)(int64_t)g.vw[v]);
+      }
+    }
+    eng_sync();
+    if (lead) {  // the cut bucket of each overloaded block
+      for (int32_t A = threadIdx.x; A < J.topo.kc; A += blockDim.x) {
+        if (J.W[A] <= J.lmax) continue;
+        const int64_t E = J.W[A] - J.lmax;
+        int64_t cum = 0, r = 0;
+        int32_t cut = kBuckets;
+        for (int bb = 0; bb < kBuckets; bb++) {
+          const int64_t tt = J.tab[(int64_t)A * kBuckets + bb];
+          J.tab[(int64_t)A * kBuckets + bb] = 0;
+          if (cut == kBuckets) {
+            if (cum + tt <= E) {
+              cum += tt;
+            } else {
+              cut = bb;
+              r = E - cum;
+            }
+          }
+        }
+        J.bcut[A] = cut;
+        J.rem[A] = r;
+      }
+      if (threadIdx.x == 0) J.cnt[CNT_ELIG] = 0;
+    }
+    eng_sync();
+    const int idbits = bits_for_n(n);
+    for (int64_t v = gt; v < n; v += GT) {
+      if (!J.elig[v]) continue;
+      const int32_t A = J.pi[v];
+      const int32_t bb = J.bkt[v], cut = J.bcut[A];
+      if (bb != cut) {
+        J.sel[v] = bb < cut ? 1 : 0;
+        continue;
+      }
+      J.sel[v] = 0;
+      if (J.rem[A] > 0) {
+        const unsigned long long i = atomicAdd((unsigned long long*)&J.cnt[CNT_ELIG], 1ULL);
+        J.key0[i] = ((uint64_t)(uint32_t)A << idbits) | (uint64_t)v;
+        J.val0[i] = (int32_t)v;
+      }
+    }
+    eng_sync();
+    if (lead) {  // the cut-bucket list by (block, id), per-block prefix
+      const int ln = (int)*(volatile int64_t*)&J.cnt[CNT_ELIG];
+      if (ln > 0) {
+        const int cur = cta_sort_global(J.key0, J.val0, J.key1, J.val1, ln, J.topo.code_bits + idbits, S);
+        const uint64_t* K = cur ? J.key1 : J.key0;
+        const int32_t* V = cur ? J.val1 : J.val0;
+        cta_scan(
+            ln, [&](int64_t i) { return (int64_t)g.vw[V[i]]; },
+            [&](int64_t i, int64_t e, int64_t) {
+              J.P[i] = e;
+              if (i == 0 || (K[i] >> idbits) != (K[i - 1] >> idbits)) J.headP[K[i] >> idbits] = e;
+            },
+            S.sm);
+        __syncthreads();
+        for (int i = threadIdx.x; i < ln; i += blockDim.x) {
+          const int32_t A = (int32_t)(K[i] >> idbits);
+          J.sel[V[i]] = (J.P[i] - J.headP[A] < J.rem[A]) ? 1 : 0;
+        }
+      }
+    }
+    eng_sync();
+    if (!strong) {
+      for (int64_t v = gt; v < n; v += GT) {
+        if (!J.elig[v] || !J.sel[v]) continue;
+        const int32_t p = J.pi[v], q = J.dest[v];
+        const int64_t c = g.vw[v];
+        J.pi[v] = q;
+        atomicAdd((unsigned long long*)&J.W[p], (unsigned long long)(-c));
+        atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
+      }
+      eng_sync();
+      continue;
+    }
+    if (lead) {  // strong: destinations in (bucket, id) order, acceptance, water-filling
+      const int64_t ns = cta_scan(
+          n, [&](int64_t v) { return (int64_t)((J.elig[v] && J.sel[v]) ? 1 : 0); },
+          [&](int64_t v, int64_t e, int64_t x) {
+            if (x) {
+              J.key0[e] = ((uint64_t)(uint32_t)J.dest[v] << kBucketBits) | J.bkt[v];
+              J.val0[e] = (int32_t)v;
+            }
+          },
+          S.sm);
+      __syncthreads();
+      const int cur = ns ? cta_sort_global(J.key0, J.val0, J.key1, J.val1, (int)ns,
+                                           J.topo.code_bits + kBucketBits, S)
+                         : 0;
+      const uint64_t* K = cur ? J.key1 : J.key0;
+      const int32_t* V = cur ? J.val1 : J.val0;
+      cta_scan(
+          ns, [&](int64_t i) { return (int64_t)g.vw[V[i]]; },
+          [&](int64_t i, int64_t e, int64_t) {
+            J.P[i] = e;
+            if (i == 0 || (K[i] >> kBucketBits) != (K[i - 1] >> kBucketBits)) J.headP[K[i] >> kBucketBits] = e;
+          },
+          S.sm);
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int32_t d = (int32_t)(K[i] >> kBucketBits);
+        const int32_t v = V[i];
+        const int64_t inc = J.P[i] + g.vw[v] - J.headP[d];
+        const bool ok = J.W[d] + inc <= J.lmax;
+        J.acc[v] = ok ? 1 : 0;
+        if (ok) atomicAdd((unsigned long long*)&J.accepted[d], (unsigned long long)(int64_t)g.vw[v]);
+      }
+      __syncthreads();
+      cta_scan(
+          n,
+          [&](int64_t v) { return (J.elig[v] && J.sel[v] && !J.acc[v]) ? (int64_t)g.vw[v] : (int64_t)0; },
+          [&](int64_t v, int64_t e, int64_t x) {
+            if (x) J.sarr[v] = e;
+          },
+          S.sm);
+      const int32_t kc = J.topo.kc;
+      const int64_t tot = cta_scan(
+          kc,
+          [&](int64_t b) {
+            int64_t r = 0;
+            if (J.pe_of_code[b] >= 0 && J.W[b] <= J.lmax) {
+              r = J.lmax - J.W[b] - J.accepted[b];
+              if (r < 0) r = 0;
+            }
+            return r;
+          },
+          [&](int64_t b, int64_t e, int64_t) { J.Rb[b] = e; }, S.sm);
+      if (threadIdx.x == 0) J.Rb[kc] = tot;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int32_t v = V[i];
+        const int64_t c = g.vw[v];
+        int32_t q = -1;
+        if (J.acc[v]) {
+          q = (int32_t)(K[i] >> kBucketBits);
+        } else {
+          const int64_t sv = J.sarr[v];
+          int32_t lo = 0, hi = kc + 1;
+          while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (J.Rb[mid] <= sv) lo = mid + 1;
+            else hi = mid;
+          }
+          const int32_t bb = lo - 1;
+          if (bb >= 0 && bb < kc && sv + c <= J.Rb[bb + 1]) q = bb;
+        }
+        if (q < 0) continue;
+        const int32_t p = J.pi[v];
+        J.pi[v] = q;
+        atomicAdd((unsigned long long*)&J.W[p], (unsigned long long)(-c));
+        atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
+      }
+    }
+    eng_sync();
+  }
+  for (int64_t v = gt; v < n; v += GT) J.pi[v] = J.best[v];
+}
+
 }  // namespace
 
 // The strong variant continues from the selection made by launch_rebalance:
@@ -1576,8 +2063,121 @@ static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* m
   if (iters) *iters = h.t;
 }
 
+// Cluster size of the fused engine for a level of n vertices (0: not used).
+static int engine_cluster(Ctx& c, const Level& L) {
+  if (!c.use_graphs || c.prof || L.n > kEngMaxN || L.n_hi > 0) return 0;
+  int C = (L.n + 2047) / 2048;
+  if (C < 1) C = 1;
+  if (C > c.eng_max_cluster) C = c.eng_max_cluster;
+  return C;
+}
+
+static void engine_setup(Ctx& c) {
+  if (c.eng_max_cluster > 0) return;
+  int C = 8;
+  if (cudaFuncSetAttribute(k_engine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kEngMaxCluster);
+    cfg.blockDim = dim3(kEngThreads);
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kEngMaxCluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_engine, &cfg) == cudaSuccess && nclusters > 0)
+      C = kEngMaxCluster;
+  }
+  cudaGetLastError();
+  c.eng_max_cluster = C;
+  if (!c.eng_job) {
+    c.eng_job = c.mem.make<EngineJob>(1);
+    GM_CUDA(cudaMallocHost(&c.h_eng_job, sizeof(EngineJob)));
+  }
+}
+
+static EngineJob engine_job(Ctx& c, int lvl, int32_t rounds) {
+  Level& L = c.lv[lvl];
+  EngineJob j{};
+  j.g = view(L);
+  j.pi = L.pi;
+  j.pp = c.pp;
+  j.gain = c.gain;
+  j.inx = c.inx;
+  j.lock = c.lock;
+  j.best = c.pi_best;
+  j.dest = c.dest;
+  j.elig = c.elig;
+  j.bkt = c.sel;
+  j.sel = c.inx;
+  j.acc = c.acc;
+  j.sarr = c.sarr;
+  j.P = c.P64;
+  j.W = c.W;
+  j.accepted = c.accepted;
+  j.U = c.U;
+  j.tab = c.tab;
+  j.bcut = c.bcut;
+  j.rem = c.rem;
+  j.headP = c.headP;
+  j.Rb = c.Rb;
+  j.key0 = c.sort.key[0];
+  j.val0 = c.sort.val[0];
+  j.key1 = c.sort.key[1];
+  j.val1 = c.sort.val[1];
+  j.cnt = c.counters;
+  j.Jacc = c.Jacc;
+  j.s = c.state;
+  j.pe_of_code = c.d_pe_of_code;
+  j.topo = c.topo;
+  j.ctl = ctl_args(c);
+  j.lmax = c.lmax;
+  j.cV = c.cV;
+  j.seed = c.cfg.seed;
+  j.k = c.k;
+  j.sigma_gap = c.cfg.sigma_gap;
+  j.level = lvl;
+  j.rounds = rounds;
+  return j;
+}
+
+static void launch_engine(Ctx& c, const EngineJob* d_jobs, int njobs, int C) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(C * njobs));
+  cfg.blockDim = dim3(kEngThreads);
+  cfg.stream = c.st;
+  cudaLaunchAttribute attr{};
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)C;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  GM_CUDA(cudaLaunchKernelEx(&cfg, k_engine, d_jobs));
+  count_launch();
+}
+
+static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, int64_t* maxw, int32_t* iters) {
+  *static_cast<EngineJob*>(c.h_eng_job) = engine_job(c, lvl, rounds);
+  GM_CUDA(cudaMemcpyAsync(c.eng_job, c.h_eng_job, sizeof(EngineJob), cudaMemcpyHostToDevice, c.st));
+  launch_engine(c, static_cast<const EngineJob*>(c.eng_job), 1, C);
+  GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  const RefineState h = *c.h_state;
+  if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
+  c.last_iters = h.t;
+  if (J) *J = h.best_J;
+  if (maxw) *maxw = h.best_maxw;
+  if (iters) *iters = h.t;
+}
+
 void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
-  if (c.use_graphs && !c.prof) refine_graph(c, lvl, rounds, J, maxw, iters);
+  engine_setup(c);
+  const int C = engine_cluster(c, c.lv[lvl]);
+  if (C > 0) refine_engine(c, lvl, rounds, C, J, maxw, iters);
+  else if (c.use_graphs && !c.prof) refine_graph(c, lvl, rounds, J, maxw, iters);
   else refine_stream(c, lvl, rounds, J, maxw, iters);
 }
 
