@@ -86,6 +86,8 @@ typedef struct {
   map_free_fn free;
   void* alloc_user;
   int32_t launch_mode;   /* 0: refinement and clustering loops as CUDA graphs (default); 1: stream launches */
+  int32_t engine_max_n;  /* levels with at most this many vertices (and no vertex of degree > 128) are refined
+                            by the fused one-launch engine; 0: library default (32768); -1: never */
 } map_config;
 
 typedef struct {
@@ -96,6 +98,7 @@ typedef struct {
   int32_t iters[65];       /* Alg. 6 iterations per level (map_run) */
   double ms_coarsen, ms_initial, ms_refine, ms_project;  /* host wall time per phase */
   int64_t device_bytes;    /* device memory held by the context */
+  int64_t device_bytes_peak; /* largest device memory the context has held */
 } map_stats_t;
 
 /* Fills *cfg with the defaults listed above (seed 0x5EED0000, no allocator). */
@@ -262,6 +265,149 @@ GPUMAP_API long long map_launch_count(void);
 GPUMAP_API map_status map_objective_noalloc(const int64_t* xadj, const int32_t* adjncy, const int32_t* adjwgt,
                                             const int32_t* vwgt, int32_t n, const int32_t* pi, const int32_t* hier,
                                             const int32_t* dist, int32_t levels, int64_t* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched refinement.  The paper refines one graph at a time; it has no
+ * batched mode.  Here many contexts (graphs of uneven size, each with its own
+ * hierarchy, distances and eps) are refined in ONE persistent kernel launch,
+ * captured in a CUDA graph on the first map_batch_launch and replayed by
+ * later ones: every job runs Alg. 6 on one level of its context (after
+ * map_set_mapping, map_initial or map_project put a mapping there) from start
+ * to end on one cluster of thread blocks, and the clusters take the jobs
+ * largest first.  The result of each job is identical to map_refine(ctx,
+ * level, rounds) on the same context, whatever the schedule.
+ *
+ * The schedule (CTAs per job and staged CSR entries per warp tile) is picked
+ * by timing every candidate on the batch itself during the first launch (the
+ * jobs' mappings are saved and restored around the trials) and cached per
+ * batch shape for the rest of the process; autotune = 0 takes `cluster` and
+ * `tile_entries` instead (0: a size-based default).
+ *
+ * Limits: all contexts on the current device, no context twice, and no
+ * vertex of degree > 128 on the refined level (MAP_E_INVALID: refine such a
+ * job with map_refine).  The batch keeps pointers into the contexts: destroy
+ * it before them, and do not run map_coarsen on a job (which may move its
+ * level buffers) while the batch exists.  The launch is asynchronous on the
+ * stream given at creation; it waits for the jobs' pending work on their own
+ * streams, and their later work waits for it.  map_batch_results
+ * synchronises and returns the jobs' best J, maximum block weight and
+ * iteration count in the order of `jobs`; afterwards map_get_mapping(job,
+ * level) returns each job's refined mapping.  Errors of map_batch_create are
+ * read with map_batch_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+typedef struct map_batch map_batch;
+
+typedef struct {
+  int32_t level;         /* level refined in every job (0 = input graph) */
+  int32_t rounds;        /* > 0: exactly that many Alg. 6 iterations; -1: Alg. 6 termination */
+  int32_t autotune;      /* 1 (default): time the candidate schedules on the first launch */
+  int32_t cluster;       /* autotune 0: CTAs per job, 1, 2, 4, 8 or 16; 0: size-based default */
+  int32_t tile_entries;  /* autotune 0: staged CSR entries per warp tile, 256 or 512; 0: 512 */
+} map_batch_opts;
+
+/* level 0, rounds 10, autotune 1, the rest 0. */
+GPUMAP_API void map_batch_opts_default(map_batch_opts* opts);
+GPUMAP_API map_status map_batch_create(map_ctx* const* jobs, int32_t njobs, const map_batch_opts* opts,
+                                       void* cuda_stream, map_batch** out);
+GPUMAP_API map_status map_batch_launch(map_batch* batch);
+/* Host arrays of njobs entries each (any may be NULL); MAP_E_TIMEOUT if a job
+ * stopped at the iteration cap. */
+GPUMAP_API map_status map_batch_results(map_batch* batch, int64_t* J, int64_t* max_block_weight, int32_t* iters);
+/* The schedule in use (after the first launch): CTAs per job, staged entries
+ * per warp tile, clusters in the persistent grid, and the wall time the
+ * autotuner spent (0 when the schedule came from the cache or the options). */
+GPUMAP_API map_status map_batch_schedule(const map_batch* batch, int32_t* cluster, int32_t* tile_entries,
+                                         int32_t* clusters, double* tune_ms);
+GPUMAP_API const char* map_batch_last_error(const map_batch* batch);
+GPUMAP_API void map_batch_destroy(map_batch* batch);
+
+/* ------------------------------------------------------------------------
+ * Serving.  The paper maps one graph per program run; it has no serving
+ * mode.  A server runs a request loop: submitted jobs wait in a queue and are
+ * admitted by device memory; `slots` worker threads, each with its own CUDA
+ * stream, run the admitted jobs concurrently, so a request that arrives while
+ * others are on the GPU starts as soon as a slot and memory are free and its
+ * kernels overlap with theirs (continuous batching).  A job is admissible
+ * when the estimated device bytes of the running jobs plus its own
+ * (map_job_estimate_bytes) fit in `mem_budget`; a job that alone exceeds the
+ * budget starts only when nothing else runs.  Admission examines the oldest
+ * `lookahead` queued jobs in arrival order, so a small job may overtake a
+ * large one that does not fit yet; after the oldest job has been overtaken
+ * 4 x lookahead times, admission is in strict arrival order until it starts.
+ * A job is the whole pipeline: map_create from host buffers, map_run,
+ * download of the mapping, map_destroy; its result equals the one it has
+ * when run alone.  The job's host buffers are read while it runs: keep them
+ * valid until map_server_wait returns it.  All calls are thread-safe; do not
+ * call any of them on a server after map_server_destroy.
+ * ------------------------------------------------------------------------ */
+typedef struct map_server map_server;
+
+typedef struct {
+  const int64_t* xadj;        /* host CSR as for map_create (inputs_on_device = 0) */
+  const int32_t* adjncy;
+  const int32_t* adjwgt;      /* NULL: unit weights */
+  const int32_t* vwgt;        /* NULL: unit weights */
+  int32_t n;
+  const int32_t* hier;        /* copied at submission */
+  const int32_t* dist;        /* copied at submission */
+  int32_t levels;
+  double eps;
+  const map_config* cfg;      /* copied at submission; NULL: map_config_default */
+  int32_t* out_pi;            /* host, n entries (PE ids); NULL: not downloaded */
+  void* user;                 /* returned in the result */
+} map_job;
+
+typedef struct {
+  uint64_t ticket;
+  map_status status;          /* of the job's pipeline */
+  int32_t levels;
+  int64_t J;
+  int64_t device_bytes_est;   /* estimate used for admission */
+  int64_t device_bytes_peak;  /* what the job's context held at most */
+  double t_submit_ms, t_start_ms, t_done_ms;  /* milliseconds since map_server_create */
+  void* user;
+  char error[256];
+} map_job_result;
+
+/* Replaces the pipeline of every job (a dry run, or a test of the request
+ * loop without a GPU): called on a worker thread with the worker's stream
+ * (NULL when a runner is set); returns the job's status and may fill J and
+ * levels of *out. */
+typedef int32_t (*map_job_runner)(const map_job* job, void* stream, void* user, map_job_result* out);
+
+typedef struct {
+  int32_t slots;              /* jobs running at once (worker threads); 0: 8 */
+  int32_t lookahead;          /* queued jobs examined for admission; 0: 8 (1: strict arrival order) */
+  int64_t mem_budget;         /* device bytes for the running jobs; 0: 90% of the free memory at creation */
+  map_job_runner runner;      /* NULL: the mapping pipeline */
+  void* runner_user;
+} map_server_opts;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t queued, running;
+  int64_t bytes_in_flight, peak_bytes_in_flight, mem_budget;
+  int32_t peak_running;
+  double uptime_ms;
+} map_server_stats_t;
+
+/* slots 8, lookahead 8, mem_budget 0 (automatic), no runner. */
+GPUMAP_API void map_server_opts_default(map_server_opts* opts);
+/* Device bytes a job's context may hold (an upper estimate for graphs whose
+ * coarser levels together hold at most twice the input's CSR entries, which
+ * covers grids, geometric and R-MAT graphs); -1 on bad arguments. */
+GPUMAP_API int64_t map_job_estimate_bytes(int32_t n, int64_t m_dir, const int32_t* hier, int32_t levels);
+GPUMAP_API map_status map_server_create(const map_server_opts* opts, map_server** out);
+GPUMAP_API map_status map_server_submit(map_server* server, const map_job* job, uint64_t* ticket);
+/* Waits for the job (timeout_ms < 0: without limit; MAP_E_TIMEOUT when the
+ * limit passes first), copies its result to *out and retires the ticket. */
+GPUMAP_API map_status map_server_wait(map_server* server, uint64_t ticket, double timeout_ms, map_job_result* out);
+GPUMAP_API map_status map_server_poll(map_server* server, uint64_t ticket, int32_t* done);
+GPUMAP_API map_status map_server_stats(map_server* server, map_server_stats_t* out);
+GPUMAP_API const char* map_server_last_error(const map_server* server);
+/* Lets running jobs finish, cancels queued ones (status MAP_E_STATE), joins
+ * the workers and frees the server. */
+GPUMAP_API void map_server_destroy(map_server* server);
 
 #ifdef __cplusplus
 }

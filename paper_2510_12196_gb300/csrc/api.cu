@@ -9,10 +9,6 @@
 
 #include "engine.h"
 
-struct map_ctx {
-  gm::Ctx c;
-};
-
 namespace gm {
 
 void* DevMem::get(size_t bytes) {
@@ -32,6 +28,7 @@ void* DevMem::get(size_t bytes) {
   }
   blocks.push_back({p, bytes});
   total += bytes;
+  peak = std::max(peak, total);
   return p;
 }
 
@@ -243,6 +240,7 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       throw ApiError(MAP_E_INVALID, "map_config field out of range");
     if (c.cfg.launch_mode < 0 || c.cfg.launch_mode > 1) throw ApiError(MAP_E_INVALID, "launch_mode must be 0 or 1");
     c.use_graphs = c.cfg.launch_mode == 0;
+    if (c.cfg.engine_max_n < -1) throw ApiError(MAP_E_INVALID, "engine_max_n must be >= -1");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     for (auto& cs : c.cap.s) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -580,6 +578,7 @@ map_status map_stats(map_ctx* ctx, map_stats_t* out) {
     out->ms_refine = c.ms_refine;
     out->ms_project = c.ms_project;
     out->device_bytes = (int64_t)c.mem.total;
+    out->device_bytes_peak = (int64_t)c.mem.peak;
   });
 }
 

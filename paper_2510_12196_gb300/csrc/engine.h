@@ -81,6 +81,7 @@ struct Level {
   int32_t* hi = nullptr;       // vertices of degree > kLowDeg, ascending
   int32_t n_hi = 0;
   int64_t m_hi = 0;            // CSR entries of the high-degree vertices
+  int64_t max_deg = 0;         // largest degree (0 when n_hi == 0, i.e. at most kLowDeg)
   int64_t* hi_off = nullptr;   // hash-table offsets of the high-degree vertices (n_hi + 1)
   int64_t hi_slots = 0;
   int32_t max_vw = 0;
@@ -106,6 +107,7 @@ struct DevMem {
   };
   std::vector<Block> blocks;
   size_t total = 0;
+  size_t peak = 0;  // largest `total` so far
   void* get(size_t bytes);
   void put(void* p);
   void release_all();
@@ -231,6 +233,13 @@ int32_t lp_step(Ctx& c, int lvl);
 int32_t rebalance_step(Ctx& c, int lvl, bool strong, int32_t t);
 void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters);
 void classify_degrees(Ctx& c, int lvl);
+
+// Fused refinement engine (one cluster of CTAs per job), shared with the
+// batch entry points.
+int engine_max_clusters(int C, int te);  // resident clusters of C CTAs (0: not launchable)
+size_t engine_job_bytes();
+bool engine_job_write(Ctx& c, int lvl, int32_t rounds, void* dst);  // false: level unsuited to the engine
+void engine_launch(cudaStream_t st, const void* d_jobs, int njobs, unsigned int* queue, int C, int te, int nclusters);
 void drop_graph(Level& L);
 
 // coarsen.cu
@@ -241,3 +250,8 @@ void project(Ctx& c, int lvl);
 void validate_graph(Ctx& c);
 
 }  // namespace gm
+
+// The opaque handle of the C ABI.
+struct map_ctx {
+  gm::Ctx c;
+};

@@ -11,6 +11,7 @@
 // connectivity array over the PE code space; per-level group sums of that
 // array give the gain of every candidate PE in O(levels).
 #include <algorithm>
+#include <mutex>
 
 #include "engine.h"
 #include "tile.cuh"
@@ -205,6 +206,54 @@ __device__ __forceinline__ bool best_target(const Row& r, int deg, int32_t p, co
   return any;
 }
 
+// Sub-warp work queue of a staged tile: the lanes in `work` (vertices with a
+// neighbour outside their own PE) are served four at a time by 8-lane
+// sub-warps; each sub-warp evaluates T(q) for every distinct neighbouring PE
+// q != p of its vertex from the staged entries and keeps the minimum (lowest
+// code on ties).  out(lane, G = T(p) - T(q*), q*, p) runs on the sub-warp's
+// first lane.
+template <class Out>
+__device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t, int32_t p, int64_t Tp,
+                                                const int32_t* sc, const int32_t* sw, const int32_t* sdist, int lane,
+                                                Out out) {
+  const int sub = lane >> 3, sl = lane & 7;
+  const int rounds = (__popc(work) + 3) / 4;
+  for (int r = 0; r < rounds; r++) {
+    const int src = tile_worker(work, r, sub);
+    const int s2 = src < 0 ? 0 : src;
+    const int64_t vb = __shfl_sync(0xffffffffu, t.b, s2);
+    const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - vb);
+    const int32_t pv = __shfl_sync(0xffffffffu, p, s2);
+    const int64_t tp = __shfl_sync(0xffffffffu, Tp, s2);
+    const int32_t* c = sc + (vb - t.E0);
+    const int32_t* w = sw + (vb - t.E0);
+    int64_t bt = INT64_MAX;
+    int32_t bc = INT32_MAX;
+    if (src >= 0) {
+      for (int j = sl; j < dg; j += kSubWarp) {
+        const int32_t q = c[j];
+        if (q == pv) continue;
+        int64_t T = 0;
+        for (int l = 0; l < dg; l++) T += (int64_t)w[l] * dcode(sdist, q, c[l]);
+        if (T < bt || (T == bt && q < bc)) {
+          bt = T;
+          bc = q;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+      const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ot < bt || (ot == bt && oc < bc)) {
+        bt = ot;
+        bc = oc;
+      }
+    }
+    if (src >= 0 && sl == 0) out(src, tp - bt, bc, pv);
+  }
+}
+
 // Alg. 4 step 1 for the low-degree vertices.  Warp tiles stage the
 // neighbour PEs; each lane checks its own vertex (T(P(v)), any neighbour
 // outside P(v)); the vertices with candidates are then evaluated four at a
@@ -220,7 +269,6 @@ __global__ void __launch_bounds__(kTileThreads) k_lp_gain_tile(GraphView g, cons
   load_sdist(sdist, topo);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane >> 3, sl = lane & 7;
   const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
   const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
   for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
@@ -263,48 +311,14 @@ __global__ void __launch_bounds__(kTileThreads) k_lp_gain_tile(GraphView g, cons
     }
   done_lane:
     const unsigned work = __ballot_sync(0xffffffffu, cand);
-    const int rounds = (__popc(work) + 3) / 4;
-    for (int r = 0; r < rounds; r++) {
-      const int src = tile_worker(work, r, sub);
-      const int s2 = src < 0 ? 0 : src;
-      const int64_t vb = __shfl_sync(0xffffffffu, t.b, s2);
-      const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - vb);
-      const int32_t pv = __shfl_sync(0xffffffffu, p, s2);
-      const int64_t tp = __shfl_sync(0xffffffffu, Tp, s2);
-      const int32_t* c = sc[warp] + (vb - t.E0);
-      const int32_t* w = sw[warp] + (vb - t.E0);
-      int64_t bt = INT64_MAX;
-      int32_t bc = INT32_MAX;
-      if (src >= 0) {
-        for (int j = sl; j < dg; j += kSubWarp) {
-          const int32_t q = c[j];
-          if (q == pv) continue;
-          int64_t T = 0;
-          for (int l = 0; l < dg; l++) T += (int64_t)w[l] * dcode(sdist, q, c[l]);
-          if (T < bt || (T == bt && q < bc)) {
-            bt = T;
-            bc = q;
-          }
-        }
-      }
-#pragma unroll
-      for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-        const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
-        const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
-        if (ot < bt || (ot == bt && oc < bc)) {
-          bt = ot;
-          bc = oc;
-        }
-      }
-      if (src >= 0 && sl == 0) {
-        const int64_t v = tile * kTileV + src;
-        const int64_t G = tp - bt;
-        const bool in = G >= 0;
-        inx[v] = in ? 1 : 0;
-        pp[v] = in ? bc : pv;
-        gain[v] = in ? G : 0;
-      }
-    }
+    tile_gain_queue(work, t, p, Tp, sc[warp], sw[warp], sdist, lane,
+                    [&](int src, int64_t G, int32_t bc, int32_t pv) {
+                      const int64_t v = tile * kTileV + src;
+                      const bool in = G >= 0;
+                      inx[v] = in ? 1 : 0;
+                      pp[v] = in ? bc : pv;
+                      gain[v] = in ? G : 0;
+                    });
     __syncwarp();
   }
 }
@@ -1305,8 +1319,10 @@ __global__ void k_strong_gate(const RefineState* st, int64_t* d_sel) {
 // barriers order the phases across the cluster's SMs.
 // ---------------------------------------------------------------------------
 constexpr int kEngThreads = 1024;
-constexpr int kEngMaxN = 1 << 15;  // vertices handled by the fused engine
+constexpr int kEngMaxN = 1 << 15;   // default: levels of at most this many vertices use the engine
+constexpr int kEngMaxDeg = 128;     // and no vertex of larger degree
 constexpr int kEngMaxCluster = 16;
+static_assert(kEngThreads == kSmallThreads, "the engine's CTA sorts with the single-CTA sort");
 
 struct EngineJob {
   GraphView g;
@@ -1379,6 +1395,7 @@ __device__ int64_t cta_scan(int64_t n, F f, O out, int64_t* sm) {
 struct EngSmem {
   int32_t hist[256];
   int32_t ctot[256];
+  int32_t dbase[256];
   int32_t wcnt[32 * 256];
   int64_t sm[33];
   int32_t sdist[32];
@@ -1444,6 +1461,56 @@ __device__ int cta_sort_global(uint64_t* k0, int32_t* v0, uint64_t* k1, int32_t*
   return cur;
 }
 
+// Sorts the n (key, value) pairs in J.key0 / J.val0 by key bits [0, bits)
+// (stable), by the calling CTA: in shared memory (dyn) when n <= kSmallSort,
+// else through the global double buffers.  K / V point to the result.
+__device__ void eng_sort(const EngineJob& J, EngSmem& S, int32_t* dyn, int n, int bits, const uint64_t*& K,
+                         const int32_t*& V) {
+  if (n <= (int)blockDim.x) {
+    // rank sort: the position of pair i is the number of pairs with a smaller
+    // key, or an equal key and a smaller index (stable)
+    uint64_t* ks = reinterpret_cast<uint64_t*>(dyn);
+    int32_t* vs = reinterpret_cast<int32_t*>(ks + 2 * kSmallSort);
+    const uint64_t mask = bits >= 64 ? ~0ULL : ((1ULL << bits) - 1ULL);
+    const int i = threadIdx.x;
+    uint64_t ki = 0;
+    int32_t vi = 0;
+    if (i < n) {
+      ki = J.key0[i] & mask;
+      vi = J.val0[i];
+      ks[i] = ki;
+    }
+    __syncthreads();
+    if (i < n) {
+      int r = 0;
+      for (int j = 0; j < n; j++) {
+        const uint64_t kj = ks[j];
+        r += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+      }
+      ks[kSmallSort + r] = J.key0[i];
+      vs[kSmallSort + r] = vi;
+    }
+    __syncthreads();
+    K = ks + kSmallSort;
+    V = vs + kSmallSort;
+  } else if (n <= kSmallSort) {
+    uint64_t* ks = reinterpret_cast<uint64_t*>(dyn);
+    int32_t* vs = reinterpret_cast<int32_t*>(ks + 2 * kSmallSort);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      ks[i] = J.key0[i];
+      vs[i] = J.val0[i];
+    }
+    __syncthreads();
+    const int cur = cta_sort_small(ks, vs, S.wcnt, S.dbase, S.sm, n, bits);
+    K = ks + cur * kSmallSort;
+    V = vs + cur * kSmallSort;
+  } else {
+    const int cur = cta_sort_global(J.key0, J.val0, J.key1, J.val1, n, bits, S);
+    K = cur ? J.key1 : J.key0;
+    V = cur ? J.val1 : J.val0;
+  }
+}
+
 // Alg. 5 destination of one vertex (thread level): edge-cut gain, lowest id
 // on ties, the random-block fallback; returns false if the vertex cannot move.
 __device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int64_t nU, int32_t t, int32_t& dst,
@@ -1490,18 +1557,129 @@ __device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int
   return true;
 }
 
-__global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __restrict__ jobs) {
-  __shared__ EngSmem S;
-  cg::cluster_group cl = cg::this_cluster();
-  const int csize = (int)cl.num_blocks();
-  const int crank = (int)cl.block_rank();
-  const EngineJob& J = jobs[blockIdx.x / csize];
-  const GraphView& g = J.g;
+// Cluster-wide position of the calling thread.
+struct EngGeom {
+  int64_t gt, GT;  // thread index and thread count of the cluster
+  int64_t gw, GW;  // warp index and warp count of the cluster
+  int lane;
+  bool lead;  // first CTA of the cluster
+};
+
+struct PlainGather {  // neighbour PEs through plain loads (the mapping changes inside the launch)
+  const int32_t* pi;
+  __device__ __forceinline__ int32_t operator()(int32_t u) const { return pi[u]; }
+};
+
+// Stages one tile of neighbour PEs and returns T(P(v)) = sum_j w_j D(P(v), c_j)
+// of the lane's vertex; `cand` tells whether a staged row has a neighbour
+// outside P(v) (oversized tiles are left to the global path: cand false).
+template <int kTE>
+__device__ __forceinline__ TileLane eng_stage(const EngineJob& J, const TileGraph& tg, int64_t tile, int lane,
+                                              int32_t* sc, int32_t* sw, const int32_t* sdist, int64_t& Tp,
+                                              bool& cand) {
+  const TileLane t = stage_tile<kTE>(tg, tile * kTileV, lane, sc, sw, PlainGather{J.pi});
+  Tp = 0;
+  cand = false;
+  if (t.v < tg.n) {
+    const int deg = (int)(t.e - t.b);
+    const int32_t p = J.pi[t.v];
+    if (t.staged) {
+      const int32_t* c = sc + (t.b - t.E0);
+      const int32_t* w = sw + (t.b - t.E0);
+      for (int j = 0; j < deg; j++) {
+        Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
+        cand |= c[j] != p;
+      }
+    } else {
+      Tp = row_cost(PlainRow{tg.adj + t.b, tg.adjw + t.b, J.pi}, deg, sdist, p);
+    }
+  }
+  return t;
+}
+
+// Alg. 5 destinations of the lanes in `work` (vertices of an overloaded block
+// that are not heavy) from their staged rows, four at a time by 8-lane
+// sub-warps: the neighbouring block q != A with W(q) <= sigma of largest
+// conn(v, q), lowest id on ties.  out(lane, A, best conn or -1, q, conn(v, A))
+// runs on the sub-warp's first lane.
+template <class Out>
+__device__ __forceinline__ void reb_tile_queue(unsigned work, const TileLane& tl, int32_t A, const int32_t* sc,
+                                               const int32_t* sw, const int64_t* W, int64_t sigma, int lane,
+                                               Out out) {
+  const int sub = lane >> 3, sl = lane & 7;
+  const int rounds = (__popc(work) + 3) / 4;
+  for (int r = 0; r < rounds; r++) {
+    const int src = tile_worker(work, r, sub);
+    const int s2 = src < 0 ? 0 : src;
+    const int64_t vb = __shfl_sync(0xffffffffu, tl.b, s2);
+    const int dg = (int)(__shfl_sync(0xffffffffu, tl.e, s2) - vb);
+    const int32_t a = __shfl_sync(0xffffffffu, A, s2);
+    const int32_t* c = sc + (vb - tl.E0);
+    const int32_t* w = sw + (vb - tl.E0);
+    int32_t ca = 0, bconn = -1, bc = INT32_MAX;
+    if (src >= 0) {
+      for (int j = sl; j < dg; j += kSubWarp) {
+        const int32_t q = c[j];
+        if (q == a) {
+          ca += w[j];
+          continue;
+        }
+        if (W[q] > sigma) continue;
+        bool seen = false;
+        for (int l = 0; l < j; l++)
+          if (c[l] == q) {
+            seen = true;
+            break;
+          }
+        if (seen) continue;
+        int32_t cc = 0;
+        for (int l = j; l < dg; l++) cc += (c[l] == q) ? w[l] : 0;
+        if (cc > bconn || (cc == bconn && q < bc)) {
+          bconn = cc;
+          bc = q;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+      ca += __shfl_xor_sync(0xffffffffu, ca, o);
+      const int32_t oc = __shfl_xor_sync(0xffffffffu, bconn, o);
+      const int32_t oq = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (oc > bconn || (oc == bconn && oq < bc)) {
+        bconn = oc;
+        bc = oq;
+      }
+    }
+    if (src >= 0 && sl == 0) out(src, a, bconn, bc, ca);
+  }
+}
+
+// Inclusive prefix sum over the 32 lanes of a warp.
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Alg. 6 on one job by the calling cluster (all its threads call it).
+template <int kTE>
+__device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int32_t* sc, int32_t* sw,
+                               const EngGeom& eg) {
+  const GraphView g = J.g;
   const int32_t n = g.n;
-  const int64_t gt = (int64_t)crank * blockDim.x + threadIdx.x;
-  const int64_t GT = (int64_t)csize * blockDim.x;
-  const bool lead = crank == 0;
+  const int64_t gt = eg.gt, GT = eg.GT;
+  const int lane = eg.lane;
+  const bool lead = eg.lead;
+  const TileGraph tg{n, g.xadj, g.adj, g.adjw};
+  const int64_t ntiles = ((int64_t)n + kTileV - 1) / kTileV;
+  // with at most one tile per warp, the entries staged for J stay valid for
+  // the gain pass of the same iteration (the mapping does not change between)
+  const bool single = ntiles <= eg.GW;
   RefineState* s = J.s;
+  __syncthreads();
   load_sdist(S.sdist, J.topo);
   __syncthreads();
 
@@ -1522,12 +1700,23 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     J.best[v] = J.pi[v];
   }
   int phase = 0;
+  TileLane t0{};
+  int64_t Tp0 = 0;
+  bool cand0 = false;
   while (true) {
     // J of the current mapping, then the Alg. 6 decision
     int64_t acc = 0;
-    for (int64_t v = gt; v < n; v += GT) {
-      const int64_t b = g.xadj[v];
-      acc += row_cost(PlainRow{g.adj + b, g.adjw + b, J.pi}, (int)(g.xadj[v + 1] - b), S.sdist, J.pi[v]);
+    for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+      int64_t Tp;
+      bool cand;
+      const TileLane t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
+      acc += Tp;
+      if (single) {
+        t0 = t;
+        Tp0 = Tp;
+        cand0 = cand;
+      }
+      __syncwarp();
     }
     acc = block_sum(acc, S.sm);
     if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
@@ -1549,45 +1738,75 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     if (done) break;
     phase = 1;
     if (kind == KIND_LP) {
-      // Alg. 4 step 1
-      for (int64_t v = gt; v < n; v += GT) {
-        const int32_t p = J.pi[v];
-        bool in = false;
-        int32_t bc = p;
-        int64_t G = 0;
-        if (J.lock[v]) {
-          J.lock[v] = 0;
-        } else {
-          const int64_t b = g.xadj[v];
-          const int deg = (int)(g.xadj[v + 1] - b);
-          const PlainRow r{g.adj + b, g.adjw + b, J.pi};
-          int64_t bt;
-          if (best_target(r, deg, p, S.sdist, bc, bt)) {
-            G = row_cost(r, deg, S.sdist, p) - bt;
-            in = G >= 0;
+      // Alg. 4 step 1: staged tiles, lane check, sub-warp work queue
+      for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+        TileLane t = t0;
+        int64_t Tp = Tp0;
+        bool cand = cand0;
+        if (!single) t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
+        int32_t p = -1;
+        if (t.v < n) {
+          p = J.pi[t.v];
+          bool written = false;
+          if (J.lock[t.v]) {
+            J.lock[t.v] = 0;
+            cand = false;
+          } else if (!t.staged) {  // oversized tile: this lane alone, from global memory
+            const PlainRow r{g.adj + t.b, g.adjw + t.b, J.pi};
+            int32_t bc;
+            int64_t bt;
+            if (best_target(r, (int)(t.e - t.b), p, S.sdist, bc, bt) && Tp - bt >= 0) {
+              J.inx[t.v] = 1;
+              J.pp[t.v] = bc;
+              J.gain[t.v] = Tp - bt;
+              written = true;
+            }
+          }
+          if (!cand && !written) {
+            J.inx[t.v] = 0;
+            J.pp[t.v] = p;
+            J.gain[t.v] = 0;
           }
         }
-        J.inx[v] = in ? 1 : 0;
-        J.pp[v] = in ? bc : p;
-        J.gain[v] = in ? G : 0;
+        const unsigned work = __ballot_sync(0xffffffffu, cand);
+        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane, [&](int src, int64_t Gv, int32_t bc, int32_t pv) {
+          const int64_t v = tile * kTileV + src;
+          const bool in = Gv >= 0;
+          J.inx[v] = in ? 1 : 0;
+          J.pp[v] = in ? bc : pv;
+          J.gain[v] = in ? Gv : 0;
+        });
+        __syncwarp();
       }
       eng_sync();
-      // step 2: recomputed gain under ord
-      for (int64_t v = gt; v < n; v += GT) {
-        if (!J.inx[v]) continue;
-        const int32_t p = J.pi[v], q = J.pp[v];
-        const int64_t gv = J.gain[v];
-        int64_t sum = 0;
-        for (int64_t x = g.xadj[v]; x < g.xadj[v + 1]; x++) {
-          const int32_t u = g.adj[x];
-          int32_t bu = J.pi[u];
-          if (J.inx[u]) {
-            const int64_t gu = J.gain[u];
-            if (gu > gv || (gu == gv && u < v)) bu = J.pp[u];
+      // step 2: recomputed gain under ord, one 8-lane sub-warp per candidate
+      for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+        const int64_t v = tile * kTileV + lane;
+        const unsigned work = __ballot_sync(0xffffffffu, v < n && J.inx[v]);
+        const int sub = lane >> 3, sl = lane & 7;
+        const int rounds = (__popc(work) + 3) / 4;
+        for (int r = 0; r < rounds; r++) {
+          const int src = tile_worker(work, r, sub);
+          const int64_t vv = tile * kTileV + (src < 0 ? 0 : src);
+          int64_t sum = 0;
+          if (src >= 0) {
+            const int32_t p = J.pi[vv], q = J.pp[vv];
+            const int64_t gv = J.gain[vv];
+            const int64_t xe = g.xadj[vv + 1];
+            for (int64_t x = g.xadj[vv] + sl; x < xe; x += kSubWarp) {
+              const int32_t u = g.adj[x];
+              int32_t bu = J.pi[u];
+              if (J.inx[u]) {
+                const int64_t gu = J.gain[u];
+                if (gu > gv || (gu == gv && u < vv)) bu = J.pp[u];
+              }
+              sum += (int64_t)g.adjw[x] * (dcode(S.sdist, p, bu) - dcode(S.sdist, q, bu));
+            }
           }
-          sum += (int64_t)g.adjw[x] * (dcode(S.sdist, p, bu) - dcode(S.sdist, q, bu));
+#pragma unroll
+          for (int o = kSubWarp / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (src >= 0 && sl == 0 && sum >= 0) J.lock[vv] = 1;
         }
-        if (sum >= 0) J.lock[v] = 1;
       }
       eng_sync();
       // step 3: simultaneous move of M
@@ -1612,41 +1831,83 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     eng_sync();
     const int64_t sigma = *(volatile int64_t*)&J.cnt[CNT_SIGMA];
     const int64_t nU = *(volatile int64_t*)&J.cnt[CNT_NU];
-    for (int64_t v = gt; v < n; v += GT) {
-      int32_t dst, bk;
-      const bool ok = eng_reb_select(J, (int32_t)v, sigma, nU, t, dst, bk);
-      J.elig[v] = ok ? 1 : 0;
-      if (ok) {
-        J.dest[v] = dst;
-        J.bkt[v] = (uint8_t)bk;
-        atomicAdd((unsigned long long*)&J.tab[(int64_t)J.pi[v] * kBuckets + bk],
-                  (unsigned long long)(int64_t)g.vw[v]);
+    // eligible vertices and their destinations: lane check, then staged rows
+    for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+      const int64_t v = tile * kTileV + lane;
+      int32_t A = -1;
+      bool cand = false;
+      if (v < n) {
+        A = J.pi[v];
+        const int64_t WA = J.W[A];
+        cand = WA > J.lmax && 2 * (int64_t)J.k * g.vw[v] <= 3 * ((int64_t)J.k * WA - J.cV);
+        if (!cand) J.elig[v] = 0;
       }
+      if (__ballot_sync(0xffffffffu, cand) == 0) continue;
+      const TileLane tl = stage_tile<kTE>(tg, tile * kTileV, lane, sc, sw, PlainGather{J.pi});
+      if (cand && !tl.staged) {  // oversized tile: this lane alone, from global memory
+        int32_t dst, bk;
+        const bool ok = eng_reb_select(J, (int32_t)v, sigma, nU, t, dst, bk);
+        J.elig[v] = ok ? 1 : 0;
+        if (ok) {
+          J.dest[v] = dst;
+          J.bkt[v] = (uint8_t)bk;
+          atomicAdd((unsigned long long*)&J.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
+        }
+        cand = false;
+      }
+      const unsigned work = __ballot_sync(0xffffffffu, cand);
+      reb_tile_queue(work, tl, A, sc, sw, J.W, sigma, lane,
+                     [&](int src, int32_t a, int32_t bconn, int32_t bc, int32_t ca) {
+                       const int64_t u = tile * kTileV + src;
+                       int64_t gcut;
+                       int32_t dst;
+                       if (bconn >= 0) {
+                         gcut = (int64_t)bconn - ca;
+                         dst = bc;
+                       } else if (nU > 0) {
+                         dst = J.U[h_rebalance(J.seed, J.level, t, u) % (uint64_t)nU];
+                         gcut = -(int64_t)ca;
+                       } else {
+                         J.elig[u] = 0;
+                         return;
+                       }
+                       const int bk = loss_bucket(gcut);
+                       J.elig[u] = 1;
+                       J.dest[u] = dst;
+                       J.bkt[u] = (uint8_t)bk;
+                       atomicAdd((unsigned long long*)&J.tab[(int64_t)a * kBuckets + bk],
+                                 (unsigned long long)(int64_t)g.vw[u]);
+                     });
+      __syncwarp();
     }
     eng_sync();
-    if (lead) {  // the cut bucket of each overloaded block
-      for (int32_t A = threadIdx.x; A < J.topo.kc; A += blockDim.x) {
-        if (J.W[A] <= J.lmax) continue;
-        const int64_t E = J.W[A] - J.lmax;
-        int64_t cum = 0, r = 0;
-        int32_t cut = kBuckets;
-        for (int bb = 0; bb < kBuckets; bb++) {
-          const int64_t tt = J.tab[(int64_t)A * kBuckets + bb];
-          J.tab[(int64_t)A * kBuckets + bb] = 0;
-          if (cut == kBuckets) {
-            if (cum + tt <= E) {
-              cum += tt;
-            } else {
-              cut = bb;
-              r = E - cum;
-            }
-          }
-        }
+    // the cut bucket of each overloaded block A: the first bucket whose
+    // inclusive prefix of eligible weight exceeds W(A) - L_max (one warp per
+    // block, buckets lane and 32 + lane)
+    static_assert(kBuckets == 64, "two buckets per lane");
+    for (int64_t A = eg.gw; A < J.topo.kc; A += eg.GW) {
+      const int64_t WA = J.W[A];
+      if (WA <= J.lmax) continue;
+      const int64_t E = WA - J.lmax;
+      int64_t* row = J.tab + A * kBuckets;
+      const int64_t x0 = row[lane], x1 = row[32 + lane];
+      row[lane] = 0;
+      row[32 + lane] = 0;
+      const int64_t p0 = warp_incl_scan(x0, lane);
+      const int64_t p1 = warp_incl_scan(x1, lane) + __shfl_sync(0xffffffffu, p0, 31);
+      const unsigned m0 = __ballot_sync(0xffffffffu, p0 > E), m1 = __ballot_sync(0xffffffffu, p1 > E);
+      const int cut = m0 ? __ffs(m0) - 1 : (m1 ? 32 + __ffs(m1) - 1 : kBuckets);
+      // exclusive prefix of the cut bucket
+      const int pl = cut - 1;
+      const int64_t q0 = __shfl_sync(0xffffffffu, p0, pl < 0 ? 0 : (pl & 31));
+      const int64_t q1 = __shfl_sync(0xffffffffu, p1, pl < 32 ? 0 : (pl & 31));
+      const int64_t excl = pl < 0 ? 0 : (pl < 32 ? q0 : q1);
+      if (lane == 0) {
         J.bcut[A] = cut;
-        J.rem[A] = r;
+        J.rem[A] = cut < kBuckets ? E - excl : 0;
       }
-      if (threadIdx.x == 0) J.cnt[CNT_ELIG] = 0;
     }
+    if (lead && threadIdx.x == 0) J.cnt[CNT_ELIG] = 0;
     eng_sync();
     const int idbits = bits_for_n(n);
     for (int64_t v = gt; v < n; v += GT) {
@@ -1668,9 +1929,9 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     if (lead) {  // the cut-bucket list by (block, id), per-block prefix
       const int ln = (int)*(volatile int64_t*)&J.cnt[CNT_ELIG];
       if (ln > 0) {
-        const int cur = cta_sort_global(J.key0, J.val0, J.key1, J.val1, ln, J.topo.code_bits + idbits, S);
-        const uint64_t* K = cur ? J.key1 : J.key0;
-        const int32_t* V = cur ? J.val1 : J.val0;
+        const uint64_t* K;
+        const int32_t* V;
+        eng_sort(J, S, dyn, ln, J.topo.code_bits + idbits, K, V);
         cta_scan(
             ln, [&](int64_t i) { return (int64_t)g.vw[V[i]]; },
             [&](int64_t i, int64_t e, int64_t) {
@@ -1709,11 +1970,9 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
           },
           S.sm);
       __syncthreads();
-      const int cur = ns ? cta_sort_global(J.key0, J.val0, J.key1, J.val1, (int)ns,
-                                           J.topo.code_bits + kBucketBits, S)
-                         : 0;
-      const uint64_t* K = cur ? J.key1 : J.key0;
-      const int32_t* V = cur ? J.val1 : J.val0;
+      const uint64_t* K = J.key0;
+      const int32_t* V = J.val0;
+      if (ns) eng_sort(J, S, dyn, (int)ns, J.topo.code_bits + kBucketBits, K, V);
       cta_scan(
           ns, [&](int64_t i) { return (int64_t)g.vw[V[i]]; },
           [&](int64_t i, int64_t e, int64_t) {
@@ -1779,6 +2038,41 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     eng_sync();
   }
   for (int64_t v = gt; v < n; v += GT) J.pi[v] = J.best[v];
+}
+
+template <int kTE>
+__global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __restrict__ jobs, int32_t njobs,
+                                                          unsigned int* queue) {
+  __shared__ EngSmem S;
+  __shared__ int32_t job_slot;
+  extern __shared__ __align__(16) int32_t eng_dyn[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int warp = threadIdx.x >> 5;
+  EngGeom eg;
+  eg.lane = threadIdx.x & 31;
+  eg.lead = crank == 0;
+  eg.gt = (int64_t)crank * blockDim.x + threadIdx.x;
+  eg.GT = (int64_t)csize * blockDim.x;
+  eg.gw = (int64_t)crank * (blockDim.x >> 5) + warp;
+  eg.GW = (int64_t)csize * (blockDim.x >> 5);
+  int32_t* sc = eng_dyn + warp * 2 * kTE;
+  int32_t* sw = sc + kTE;
+  if (!queue) {  // one job per cluster
+    const int32_t jid = (int32_t)(blockIdx.x / csize);
+    if (jid < njobs) engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg);
+    return;
+  }
+  // persistent clusters: the next job from the queue (jobs in the order given)
+  while (true) {
+    if (eg.lead && threadIdx.x == 0) job_slot = (int32_t)atomicAdd(queue, 1u);
+    eng_sync();
+    const int32_t jid = *cl.map_shared_rank(&job_slot, 0);
+    eng_sync();
+    if (jid >= njobs) break;
+    engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg);
+  }
 }
 
 }  // namespace
@@ -2063,35 +2357,71 @@ static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* m
   if (iters) *iters = h.t;
 }
 
-// Cluster size of the fused engine for a level of n vertices (0: not used).
+// Cluster size of the fused engine for a level (0: not used).
 static int engine_cluster(Ctx& c, const Level& L) {
-  if (!c.use_graphs || c.prof || L.n > kEngMaxN || L.n_hi > 0) return 0;
+  const int64_t lim = c.cfg.engine_max_n > 0 ? c.cfg.engine_max_n : (c.cfg.engine_max_n < 0 ? -1 : kEngMaxN);
+  if (!c.use_graphs || c.prof || L.n > lim || L.max_deg > kEngMaxDeg) return 0;
   int C = (L.n + 2047) / 2048;
   if (C < 1) C = 1;
   if (C > c.eng_max_cluster) C = c.eng_max_cluster;
   return C;
 }
 
+using EngineKernel = void (*)(const EngineJob*, int32_t, unsigned int*);
+static EngineKernel engine_kernel(int te) { return te == 256 ? k_engine<256> : k_engine<512>; }
+// dynamic shared memory: the warps' staging arrays, or the two key / value
+// buffers of the single-CTA sort (used at other times)
+static size_t engine_smem(int te) {
+  return std::max((size_t)(kEngThreads / 32) * 2 * te * sizeof(int32_t),
+                  (size_t)2 * kSmallSort * (sizeof(uint64_t) + sizeof(int32_t)));
+}
+
+static cudaLaunchConfig_t engine_config(int C, int te, unsigned grid, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kEngThreads);
+  cfg.dynamicSmemBytes = engine_smem(te);
+  cfg.stream = st;
+  attr->id = cudaLaunchAttributeClusterDimension;
+  attr->val.clusterDim.x = (unsigned)C;
+  attr->val.clusterDim.y = 1;
+  attr->val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Kernel attributes of both engine variants (once per process and device).
+static void engine_attributes() {
+  static std::mutex mu;
+  static bool done[256] = {false};
+  int dev = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 256 || done[dev]) return;
+  for (int te : {256, 512}) {
+    GM_CUDA(cudaFuncSetAttribute(engine_kernel(te), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(te)));
+    if (cudaFuncSetAttribute(engine_kernel(te), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      cudaGetLastError();
+  }
+  done[dev] = true;
+}
+
+int engine_max_clusters(int C, int te) {
+  engine_attributes();
+  cudaLaunchAttribute attr{};
+  cudaLaunchConfig_t cfg = engine_config(C, te, (unsigned)C, nullptr, &attr);
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)engine_kernel(te), &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nclusters;
+}
+
 static void engine_setup(Ctx& c) {
   if (c.eng_max_cluster > 0) return;
-  int C = 8;
-  if (cudaFuncSetAttribute(k_engine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(kEngMaxCluster);
-    cfg.blockDim = dim3(kEngThreads);
-    cudaLaunchAttribute attr{};
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = kEngMaxCluster;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_engine, &cfg) == cudaSuccess && nclusters > 0)
-      C = kEngMaxCluster;
-  }
-  cudaGetLastError();
-  c.eng_max_cluster = C;
+  c.eng_max_cluster = engine_max_clusters(kEngMaxCluster, 512) > 0 ? kEngMaxCluster : 8;
   if (!c.eng_job) {
     c.eng_job = c.mem.make<EngineJob>(1);
     GM_CUDA(cudaMallocHost(&c.h_eng_job, sizeof(EngineJob)));
@@ -2143,26 +2473,29 @@ static EngineJob engine_job(Ctx& c, int lvl, int32_t rounds) {
   return j;
 }
 
-static void launch_engine(Ctx& c, const EngineJob* d_jobs, int njobs, int C) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)(C * njobs));
-  cfg.blockDim = dim3(kEngThreads);
-  cfg.stream = c.st;
+size_t engine_job_bytes() { return sizeof(EngineJob); }
+
+bool engine_job_write(Ctx& c, int lvl, int32_t rounds, void* dst) {
+  engine_setup(c);
+  const Level& L = c.lv[lvl];
+  if (L.max_deg > kEngMaxDeg) return false;
+  *static_cast<EngineJob*>(dst) = engine_job(c, lvl, rounds);
+  return true;
+}
+
+void engine_launch(cudaStream_t st, const void* d_jobs, int njobs, unsigned int* queue, int C, int te,
+                   int nclusters) {
+  engine_attributes();
   cudaLaunchAttribute attr{};
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = (unsigned)C;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  GM_CUDA(cudaLaunchKernelEx(&cfg, k_engine, d_jobs));
+  cudaLaunchConfig_t cfg = engine_config(C, te, (unsigned)(C * nclusters), st, &attr);
+  GM_CUDA(cudaLaunchKernelEx(&cfg, engine_kernel(te), static_cast<const EngineJob*>(d_jobs), (int32_t)njobs, queue));
   count_launch();
 }
 
 static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, int64_t* maxw, int32_t* iters) {
   *static_cast<EngineJob*>(c.h_eng_job) = engine_job(c, lvl, rounds);
   GM_CUDA(cudaMemcpyAsync(c.eng_job, c.h_eng_job, sizeof(EngineJob), cudaMemcpyHostToDevice, c.st));
-  launch_engine(c, static_cast<const EngineJob*>(c.eng_job), 1, C);
+  engine_launch(c.st, c.eng_job, 1, nullptr, C, 512, 1);
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
   const RefineState h = *c.h_state;
@@ -2197,6 +2530,19 @@ struct LoadHighDeg {
 struct StoreNothing {
   __device__ void operator()(int64_t, int64_t, int64_t) const {}
 };
+__global__ void k_max_deg(int32_t n, const int64_t* __restrict__ xadj, unsigned long long* out) {
+  unsigned long long mx = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long d = (unsigned long long)(xadj[v + 1] - xadj[v]);
+    mx = d > mx ? d : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
 struct StoreHigh {
   int32_t* out;
   __device__ void operator()(int64_t v, int64_t e, int64_t x) const {
@@ -2215,7 +2561,16 @@ void classify_degrees(Ctx& c, int lvl) {
   GM_CUDA(cudaStreamSynchronize(c.st));
   L.n_hi = (int32_t)cnt;
   L.m_hi = 0;
+  L.max_deg = 0;
   if (cnt) {
+    unsigned long long* d_mx = reinterpret_cast<unsigned long long*>(c.counters + CNT_TMP);
+    GM_CUDA(cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long), c.st));
+    const int64_t blocks = std::min<int64_t>(((int64_t)L.n + 255) / 256, (int64_t)c.num_sms * 8);
+    k_max_deg<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, c.st>>>(L.n, L.xadj, d_mx); count_launch();
+    unsigned long long mx = 0;
+    GM_CUDA(cudaMemcpyAsync(&mx, d_mx, sizeof(mx), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+    L.max_deg = (int64_t)mx;
     scan(LoadHighDeg{L.xadj}, StoreNothing{}, L.n, nullptr, c.scan, c.st);
     GM_CUDA(cudaMemcpyAsync(&L.m_hi, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
                             cudaMemcpyDeviceToHost, c.st));

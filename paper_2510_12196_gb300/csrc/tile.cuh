@@ -52,8 +52,9 @@ struct TileLane {
   int64_t E0;
 };
 
-// Stages the tile starting at vertex v0 (all 32 lanes call it).
-template <class Gather>
+// Stages the tile starting at vertex v0 (all 32 lanes call it); kTE is the
+// capacity of the warp's staging arrays sc and sw.
+template <int kTE = kTileE, class Gather>
 __device__ __forceinline__ TileLane stage_tile(const TileGraph& g, int64_t v0, int lane, int32_t* sc, int32_t* sw,
                                                Gather gather) {
   TileLane t;
@@ -65,11 +66,11 @@ __device__ __forceinline__ TileLane stage_tile(const TileGraph& g, int64_t v0, i
   t.E0 = __shfl_sync(0xffffffffu, t.b, 0);
   const int64_t E1 = __shfl_sync(0xffffffffu, t.e, last);
   const int64_t span = E1 - t.E0;
-  t.staged = span <= kTileE;
+  t.staged = span <= kTE;
   if (t.staged) {
     // every load of the tile is issued before any is used: one round trip
     // for the adjacency and weights, one for the gathers
-    constexpr int kQ = kTileE / 32;
+    constexpr int kQ = kTE / 32;
     int32_t u[kQ];
 #pragma unroll
     for (int q = 0; q < kQ; q++) {

@@ -40,14 +40,14 @@ class MapConfig(C.Structure):
                 ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
                 ("stall_num", C.c_int32), ("stall_den", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("launch_mode", C.c_int32)]
+                ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32)]
 
 
 class MapStats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("n", C.c_int32 * 65), ("m_dir", C.c_int64 * 65),
                 ("J", C.c_int64 * 65), ("iters", C.c_int32 * 65), ("ms_coarsen", C.c_double),
                 ("ms_initial", C.c_double), ("ms_refine", C.c_double), ("ms_project", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("device_bytes_peak", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -80,6 +80,22 @@ _SIGS = {
     "map_profile_read": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
     "map_launch_count": (C.c_longlong, []),
     "map_objective_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, C.c_int32, _P, _P]),
+    "map_batch_opts_default": (None, [_P]),
+    "map_batch_create": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "map_batch_launch": (C.c_int, [_P]),
+    "map_batch_results": (C.c_int, [_P, _P, _P, _P]),
+    "map_batch_schedule": (C.c_int, [_P, _P, _P, _P, _P]),
+    "map_batch_last_error": (C.c_char_p, [_P]),
+    "map_batch_destroy": (None, [_P]),
+    "map_server_opts_default": (None, [_P]),
+    "map_job_estimate_bytes": (C.c_int64, [C.c_int32, C.c_int64, _P, C.c_int32]),
+    "map_server_create": (C.c_int, [_P, _P]),
+    "map_server_submit": (C.c_int, [_P, _P, _P]),
+    "map_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, _P]),
+    "map_server_poll": (C.c_int, [_P, C.c_uint64, _P]),
+    "map_server_stats": (C.c_int, [_P, _P]),
+    "map_server_last_error": (C.c_char_p, [_P]),
+    "map_server_destroy": (None, [_P]),
 }
 
 
@@ -344,6 +360,159 @@ def map_objective_noalloc(xadj, adjncy, adjwgt, vwgt, n: int, pi, hier, dist, ou
     if st != 0:
         msg = lib().map_last_error(None)
         raise MapError(st, "map_objective_noalloc", msg.decode() if msg else "")
+
+
+class MapBatchOpts(C.Structure):
+    _fields_ = [("level", C.c_int32), ("rounds", C.c_int32), ("autotune", C.c_int32),
+                ("cluster", C.c_int32), ("tile_entries", C.c_int32)]
+
+
+def map_batch_opts_default(**over) -> MapBatchOpts:
+    o = MapBatchOpts()
+    lib().map_batch_opts_default(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def _check_batch(b, st: int, where: str):
+    if st != 0:
+        msg = lib().map_batch_last_error(b)
+        raise MapError(st, where, msg.decode() if msg else "")
+
+
+def map_batch_create(ctxs, opts: Optional[MapBatchOpts] = None, stream=None):
+    """One batch over the contexts ``ctxs`` (see include/gpumap.h)."""
+    arr = (C.c_void_p * len(ctxs))(*[C.cast(c, C.c_void_p) for c in ctxs])
+    out = C.c_void_p()
+    st = lib().map_batch_create(arr, len(ctxs), C.byref(opts) if opts is not None else None,
+                                _stream_handle(stream), C.byref(out))
+    _check_batch(None, st, "map_batch_create")
+    return out
+
+
+def map_batch_launch(b) -> None:
+    _check_batch(b, lib().map_batch_launch(b), "map_batch_launch")
+
+
+def map_batch_results(b, njobs: int):
+    J = np.zeros(njobs, np.int64)
+    mw = np.zeros(njobs, np.int64)
+    it = np.zeros(njobs, np.int32)
+    _check_batch(b, lib().map_batch_results(b, J.ctypes.data, mw.ctypes.data, it.ctypes.data), "map_batch_results")
+    return J, mw, it
+
+
+def map_batch_schedule(b):
+    """(CTAs per job, staged entries per warp tile, clusters, autotune ms)."""
+    c, te, ncl, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+    _check_batch(b, lib().map_batch_schedule(b, C.byref(c), C.byref(te), C.byref(ncl), C.byref(ms)),
+                 "map_batch_schedule")
+    return c.value, te.value, ncl.value, ms.value
+
+
+def map_batch_destroy(b) -> None:
+    lib().map_batch_destroy(b)
+
+
+class MapJob(C.Structure):
+    _fields_ = [("xadj", C.c_void_p), ("adjncy", C.c_void_p), ("adjwgt", C.c_void_p), ("vwgt", C.c_void_p),
+                ("n", C.c_int32), ("hier", C.c_void_p), ("dist", C.c_void_p), ("levels", C.c_int32),
+                ("eps", C.c_double), ("cfg", C.c_void_p), ("out_pi", C.c_void_p), ("user", C.c_void_p)]
+
+
+class MapJobResult(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int), ("levels", C.c_int32), ("J", C.c_int64),
+                ("device_bytes_est", C.c_int64), ("device_bytes_peak", C.c_int64),
+                ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double), ("t_done_ms", C.c_double),
+                ("user", C.c_void_p), ("error", C.c_char * 256)]
+
+
+JOB_RUNNER = C.CFUNCTYPE(C.c_int32, C.POINTER(MapJob), C.c_void_p, C.c_void_p, C.POINTER(MapJobResult))
+
+
+class MapServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("lookahead", C.c_int32), ("mem_budget", C.c_int64),
+                ("runner", JOB_RUNNER), ("runner_user", C.c_void_p)]
+
+
+class MapServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("queued", C.c_int64), ("running", C.c_int64), ("bytes_in_flight", C.c_int64),
+                ("peak_bytes_in_flight", C.c_int64), ("mem_budget", C.c_int64), ("peak_running", C.c_int32),
+                ("uptime_ms", C.c_double)]
+
+
+def map_job_estimate_bytes(n: int, m_dir: int, hier) -> int:
+    h = np.ascontiguousarray(hier, dtype=np.int32)
+    return int(lib().map_job_estimate_bytes(int(n), int(m_dir), h.ctypes.data, len(h)))
+
+
+class MapServer:
+    """Request loop over the C server (see include/gpumap.h).  Keeps every
+    submitted job's host arrays alive until its result is collected."""
+
+    def __init__(self, slots: int = 8, lookahead: int = 8, mem_budget: int = 0, runner=None):
+        o = MapServerOpts()
+        lib().map_server_opts_default(C.byref(o))
+        o.slots, o.lookahead, o.mem_budget = slots, lookahead, mem_budget
+        self._runner = JOB_RUNNER(runner) if runner is not None else None
+        if self._runner is not None:
+            o.runner = self._runner
+        out = C.c_void_p()
+        st = lib().map_server_create(C.byref(o), C.byref(out))
+        if st != 0:
+            msg = lib().map_server_last_error(None)
+            raise MapError(st, "map_server_create", msg.decode() if msg else "")
+        self.h = out
+        self._keep = {}
+
+    def _check(self, st, where):
+        if st != 0:
+            msg = lib().map_server_last_error(self.h)
+            raise MapError(st, where, msg.decode() if msg else "")
+
+    def submit(self, graph, hier, dist, eps=0.03, cfg: Optional[MapConfig] = None, out_pi=None, user: int = 0):
+        """Queues one job on host arrays; returns its ticket."""
+        arrs = [np.ascontiguousarray(graph.xadj, np.int64), np.ascontiguousarray(graph.adj, np.int32),
+                np.ascontiguousarray(graph.adjw, np.int32), np.ascontiguousarray(graph.vw, np.int32)]
+        h = np.ascontiguousarray(hier, dtype=np.int32)
+        d = np.ascontiguousarray(dist, dtype=np.int32)
+        if out_pi is None:
+            out_pi = np.zeros(graph.n, np.int32)
+        j = MapJob()
+        j.xadj, j.adjncy, j.adjwgt, j.vwgt = [a.ctypes.data for a in arrs]
+        j.n, j.hier, j.dist, j.levels, j.eps = graph.n, h.ctypes.data, d.ctypes.data, len(h), float(eps)
+        j.cfg = C.cast(C.pointer(cfg), C.c_void_p) if cfg is not None else None
+        j.out_pi = out_pi.ctypes.data
+        j.user = user
+        t = C.c_uint64()
+        self._check(lib().map_server_submit(self.h, C.byref(j), C.byref(t)), "map_server_submit")
+        self._keep[t.value] = (arrs, h, d, cfg, out_pi, j)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        """(result, mapping) of a job; MapError with status MAP_E_TIMEOUT (5) if not done in time."""
+        r = MapJobResult()
+        self._check(lib().map_server_wait(self.h, ticket, float(timeout_ms), C.byref(r)), "map_server_wait")
+        keep = self._keep.pop(ticket)
+        return r, keep[4]
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int32()
+        self._check(lib().map_server_poll(self.h, ticket, C.byref(d)), "map_server_poll")
+        return bool(d.value)
+
+    def stats(self) -> MapServerStats:
+        s = MapServerStats()
+        self._check(lib().map_server_stats(self.h, C.byref(s)), "map_server_stats")
+        return s
+
+    def close(self):
+        if self.h:
+            lib().map_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
 
 
 class Mapper:

@@ -1,0 +1,203 @@
+"""Batched refinement (one persistent launch over many contexts) against the
+CPU oracle: every job of the batch must equal Alg. 6 run on that graph alone,
+for every schedule the autotuner can pick, on graph replays, and on the full
+64-graph batch workload (RGGs of 2^12..2^18 vertices, 10 fixed rounds)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_12196_gb300 import gpumap as G
+from paper_2510_12196_gb300 import inputs as I
+
+from gpu_helpers import make_ctx, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(sizes, seed0=0x5EED1000):
+    hiers = ((4, 8), (4, 8, 8), (2, 4, 16, 8))
+    out = []
+    for i, n in enumerate(sizes):
+        seed = seed0 + i
+        hier = hiers[i % len(hiers)]
+        dist = (1, 10, 100, 1000)[:len(hier)]
+        g = I.rgg2d(n, I.rgg_radius(n, 10.0), seed, wmax=10)
+        k = int(np.prod(hier))
+        out.append((g, hier, dist, I.random_mapping(n, k, seed)))
+    return out
+
+
+def _oracle(jobs, rounds):
+    res = []
+    for g, hier, dist, pi0 in jobs:
+        L = O.lmax(int(g.vw.sum()), int(np.prod(hier)), 0.03)
+        opi, oJ, omx, oit, okinds, _, _ = O.refine(g, hier, dist, L, pi0, rounds=rounds, params=oracle_params())
+        res.append((opi, oJ, omx, oit, okinds))
+    return res
+
+
+def _make(jobs):
+    ctxs = []
+    for g, hier, dist, pi0 in jobs:
+        c = make_ctx(g, hier, dist)
+        G.map_set_mapping(c, 0, pi0)
+        ctxs.append(c)
+    return ctxs
+
+
+def _reset(ctxs, jobs):
+    for c, (_, _, _, pi0) in zip(ctxs, jobs):
+        G.map_set_mapping(c, 0, pi0)
+
+
+def _run_batch(ctxs, **opts):
+    b = G.map_batch_create(ctxs, G.map_batch_opts_default(**opts))
+    try:
+        G.map_batch_launch(b)
+        J, mw, it = G.map_batch_results(b, len(ctxs))
+        sched = G.map_batch_schedule(b)
+    finally:
+        G.map_batch_destroy(b)
+    return J, mw, it, sched
+
+
+def _check(ctxs, J, mw, it, ref):
+    for i, (c, (opi, oJ, omx, oit, okinds)) in enumerate(zip(ctxs, ref)):
+        assert (J[i], mw[i], it[i]) == (oJ, omx, oit), i
+        assert np.array_equal(G.map_get_mapping(c, 0), opi), i
+        kinds, _, _, cnt = G.map_get_refine_trace(c)
+        assert cnt == oit and np.array_equal(kinds, okinds), i
+
+
+SIZES = [700, 4096, 1500, 20000, 9000, 300, 40000, 2500, 6000, 12000, 1024, 33000]
+
+
+def test_batch_fixed_rounds_matches_oracle():
+    jobs = _jobs(SIZES)
+    ref = _oracle(jobs, 10)
+    ctxs = _make(jobs)
+    try:
+        J, mw, it, sched = _run_batch(ctxs, rounds=10)
+        _check(ctxs, J, mw, it, ref)
+        assert sched[0] in (1, 2, 4, 8, 16) and sched[1] in (256, 512) and sched[2] >= 1
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
+def test_batch_schedules_and_replay_agree():
+    """Results do not depend on CTAs per job, staging capacity or replays."""
+    jobs = _jobs(SIZES[:8], seed0=0x5EED1100)
+    ref = _oracle(jobs, 10)
+    ctxs = _make(jobs)
+    try:
+        for cl, te in ((1, 512), (4, 256), (16, 512), (2, 256)):
+            _reset(ctxs, jobs)
+            J, mw, it, sched = _run_batch(ctxs, rounds=10, autotune=0, cluster=cl, tile_entries=te)
+            assert sched[:2] == (cl, te)
+            _check(ctxs, J, mw, it, ref)
+        # one batch object launched twice (the second launch replays the graph)
+        _reset(ctxs, jobs)
+        b = G.map_batch_create(ctxs, G.map_batch_opts_default(rounds=10, autotune=0))
+        try:
+            G.map_batch_launch(b)
+            G.map_batch_results(b, len(ctxs))
+            _reset(ctxs, jobs)
+            G.map_batch_launch(b)
+            J, mw, it = G.map_batch_results(b, len(ctxs))
+            _check(ctxs, J, mw, it, ref)
+        finally:
+            G.map_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
+def test_batch_alg6_termination_and_single_path():
+    """rounds = -1 (Alg. 6 termination) in the batch equals map_refine alone."""
+    jobs = _jobs([3000, 800, 15000, 5000], seed0=0x5EED1200)
+    ref = _oracle(jobs, -1)
+    ctxs = _make(jobs)
+    try:
+        J, mw, it, _ = _run_batch(ctxs, rounds=-1)
+        _check(ctxs, J, mw, it, ref)
+        for c, (g, hier, dist, pi0), (opi, oJ, omx, oit, _) in zip(ctxs, jobs, ref):
+            G.map_set_mapping(c, 0, pi0)
+            assert G.map_refine(c, 0, -1) == (oJ, omx, oit)
+            assert np.array_equal(G.map_get_mapping(c, 0), opi)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
+def test_batch_coarse_level_jobs():
+    """A batch over a coarse level of each context (after map_coarsen and a
+    projected mapping) refines that level like map_refine does."""
+    jobs = _jobs([30000, 20000], seed0=0x5EED1300)
+    ctxs = [make_ctx(g, h, d) for g, h, d, _ in jobs]
+    try:
+        singles = []
+        for c, (g, h, d, _) in zip(ctxs, jobs):
+            assert G.map_coarsen(c) >= 2
+            xadj, adj, w, vw, _ = G.map_get_level_graph(c, 1)
+            pc = I.random_mapping(len(vw), int(np.prod(h)), 9)
+            cg = I.Graph(len(vw), xadj, adj, w, vw)
+            L = O.lmax(int(g.vw.sum()), int(np.prod(h)), 0.03)
+            opi, oJ, omx, oit, _, _, _ = O.refine(cg, h, d, L, pc, rounds=10, params=oracle_params(), level=1)
+            singles.append((pc, opi, oJ, omx, oit))
+            G.map_set_mapping(c, 1, pc)
+        J, mw, it, _ = _run_batch(ctxs, rounds=10, level=1)
+        for i, (c, (pc, opi, oJ, omx, oit)) in enumerate(zip(ctxs, singles)):
+            assert (J[i], mw[i], it[i]) == (oJ, omx, oit)
+            assert np.array_equal(G.map_get_mapping(c, 1), opi)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
+def test_batch_errors():
+    jobs = _jobs([500, 600], seed0=0x5EED1400)
+    ctxs = _make(jobs)
+    star = I.csr_from_pairs(300, np.zeros(299, np.int64), np.arange(1, 300), name="star300")
+    cs = make_ctx(star, (4, 8), (1, 10))
+    try:
+        with pytest.raises(G.MapError) as e:
+            G.map_batch_create([ctxs[0], ctxs[0]])
+        assert e.value.status == 1
+        with pytest.raises(G.MapError) as e:
+            G.map_batch_create(ctxs, G.map_batch_opts_default(level=3))
+        assert e.value.status == 6
+        with pytest.raises(G.MapError) as e:
+            G.map_batch_create([ctxs[1], cs])  # a vertex of degree 299
+        assert e.value.status == 1
+        with pytest.raises(G.MapError) as e:
+            G.map_batch_create(ctxs, G.map_batch_opts_default(rounds=0))
+        assert e.value.status == 1
+        with pytest.raises(G.MapError) as e:
+            G.map_batch_create(ctxs, G.map_batch_opts_default(autotune=0, cluster=3))
+        assert e.value.status == 1
+    finally:
+        for c in ctxs + [cs]:
+            G.map_destroy(c)
+
+
+def test_batch_workload_64_rggs_full_size():
+    """The 64-graph batch workload (n log-uniform in 2^12..2^18, mean degree
+    10, hierarchies from {4:8, 4:8:8, 2:4:16:8}, 10 fixed rounds from
+    h(v) mod k): every job bit-identical to the oracle."""
+    ws = I.workload_batch()
+    jobs = [(w.graph, w.topo.hier, w.topo.dist, w.pi0) for w in ws]
+    ctxs = [make_ctx(g, h, d, seed=w.seed) for (g, h, d, _), w in zip(jobs, ws)]
+    try:
+        _reset(ctxs, jobs)
+        ref = []  # each job with its own seed (the hash streams of Alg. 5)
+        for (g, hier, dist, pi0), w in zip(jobs, ws):
+            L = O.lmax(int(g.vw.sum()), int(np.prod(hier)), 0.03)
+            opi, oJ, omx, oit, okinds, _, _ = O.refine(g, hier, dist, L, pi0, rounds=10,
+                                                       params=oracle_params(w.seed))
+            ref.append((opi, oJ, omx, oit, okinds))
+        J, mw, it, _ = _run_batch(ctxs, rounds=10)
+        _check(ctxs, J, mw, it, ref)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
