@@ -43,9 +43,12 @@ if ROOT not in sys.path:
 METRIC = "edges/s per refine round, end-to-end map time at equal J, % HBM peak"
 UNIT = "edges/s"
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes per algorithmic byte of the reported kernel from an ncu capture,
-# valid only for the kernel source it was measured on (see profiles/).
-TRAFFIC = {}
+# DRAM bytes per algorithmic byte of a kernel class from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the input
+# graph of the RGG 2^20 workload; profiles/k_eval_tile_k_lp_gain_tile_k_cluster_tile_rgg2e20_level0.md),
+# valid only while the kernel's source hash matches.
+TRAFFIC = {"eval_J": {"kernel": "k_eval_tile", "kernel_hash": "1ec779b5c4c730d0", "dram_bytes": 116370432,
+                      "alg_bytes": 163348488, "dram_per_alg_byte": 116370432 / 163348488}}
 
 
 def parse():
@@ -166,10 +169,18 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def kernel_hash():
+def kernel_hash(kernel="k_eval_tile"):
+    """Hash of the source of one kernel (its function text in refine.cu, the
+    row helper and the tile staging it uses, and common.cuh)."""
+    import re
+    csrc = os.path.join(ROOT, "paper_2510_12196_gb300", "csrc")
+    ref = open(os.path.join(csrc, "refine.cu")).read()
     h = hashlib.sha256()
-    for f in ("refine.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2510_12196_gb300", "csrc", f), "rb").read())
+    for name in (kernel, "row_cost"):
+        m = re.search(r"\b" + name + r"\(.*?\n}\n", ref, re.S)
+        h.update((m.group(0) if m else "").encode())
+    for f in ("tile.cuh", "common.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -294,7 +305,7 @@ def run_ours(args, ws, rank, local):
     achieved = tv["bytes"] / (tv["ms"] / 1000.0) / 1e9 if tv["ms"] > 0 else 0.0
     tr = TRAFFIC.get(tn)
     traffic = None
-    if tr and tr.get("kernel_hash") == kernel_hash() and tv["launches"]:
+    if tr and tr.get("kernel_hash") == kernel_hash(tr["kernel"]) and tv["launches"]:
         traffic = tr["dram_per_alg_byte"] * tv["bytes"] / tv["launches"]
     roof = {"bound": "hbm", "kernel": tn,
             "scope": "launches on the input graph (level 0), CUDA events on the library stream during "

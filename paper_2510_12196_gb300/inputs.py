@@ -27,6 +27,8 @@ import dataclasses
 import math
 from typing import List, Optional, Sequence, Tuple
 
+import os
+
 import numpy as np
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -243,8 +245,8 @@ def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int,
     n = 1 << scale
     total = edge_factor * n
     ab, abc = a + b, a + b + c
-    keys = []
-    for s0 in range(0, total, chunk):
+
+    def block(s0):
         s = np.arange(s0, min(total, s0 + chunk), dtype=np.uint64)
         u = np.zeros(s.size, dtype=np.int64)
         v = np.zeros(s.size, dtype=np.int64)
@@ -257,8 +259,20 @@ def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int,
         keep = u != v
         lo = np.minimum(u[keep], v[keep])
         hi = np.maximum(u[keep], v[keep])
-        keys.append(np.unique(lo * n + hi))
-    key = np.unique(np.concatenate(keys))
+        return lo * n + hi
+
+    # chunks are independent (counter-based draws): numpy releases the GIL,
+    # so threads shorten the generation of the large graphs
+    starts = list(range(0, total, chunk))
+    if len(starts) > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1)) as ex:
+            keys = list(ex.map(block, starts))
+    else:
+        keys = [block(s0) for s0 in starts]
+    key = np.sort(np.concatenate(keys))  # sorted distinct keys (a sort is faster than a hash here)
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     lo, hi = key // n, key % n
     perm = random_permutation(n, seed ^ 0xA11CE if relabel_seed is None else relabel_seed)
     lo, hi = perm[lo], perm[hi]

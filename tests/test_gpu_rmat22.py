@@ -1,0 +1,82 @@
+"""The R-MAT scale-22 workload at full size (4.19M vertices, edge factor 16,
+hierarchy 4:16:8, distances 1:10:100, eps 0.03; the degree-skewed case).  The
+oracle cannot run the whole multilevel map at this size in test time, so the
+GPU result is checked through outputs the oracle computes exactly: J and the
+block weights of the returned mapping, the first clustering level and its
+contraction on the same input, and the Alg. 4 decisions of the hubs and of
+sampled vertices; plus determinism."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_12196_gb300 import gpumap as G
+from paper_2510_12196_gb300 import inputs as I
+
+from gpu_helpers import make_ctx, oracle_params
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    return I.workload_rmat(22)
+
+
+def test_rmat22_full_map(rmat22):
+    w = rmat22
+    g, t = w.graph, w.topo
+    k = t.k
+    L = O.lmax(int(g.vw.sum()), k, t.eps)
+    ctx = make_ctx(g, t.hier, t.dist, eps=t.eps, seed=w.seed)
+    try:
+        pi = np.zeros(g.n, np.int32)
+        J = G.map_run(ctx, pi)
+        st = G.map_stats(ctx)
+        assert st.levels >= 3
+        # J and balance of the returned mapping, recomputed by the oracle
+        oJ, omx, _ = O.objective(g, t.hier, t.dist, pi)
+        assert J == oJ == st.J[0]
+        assert omx <= L
+        assert pi.min() >= 0 and pi.max() < k
+
+        # determinism: a second run (graphs replayed) gives the same mapping
+        pi2 = np.zeros(g.n, np.int32)
+        assert G.map_run(ctx, pi2) == J and np.array_equal(pi, pi2)
+
+        # the first clustering level and its contraction, exactly as the oracle
+        prm = oracle_params(w.seed)
+        wcap = max(L // prm.cluster_cap_div, int(g.vw.max()))
+        M, nc = O.cluster(g, wcap, prm, level=0)
+        _, _, _, _, M_gpu = G.map_get_level_graph(ctx, 0, with_M=True)
+        assert np.array_equal(M_gpu, M)
+        xc, ac, wc, vc = O.contract(g, M, nc)
+        x1, a1, w1, v1, _ = G.map_get_level_graph(ctx, 1, with_M=False)
+        assert np.array_equal(x1, xc) and np.array_equal(a1, ac)
+        assert np.array_equal(w1, wc) and np.array_equal(v1, vc)
+        assert int(v1.sum()) == int(g.vw.sum())
+
+        # one Alg. 4 step on the input graph from the final mapping: the
+        # decisions of the 32 largest hubs and of 2000 sampled vertices
+        G.map_set_mapping(ctx, 0, pi)
+        G.map_set_lock(ctx, 0, np.zeros(g.n, np.uint8))
+        G.map_lp_step(ctx, 0)
+        pp, gain, inx, _ = G.map_get_lp_state(ctx, 0)
+        deg = np.diff(g.xadj)
+        rng = np.random.default_rng(22)
+        sample = np.unique(np.concatenate([np.argsort(-deg, kind="stable")[:32],
+                                           rng.choice(g.n, 2000, replace=False)]))
+        for v in sample.tolist():
+            nb = np.unique(pi[g.adj[g.xadj[v]:g.xadj[v + 1]]])
+            cands = [int(q) for q in nb if q != pi[v]]
+            if not cands:
+                assert inx[v] == 0
+                continue
+            gains = [O.gain(g, t.hier, t.dist, pi, v, q) for q in cands]
+            best = max(gains)
+            q_best = min(q for q, gq in zip(cands, gains) if gq == best)
+            if best >= 0:
+                assert inx[v] == 1 and pp[v] == q_best and gain[v] == best, v
+            else:
+                assert inx[v] == 0, v
+    finally:
+        G.map_destroy(ctx)
