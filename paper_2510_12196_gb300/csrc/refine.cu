@@ -126,6 +126,13 @@ struct EvalCtl {
 };
 __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec);
 
+// True when the J evaluation closing an Alg. 6 iteration has nothing to do:
+// after an LP or weak step the step itself added its exact change of J to the
+// accumulator, which the previous decision had set to the old J.
+__device__ __forceinline__ bool incremental_j(const RefineState* st, int phase) {
+  return st && phase == 1 && (st->kind == KIND_LP || st->kind == KIND_WEAK);
+}
+
 // J contribution of the low-degree vertices (warp tiles, one lane per vertex).
 // With a controller attached, the last block to finish runs the Alg. 6
 // decision on the complete J (the high-degree part is added before).
@@ -139,7 +146,8 @@ __global__ void __launch_bounds__(kTileThreads) k_eval_tile(GraphView g, const i
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
-  const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
+  // after an LP or weak step Jacc already holds J (old J + the exact change)
+  const int64_t ntiles = incremental_j(ec.s, ec.phase) ? 0 : ((int64_t)g.n + kTileV - 1) / kTileV;
   int64_t acc = 0;
   for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
     const TileLane t = stage_tile(tg, tile * kTileV, lane, sc[warp], sw[warp], GatherPi{pi});
@@ -158,9 +166,11 @@ __global__ void __launch_bounds__(kTileThreads) k_eval_tile(GraphView g, const i
 
 // J contribution of the high-degree vertices (one CTA per vertex).
 __global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
-                                                          const int32_t* __restrict__ pi, Topo topo, int64_t* Jacc) {
+                                                          const int32_t* __restrict__ pi, Topo topo, int64_t* Jacc,
+                                                          const RefineState* st, int phase) {
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
+  if (incremental_j(st, phase)) return;
   load_sdist(sdist, topo);
   __syncthreads();
   int64_t acc = 0;
@@ -508,6 +518,83 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_after_high(GraphView g, const
     s = block_sum(s, sm);
     if (threadIdx.x == 0 && s >= 0) lock[v] = 1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Exact change of J by a simultaneous move (LP step 3, weak rebalancing)
+// ---------------------------------------------------------------------------
+// With M the movers, J changes by the sum over the CSR entries (v, u) of the
+// movers' rows of w (D(new v, new u) - D(old v, old u)), doubled when u stays
+// (the entry (u, v) of u's row changes by the same amount but u's row is not
+// visited) and taken once when u moves too (its own row adds the twin entry).
+// Launched before the move is applied (P still holds the old mapping).
+struct LpMoves {  // LP: M = lock, target P'
+  const uint8_t* lock;
+  const int32_t* pp;
+  __device__ __forceinline__ bool moved(int64_t v) const { return lock[v] != 0; }
+  __device__ __forceinline__ int32_t target(int64_t v) const { return pp[v]; }
+};
+struct WeakMoves {  // weak rebalancing: M = eligible and selected, target the destination
+  const uint8_t* elig;
+  const uint8_t* sel;
+  const int32_t* dest;
+  __device__ __forceinline__ bool moved(int64_t v) const { return elig[v] && sel[v]; }
+  __device__ __forceinline__ int32_t target(int64_t v) const { return dest[v]; }
+};
+
+template <class Mv>
+__device__ __forceinline__ int64_t delta_entry(const Mv& mv, const int32_t* pi, const int32_t* sdist,
+                                               int32_t ov, int32_t nv, int32_t u, int32_t w) {
+  const int32_t ou = pi[u];
+  const bool um = mv.moved(u);
+  const int32_t nu = um ? mv.target(u) : ou;
+  const int64_t d = (int64_t)w * (dcode(sdist, nv, nu) - dcode(sdist, ov, ou));
+  return um ? d : 2 * d;
+}
+
+// movers of degree <= kLowDeg: one 8-lane sub-warp per vertex
+template <class Mv>
+__global__ void __launch_bounds__(kThreads) k_delta_low(GraphView g, const int32_t* __restrict__ pi, Mv mv, Topo topo,
+                                                        int64_t* Jacc, const RefineState* st, int kind) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  if (st->kind != kind) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  const int lane = threadIdx.x & (kSubWarp - 1);
+  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  int64_t acc = 0;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
+    if (!mv.moved(v)) continue;
+    const int64_t b = g.xadj[v], e = g.xadj[v + 1];
+    if (e - b > kLowDeg) continue;
+    const int32_t ov = pi[v], nv = mv.target(v);
+    for (int64_t x = b + lane; x < e; x += kSubWarp) acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[x], g.adjw[x]);
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
+}
+
+// movers of degree > kLowDeg: one CTA per vertex
+template <class Mv>
+__global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                           const int32_t* __restrict__ pi, Mv mv, Topo topo,
+                                                           int64_t* Jacc, const RefineState* st, int kind) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  if (st->kind != kind) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  int64_t acc = 0;
+  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
+    const int32_t v = hi[i];
+    if (!mv.moved(v)) continue;
+    const int32_t ov = pi[v], nv = mv.target(v);
+    for (int64_t x = g.xadj[v] + threadIdx.x; x < g.xadj[v + 1]; x += blockDim.x)
+      acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[x], g.adjw[x]);
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
 }
 
 // Alg. 4 step 3: simultaneous move of M (lock = moved), block weights.
@@ -1153,6 +1240,12 @@ __device__ void control_step(RefineState* s, int64_t mx, int64_t J, const CtlArg
 }
 
 // Last block of a fused J evaluation: the Alg. 6 decision on the complete J.
+// Value of the J accumulator for the step just decided: the current J when
+// that step adds its exact change (LP, weak), else 0 (a full evaluation).
+__device__ __forceinline__ int64_t next_j_base(const RefineState* s, int64_t J) {
+  return (s->kind == KIND_LP || s->kind == KIND_WEAK) ? J : 0;
+}
+
 __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec) {
   __shared__ unsigned int last;
   __shared__ int64_t smax[32];
@@ -1168,9 +1261,9 @@ __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec) {
   const int64_t mx = block_max_w(ec.W, ec.a.kc, smax);
   if (threadIdx.x == 0) {
     const int64_t J = (int64_t)atomicAdd((unsigned long long*)Jacc, 0ULL);
-    *Jacc = 0;
     *ec.ctr = 0;
     control_step(ec.s, mx, J, ec.a, ec.phase, ec.h, ec.use_h);
+    *Jacc = next_j_base(ec.s, J);
   }
 }
 
@@ -1221,13 +1314,24 @@ void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr) {
   Level& L = c.lv[lvl];
   c.prof_level = lvl;
   if (L.n_hi)
-    k_eval_high<<<std::min(L.n_hi, c.num_sms * 8), kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc); count_launch();
+    k_eval_high<<<std::min(L.n_hi, c.num_sms * 8), kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc,
+                                                                         ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
   cudaEvent_t ev = c.prof_begin();
   const EvalCtl none{nullptr, nullptr, nullptr, CtlArgs{}, 0, 0, 0};
   k_eval_tile<<<tile_grid(c, (const void*)k_eval_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc,
                                                                                        ec ? *ec : none); count_launch();
   // xadj (8) + P(v) (4) per vertex; adjacency (4) + weight (4) + gathered P(u) (4) per entry
   c.prof_end(ev, PK_EVAL, 12 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+}
+
+template <class Mv>
+void launch_delta(Ctx& c, int lvl, Mv mv, int kind) {
+  Level& L = c.lv[lvl];
+  k_delta_low<Mv><<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.pi, mv, c.topo, c.Jacc,
+                                                                                 c.state, kind); count_launch();
+  if (L.n_hi)
+    k_delta_high<Mv><<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
+        view(L), L.hi, L.n_hi, L.pi, mv, c.topo, c.Jacc, c.state, kind); count_launch();
 }
 
 void launch_lp(Ctx& c, int lvl) {
@@ -1250,6 +1354,7 @@ void launch_lp(Ctx& c, int lvl) {
   if (L.n_hi)
     k_lp_after_high<<<gh, kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.pp, c.gain, c.inx, c.lock, c.topo,
                                                  c.state); count_launch();
+  launch_delta(c, lvl, LpMoves{c.lock, c.pp}, KIND_LP);
   k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.state); count_launch();
 }
 
@@ -1301,6 +1406,7 @@ void launch_rebalance(Ctx& c, int lvl, bool prep_done = false) {
   } else {
     big(c.st, nullptr, nullptr);
   }
+  launch_delta(c, lvl, WeakMoves{c.elig, selected, c.dest}, KIND_WEAK);
   k_reb_apply_sel<<<g, kThreads, 0, c.st>>>(L.n, c.elig, selected, c.dest, L.pi, L.vw, c.W, c.state); count_launch();
 }
 
@@ -1664,6 +1770,32 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane) {
   return x;
 }
 
+// Exact change of J by the moves of an LP or weak step, added to the J
+// accumulator (the mapping still holds the old values): the movers of each
+// warp tile are served four at a time by 8-lane sub-warps.
+template <class Mv>
+__device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const EngGeom& eg, int64_t ntiles) {
+  const GraphView& g = J.g;
+  const int lane = eg.lane, sub = lane >> 3, sl = lane & 7;
+  int64_t acc = 0;
+  for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+    const int64_t v = tile * kTileV + lane;
+    const unsigned work = __ballot_sync(0xffffffffu, v < g.n && mv.moved(v));
+    const int rounds = (__popc(work) + 3) / 4;
+    for (int r = 0; r < rounds; r++) {
+      const int src = tile_worker(work, r, sub);
+      if (src < 0) continue;
+      const int64_t vv = tile * kTileV + src;
+      const int32_t ov = J.pi[vv], nv = mv.target(vv);
+      const int64_t xe = g.xadj[vv + 1];
+      for (int64_t x = g.xadj[vv] + sl; x < xe; x += kSubWarp)
+        acc += delta_entry(mv, J.pi, S.sdist, ov, nv, g.adj[x], g.adjw[x]);
+    }
+  }
+  acc = block_sum(acc, S.sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
+}
+
 // Alg. 6 on one job by the calling cluster (all its threads call it).
 template <int kTE>
 __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int32_t* sc, int32_t* sw,
@@ -1700,13 +1832,18 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     J.best[v] = J.pi[v];
   }
   int phase = 0;
+  int32_t prev_kind = KIND_NONE;
   TileLane t0{};
   int64_t Tp0 = 0;
   bool cand0 = false;
   while (true) {
-    // J of the current mapping, then the Alg. 6 decision
+    // J of the current mapping (after an LP or weak step the accumulator
+    // already holds it: old J plus the step's exact change), then the Alg. 6
+    // decision
+    const bool full = phase == 0 || !(prev_kind == KIND_LP || prev_kind == KIND_WEAK);
+    const bool reuse = single && full;  // the gain pass may use this pass's staged tiles
     int64_t acc = 0;
-    for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+    for (int64_t tile = full ? eg.gw : ntiles; tile < ntiles; tile += eg.GW) {
       int64_t Tp;
       bool cand;
       const TileLane t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
@@ -1725,8 +1862,8 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       const int64_t mx = block_max_w(J.W, J.topo.kc, S.smax);
       if (threadIdx.x == 0) {
         const int64_t Jv = *(volatile int64_t*)J.Jacc;
-        *J.Jacc = 0;
         control_step(s, mx, Jv, J.ctl, phase, 0, 0);
+        *J.Jacc = next_j_base(s, Jv);
       }
     }
     eng_sync();
@@ -1737,13 +1874,14 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       for (int64_t v = gt; v < n; v += GT) J.best[v] = J.pi[v];
     if (done) break;
     phase = 1;
+    prev_kind = kind;
     if (kind == KIND_LP) {
       // Alg. 4 step 1: staged tiles, lane check, sub-warp work queue
       for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
         TileLane t = t0;
         int64_t Tp = Tp0;
         bool cand = cand0;
-        if (!single) t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
+        if (!reuse) t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
         int32_t p = -1;
         if (t.v < n) {
           p = J.pi[t.v];
@@ -1808,6 +1946,8 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
           if (src >= 0 && sl == 0 && sum >= 0) J.lock[vv] = 1;
         }
       }
+      eng_sync();
+      eng_delta(J, LpMoves{J.lock, J.pp}, S, eg, ntiles);
       eng_sync();
       // step 3: simultaneous move of M
       for (int64_t v = gt; v < n; v += GT) {
@@ -1948,6 +2088,8 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     }
     eng_sync();
     if (!strong) {
+      eng_delta(J, WeakMoves{J.elig, J.sel, J.dest}, S, eg, ntiles);
+      eng_sync();
       for (int64_t v = gt; v < n; v += GT) {
         if (!J.elig[v] || !J.sel[v]) continue;
         const int32_t p = J.pi[v], q = J.dest[v];
