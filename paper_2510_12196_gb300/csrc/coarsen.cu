@@ -346,14 +346,77 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const 
   }
 }
 
-// 1: admitted without ordering (the whole demand fits), 2: contested
+// 1: admitted without ordering (the whole demand fits), 2: contested.  The
+// contested requests are also appended (in any order) as (target << 32 |
+// tie-hash, id) pairs for the single-CTA resolution below.
 __global__ void k_cluster_classify(int32_t n, const int32_t* __restrict__ req, const int32_t* __restrict__ Wc,
-                                   const int32_t* __restrict__ ReqW, int64_t wcap, uint8_t* flag) {
+                                   const int32_t* __restrict__ ReqW, int64_t wcap, uint8_t* flag, uint64_t seed,
+                                   int32_t level, uint64_t* key, int32_t* val, ClusterState* cs) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t = req[v];
     uint8_t f = 0;
     if (t >= 0) f = ((int64_t)Wc[t] + ReqW[t] <= wcap) ? 1 : 2;
     flag[v] = f;
+    if (f == 2) {
+      const unsigned long long i = atomicAdd((unsigned long long*)&cs->ncont, 1ULL);
+      const uint32_t hk = (uint32_t)(h_active(seed, level, (int32_t)v) >> 32);
+      key[i] = ((uint64_t)(uint32_t)t << 32) | hk;
+      val[i] = (int32_t)v;
+    }
+  }
+}
+
+// Contested requests, when there are at most kSmallThreads of them: one CTA
+// orders them by (target, tie-hash, id) with a rank sort (the position of a
+// request is the number of requests before it in that order, so the result
+// does not depend on the append order) and admits each while the target's
+// weight plus the requests up to it stay within the cap.  Longer lists take
+// the multi-CTA path (scan compaction in id order, stable radix sort).
+__global__ void __launch_bounds__(kSmallThreads) k_cluster_resolve(const uint64_t* __restrict__ key,
+                                                                   const int32_t* __restrict__ val,
+                                                                   const ClusterState* cs,
+                                                                   const int32_t* __restrict__ Wc,
+                                                                   const int32_t* __restrict__ vw, int64_t wcap,
+                                                                   uint8_t* flag, cudaGraphConditionalHandle h_big) {
+  __shared__ uint64_t sk[kSmallThreads];
+  __shared__ int32_t sv[kSmallThreads];
+  __shared__ uint64_t ok[kSmallThreads];
+  __shared__ int32_t ov[kSmallThreads];
+  __shared__ int64_t ex[kSmallThreads];
+  __shared__ int64_t sm[33];
+  const int64_t n64 = cs->ncont;
+  if (threadIdx.x == 0) cudaGraphSetConditional(h_big, n64 > kSmallThreads ? 1u : 0u);
+  if (n64 <= 0 || n64 > kSmallThreads) return;
+  const int n = (int)n64, i = threadIdx.x;
+  uint64_t ki = 0;
+  int32_t vi = 0;
+  if (i < n) {
+    ki = key[i];
+    vi = val[i];
+    sk[i] = ki;
+    sv[i] = vi;
+  }
+  __syncthreads();
+  if (i < n) {
+    int r = 0;
+    for (int j = 0; j < n; j++) {
+      const uint64_t kj = sk[j];
+      r += (kj < ki || (kj == ki && sv[j] < vi)) ? 1 : 0;
+    }
+    ok[r] = ki;
+    ov[r] = vi;
+  }
+  __syncthreads();
+  const int64_t c = i < n ? (int64_t)vw[ov[i]] : 0;
+  int64_t tot;
+  const int64_t e = block_exclusive_scan(c, sm, &tot);
+  ex[i] = e;
+  __syncthreads();
+  if (i < n) {
+    const uint32_t t = (uint32_t)(ok[i] >> 32);
+    int h = i;
+    while (h > 0 && (uint32_t)(ok[h - 1] >> 32) == t) h--;  // first request of the same target
+    flag[ov[i]] = ((int64_t)Wc[t] + (e + c - ex[h]) <= wcap) ? 1 : 0;
   }
 }
 
@@ -407,7 +470,8 @@ __global__ void k_cluster_admit(const uint64_t* __restrict__ key, const int32_t*
 
 __global__ void k_cluster_apply(int32_t n, const int32_t* __restrict__ req, const uint8_t* __restrict__ flag,
                                 int32_t* C, int32_t* Wc, int32_t* ReqW, const int32_t* __restrict__ vw,
-                                int64_t* moved) {
+                                int64_t* moved, ClusterState* cs) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) cs->ncont = 0;  // for the next sub-round
   int32_t mine = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t = req[v];
@@ -430,6 +494,7 @@ __global__ void k_cl_init(ClusterState* cs, int32_t iters, cudaGraphConditionalH
   cs->done = iters <= 0;
   cs->moved = 0;
   cs->kernels = 0;
+  cs->ncont = 0;
   if (use_h) cudaGraphSetConditional(h, iters > 0 ? 1u : 0u);
 }
 __global__ void k_cl_begin(ClusterState* cs) { cs->moved = 0; }
@@ -703,6 +768,9 @@ void check_err(Ctx& c) {
 
 // One clustering sub-round: ratings and requests, classification, ordered
 // admission of the contested requests, moves.
+// adds the kernels of a conditional body that ran to the graph's count
+__global__ void k_count_body(unsigned long long* kernels, unsigned long long n) { *kernels += n; }
+
 void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
   Level& L = c.lv[lvl];
   const int32_t n = L.n;
@@ -720,16 +788,41 @@ void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
   if (L.n_hi)
     k_cluster_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
         view(L), L.hi, L.n_hi, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
-  k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag); count_launch();
-  scan(LoadContested{flag}, StoreContested{c.req, c.cfg.seed, lvl, c.sort.key[0], c.sort.val[0]}, n, nullptr,
-       c.scan, c.st);
-  k_copy_i64<<<1, 1, 0, c.st>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_cont); count_launch();
-  const int cur = radix_sort_pairs(c.sort, n, d_cont, kbits, c.st, &c.cap, &c.cstate->kernels);
-  scan(LoadSortedVw{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_cont, c.scan, c.st);
-  k_cluster_heads<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.P64, d_cont, n, c.headP); count_launch();
-  k_cluster_admit<<<gv, kThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_cont, n, c.Wc,
+  k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag, c.cfg.seed, lvl, c.sort.key[0],
+                                                c.sort.val[0], c.cstate); count_launch();
+  // contested requests: compaction in id order, stable sort by (target,
+  // tie-hash), per-target prefix, admission
+  auto big = [&](cudaStream_t bs) {
+    cudaStream_t saved = c.st;
+    c.st = bs;
+    scan(LoadContested{flag}, StoreContested{c.req, c.cfg.seed, lvl, c.sort.key[0], c.sort.val[0]}, n, nullptr,
+         c.scan, bs);
+    k_copy_i64<<<1, 1, 0, bs>>>(c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)), d_cont); count_launch();
+    const int cur = radix_sort_pairs(c.sort, n, d_cont, kbits, bs, &c.cap, &c.cstate->kernels);
+    scan(LoadSortedVw{c.sort.val[cur], L.vw}, StoreExcl{c.P64}, n, d_cont, c.scan, bs);
+    k_cluster_heads<<<gv, kThreads, 0, bs>>>(c.sort.key[cur], c.P64, d_cont, n, c.headP); count_launch();
+    k_cluster_admit<<<gv, kThreads, 0, bs>>>(c.sort.key[cur], c.sort.val[cur], c.P64, c.headP, d_cont, n, c.Wc,
                                              L.vw, wcap, flag); count_launch();
-  k_cluster_apply<<<gv, kThreads, 0, c.st>>>(n, c.req, flag, c.C, c.Wc, c.ReqW, L.vw, &c.cstate->moved); count_launch();
+    c.st = saved;
+  };
+  if (c.cap.on()) {
+    // a short list is resolved by one CTA; the multi-CTA path runs only for
+    // longer ones (conditional node)
+    cudaGraphConditionalHandle h = cap_handle(c.st, 0);
+    k_cluster_resolve<<<1, kSmallThreads, 0, c.st>>>(c.sort.key[0], c.sort.val[0], c.cstate, c.Wc, L.vw, wcap, flag,
+                                                     h); count_launch();
+    long long body = 0;
+    long long* outer = set_capture_counter(&body);
+    cap_cond(c.cap, c.st, h, cudaGraphCondTypeIf, [&](cudaStream_t bs) {
+      big(bs);
+      k_count_body<<<1, 1, 0, bs>>>(&c.cstate->kernels, (unsigned long long)body + 1); count_launch();
+    });
+    set_capture_counter(outer);
+  } else {
+    big(c.st);  // stream launches: always the multi-CTA path (same admissions)
+  }
+  k_cluster_apply<<<gv, kThreads, 0, c.st>>>(n, c.req, flag, c.C, c.Wc, c.ReqW, L.vw, &c.cstate->moved,
+                                             c.cstate); count_launch();
 }
 
 // Captures the clustering loop of one level: init; WHILE(continue) {

@@ -57,6 +57,7 @@ struct ClusterState {
   int32_t done;
   int64_t moved;       // vertices moved in the current iteration
   unsigned long long kernels;  // kernels run by conditional graph bodies
+  int64_t ncont;       // contested requests of the current sub-round (appended)
 };
 
 // Kernel classes timed by the optional CUDA-event profiler.
