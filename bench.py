@@ -170,14 +170,15 @@ def measured_peak():
 
 
 def kernel_hash(kernel="k_eval_tile"):
-    """Hash of the source of one kernel (its function text in refine.cu, the
-    row helper and the tile staging it uses, and common.cuh)."""
+    """Hash of the source of one kernel: its definition (launch bounds and
+    body, from refine.cu or coarsen.cu), the row helper, the tile staging and
+    common.cuh."""
     import re
     csrc = os.path.join(ROOT, "paper_2510_12196_gb300", "csrc")
-    ref = open(os.path.join(csrc, "refine.cu")).read()
+    text = "".join(open(os.path.join(csrc, f)).read() for f in ("refine.cu", "coarsen.cu"))
     h = hashlib.sha256()
     for name in (kernel, "row_cost"):
-        m = re.search(r"\b" + name + r"\(.*?\n}\n", ref, re.S)
+        m = re.search(r"\n[^\n]*\b" + name + r"\(.*?\n}\n", text, re.S)
         h.update((m.group(0) if m else "").encode())
     for f in ("tile.cuh", "common.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())

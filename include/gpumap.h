@@ -87,7 +87,11 @@ typedef struct {
   void* alloc_user;
   int32_t launch_mode;   /* 0: refinement and clustering loops as CUDA graphs (default); 1: stream launches */
   int32_t engine_max_n;  /* levels with at most this many vertices (and no vertex of degree > 128) are refined
-                            by the fused one-launch engine; 0: library default (32768); -1: never */
+                            by the fused one-launch engine on one thread-block cluster; 0: library default
+                            (32768); -1: never */
+  int32_t grid_engine_max_n; /* larger levels with at most this many vertices (and no vertex of degree > 128)
+                            run the same engine over all SMs (cooperative launch); 0: library default
+                            (262144); -1: never */
 } map_config;
 
 typedef struct {

@@ -240,7 +240,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       throw ApiError(MAP_E_INVALID, "map_config field out of range");
     if (c.cfg.launch_mode < 0 || c.cfg.launch_mode > 1) throw ApiError(MAP_E_INVALID, "launch_mode must be 0 or 1");
     c.use_graphs = c.cfg.launch_mode == 0;
-    if (c.cfg.engine_max_n < -1) throw ApiError(MAP_E_INVALID, "engine_max_n must be >= -1");
+    if (c.cfg.engine_max_n < -1 || c.cfg.grid_engine_max_n < -1)
+      throw ApiError(MAP_E_INVALID, "engine_max_n and grid_engine_max_n must be >= -1");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     for (auto& cs : c.cap.s) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -315,6 +316,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       ctx->c.h_state = nullptr;
       if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
       ctx->c.h_cstate = nullptr;
+      if (ctx->c.h_small) cudaFreeHost(ctx->c.h_small);
+      ctx->c.h_small = nullptr;
       cudaStreamSynchronize(ctx->c.st);
       for (auto& cs : ctx->c.cap.s)
         if (cs) cudaStreamDestroy(cs);
@@ -337,6 +340,7 @@ void map_destroy(map_ctx* ctx) {
     cudaStreamSynchronize(ctx->c.st);
     if (ctx->c.h_state) cudaFreeHost(ctx->c.h_state);
     if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
+    if (ctx->c.h_small) cudaFreeHost(ctx->c.h_small);
     if (ctx->c.h_eng_job) cudaFreeHost(ctx->c.h_eng_job);
     for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
     for (auto& L : ctx->c.lv) {

@@ -164,6 +164,8 @@ struct Ctx {
   unsigned int* evctr = nullptr;  // blocks finished in a fused J evaluation
   RefineState* state = nullptr;
   RefineState* h_state = nullptr;  // pinned mirror
+  int64_t* h_small = nullptr;      // pinned, a few values read back together
+  int64_t* d_stats = nullptr;      // device, per-level statistics
   int32_t* trace_kind = nullptr;
   int64_t* trace_J = nullptr;
   int64_t* trace_maxw = nullptr;
@@ -192,6 +194,8 @@ struct Ctx {
   // fused small-level engine
   int eng_max_cluster = 0;
   void* eng_job = nullptr;    // device job descriptor
+  void* gbar = nullptr;       // device barrier state of the grid-wide engine
+  int eng_grid_blocks = 0;    // resident blocks of the grid-wide engine (0: not known yet)
   void* h_eng_job = nullptr;  // pinned staging
 
   // resident blocks per SM of a kernel (occupancy API, cached)

@@ -200,12 +200,33 @@ __global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const int32_t* 
 // index holding the result.  Items of warp w are [w * items, (w + 1) * items)
 // in lane-strided order, so (warp, item, lane) order is index order and equal
 // digits keep it.
+// Up to kRankSortMax pairs are ordered by a rank sort instead (the position of
+// pair i is the number of pairs with a smaller key, or an equal key and a
+// smaller index: the same stable order at a cost that grows with n instead of
+// the radix passes' fixed cost over kSmallSort slots).
+constexpr int kRankSortMax = 512;
 __device__ __forceinline__ int cta_sort_small(uint64_t* ks, int32_t* vs, int32_t* wcnt, int32_t* dbase, int64_t* sm,
                                               int n, int bits) {
   constexpr int kW = kSmallThreads / 32;
   constexpr int kItems = kSmallSort / kSmallThreads;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const unsigned lt = (1u << l) - 1u;
+  if (n <= kRankSortMax) {
+    const uint64_t mask = bits >= 64 ? ~0ULL : ((1ULL << bits) - 1ULL);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+      const uint64_t ki = ks[i] & mask;
+      int r = 0;
+      for (int j = 0; j < n; j++) {
+        const uint64_t kj = ks[j] & mask;
+        r += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+      }
+      ks[kSmallSort + r] = ks[i];
+      vs[kSmallSort + r] = vs[i];
+    }
+    __syncthreads();
+    return 1;
+  }
   int cur = 0;
   for (int shift = 0; shift < bits; shift += 8) {
     const uint64_t* kc = ks + cur * kSmallSort;

@@ -136,7 +136,7 @@ __device__ __forceinline__ bool incremental_j(const RefineState* st, int phase) 
 // J contribution of the low-degree vertices (warp tiles, one lane per vertex).
 // With a controller attached, the last block to finish runs the Alg. 6
 // decision on the complete J (the high-degree part is added before).
-__global__ void __launch_bounds__(kTileThreads) k_eval_tile(GraphView g, const int32_t* __restrict__ pi, Topo topo,
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_eval_tile(GraphView g, const int32_t* __restrict__ pi, Topo topo,
                                                             int64_t* Jacc, EvalCtl ec) {
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
@@ -268,7 +268,7 @@ __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t
 // neighbour PEs; each lane checks its own vertex (T(P(v)), any neighbour
 // outside P(v)); the vertices with candidates are then evaluated four at a
 // time by 8-lane sub-warps from the staged entries.
-__global__ void __launch_bounds__(kTileThreads) k_lp_gain_tile(GraphView g, const int32_t* __restrict__ pi,
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_lp_gain_tile(GraphView g, const int32_t* __restrict__ pi,
                                                                uint8_t* __restrict__ lock, int32_t* __restrict__ pp,
                                                                int64_t* __restrict__ gain, uint8_t* __restrict__ inx,
                                                                Topo topo, const RefineState* st) {
@@ -293,12 +293,13 @@ __global__ void __launch_bounds__(kTileThreads) k_lp_gain_tile(GraphView g, cons
       if (lock[t.v]) {
         lock[t.v] = 0;
       } else if (t.staged) {
+        // T(P(v)) only for vertices with a neighbour outside P(v): interior
+        // vertices (most of them on a refined level) skip the distance sum
         const int32_t* c = sc[warp] + (t.b - t.E0);
         const int32_t* w = sw[warp] + (t.b - t.E0);
-        for (int j = 0; j < deg; j++) {
-          Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
-          cand |= c[j] != p;
-        }
+        for (int j = 0; j < deg; j++) cand |= c[j] != p;
+        if (cand)
+          for (int j = 0; j < deg; j++) Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
       } else {  // oversized tile: this lane alone, from global memory
         const GlobalRow<GatherPi> r{g.adj + t.b, g.adjw + t.b, GatherPi{pi}};
         int32_t bc;
@@ -1138,7 +1139,8 @@ __global__ void k_reb_apply_strong(const uint64_t* __restrict__ key, const int32
     atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
     mine++;
   }
-  if (mine) atomicAdd(&st->moved, mine);
+  mine = warp_sum(mine);  // one update of the shared counter per warp
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&st->moved, mine);
 }
 
 // ---------------------------------------------------------------------------
@@ -1480,6 +1482,56 @@ struct PlainRow {  // neighbour PEs through plain loads (the mapping changes ins
   __device__ __forceinline__ int32_t weight(int j) const { return adjw[j]; }
 };
 
+// Barrier between the engine's phases: the cluster's hardware barrier, or a
+// grid-wide barrier for the cooperative launch over all SMs.
+struct ClusterSync {
+  __device__ __forceinline__ void sync() const { cg::this_cluster().sync(); }
+};
+
+// Grid barrier state (zero-initialised; count returns to 0 after each use).
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  unsigned int err;  // set when a wait gave up
+  unsigned int pad;
+};
+constexpr unsigned kBarSpinLimit = 1u << 24;  // polls of about 64 ns: ~1 s
+
+struct GridSync {
+  GridBar* bar;
+  unsigned int* flag;  // shared memory of the calling block
+  // Every block arrives once; the last one resets the count and advances the
+  // generation the others poll.  Fences order each block's phase writes
+  // before its arrival and the following reads after the release.  A wait
+  // that exceeds the limit marks the barrier failed; the blocks then leave
+  // the kernel at their next barrier and the host reports the failure.
+  __device__ __forceinline__ void sync() const {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned g0 = *(volatile unsigned*)&bar->gen;
+      __threadfence();
+      if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+        bar->count = 0;
+        __threadfence();
+        atomicAdd(&bar->gen, 1u);
+      } else {
+        unsigned spins = 0;
+        while (*(volatile unsigned*)&bar->gen == g0) {
+          if (++spins > kBarSpinLimit || *(volatile unsigned*)&bar->err) {
+            atomicOr(&bar->err, 1u);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+      *flag = *(volatile unsigned*)&bar->err;
+    }
+    __syncthreads();
+    if (*(volatile unsigned*)flag) asm volatile("exit;");
+  }
+};
+
 __device__ __forceinline__ void eng_sync() { cg::this_cluster().sync(); }
 
 // block-wide exclusive scan over chunks of blockDim values: f(i) for i < n,
@@ -1682,7 +1734,7 @@ struct PlainGather {  // neighbour PEs through plain loads (the mapping changes 
 template <int kTE>
 __device__ __forceinline__ TileLane eng_stage(const EngineJob& J, const TileGraph& tg, int64_t tile, int lane,
                                               int32_t* sc, int32_t* sw, const int32_t* sdist, int64_t& Tp,
-                                              bool& cand) {
+                                              bool& cand, bool all_tp) {
   const TileLane t = stage_tile<kTE>(tg, tile * kTileV, lane, sc, sw, PlainGather{J.pi});
   Tp = 0;
   cand = false;
@@ -1692,10 +1744,9 @@ __device__ __forceinline__ TileLane eng_stage(const EngineJob& J, const TileGrap
     if (t.staged) {
       const int32_t* c = sc + (t.b - t.E0);
       const int32_t* w = sw + (t.b - t.E0);
-      for (int j = 0; j < deg; j++) {
-        Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
-        cand |= c[j] != p;
-      }
+      for (int j = 0; j < deg; j++) cand |= c[j] != p;
+      if (cand || all_tp)
+        for (int j = 0; j < deg; j++) Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
     } else {
       Tp = row_cost(PlainRow{tg.adj + t.b, tg.adjw + t.b, J.pi}, deg, sdist, p);
     }
@@ -1791,15 +1842,16 @@ __device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const En
       for (int64_t x = g.xadj[vv] + sl; x < xe; x += kSubWarp)
         acc += delta_entry(mv, J.pi, S.sdist, ov, nv, g.adj[x], g.adjw[x]);
     }
+    __syncwarp();
   }
   acc = block_sum(acc, S.sm);
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
 }
 
 // Alg. 6 on one job by the calling cluster (all its threads call it).
-template <int kTE>
+template <int kTE, class Sync>
 __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int32_t* sc, int32_t* sw,
-                               const EngGeom& eg) {
+                               const EngGeom& eg, const Sync& sy) {
   const GraphView g = J.g;
   const int32_t n = g.n;
   const int64_t gt = eg.gt, GT = eg.GT;
@@ -1825,7 +1877,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     *s = z;
     *J.Jacc = 0;
   }
-  eng_sync();
+  sy.sync();
   for (int64_t v = gt; v < n; v += GT) {
     atomicAdd((unsigned long long*)&J.W[J.pi[v]], (unsigned long long)(int64_t)g.vw[v]);
     J.lock[v] = 0;
@@ -1846,7 +1898,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     for (int64_t tile = full ? eg.gw : ntiles; tile < ntiles; tile += eg.GW) {
       int64_t Tp;
       bool cand;
-      const TileLane t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
+      const TileLane t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand, true);
       acc += Tp;
       if (single) {
         t0 = t;
@@ -1857,7 +1909,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     }
     acc = block_sum(acc, S.sm);
     if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
-    eng_sync();
+    sy.sync();
     if (lead) {
       const int64_t mx = block_max_w(J.W, J.topo.kc, S.smax);
       if (threadIdx.x == 0) {
@@ -1865,8 +1917,15 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         control_step(s, mx, Jv, J.ctl, phase, 0, 0);
         *J.Jacc = next_j_base(s, Jv);
       }
+      __syncthreads();
+      // a rebalancing step: its threshold sigma and destination list U now
+      const int32_t next = *(volatile int32_t*)&s->kind;
+      if (next == KIND_WEAK || next == KIND_STRONG) {
+        const RebPrepArgs pa{J.W, J.pe_of_code, J.topo, J.lmax, J.cV, J.sigma_gap, J.U, J.cnt, J.accepted};
+        reb_prep_body(pa, next == KIND_STRONG);
+      }
     }
-    eng_sync();
+    sy.sync();
     const int32_t done = *(volatile int32_t*)&s->done;
     const int32_t kind = *(volatile int32_t*)&s->kind;
     const int32_t copy = *(volatile int32_t*)&s->copy_best;
@@ -1881,7 +1940,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         TileLane t = t0;
         int64_t Tp = Tp0;
         bool cand = cand0;
-        if (!reuse) t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand);
+        if (!reuse) t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand, false);
         int32_t p = -1;
         if (t.v < n) {
           p = J.pi[t.v];
@@ -1907,7 +1966,8 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
           }
         }
         const unsigned work = __ballot_sync(0xffffffffu, cand);
-        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane, [&](int src, int64_t Gv, int32_t bc, int32_t pv) {
+        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane,
+                        [&](int src, int64_t Gv, int32_t bc, int32_t pv) {
           const int64_t v = tile * kTileV + src;
           const bool in = Gv >= 0;
           J.inx[v] = in ? 1 : 0;
@@ -1916,7 +1976,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         });
         __syncwarp();
       }
-      eng_sync();
+      sy.sync();
       // step 2: recomputed gain under ord, one 8-lane sub-warp per candidate
       for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
         const int64_t v = tile * kTileV + lane;
@@ -1945,10 +2005,11 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
           for (int o = kSubWarp / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
           if (src >= 0 && sl == 0 && sum >= 0) J.lock[vv] = 1;
         }
+        __syncwarp();
       }
-      eng_sync();
+      sy.sync();
       eng_delta(J, LpMoves{J.lock, J.pp}, S, eg, ntiles);
-      eng_sync();
+      sy.sync();
       // step 3: simultaneous move of M
       for (int64_t v = gt; v < n; v += GT) {
         if (!J.lock[v]) continue;
@@ -1958,17 +2019,12 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         atomicAdd((unsigned long long*)&J.W[p], (unsigned long long)(-c));
         atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
       }
-      eng_sync();
+      sy.sync();
       continue;
     }
     // --- weak / strong rebalancing ---
     const bool strong = kind == KIND_STRONG;
     const int32_t t = *(volatile int32_t*)&s->t;
-    if (lead) {
-      const RebPrepArgs pa{J.W, J.pe_of_code, J.topo, J.lmax, J.cV, J.sigma_gap, J.U, J.cnt, J.accepted};
-      reb_prep_body(pa, strong);
-    }
-    eng_sync();
     const int64_t sigma = *(volatile int64_t*)&J.cnt[CNT_SIGMA];
     const int64_t nU = *(volatile int64_t*)&J.cnt[CNT_NU];
     // eligible vertices and their destinations: lane check, then staged rows
@@ -2020,7 +2076,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
                      });
       __syncwarp();
     }
-    eng_sync();
+    sy.sync();
     // the cut bucket of each overloaded block A: the first bucket whose
     // inclusive prefix of eligible weight exceeds W(A) - L_max (one warp per
     // block, buckets lane and 32 + lane)
@@ -2048,7 +2104,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       }
     }
     if (lead && threadIdx.x == 0) J.cnt[CNT_ELIG] = 0;
-    eng_sync();
+    sy.sync();
     const int idbits = bits_for_n(n);
     for (int64_t v = gt; v < n; v += GT) {
       if (!J.elig[v]) continue;
@@ -2065,7 +2121,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         J.val0[i] = (int32_t)v;
       }
     }
-    eng_sync();
+    sy.sync();
     if (lead) {  // the cut-bucket list by (block, id), per-block prefix
       const int ln = (int)*(volatile int64_t*)&J.cnt[CNT_ELIG];
       if (ln > 0) {
@@ -2086,10 +2142,10 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         }
       }
     }
-    eng_sync();
+    sy.sync();
     if (!strong) {
       eng_delta(J, WeakMoves{J.elig, J.sel, J.dest}, S, eg, ntiles);
-      eng_sync();
+      sy.sync();
       for (int64_t v = gt; v < n; v += GT) {
         if (!J.elig[v] || !J.sel[v]) continue;
         const int32_t p = J.pi[v], q = J.dest[v];
@@ -2098,7 +2154,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         atomicAdd((unsigned long long*)&J.W[p], (unsigned long long)(-c));
         atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
       }
-      eng_sync();
+      sy.sync();
       continue;
     }
     if (lead) {  // strong: destinations in (bucket, id) order, acceptance, water-filling
@@ -2177,7 +2233,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
       }
     }
-    eng_sync();
+    sy.sync();
   }
   for (int64_t v = gt; v < n; v += GT) J.pi[v] = J.best[v];
 }
@@ -2203,7 +2259,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
   int32_t* sw = sc + kTE;
   if (!queue) {  // one job per cluster
     const int32_t jid = (int32_t)(blockIdx.x / csize);
-    if (jid < njobs) engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg);
+    if (jid < njobs) engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg, ClusterSync{});
     return;
   }
   // persistent clusters: the next job from the queue (jobs in the order given)
@@ -2213,8 +2269,29 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     const int32_t jid = *cl.map_shared_rank(&job_slot, 0);
     eng_sync();
     if (jid >= njobs) break;
-    engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg);
+    engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg, ClusterSync{});
   }
+}
+
+// The same engine over the whole grid (cooperative launch, one block per SM):
+// for levels too large for one cluster, whose graph-launched iterations are
+// dominated by launch gaps.
+template <int kTE>
+__global__ void __launch_bounds__(kEngThreads, 1) k_engine_grid(const EngineJob* __restrict__ job, GridBar* bar) {
+  __shared__ EngSmem S;
+  __shared__ unsigned int bar_flag;
+  extern __shared__ __align__(16) int32_t eng_dyn[];
+  const int warp = threadIdx.x >> 5;
+  EngGeom eg;
+  eg.lane = threadIdx.x & 31;
+  eg.lead = blockIdx.x == 0;
+  eg.gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  eg.GT = (int64_t)gridDim.x * blockDim.x;
+  eg.gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  eg.GW = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int32_t* sc = eng_dyn + warp * 2 * kTE;
+  int32_t* sw = sc + kTE;
+  engine_run_job<kTE>(*job, S, eng_dyn, sc, sw, eg, GridSync{bar, &bar_flag});
 }
 
 }  // namespace
@@ -2287,6 +2364,10 @@ void refine_alloc(Ctx& c) {
   GM_CUDA(cudaMemsetAsync(c.counters, 0, CNT_N * sizeof(int64_t), c.st));
   GM_CUDA(cudaMemsetAsync(c.state, 0, sizeof(RefineState), c.st));
   if (!c.h_state) GM_CUDA(cudaMallocHost(&c.h_state, sizeof(RefineState)));
+  if (!c.h_small) GM_CUDA(cudaMallocHost(&c.h_small, 8 * sizeof(int64_t)));
+  c.gbar = c.mem.make<GridBar>(1);
+  GM_CUDA(cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.st));
+  c.d_stats = c.mem.make<int64_t>(4);
   const size_t smem = conn_smem(c);
   if (smem > 48 * 1024) {
     GM_CUDA(cudaFuncSetAttribute(k_lp_gain_high, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2503,7 +2584,7 @@ static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* m
 static int engine_cluster(Ctx& c, const Level& L) {
   const int64_t lim = c.cfg.engine_max_n > 0 ? c.cfg.engine_max_n : (c.cfg.engine_max_n < 0 ? -1 : kEngMaxN);
   if (!c.use_graphs || c.prof || L.n > lim || L.max_deg > kEngMaxDeg) return 0;
-  int C = (L.n + 2047) / 2048;
+  int C = (L.n + 1023) / 1024;  // about one vertex per thread
   if (C < 1) C = 1;
   if (C > c.eng_max_cluster) C = c.eng_max_cluster;
   return C;
@@ -2541,6 +2622,7 @@ static void engine_attributes() {
   GM_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (dev < 0 || dev >= 256 || done[dev]) return;
+  GM_CUDA(cudaFuncSetAttribute(k_engine_grid<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(512)));
   for (int te : {256, 512}) {
     GM_CUDA(cudaFuncSetAttribute(engine_kernel(te), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(te)));
     if (cudaFuncSetAttribute(engine_kernel(te), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -2648,10 +2730,62 @@ static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, in
   if (iters) *iters = h.t;
 }
 
+// Whether a level runs the grid-wide engine (levels above the cluster
+// engine's size, up to grid_engine_max_n vertices).
+static bool engine_grid_ok(Ctx& c, const Level& L) {
+  const int64_t lim =
+      c.cfg.grid_engine_max_n > 0 ? c.cfg.grid_engine_max_n : (c.cfg.grid_engine_max_n < 0 ? -1 : (1 << 18));
+  if (!c.use_graphs || c.prof || L.n > lim || L.max_deg > kEngMaxDeg) return false;
+  if (c.eng_grid_blocks == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine_grid<512>, kEngThreads, engine_smem(512)) !=
+            cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.dev);
+    c.eng_grid_blocks = (coop && per_sm > 0) ? c.num_sms * per_sm : -1;
+  }
+  return c.eng_grid_blocks > 0;
+}
+
+static void refine_engine_grid(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
+  *static_cast<EngineJob*>(c.h_eng_job) = engine_job(c, lvl, rounds);
+  GM_CUDA(cudaMemcpyAsync(c.eng_job, c.h_eng_job, sizeof(EngineJob), cudaMemcpyHostToDevice, c.st));
+  GM_CUDA(cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.st));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)c.eng_grid_blocks);
+  cfg.blockDim = dim3(kEngThreads);
+  cfg.dynamicSmemBytes = engine_smem(512);
+  cfg.stream = c.st;
+  cudaLaunchAttribute attr{};
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  GM_CUDA(cudaLaunchKernelEx(&cfg, k_engine_grid<512>, static_cast<const EngineJob*>(c.eng_job),
+                             static_cast<GridBar*>(c.gbar)));
+  count_launch();
+  GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(c.h_small, c.gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  if (reinterpret_cast<const GridBar*>(c.h_small)->err)
+    throw ApiError(MAP_E_TIMEOUT, "a grid barrier of the refinement engine gave up waiting");
+  const RefineState h = *c.h_state;
+  if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
+  c.last_iters = h.t;
+  if (J) *J = h.best_J;
+  if (maxw) *maxw = h.best_maxw;
+  if (iters) *iters = h.t;
+}
+
 void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
   engine_setup(c);
   const int C = engine_cluster(c, c.lv[lvl]);
   if (C > 0) refine_engine(c, lvl, rounds, C, J, maxw, iters);
+  else if (engine_grid_ok(c, c.lv[lvl])) refine_engine_grid(c, lvl, rounds, J, maxw, iters);
   else if (c.use_graphs && !c.prof) refine_graph(c, lvl, rounds, J, maxw, iters);
   else refine_stream(c, lvl, rounds, J, maxw, iters);
 }
@@ -2662,62 +2796,56 @@ struct LoadHigh {
   const int64_t* xadj;
   __device__ int64_t operator()(int64_t v) const { return (xadj[v + 1] - xadj[v] > kLowDeg) ? 1 : 0; }
 };
-struct LoadHighDeg {
-  const int64_t* xadj;
-  __device__ int64_t operator()(int64_t v) const {
-    const int64_t d = xadj[v + 1] - xadj[v];
-    return d > kLowDeg ? d : 0;
-  }
-};
-struct StoreNothing {
-  __device__ void operator()(int64_t, int64_t, int64_t) const {}
-};
-__global__ void k_max_deg(int32_t n, const int64_t* __restrict__ xadj, unsigned long long* out) {
-  unsigned long long mx = 0;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long d = (unsigned long long)(xadj[v + 1] - xadj[v]);
-    mx = d > mx ? d : mx;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = y > mx ? y : mx;
-  }
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
-}
 struct StoreHigh {
   int32_t* out;
   __device__ void operator()(int64_t v, int64_t e, int64_t x) const {
     if (x) out[e] = (int32_t)v;
   }
 };
+
+__global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const int32_t* __restrict__ vw,
+                              unsigned long long* out) {
+  unsigned long long mhi = 0, mdeg = 0, mvw = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long d = (unsigned long long)(xadj[v + 1] - xadj[v]);
+    if (d > (unsigned long long)kLowDeg) mhi += d;
+    mdeg = d > mdeg ? d : mdeg;
+    const unsigned long long w = (unsigned long long)vw[v];
+    mvw = w > mvw ? w : mvw;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mhi += __shfl_xor_sync(0xffffffffu, mhi, o);
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mdeg, o);
+    mdeg = y > mdeg ? y : mdeg;
+    const unsigned long long z = __shfl_xor_sync(0xffffffffu, mvw, o);
+    mvw = z > mvw ? z : mvw;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mhi) atomicAdd(&out[0], mhi);
+    if (mdeg) atomicMax(&out[1], mdeg);
+    if (mvw) atomicMax(&out[2], mvw);
+  }
+}
 }  // namespace
 
 void classify_degrees(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
   if (!L.hi) L.hi = c.mem.make<int32_t>((size_t)std::max(1, L.n));
   scan(LoadHigh{L.xadj}, StoreHigh{L.hi}, L.n, nullptr, c.scan, c.st);
-  int64_t cnt = 0;
-  GM_CUDA(cudaMemcpyAsync(&cnt, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
+  unsigned long long* st = reinterpret_cast<unsigned long long*>(c.d_stats);
+  GM_CUDA(cudaMemsetAsync(st, 0, 3 * sizeof(int64_t), c.st));
+  const int64_t blocks = std::min<int64_t>(((int64_t)L.n + 255) / 256, (int64_t)c.num_sms * 8);
+  k_level_stats<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, c.st>>>(L.n, L.xadj, L.vw, st); count_launch();
+  // count of high-degree vertices and the three statistics, one synchronisation
+  GM_CUDA(cudaMemcpyAsync(c.h_small, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
                           cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(c.h_small + 1, st, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
-  L.n_hi = (int32_t)cnt;
-  L.m_hi = 0;
-  L.max_deg = 0;
-  if (cnt) {
-    unsigned long long* d_mx = reinterpret_cast<unsigned long long*>(c.counters + CNT_TMP);
-    GM_CUDA(cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long), c.st));
-    const int64_t blocks = std::min<int64_t>(((int64_t)L.n + 255) / 256, (int64_t)c.num_sms * 8);
-    k_max_deg<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, c.st>>>(L.n, L.xadj, d_mx); count_launch();
-    unsigned long long mx = 0;
-    GM_CUDA(cudaMemcpyAsync(&mx, d_mx, sizeof(mx), cudaMemcpyDeviceToHost, c.st));
-    GM_CUDA(cudaStreamSynchronize(c.st));
-    L.max_deg = (int64_t)mx;
-    scan(LoadHighDeg{L.xadj}, StoreNothing{}, L.n, nullptr, c.scan, c.st);
-    GM_CUDA(cudaMemcpyAsync(&L.m_hi, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, c.st));
-    GM_CUDA(cudaStreamSynchronize(c.st));
-  }
+  L.n_hi = (int32_t)c.h_small[0];
+  L.m_hi = c.h_small[1];
+  L.max_deg = c.h_small[2];
+  L.max_vw = (int32_t)c.h_small[3];
 }
 
 }  // namespace gm

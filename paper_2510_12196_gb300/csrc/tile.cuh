@@ -20,6 +20,9 @@ constexpr int kTileV = 32;        // vertices per warp tile
 constexpr int kTileE = 512;       // staged CSR entries per warp tile
 constexpr int kTileWarps = 4;     // warps per block
 constexpr int kTileThreads = kTileWarps * 32;
+// resident blocks per SM the tile kernels are compiled for (caps registers at
+// 48 per thread: 40 warps per SM keep more gathers in flight)
+constexpr int kTileMinBlocks = 10;
 
 struct TileGraph {
   int32_t n;

@@ -40,7 +40,8 @@ class MapConfig(C.Structure):
                 ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
                 ("stall_num", C.c_int32), ("stall_den", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32)]
+                ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32),
+                ("grid_engine_max_n", C.c_int32)]
 
 
 class MapStats(C.Structure):

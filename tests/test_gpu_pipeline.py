@@ -87,7 +87,8 @@ def _map_run_compare(g, hier, dist, eps=0.03, seed=0x5EED0000, **over):
         st = G.map_stats(ctx)
     finally:
         G.map_destroy(ctx)
-    opi, oJ, ost = O.map_run(g, hier, dist, eps, oracle_params(seed, **over))
+    fields = {f[0] for f in O.Params._fields_}  # execution settings do not reach the oracle
+    opi, oJ, ost = O.map_run(g, hier, dist, eps, oracle_params(seed, **{k: v for k, v in over.items() if k in fields}))
     assert st.levels == ost.levels
     assert [st.n[i] for i in range(st.levels)] == [ost.n[i] for i in range(ost.levels)]
     assert [st.iters[i] for i in range(st.levels)] == [ost.iters[i] for i in range(ost.levels)]
@@ -243,3 +244,18 @@ def test_graph_and_stream_paths_agree():
             assert r[0] == base[0] and np.array_equal(r[1], base[1]) and r[2] == base[2]
     fixed = [r for r in res if not isinstance(r[1], np.ndarray)]
     assert all(f == fixed[0] for f in fixed)
+
+
+@pytest.mark.parametrize("mode", ["grid_engine", "cluster_engine_large", "graphs_only", "stream"])
+def test_engine_modes_match_oracle(mode):
+    """The Alg. 6 loop of a level runs as a cluster launch, a cooperative
+    grid-wide launch, a graph of kernels or host-driven stream launches,
+    depending on the level size and the configuration: every mode gives the
+    oracle's result (RGG 2^17, whose input level takes the grid engine by
+    default)."""
+    g = I.rgg2d(1 << 17, I.rgg_radius(1 << 17, 12), 41, wmax=10)
+    over = {"grid_engine": {},
+            "cluster_engine_large": {"engine_max_n": 1 << 18, "grid_engine_max_n": -1},
+            "graphs_only": {"engine_max_n": -1, "grid_engine_max_n": -1},
+            "stream": {"launch_mode": 1}}[mode]
+    _map_run_compare(g, (4, 8, 8), (1, 10, 100), **over)
