@@ -17,6 +17,7 @@
 // are reduced by a prefix sum of the weights, and the coarse CSR rows follow
 // from the sorted unique keys, so adjacency order is deterministic.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 
 #include "engine.h"
@@ -98,9 +99,18 @@ __global__ void __launch_bounds__(kThreads) k_validate(GraphView g, int64_t m, u
       if (lo >= rend || g.adj[lo] != v || g.adjw[lo] != w) e_local |= ERR_ASYM;
     }
   }
-  if (e_local) atomicOr(err, e_local);
-  if (sw) atomicAdd(&sums[1], sw);
-  if (sv) atomicAdd(&sums[0], sv);
+  // one update of the shared words per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e_local |= __shfl_xor_sync(0xffffffffu, e_local, o);
+    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    sv += __shfl_xor_sync(0xffffffffu, sv, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (e_local) atomicOr(err, e_local);
+    if (sw) atomicAdd(&sums[1], sw);
+    if (sv) atomicAdd(&sums[0], sv);
+  }
 }
 
 __global__ void k_iota(int32_t* a, int64_t n) {
@@ -198,18 +208,6 @@ __device__ __forceinline__ int32_t best_cluster(const Row& r, int deg, int32_t o
   return bt;
 }
 
-// a better than b under (score desc, tie-hash asc, label asc); hashes are
-// computed only for equal scores
-__device__ __forceinline__ bool better_lazy(int32_t as, int32_t at, int32_t bs, int32_t bt, const ClusterArgs& a) {
-  if (at < 0) return false;
-  if (bt < 0) return true;
-  if (as != bs) return as > bs;
-  if (at == bt) return false;
-  const uint64_t ha = h_tie(a.seed, a.level, at), hb = h_tie(a.seed, a.level, bt);
-  if (ha != hb) return ha < hb;
-  return at < bt;
-}
-
 // Clustering ratings for the low-degree vertices.  Warp tiles stage the
 // neighbour labels; the active vertices of a tile are then rated four at a
 // time by 8-lane sub-warps reading the staged entries from shared memory.
@@ -242,34 +240,58 @@ __global__ void __launch_bounds__(kTileThreads) k_cluster_tile(GraphView g, Clus
       const int32_t ow = __shfl_sync(0xffffffffu, own, s2);
       const int32_t* c = sc[warp] + off;
       const int32_t* w = sw[warp] + off;
+      // best (score, tie-hash, label) over this lane's candidates; the hash
+      // of the current best is computed once, on the first tie
       int32_t bs = 0, bt = -1, so = 0;
+      uint64_t bh = 0;
+      bool bhk = false;
       if (src >= 0) {
         for (int j = sl; j < dg; j += kSubWarp) {
           const int32_t cj = c[j];
           so += (cj == ow) ? w[j] : 0;
-          if (cj == ow) continue;
+          if (cj == ow || cj == bt) continue;
           int32_t scj = 0;
           for (int l = 0; l < dg; l++) scj += (c[l] == cj) ? w[l] : 0;
-          if (better_lazy(scj, cj, bs, bt, a)) {
+          if (bt < 0 || scj > bs) {
             bs = scj;
             bt = cj;
+            bhk = false;
+            continue;
+          }
+          if (scj < bs) continue;
+          if (!bhk) {
+            bh = h_tie(a.seed, a.level, bt);
+            bhk = true;
+          }
+          const uint64_t hj = h_tie(a.seed, a.level, cj);
+          if (hj < bh || (hj == bh && cj < bt)) {
+            bt = cj;
+            bh = hj;
           }
         }
       }
+      if (bt >= 0 && !bhk) bh = h_tie(a.seed, a.level, bt);
 #pragma unroll
       for (int o = kSubWarp / 2; o > 0; o >>= 1) {
         so += __shfl_xor_sync(0xffffffffu, so, o);
         const int32_t os = __shfl_xor_sync(0xffffffffu, bs, o);
         const int32_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
-        if (better_lazy(os, ot, bs, bt, a)) {
+        const uint64_t oh = __shfl_xor_sync(0xffffffffu, bh, o);
+        if (ot >= 0 && (bt < 0 || os > bs || (os == bs && (oh < bh || (oh == bh && ot < bt))))) {
           bs = os;
           bt = ot;
+          bh = oh;
         }
       }
       if (src >= 0 && sl == 0) {
         const int32_t v = (int32_t)(tile * kTileV + src);
-        const int32_t best = better_lazy(bs, bt, so, ow, a) ? bt : ow;
-        cluster_request(a, v, ow, best, g.vw[v]);
+        // against the own cluster: larger score, then smaller tie-hash, then smaller label
+        bool take = bt >= 0 && bs >= so;
+        if (take && bs == so) {
+          const uint64_t ho = h_tie(a.seed, a.level, ow);
+          take = bh < ho || (bh == ho && bt < ow);
+        }
+        cluster_request(a, v, ow, take ? bt : ow, g.vw[v]);
       }
     }
     __syncwarp();
@@ -484,7 +506,8 @@ __global__ void k_cluster_apply(int32_t n, const int32_t* __restrict__ req, cons
     C[v] = t;
     mine++;
   }
-  if (mine) atomicAdd((unsigned long long*)moved, (unsigned long long)mine);
+  mine = warp_sum(mine);  // one update of the shared counter per warp
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd((unsigned long long*)moved, (unsigned long long)mine);
 }
 
 // Iteration control of the clustering loop: stop after cluster_iters
@@ -636,12 +659,20 @@ __global__ void k_project(int32_t n, const int32_t* __restrict__ M, const int32_
 // ---------------------------------------------------------------------------
 // initial mapping: breadth-first order in one CTA, cut into k weight chunks
 // ---------------------------------------------------------------------------
+constexpr int kInitSmemN = 12288;  // coarsest graphs up to this size keep the BFS state in shared memory
+
 __global__ void __launch_bounds__(1024) k_initial(GraphView g, int32_t* order, int32_t* claim, int32_t* seen,
                                                   const int32_t* __restrict__ code_of_pe, int64_t k, int64_t cV,
                                                   int32_t* pi, uint32_t* err) {
   __shared__ int64_t sm[33];
   __shared__ int32_t s_tail, s_head, s_next;
+  extern __shared__ __align__(16) int32_t init_smem[];
   const int32_t n = g.n;
+  if (n <= kInitSmemN) {  // same algorithm, state on chip (the launch provides 3 * n words)
+    order = init_smem;
+    claim = init_smem + n;
+    seen = init_smem + 2 * (size_t)n;
+  }
   for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
     seen[v] = 0;
     claim[v] = INT32_MAX;
@@ -902,6 +933,7 @@ int32_t cluster_level(Ctx& c, int lvl) {
     }
   }
   ClusterState* cs = c.cstate;
+  bool graph_ran = false;
   if (c.use_graphs && !c.prof) {
     const int64_t key[6] = {(int64_t)L.n, L.m, (int64_t)L.n_hi, L.hi_slots, wcap, (int64_t)(intptr_t)c.hkey};
     bool same = L.cgexec != nullptr;
@@ -911,9 +943,9 @@ int32_t cluster_level(Ctx& c, int lvl) {
       for (int i = 0; i < 6; i++) L.cg_key[i] = key[i];
     }
     GM_CUDA(cudaGraphLaunch(L.cgexec, c.st));
+    // read back with the cluster count below (kernel accounting only)
     GM_CUDA(cudaMemcpyAsync(c.h_cstate, cs, sizeof(ClusterState), cudaMemcpyDeviceToHost, c.st));
-    GM_CUDA(cudaStreamSynchronize(c.st));
-    add_launches(L.cg_root + (long long)c.h_cstate->kernels);
+    graph_ran = true;
   } else {
     k_iota<<<gv, kThreads, 0, c.st>>>(c.C, n); count_launch();
     GM_CUDA(cudaMemcpyAsync(c.Wc, L.vw, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.st));
@@ -935,11 +967,20 @@ int32_t cluster_level(Ctx& c, int lvl) {
   GM_CUDA(cudaMemsetAsync(c.rank, 0, (size_t)nlab * sizeof(int32_t), c.st));
   k_mark_used<<<gv, kThreads, 0, c.st>>>(n, c.C, c.rank); count_launch();
   scan(LoadI32{c.rank}, StoreRankI32{c.rank}, nlab, nullptr, c.scan, c.st);
-  const int64_t nc = read_i64(c, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(nlab)));
+  // the cluster count and the error flags with one synchronisation
+  GM_CUDA(cudaMemcpyAsync(c.h_small, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(nlab)), sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, c.st));
+  c.h_small[1] = 0;
+  GM_CUDA(cudaMemcpyAsync(c.h_small + 1, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
   if (!L.M) L.M = c.mem.make<int32_t>((size_t)std::max(1, n));
   k_apply_rank<<<gv, kThreads, 0, c.st>>>(n, c.C, c.rank, L.M); count_launch();
   GM_CUDA(cudaGetLastError());
-  check_err(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  if (graph_ran) add_launches(L.cg_root + (long long)c.h_cstate->kernels);
+  const int64_t nc = c.h_small[0];
+  const uint32_t e = (uint32_t)(c.h_small[1] & 0xffffffffLL);
+  if (e & ERR_TIMEOUT) throw ApiError(MAP_E_TIMEOUT, "a bounded device loop gave up");
+  if (e) throw ApiError(MAP_E_INTERNAL, "device consistency check failed (flags " + std::to_string(e) + ")");
   return (int32_t)nc;
 }
 
@@ -1100,9 +1141,7 @@ int32_t coarsen(Ctx& c) {
       break;
     }
     contract_level(c, lvl, nc, lvl < (int)spare.size() ? &spare[lvl] : nullptr);
-    Level& N = c.lv.back();
-    classify_degrees(c, (int)c.lv.size() - 1);
-    N.max_vw = device_max_vw(c, N);
+    classify_degrees(c, (int)c.lv.size() - 1);  // also the level's largest vertex weight
   }
   for (Level& L : spare) free_level(c, L);
   return (int32_t)c.lv.size();
@@ -1110,7 +1149,15 @@ int32_t coarsen(Ctx& c) {
 
 void initial_map(Ctx& c) {
   Level& L = c.lv.back();
-  k_initial<<<1, 1024, 0, c.st>>>(view(L), c.C, c.req, c.Wc, c.d_code_of_pe, c.k, c.cV, L.pi, c.errword); count_launch();
+  const size_t smem = L.n <= kInitSmemN ? (size_t)3 * L.n * sizeof(int32_t) : 0;
+  static std::atomic<unsigned long long> attr_done{0};  // one bit per device
+  const unsigned long long bit = 1ULL << (c.dev & 63);
+  if (!(attr_done.load() & bit)) {
+    GM_CUDA(cudaFuncSetAttribute(k_initial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(3 * kInitSmemN * sizeof(int32_t))));
+    attr_done.fetch_or(bit);
+  }
+  k_initial<<<1, 1024, smem, c.st>>>(view(L), c.C, c.req, c.Wc, c.d_code_of_pe, c.k, c.cV, L.pi, c.errword); count_launch();
   GM_CUDA(cudaGetLastError());
   check_err(c);
 }
