@@ -573,28 +573,85 @@ __global__ void k_coarse_vw(int32_t n, const int32_t* __restrict__ M, const int3
     atomicAdd(&vwc[M[v]], vw[v]);
 }
 
+// Keys (M(u), M(v)) and weights of the inter-cluster CSR entries, compacted
+// to the front of the sort buffers.  Their order does not matter: parallel
+// entries are summed after the sort.  A warp takes 32 consecutive vertices,
+// whose rows form one contiguous range, and walks it 32 entries at a time;
+// each lane finds the row of its entry among the 32 row starts.  A first walk
+// counts the warp's valid entries, the block reserves one range for its eight
+// warps with a single atomic, and a second walk (gathers now cached) writes.
+__device__ __forceinline__ int contract_owner(int64_t x, int64_t b, int last) {
+  // largest lane L <= last with row start(L) <= x (starts are non-decreasing)
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = lo + step;
+    const int64_t s = __shfl_sync(0xffffffffu, b, cand > 31 ? 31 : cand);
+    if (cand <= last && s <= x) lo = cand;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(kThreads) k_contract_keys(GraphView g, const int32_t* __restrict__ M, int bits,
                                                             uint64_t* key, int32_t* val, int64_t* valid) {
-  auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
-  const int lane = tile.thread_rank();
-  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
-  const uint64_t sentinel = (bits >= 32 ? ~0ULL : ((1ULL << (2 * bits)) - 1ULL));
-  int64_t mine = 0;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
-    const int32_t mv = M[v];
-    for (int64_t e = g.xadj[v] + lane; e < g.xadj[v + 1]; e += kSubWarp) {
-      const int32_t mu = M[g.adj[e]];
-      if (mu != mv) {
-        key[e] = ((uint64_t)(uint32_t)mv << bits) | (uint32_t)mu;
-        mine++;
-      } else {
-        key[e] = sentinel;
-      }
-      val[e] = g.adjw[e];
+  constexpr int kWarps = kThreads / 32;
+  __shared__ unsigned long long wcnt[kWarps];
+  __shared__ unsigned long long bbase;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t ntiles = ((int64_t)g.n + 31) / 32;
+  for (int64_t bt = blockIdx.x; bt * kWarps < ntiles; bt += gridDim.x) {
+    const int64_t tile = bt * kWarps + warp;
+    int64_t E0 = 0, E1 = 0, b = 0;
+    int32_t mv = 0;
+    int last = 0;
+    if (tile < ntiles) {  // warp-uniform
+      const int64_t v = tile * 32 + lane;
+      last = (int)min((int64_t)31, (int64_t)g.n - 1 - tile * 32);
+      const bool vv = v < g.n;
+      b = vv ? g.xadj[v] : 0;
+      const int64_t e = vv ? g.xadj[v + 1] : 0;
+      mv = vv ? M[v] : 0;
+      E0 = __shfl_sync(0xffffffffu, b, 0);
+      E1 = __shfl_sync(0xffffffffu, e, last);
     }
+    unsigned long long cnt = 0;
+    for (int64_t x0 = E0; x0 < E1; x0 += 32) {
+      const int64_t x = x0 + lane;
+      const int o = contract_owner(x, b, last);
+      const int32_t mo = __shfl_sync(0xffffffffu, mv, o);
+      const bool ok = x < E1 && M[g.adj[x]] != mo;
+      cnt += __popc(__ballot_sync(0xffffffffu, ok));
+    }
+    if (lane == 0) wcnt[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tot = 0;
+      for (int w = 0; w < kWarps; w++) {
+        const unsigned long long c = wcnt[w];
+        wcnt[w] = tot;
+        tot += c;
+      }
+      bbase = tot ? atomicAdd((unsigned long long*)valid, tot) : 0ULL;
+    }
+    __syncthreads();
+    unsigned long long pos = bbase + wcnt[warp];
+    for (int64_t x0 = E0; x0 < E1; x0 += 32) {
+      const int64_t x = x0 + lane;
+      const int o = contract_owner(x, b, last);
+      const int32_t mo = __shfl_sync(0xffffffffu, mv, o);
+      const int32_t mu = x < E1 ? M[g.adj[x]] : mo;
+      const bool ok = mu != mo;
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const unsigned long long p = pos + __popc(bal & lt);
+        key[p] = ((uint64_t)(uint32_t)mo << bits) | (uint32_t)mu;
+        val[p] = g.adjw[x];
+      }
+      pos += __popc(bal);
+    }
+    __syncthreads();  // wcnt and bbase are rewritten by the next round
   }
-  mine = warp_sum(mine);
-  if ((threadIdx.x & 31) == 0 && mine) atomicAdd((unsigned long long*)valid, (unsigned long long)mine);
 }
 
 struct LoadHead {
@@ -1021,11 +1078,11 @@ void contract_level(Ctx& c, int lvl, int32_t nc, Level* spare) {
   if (!reuse_n) C.xadj = c.mem.make<int64_t>((size_t)nc + 1);
   const int64_t old_m = reuse_n ? C.m : -1;
   if (m > 0) {
-    k_contract_keys<<<grid_for(c, kThreads / kSubWarp, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
-                                                                                   c.sort.val[0], d_valid); count_launch();
+    k_contract_keys<<<grid_for(c, kThreads, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
+                                                                       c.sort.val[0], d_valid); count_launch();
     c.prof_level = lvl;
     cudaEvent_t ev = c.prof_begin();
-    const int cur = radix_sort_pairs(c.sort, m, nullptr, 2 * bits, c.st);
+    const int cur = radix_sort_pairs(c.sort, m, d_valid, 2 * bits, c.st);  // the valid keys only
     // per 8-bit pass: keys read twice (histogram, scatter), key + value read and written once
     c.prof_end(ev, PK_SORT, (int64_t)((2 * bits + 7) / 8) * m * (8 + 12 + 12));
     uint64_t* skey = c.sort.key[cur];
