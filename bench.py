@@ -45,10 +45,17 @@ UNIT = "edges/s"
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per algorithmic byte of a kernel class from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the input
-# graph of the RGG 2^20 workload; profiles/k_eval_tile_k_lp_gain_tile_k_cluster_tile_rgg2e20_level0.md),
+# graph of the RGG 2^20 workload;
+# profiles/k_eval_tile_k_lp_gain_tile_k_cluster_tile_rgg2e20_level0.md),
 # valid only while the kernel's source hash matches.
-TRAFFIC = {"eval_J": {"kernel": "k_eval_tile", "kernel_hash": "1ec779b5c4c730d0", "dram_bytes": 116370432,
-                      "alg_bytes": 163348488, "dram_per_alg_byte": 116370432 / 163348488}}
+TRAFFIC = {
+    "eval_J": {"kernel": "k_eval_tile", "kernel_hash": "1a257be59f189df2", "dram_bytes": 116094720,
+               "alg_bytes": 163348488, "dram_per_alg_byte": 116094720 / 163348488},
+    "lp_gain": {"kernel": "k_lp_gain_tile", "kernel_hash": "7f557cd3d5da71f0", "dram_bytes": 119368448,
+                "alg_bytes": 178028552, "dram_per_alg_byte": 119368448 / 178028552},
+    "cluster": {"kernel": "k_cluster_tile", "kernel_hash": "bc5de036b3a742be", "dram_bytes": 130340864,
+                "alg_bytes": 167542792, "dram_per_alg_byte": 130340864 / 167542792},
+}
 
 
 def parse():
@@ -308,7 +315,7 @@ def run_ours(args, ws, rank, local):
     traffic = None
     if tr and tr.get("kernel_hash") == kernel_hash(tr["kernel"]) and tv["launches"]:
         traffic = tr["dram_per_alg_byte"] * tv["bytes"] / tv["launches"]
-    roof = {"bound": "hbm", "kernel": tn,
+    roof = {"bound": "hbm", "kernel": tn, "kernel_name": (tr or {}).get("kernel"),
             "scope": "launches on the input graph (level 0), CUDA events on the library stream during "
                      f"{args.profile_steps} profiled steps that follow the timed region",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

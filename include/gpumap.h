@@ -225,7 +225,9 @@ enum {
   MAP_K_EVAL = 2,      /* objective J (low-degree path) */
   MAP_K_CLUSTER = 3,   /* clustering rating (low-degree path) */
   MAP_K_SORT = 4,      /* radix-sort scatter passes */
-  MAP_K_COUNT = 5
+  MAP_K_EVAL_CTL = 5,  /* J evaluation launches that only close an LP or weak step (exact change of J
+                          already accumulated): the controller, no CSR pass */
+  MAP_K_COUNT = 6
 };
 
 /* Enables (1) or disables (0) CUDA-event timing of the kernel classes above

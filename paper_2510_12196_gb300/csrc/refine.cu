@@ -1312,7 +1312,9 @@ size_t conn_smem(const Ctx& c) { return (size_t)group_layout(c.topo).total * siz
 // J of the current mapping of a level; with `ec`, the last block of the
 // low-degree pass also takes the Alg. 6 decision (the high-degree pass runs
 // first so that J is complete then).
-void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr) {
+// full: the launch streams the whole CSR (false when it only closes an LP or
+// weak step whose exact change of J is already accumulated)
+void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr, bool full = true) {
   Level& L = c.lv[lvl];
   c.prof_level = lvl;
   if (L.n_hi)
@@ -1323,7 +1325,8 @@ void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr) {
   k_eval_tile<<<tile_grid(c, (const void*)k_eval_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc,
                                                                                        ec ? *ec : none); count_launch();
   // xadj (8) + P(v) (4) per vertex; adjacency (4) + weight (4) + gathered P(u) (4) per entry
-  c.prof_end(ev, PK_EVAL, 12 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+  if (full) c.prof_end(ev, PK_EVAL, 12 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+  else c.prof_end(ev, PK_EVAL_CTL, 0);
 }
 
 template <class Mv>
@@ -2462,7 +2465,7 @@ static void refine_stream(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* 
       launch_rebalance(c, lvl);
       if (h.kind == KIND_STRONG) launch_rebalance_strong_tail(c, lvl);
     }
-    launch_eval(c, lvl, &ec1);
+    launch_eval(c, lvl, &ec1, h.kind == KIND_STRONG);
     k_copy_best<<<gcopy, kThreads, 0, c.st>>>(c.state, L.pi, c.pi_best, L.n, IterCounts{0, 0, 0, 0}); count_launch();
     GM_CUDA(cudaGetLastError());
   }
