@@ -1851,6 +1851,71 @@ __device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const En
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
 }
 
+// Shared-memory layout of the rebalancing steps in the engine's dynamic
+// shared memory: the cut bucket and remainder of every block (code spaces up
+// to kEngCutSmem) and the short-list resolution behind them; the sorts of the
+// first CTA reuse the area once the cuts are no longer read from it.
+constexpr int kEngCutSmem = 4096;
+static_assert(kEngCutSmem * 12 + kEngThreads * (8 + 8 + 4 + 8 + 1) <= 2 * kSmallSort * 12,
+              "cut tables and short-list resolution fit in the engine's smallest dynamic shared memory");
+
+// weak step, short list: movers are the selected vertices below the cut
+// bucket and those of the cut bucket that the CTA's own resolution selected
+struct WeakMovesShared {
+  const uint8_t* elig;
+  const uint8_t* sel;   // 1: below the cut bucket, 2: in the list (decision in s_sel)
+  const int32_t* dest;
+  const int64_t* slot;  // list slot of a vertex marked 2
+  const uint8_t* s_sel;
+  __device__ __forceinline__ bool moved(int64_t v) const {
+    if (!elig[v]) return false;
+    const uint8_t s = sel[v];
+    return s == 1 || (s == 2 && s_sel[slot[v]]);
+  }
+  __device__ __forceinline__ int32_t target(int64_t v) const { return dest[v]; }
+};
+
+// Resolution of a cut-bucket list of at most blockDim entries by the calling
+// CTA: rank sort by (block, id), exclusive prefix of the weights in that
+// order, selection while the weight before a vertex in its block's bucket is
+// below the block's remainder.  Returns the decisions by list slot (shared).
+__device__ uint8_t* eng_resolve_local(const EngineJob& J, EngSmem& S, int32_t* area, int ln, int idbits,
+                                      const int64_t* rem) {
+  uint64_t* rk = reinterpret_cast<uint64_t*>(area);  // keys by slot
+  uint64_t* ok = rk + kEngThreads;                   // keys in order
+  int32_t* os = reinterpret_cast<int32_t*>(ok + kEngThreads);  // slots in order
+  int64_t* ex = reinterpret_cast<int64_t*>(os + kEngThreads);  // exclusive prefix in order
+  uint8_t* s_sel = reinterpret_cast<uint8_t*>(ex + kEngThreads);
+  const int i = threadIdx.x;
+  const uint64_t idmask = (1ULL << idbits) - 1ULL;
+  uint64_t ki = 0;
+  if (i < ln) {
+    ki = J.key0[i];
+    rk[i] = ki;
+  }
+  __syncthreads();
+  if (i < ln) {
+    int r = 0;  // keys are distinct (one per vertex)
+    for (int j = 0; j < ln; j++) r += rk[j] < ki ? 1 : 0;
+    ok[r] = ki;
+    os[r] = i;
+  }
+  __syncthreads();
+  const int64_t c = i < ln ? (int64_t)J.g.vw[(int64_t)(ok[i] & idmask)] : 0;
+  int64_t tot;
+  const int64_t e = block_exclusive_scan(c, S.sm, &tot);
+  ex[i] = e;
+  __syncthreads();
+  if (i < ln) {
+    const uint64_t A = ok[i] >> idbits;
+    int h = i;
+    while (h > 0 && (ok[h - 1] >> idbits) == A) h--;  // first entry of the block
+    s_sel[os[i]] = (e - ex[h] < rem[A]) ? 1 : 0;
+  }
+  __syncthreads();
+  return s_sel;
+}
+
 // Alg. 6 on one job by the calling cluster (all its threads call it).
 template <int kTE, class Sync>
 __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int32_t* sc, int32_t* sw,
@@ -1897,28 +1962,31 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     // decision
     const bool full = phase == 0 || !(prev_kind == KIND_LP || prev_kind == KIND_WEAK);
     const bool reuse = single && full;  // the gain pass may use this pass's staged tiles
-    int64_t acc = 0;
-    for (int64_t tile = full ? eg.gw : ntiles; tile < ntiles; tile += eg.GW) {
-      int64_t Tp;
-      bool cand;
-      const TileLane t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand, true);
-      acc += Tp;
-      if (single) {
-        t0 = t;
-        Tp0 = Tp;
-        cand0 = cand;
+    if (full) {  // (uniform: the previous step's kind is known to every thread)
+      int64_t acc = 0;
+      for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
+        int64_t Tp;
+        bool cand;
+        const TileLane t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand, true);
+        acc += Tp;
+        if (single) {
+          t0 = t;
+          Tp0 = Tp;
+          cand0 = cand;
+        }
+        __syncwarp();
       }
-      __syncwarp();
+      acc = block_sum(acc, S.sm);
+      if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
+      sy.sync();
     }
-    acc = block_sum(acc, S.sm);
-    if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
-    sy.sync();
     if (lead) {
       const int64_t mx = block_max_w(J.W, J.topo.kc, S.smax);
       if (threadIdx.x == 0) {
         const int64_t Jv = *(volatile int64_t*)J.Jacc;
         control_step(s, mx, Jv, J.ctl, phase, 0, 0);
         *J.Jacc = next_j_base(s, Jv);
+        J.cnt[CNT_ELIG] = 0;  // the cut-bucket list of a rebalancing step
       }
       __syncthreads();
       // a rebalancing step: its threshold sigma and destination list U now
@@ -2084,50 +2152,97 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
     // inclusive prefix of eligible weight exceeds W(A) - L_max (one warp per
     // block, buckets lane and 32 + lane)
     static_assert(kBuckets == 64, "two buckets per lane");
-    for (int64_t A = eg.gw; A < J.topo.kc; A += eg.GW) {
+    const int idbits = bits_for_n(n);
+    const int32_t kc = J.topo.kc;
+    auto warp_cut = [&](int64_t A, bool zero, int32_t* bcut_out, int64_t* rem_out) {
       const int64_t WA = J.W[A];
-      if (WA <= J.lmax) continue;
+      if (WA <= J.lmax) return;
       const int64_t E = WA - J.lmax;
       int64_t* row = J.tab + A * kBuckets;
       const int64_t x0 = row[lane], x1 = row[32 + lane];
-      row[lane] = 0;
-      row[32 + lane] = 0;
+      if (zero) {
+        row[lane] = 0;
+        row[32 + lane] = 0;
+      }
       const int64_t p0 = warp_incl_scan(x0, lane);
       const int64_t p1 = warp_incl_scan(x1, lane) + __shfl_sync(0xffffffffu, p0, 31);
       const unsigned m0 = __ballot_sync(0xffffffffu, p0 > E), m1 = __ballot_sync(0xffffffffu, p1 > E);
       const int cut = m0 ? __ffs(m0) - 1 : (m1 ? 32 + __ffs(m1) - 1 : kBuckets);
-      // exclusive prefix of the cut bucket
-      const int pl = cut - 1;
+      const int pl = cut - 1;  // exclusive prefix of the cut bucket
       const int64_t q0 = __shfl_sync(0xffffffffu, p0, pl < 0 ? 0 : (pl & 31));
       const int64_t q1 = __shfl_sync(0xffffffffu, p1, pl < 32 ? 0 : (pl & 31));
       const int64_t excl = pl < 0 ? 0 : (pl < 32 ? q0 : q1);
       if (lane == 0) {
-        J.bcut[A] = cut;
-        J.rem[A] = cut < kBuckets ? E - excl : 0;
+        bcut_out[A] = cut;
+        rem_out[A] = cut < kBuckets ? E - excl : 0;
       }
+    };
+    // With a small code space every CTA computes the cuts itself into shared
+    // memory (no barrier before the classification; the bucket totals are
+    // cleared after the next barrier); else one warp per block, cluster-wide.
+    const bool cut_local = kc <= kEngCutSmem;
+    int64_t* s_rem = reinterpret_cast<int64_t*>(dyn);
+    int32_t* s_bcut = reinterpret_cast<int32_t*>(s_rem + kEngCutSmem);
+    if (cut_local) {
+      for (int64_t A = threadIdx.x >> 5; A < kc; A += blockDim.x >> 5) warp_cut(A, false, s_bcut, s_rem);
+      __syncthreads();
+    } else {
+      for (int64_t A = eg.gw; A < kc; A += eg.GW) warp_cut(A, true, J.bcut, J.rem);
+      sy.sync();
     }
-    if (lead && threadIdx.x == 0) J.cnt[CNT_ELIG] = 0;
-    sy.sync();
-    const int idbits = bits_for_n(n);
+    const int32_t* bcut = cut_local ? s_bcut : J.bcut;
+    const int64_t* rem = cut_local ? s_rem : J.rem;  // (the first CTA may switch to J.rem below)
+    // below the cut bucket: moves; above: stays; in it: appended to the list
+    // (in a weak step marked 2, with its list slot)
     for (int64_t v = gt; v < n; v += GT) {
       if (!J.elig[v]) continue;
       const int32_t A = J.pi[v];
-      const int32_t bb = J.bkt[v], cut = J.bcut[A];
+      const int32_t bb = J.bkt[v], cut = bcut[A];
       if (bb != cut) {
         J.sel[v] = bb < cut ? 1 : 0;
         continue;
       }
       J.sel[v] = 0;
-      if (J.rem[A] > 0) {
+      if (rem[A] > 0) {
         const unsigned long long i = atomicAdd((unsigned long long*)&J.cnt[CNT_ELIG], 1ULL);
         J.key0[i] = ((uint64_t)(uint32_t)A << idbits) | (uint64_t)v;
         J.val0[i] = (int32_t)v;
+        if (!strong) {
+          J.sel[v] = 2;
+          J.sarr[v] = (int64_t)i;
+        }
       }
     }
     sy.sync();
+    if (cut_local && lead)  // the bucket totals for the next step
+      for (int64_t i = threadIdx.x; i < (int64_t)kc * kBuckets; i += blockDim.x) J.tab[i] = 0;
+    const int ln = (int)*(volatile int64_t*)&J.cnt[CNT_ELIG];
+    if (!strong && cut_local && ln <= (int)blockDim.x) {
+      // every CTA orders the short cut-bucket list by (block, id) itself and
+      // keeps the decisions in shared memory: no barrier before the exact
+      // change of J
+      uint8_t* s_sel = eng_resolve_local(J, S, s_bcut + kEngCutSmem, ln, idbits, rem);
+      const WeakMovesShared mv{J.elig, J.sel, J.dest, J.sarr, s_sel};
+      eng_delta(J, mv, S, eg, ntiles);
+      sy.sync();
+      for (int64_t v = gt; v < n; v += GT) {
+        if (!mv.moved(v)) continue;
+        const int32_t p = J.pi[v], q = J.dest[v];
+        const int64_t c = g.vw[v];
+        J.pi[v] = q;
+        atomicAdd((unsigned long long*)&J.W[p], (unsigned long long)(-c));
+        atomicAdd((unsigned long long*)&J.W[q], (unsigned long long)c);
+      }
+      sy.sync();
+      continue;
+    }
     if (lead) {  // the cut-bucket list by (block, id), per-block prefix
-      const int ln = (int)*(volatile int64_t*)&J.cnt[CNT_ELIG];
       if (ln > 0) {
+        if (cut_local) {  // the sort below reuses the shared memory of the cuts
+          for (int64_t A = threadIdx.x; A < kc; A += blockDim.x) J.rem[A] = s_rem[A];
+          __syncthreads();
+        }
+        rem = J.rem;
         const uint64_t* K;
         const int32_t* V;
         eng_sort(J, S, dyn, ln, J.topo.code_bits + idbits, K, V);
@@ -2141,7 +2256,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         __syncthreads();
         for (int i = threadIdx.x; i < ln; i += blockDim.x) {
           const int32_t A = (int32_t)(K[i] >> idbits);
-          J.sel[V[i]] = (J.P[i] - J.headP[A] < J.rem[A]) ? 1 : 0;
+          J.sel[V[i]] = (J.P[i] - J.headP[A] < rem[A]) ? 1 : 0;
         }
       }
     }
