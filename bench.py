@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-pool", type=int, default=24,
                     help="distinct requests generated; the stream cycles through them")
-    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--probe", action="store_true",
                     help="one map_run, then one label-propagation step and one J evaluation on the input "
                          "graph inside the NVTX range 'probe' (for ncu captures of single launches)")

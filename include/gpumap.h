@@ -272,6 +272,16 @@ GPUMAP_API map_status map_objective_noalloc(const int64_t* xadj, const int32_t* 
                                             const int32_t* vwgt, int32_t n, const int32_t* pi, const int32_t* hier,
                                             const int32_t* dist, int32_t levels, int64_t* out, void* stream);
 
+/* Self-test of the engines' bounded waits (the paper has none: its
+ * kernels do not wait on each other).  Launches, on `stream`, a cooperative
+ * kernel whose grid barrier waits for one block more than the grid has, so
+ * that every wait runs out after about a second; the blocks leave the kernel
+ * and report it.  Returns MAP_E_TIMEOUT when the expiry was detected and
+ * reported as designed (the device stays usable), MAP_E_INTERNAL if the
+ * barrier was released or the expiry went unreported, MAP_E_CUDA on a CUDA
+ * error.  The text is in map_last_error(NULL). */
+GPUMAP_API map_status map_selftest_barrier_timeout(void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched refinement.  The paper refines one graph at a time; it has no
  * batched mode.  Here many contexts (graphs of uneven size, each with its own

@@ -624,4 +624,22 @@ map_status map_profile_read(map_ctx* ctx, int32_t which, int32_t level, int64_t*
 
 long long map_launch_count(void) { return gm::launch_count(); }
 
+map_status map_selftest_barrier_timeout(void* stream) {
+  last_create_error().clear();
+  try {
+    if (!barrier_selftest((cudaStream_t)stream)) {
+      last_create_error() = "the grid barrier was released or did not report the expired wait";
+      return MAP_E_INTERNAL;
+    }
+    last_create_error() = "a grid barrier wait expired (expected by this self-test)";
+    return MAP_E_TIMEOUT;
+  } catch (const CudaError& e) {
+    last_create_error() = e.what();
+    return MAP_E_CUDA;
+  } catch (const std::exception& e) {
+    last_create_error() = e.what();
+    return MAP_E_INTERNAL;
+  }
+}
+
 }  // extern "C"

@@ -246,6 +246,7 @@ int engine_max_clusters(int C, int te);  // resident clusters of C CTAs (0: not 
 size_t engine_job_bytes();
 bool engine_job_write(Ctx& c, int lvl, int32_t rounds, void* dst);  // false: level unsuited to the engine
 void engine_launch(cudaStream_t st, const void* d_jobs, int njobs, unsigned int* queue, int C, int te, int nclusters);
+bool barrier_selftest(cudaStream_t st);  // the bounded grid-barrier wait gives up and reports it
 void drop_graph(Level& L);
 
 // coarsen.cu

@@ -1498,11 +1498,19 @@ struct GridBar {
   unsigned int err;  // set when a wait gave up
   unsigned int pad;
 };
-constexpr unsigned kBarSpinLimit = 1u << 24;  // polls of about 64 ns: ~1 s
+constexpr unsigned long long kBarWaitNs = 1000000000ULL;  // a wait gives up after one second
+constexpr unsigned kBarSpinLimit = 1u << 26;               // and after this many polls in any case
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct GridSync {
   GridBar* bar;
   unsigned int* flag;  // shared memory of the calling block
+  unsigned int need;   // arrivals that release the barrier (gridDim.x)
   // Every block arrives once; the last one resets the count and advances the
   // generation the others poll.  Fences order each block's phase writes
   // before its arrival and the following reads after the release.  A wait
@@ -1513,14 +1521,15 @@ struct GridSync {
     if (threadIdx.x == 0) {
       const unsigned g0 = *(volatile unsigned*)&bar->gen;
       __threadfence();
-      if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+      if (atomicAdd(&bar->count, 1u) == need - 1) {
         bar->count = 0;
         __threadfence();
         atomicAdd(&bar->gen, 1u);
       } else {
         unsigned spins = 0;
+        const unsigned long long t0 = global_ns();
         while (*(volatile unsigned*)&bar->gen == g0) {
-          if (++spins > kBarSpinLimit || *(volatile unsigned*)&bar->err) {
+          if (++spins > kBarSpinLimit || global_ns() - t0 > kBarWaitNs || *(volatile unsigned*)&bar->err) {
             atomicOr(&bar->err, 1u);
             break;
           }
@@ -2409,7 +2418,17 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine_grid(const EngineJob*
   eg.GW = (int64_t)gridDim.x * (blockDim.x >> 5);
   int32_t* sc = eng_dyn + warp * 2 * kTE;
   int32_t* sw = sc + kTE;
-  engine_run_job<kTE>(*job, S, eng_dyn, sc, sw, eg, GridSync{bar, &bar_flag});
+  engine_run_job<kTE>(*job, S, eng_dyn, sc, sw, eg, GridSync{bar, &bar_flag, gridDim.x});
+}
+
+// Self-test of the bounded grid barrier: a barrier that waits for one more
+// block than the grid has, so every wait runs out; the blocks then leave the
+// kernel and the failure flag is set for the host.  Returns without output
+// when the barrier was (wrongly) released.
+__global__ void k_barrier_selftest(GridBar* bar, int* passed) {
+  __shared__ unsigned int bar_flag;
+  GridSync{bar, &bar_flag, gridDim.x + 1}.sync();
+  if (threadIdx.x == 0) atomicAdd(passed, 1);  // not reached when the wait gives up
 }
 
 }  // namespace
@@ -2897,6 +2916,37 @@ static void refine_engine_grid(Ctx& c, int lvl, int32_t rounds, int64_t* J, int6
   if (J) *J = h.best_J;
   if (maxw) *maxw = h.best_maxw;
   if (iters) *iters = h.t;
+}
+
+// Runs the grid barrier self-test on stream st with a few blocks; returns
+// whether the wait gave up (err set and no block passed the barrier).
+bool barrier_selftest(cudaStream_t st) {
+  GridBar* bar = nullptr;
+  int* passed = nullptr;
+  GM_CUDA(cudaMallocAsync(&bar, sizeof(GridBar), st));
+  GM_CUDA(cudaMallocAsync(&passed, sizeof(int), st));
+  GM_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), st));
+  GM_CUDA(cudaMemsetAsync(passed, 0, sizeof(int), st));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(4);
+  cfg.blockDim = dim3(128);
+  cfg.stream = st;
+  cudaLaunchAttribute attr{};
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  GM_CUDA(cudaLaunchKernelEx(&cfg, k_barrier_selftest, bar, passed));
+  count_launch();
+  GridBar hb{};
+  int hp = -1;
+  GM_CUDA(cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+  GM_CUDA(cudaMemcpyAsync(&hp, passed, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  GM_CUDA(cudaFreeAsync(bar, st));
+  GM_CUDA(cudaFreeAsync(passed, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  return hb.err != 0 && hp == 0;
 }
 
 void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {

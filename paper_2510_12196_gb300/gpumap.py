@@ -81,6 +81,7 @@ _SIGS = {
     "map_profile_read": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
     "map_launch_count": (C.c_longlong, []),
     "map_objective_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, _P, _P, C.c_int32, _P, _P]),
+    "map_selftest_barrier_timeout": (C.c_int, [_P]),
     "map_batch_opts_default": (None, [_P]),
     "map_batch_create": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "map_batch_launch": (C.c_int, [_P]),
@@ -361,6 +362,11 @@ def map_objective_noalloc(xadj, adjncy, adjwgt, vwgt, n: int, pi, hier, dist, ou
     if st != 0:
         msg = lib().map_last_error(None)
         raise MapError(st, "map_objective_noalloc", msg.decode() if msg else "")
+
+
+def map_selftest_barrier_timeout(stream=None) -> int:
+    """Status of the bounded grid-barrier self-test (MAP_E_TIMEOUT = 5 is the pass)."""
+    return int(lib().map_selftest_barrier_timeout(_stream_handle(stream)))
 
 
 class MapBatchOpts(C.Structure):
