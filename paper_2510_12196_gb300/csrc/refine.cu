@@ -125,6 +125,7 @@ struct EvalCtl {
   int use_h;
 };
 __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec);
+__device__ void eval_close(int64_t* Jacc, const EvalCtl& ec);
 
 // True when the J evaluation closing an Alg. 6 iteration has nothing to do:
 // after an LP or weak step the step itself added its exact change of J to the
@@ -146,8 +147,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_eval_tile(Grap
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
-  // after an LP or weak step Jacc already holds J (old J + the exact change)
-  const int64_t ntiles = incremental_j(ec.s, ec.phase) ? 0 : ((int64_t)g.n + kTileV - 1) / kTileV;
+  if (incremental_j(ec.s, ec.phase)) {
+    // after an LP or weak step Jacc already holds J (old J + the exact
+    // change): one block runs the decision, the others leave at once
+    if (blockIdx.x == 0) eval_close(Jacc, ec);
+    return;
+  }
+  const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
   int64_t acc = 0;
   for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
     const TileLane t = stage_tile(tg, tile * kTileV, lane, sc[warp], sw[warp], GatherPi{pi});
@@ -1246,6 +1252,17 @@ __device__ void control_step(RefineState* s, int64_t mx, int64_t J, const CtlArg
 // that step adds its exact change (LP, weak), else 0 (a full evaluation).
 __device__ __forceinline__ int64_t next_j_base(const RefineState* s, int64_t J) {
   return (s->kind == KIND_LP || s->kind == KIND_WEAK) ? J : 0;
+}
+
+// The decision on a J that is already complete in the accumulator (one block).
+__device__ void eval_close(int64_t* Jacc, const EvalCtl& ec) {
+  __shared__ int64_t smax[32];
+  const int64_t mx = block_max_w(ec.W, ec.a.kc, smax);
+  if (threadIdx.x == 0) {
+    const int64_t J = *(volatile int64_t*)Jacc;
+    control_step(ec.s, mx, J, ec.a, ec.phase, ec.h, ec.use_h);
+    *Jacc = next_j_base(ec.s, J);
+  }
 }
 
 __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec) {
