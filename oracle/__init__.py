@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("phi_num", C.c_int32), ("phi_den", C.c_int32), ("sigma_gap", C.c_int32),
                 ("coarsest_factor", C.c_int32), ("cluster_iters", C.c_int32),
                 ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
-                ("stall_num", C.c_int32), ("stall_den", C.c_int32)]
+                ("stall_num", C.c_int32), ("stall_den", C.c_int32),
+                ("coarsener", C.c_int32), ("match_rounds", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -177,6 +178,18 @@ def cluster(g, wcap: int, params: Optional[Params] = None, level: int = 0):
     nc = lib().orc_cluster(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw),
                            C.c_int64(wcap), C.byref(prm), C.c_int32(level), _p(M))
     return M, int(nc)
+
+
+def match(g, lmax_: int, params: Optional[Params] = None, level: int = 0):
+    """Two-hop matching of one level.  Returns (M, n_c, mate, stage counts:
+    heavy-edge, leaf, twin, relative, isolated matched vertices, heavy-edge rounds)."""
+    prm = params or default_params()
+    M = np.zeros(g.n, np.int32)
+    mate = np.zeros(g.n, np.int32)
+    st = np.zeros(6, np.int32)
+    nc = lib().orc_match(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw), C.c_int64(lmax_),
+                         C.byref(prm), C.c_int32(level), _p(mate), _p(M), _p(st))
+    return M, int(nc), mate, st
 
 
 def contract(g, M, nc: int):

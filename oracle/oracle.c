@@ -36,6 +36,14 @@ static uint64_t h_rebalance(uint64_t seed, int32_t level, int32_t t, int32_t v) 
   return orc_hash(seed, (3ULL << 60) | ((uint64_t)level << 52) |
                             ((uint64_t)(t & 0xFFFFF) << 32) | (uint64_t)(uint32_t)v);
 }
+/* matching: noise of the edge {a, b} (a < b), and the hash of one neighbour */
+/* (a neighbourhood hashes to the sum over its neighbours)                    */
+static uint64_t h_edge(uint64_t seed, int32_t level, int32_t a, int32_t b) {
+  return orc_hash(seed ^ ((4ULL << 60) | ((uint64_t)level << 48)), ((uint64_t)(uint32_t)a << 32) | (uint32_t)b);
+}
+static uint64_t h_nbr(uint64_t seed, int32_t u) {
+  return orc_hash(seed, (5ULL << 60) | (uint64_t)(uint32_t)u);
+}
 
 void orc_default_params(orc_params *p) {
   p->seed = 0x5EED0000ULL;
@@ -50,6 +58,8 @@ void orc_default_params(orc_params *p) {
   p->max_levels = 64;
   p->stall_num = 9;
   p->stall_den = 10;
+  p->coarsener = 0;
+  p->match_rounds = 16;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -591,6 +601,172 @@ int32_t orc_cluster(int32_t n, const int64_t *xadj, const int32_t *adj, const in
 }
 
 /* ------------------------------------------------------------------------- */
+/* Coarsening by two-hop matching (Section 4.2, "Matching", after LaSalle et */
+/* al. as used by Jet).                                                      */
+/*                                                                           */
+/* Heavy-edge rounds: every unmatched v with an unmatched neighbour u such   */
+/* that c(v) + c(u) <= L_max prefers the u of largest rating                 */
+/* exp*2 = w(v,u)^2 / (c(v) c(u)); ratings are compared exactly              */
+/* (w1^2 c(u2) against w2^2 c(u1)), equal ratings by the smaller edge hash    */
+/* (the deterministic noise), then the smaller u.  v and u are matched when  */
+/* each prefers the other.  Rounds repeat until one matches nothing (at most */
+/* match_rounds).                                                            */
+/* While at most 75% of the vertices are matched, the two-hop stages follow, */
+/* each on the still unmatched vertices, each pairing consecutive members of */
+/* a group in (group, id) order (1st with 2nd, 3rd with 4th, ...; a pair     */
+/* whose weight exceeds L_max stays unmatched), the 75% test repeated after  */
+/* each: leaves (degree 1) grouped by their neighbour; twins (degree >= 2)   */
+/* grouped by the hash of their neighbour set, paired only if the sets are   */
+/* equal; relatives (degree >= 1) grouped by their matchmaker, the neighbour */
+/* of smallest (degree, id); isolated vertices (degree 0) in one group.      */
+/* M numbers the pairs and single vertices by ascending smallest member.     */
+/* mate[v] is v's partner or -1; stage_matched[0..5] (may be NULL) counts    */
+/* the vertices matched by heavy edges, leaves, twins, relatives and        */
+/* isolated pairing, and [5] the heavy-edge rounds run.  Returns n_c.        */
+/* ------------------------------------------------------------------------- */
+typedef struct { uint64_t g; int32_t v; } group_key;
+
+static int cmp_group_key(const void *x, const void *y) {
+  const group_key *p = (const group_key *)x, *q = (const group_key *)y;
+  if (p->g != q->g) return p->g < q->g ? -1 : 1;
+  if (p->v != q->v) return p->v < q->v ? -1 : 1;
+  return 0;
+}
+
+static int same_neighbours(const int64_t *xadj, const int32_t *adj, int32_t a, int32_t b) {
+  int64_t da = xadj[a + 1] - xadj[a], db = xadj[b + 1] - xadj[b];
+  if (da != db) return 0;
+  for (int64_t i = 0; i < da; i++)
+    if (adj[xadj[a] + i] != adj[xadj[b] + i]) return 0;
+  return 1;
+}
+
+/* pairs consecutive members of each group (keys sorted); returns matched */
+static int64_t pair_groups(group_key *keys, int32_t cnt, const int32_t *vw, int64_t lmax, int twins,
+                           const int64_t *xadj, const int32_t *adj, int32_t *mate) {
+  int64_t matched = 0;
+  qsort(keys, (size_t)cnt, sizeof(group_key), cmp_group_key);
+  int32_t start = 0;
+  for (int32_t i = 0; i < cnt; i++) {
+    if (i > 0 && keys[i].g != keys[i - 1].g) start = i;
+    if ((i - start) % 2 != 0) continue;               /* the first of a candidate pair */
+    if (i + 1 >= cnt || keys[i + 1].g != keys[i].g) continue;
+    int32_t a = keys[i].v, b = keys[i + 1].v;
+    if ((int64_t)vw[a] + vw[b] > lmax) continue;
+    if (twins && !same_neighbours(xadj, adj, a, b)) continue;
+    mate[a] = b;
+    mate[b] = a;
+    matched += 2;
+  }
+  return matched;
+}
+
+int32_t orc_match(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                  const int32_t *vw, int64_t lmax, const orc_params *prm, int32_t level, int32_t *mate,
+                  int32_t *M, int32_t *stage_matched) {
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int32_t *pref = (int32_t *)malloc(nn * sizeof(int32_t));
+  group_key *keys = (group_key *)malloc(nn * sizeof(group_key));
+  int64_t st[6] = {0, 0, 0, 0, 0, 0};
+  for (int32_t v = 0; v < n; v++) mate[v] = -1;
+  int64_t matched = 0;
+
+  /* heavy-edge rounds */
+  for (int32_t r = 0; r < prm->match_rounds; r++) {
+    for (int32_t v = 0; v < n; v++) {
+      pref[v] = -1;
+      if (mate[v] >= 0) continue;
+      int32_t best = -1;
+      int64_t bw = 0;
+      for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
+        int32_t u = adj[e];
+        if (mate[u] >= 0 || (int64_t)vw[v] + vw[u] > lmax) continue;
+        int64_t w = adjw[e];
+        int better;
+        if (best < 0) {
+          better = 1;
+        } else {
+          /* w^2 / c(u) against bw^2 / c(best) */
+          unsigned __int128 lhs = (unsigned __int128)((uint64_t)(w * w)) * (uint64_t)vw[best];
+          unsigned __int128 rhs = (unsigned __int128)((uint64_t)(bw * bw)) * (uint64_t)vw[u];
+          if (lhs != rhs) {
+            better = lhs > rhs;
+          } else {
+            uint64_t hu = h_edge(prm->seed, level, v < u ? v : u, v < u ? u : v);
+            uint64_t hb = h_edge(prm->seed, level, v < best ? v : best, v < best ? best : v);
+            better = hu < hb || (hu == hb && u < best);
+          }
+        }
+        if (better) { best = u; bw = w; }
+      }
+      pref[v] = best;
+    }
+    int64_t now = 0;
+    for (int32_t v = 0; v < n; v++) {
+      int32_t u = pref[v];
+      if (u >= 0 && pref[u] == v) { mate[v] = u; now++; }
+    }
+    matched += now;
+    st[0] += now;
+    st[5] = r + 1;
+    if (now == 0) break;
+  }
+
+  /* two-hop stages while at most 75% are matched */
+  for (int stage = 1; stage <= 4; stage++) {
+    if (4 * matched > 3 * (int64_t)n) break;
+    int32_t cnt = 0;
+    for (int32_t v = 0; v < n; v++) {
+      if (mate[v] >= 0) continue;
+      int64_t d = xadj[v + 1] - xadj[v];
+      uint64_t g;
+      if (stage == 1) {          /* leaves */
+        if (d != 1) continue;
+        g = (uint64_t)(uint32_t)adj[xadj[v]];
+      } else if (stage == 2) {   /* twins */
+        if (d < 2) continue;
+        g = 0;
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) g += h_nbr(prm->seed, adj[e]);
+      } else if (stage == 3) {   /* relatives: the matchmaker */
+        if (d < 1) continue;
+        int32_t mm = -1;
+        int64_t md = 0;
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
+          int32_t u = adj[e];
+          int64_t du = xadj[u + 1] - xadj[u];
+          if (mm < 0 || du < md || (du == md && u < mm)) { mm = u; md = du; }
+        }
+        g = (uint64_t)(uint32_t)mm;
+      } else {                   /* isolated */
+        if (d != 0) continue;
+        g = 0;
+      }
+      keys[cnt].g = g;
+      keys[cnt].v = v;
+      cnt++;
+    }
+    int64_t got = pair_groups(keys, cnt, vw, lmax, stage == 2, xadj, adj, mate);
+    matched += got;
+    st[stage] = got;
+  }
+
+  /* number pairs and singles by their smallest member */
+  int32_t nc = 0;
+  for (int32_t v = 0; v < n; v++) {
+    int32_t rep = (mate[v] >= 0 && mate[v] < v) ? mate[v] : v;
+    if (rep == v) pref[v] = nc++;
+  }
+  for (int32_t v = 0; v < n; v++) {
+    int32_t rep = (mate[v] >= 0 && mate[v] < v) ? mate[v] : v;
+    M[v] = pref[rep];
+  }
+  if (stage_matched)
+    for (int i = 0; i < 6; i++) stage_matched[i] = (int32_t)st[i];
+  free(pref); free(keys);
+  return nc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Contraction (Section 2.1 and Alg. 3): every cluster becomes one coarse    */
 /* vertex of summed weight; edges between different clusters are summed      */
 /* into one coarse edge; edges inside a cluster (self-loops) are dropped.    */
@@ -706,7 +882,14 @@ int64_t orc_map_run(int32_t n, const int64_t *xadj, const int32_t *adj, const in
     int64_t wcap = lmax / prm->cluster_cap_div;
     if (wcap < maxc) wcap = maxc;
     f->M = (int32_t *)malloc((size_t)(f->n > 0 ? f->n : 1) * sizeof(int32_t));
-    int32_t nc = orc_cluster(f->n, f->xadj, f->adj, f->adjw, f->vw, wcap, prm, nl - 1, f->M);
+    int32_t nc;
+    if (prm->coarsener == 1) {
+      int32_t *mate = (int32_t *)malloc((size_t)(f->n > 0 ? f->n : 1) * sizeof(int32_t));
+      nc = orc_match(f->n, f->xadj, f->adj, f->adjw, f->vw, lmax, prm, nl - 1, mate, f->M, NULL);
+      free(mate);
+    } else {
+      nc = orc_cluster(f->n, f->xadj, f->adj, f->adjw, f->vw, wcap, prm, nl - 1, f->M);
+    }
     if ((int64_t)nc * prm->stall_den > (int64_t)prm->stall_num * f->n) { free(f->M); f->M = NULL; break; }
     level_graph *c = &L[nl];
     c->n = nc;

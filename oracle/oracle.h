@@ -33,6 +33,8 @@ typedef struct {
   int32_t cluster_cap_div;   /* cluster weight cap = L_max / 4 */
   int32_t max_levels;        /* 64 */
   int32_t stall_num, stall_den; /* stop coarsening if n_c > 9/10 n */
+  int32_t coarsener;         /* 0: label-propagation clustering, 1: two-hop matching (Section 4.2) */
+  int32_t match_rounds;      /* heavy-edge matching: at most this many rounds per level: 16 */
 } orc_params;
 
 typedef struct {
@@ -78,6 +80,10 @@ int32_t orc_refine(int32_t n, const int64_t *xadj, const int32_t *adj, const int
 int32_t orc_cluster(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
                     const int32_t *vw, int64_t wcap, const orc_params *prm, int32_t level,
                     int32_t *M);
+
+int32_t orc_match(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                  const int32_t *vw, int64_t lmax, const orc_params *prm, int32_t level, int32_t *mate,
+                  int32_t *M, int32_t *stage_matched);
 
 int64_t orc_contract(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
                      const int32_t *vw, const int32_t *M, int32_t nc,
