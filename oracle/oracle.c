@@ -616,8 +616,9 @@ int32_t orc_cluster(int32_t n, const int64_t *xadj, const int32_t *adj, const in
 /* a group in (group, id) order (1st with 2nd, 3rd with 4th, ...; a pair     */
 /* whose weight exceeds L_max stays unmatched), the 75% test repeated after  */
 /* each: leaves (degree 1) grouped by their neighbour; twins (degree >= 2)   */
-/* grouped by the hash of their neighbour set, paired only if the sets are   */
-/* equal; relatives (degree >= 1) grouped by their matchmaker, the neighbour */
+/* grouped by the top 31 bits of the hash of their neighbour set, paired     */
+/* only if the sets are equal; relatives (degree >= 1) grouped by their      */
+/* matchmaker, the neighbour                                                 */
 /* of smallest (degree, id); isolated vertices (degree 0) in one group.      */
 /* M numbers the pairs and single vertices by ascending smallest member.     */
 /* mate[v] is v's partner or -1; stage_matched[0..5] (may be NULL) counts    */
@@ -723,10 +724,11 @@ int32_t orc_match(int32_t n, const int64_t *xadj, const int32_t *adj, const int3
       if (stage == 1) {          /* leaves */
         if (d != 1) continue;
         g = (uint64_t)(uint32_t)adj[xadj[v]];
-      } else if (stage == 2) {   /* twins */
+      } else if (stage == 2) {   /* twins: the top 31 bits of the neighbour-set hash */
         if (d < 2) continue;
         g = 0;
         for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) g += h_nbr(prm->seed, adj[e]);
+        g >>= 33;
       } else if (stage == 3) {   /* relatives: the matchmaker */
         if (d < 1) continue;
         int32_t mm = -1;
