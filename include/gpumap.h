@@ -70,7 +70,8 @@ typedef void (*map_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
  * 4.2, rebalancing threshold sigma = L_max - 100), coarsest_factor 8
  * (coarsen until fewer than 8k vertices, Section 4.2, initial partitioning);
  * cluster_iters 5, cluster_cap_div 4, max_levels 64 and stall 9/10 belong to
- * the label-propagation clustering coarsener. */
+ * the label-propagation clustering coarsener; match_rounds 16 to the two-hop
+ * matching coarsener (Section 4.2, "Matching"). */
 typedef struct {
   uint64_t seed;
   int32_t patience;
@@ -92,6 +93,11 @@ typedef struct {
   int32_t grid_engine_max_n; /* larger levels with at most this many vertices (and no vertex of degree > 128)
                             run the same engine over all SMs (cooperative launch); 0: library default
                             (262144); -1: never */
+  int32_t coarsener;     /* 0: label-propagation clustering (default); 1: two-hop matching (heavy-edge rounds
+                            with the rating w^2 / (c(u) c(v)), then leaf, twin, relative and isolated pairing
+                            while at most 75% of the vertices are matched) */
+  int32_t match_rounds;  /* heavy-edge matching rounds at most (each matches mutual preferences; stops early
+                            when a round matches nothing) */
 } map_config;
 
 typedef struct {

@@ -205,6 +205,8 @@ void map_config_default(map_config* cfg) {
   cfg->max_levels = 64;
   cfg->stall_num = 9;
   cfg->stall_den = 10;
+  cfg->coarsener = 0;
+  cfg->match_rounds = 16;
 }
 
 const char* map_status_string(map_status s) {
@@ -242,6 +244,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
     c.use_graphs = c.cfg.launch_mode == 0;
     if (c.cfg.engine_max_n < -1 || c.cfg.grid_engine_max_n < -1)
       throw ApiError(MAP_E_INVALID, "engine_max_n and grid_engine_max_n must be >= -1");
+    if (c.cfg.coarsener < 0 || c.cfg.coarsener > 1 || c.cfg.match_rounds < 0)
+      throw ApiError(MAP_E_INVALID, "coarsener must be 0 or 1 and match_rounds >= 0");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     for (auto& cs : c.cap.s) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

@@ -1190,7 +1190,7 @@ int32_t coarsen(Ctx& c) {
   while ((int32_t)c.lv.size() < c.cfg.max_levels &&
          (int64_t)c.lv.back().n >= (int64_t)c.cfg.coarsest_factor * c.k) {
     const int lvl = (int)c.lv.size() - 1;
-    const int32_t nc = cluster_level(c, lvl);
+    const int32_t nc = c.cfg.coarsener == 1 ? match_level(c, lvl) : cluster_level(c, lvl);
     Level& F = c.lv[lvl];
     if ((int64_t)nc * c.cfg.stall_den > (int64_t)c.cfg.stall_num * F.n) {
       c.mem.put(F.M);

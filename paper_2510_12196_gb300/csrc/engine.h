@@ -256,6 +256,9 @@ void initial_map(Ctx& c);
 void project(Ctx& c, int lvl);
 void validate_graph(Ctx& c);
 
+// match.cu
+int32_t match_level(Ctx& c, int lvl);  // two-hop matching of level lvl into its M; returns n_c
+
 }  // namespace gm
 
 // The opaque handle of the C ABI.

@@ -41,7 +41,8 @@ class MapConfig(C.Structure):
                 ("stall_num", C.c_int32), ("stall_den", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32),
-                ("grid_engine_max_n", C.c_int32)]
+                ("grid_engine_max_n", C.c_int32), ("coarsener", C.c_int32),
+                ("match_rounds", C.c_int32)]
 
 
 class MapStats(C.Structure):

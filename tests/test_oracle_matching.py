@@ -153,3 +153,17 @@ def test_map_run_with_matching_halves_levels():
         assert st.n[i] >= st.n[i - 1] // 2  # a matching at most halves a level
     Jo, mx, _ = O.objective(g, (4, 8), (1, 10), pi)
     assert Jo == J and mx <= L
+
+
+def test_gpu_parity_graphs_reach_every_stage():
+    """The graphs of the GPU matching parity tests (R-MAT with hubs, a star,
+    K_{2,50}) between them match vertices in every stage: heavy edges, leaves,
+    twins, relatives and isolated pairs."""
+    seen = np.zeros(6, np.int64)
+    star = I.csr_from_pairs(300, np.zeros(299, np.int64), np.arange(1, 300))
+    k250 = I.csr_from_pairs(52, np.repeat(np.arange(2), 50), np.tile(np.arange(2, 52), 2))
+    for g, k in [(I.rmat(13, 8, 0.57, 0.19, 0.19, 9), 32), (star, 4), (k250, 4)]:
+        lmax = O.lmax(int(g.vw.sum()), k, 0.03)
+        _, _, _, st = O.match(g, lmax, level=0)
+        seen += st
+    assert (seen[:5] > 0).all(), seen
