@@ -191,6 +191,7 @@ struct Ctx {
   uint32_t* errword = nullptr;
   ClusterState* cstate = nullptr;
   ClusterState* h_cstate = nullptr;  // pinned mirror
+  void* mstate = nullptr;            // two-hop matching state (device)
 
   // fused small-level engine
   int eng_max_cluster = 0;

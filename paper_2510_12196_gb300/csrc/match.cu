@@ -234,6 +234,45 @@ __global__ void k_match_number(int32_t n, const int32_t* __restrict__ mate, cons
   }
 }
 
+// device state of one level's matching
+struct MatchState {
+  int64_t matched;  // vertices matched so far
+  int64_t now;      // matched by the current heavy-edge round
+  int64_t nkeys;    // keys of the current two-hop stage
+  int64_t got;      // matched by the current two-hop stage
+  int64_t nc;       // coarse vertices
+  int32_t round;
+  int32_t pad;
+  unsigned long long kernels;  // kernels run inside conditional bodies
+};
+
+__global__ void k_mt_init(MatchState* s, int32_t rounds, cudaGraphConditionalHandle h, int use_h) {
+  s->matched = 0;
+  s->now = 0;
+  s->round = 0;
+  s->kernels = 0;
+  if (use_h) cudaGraphSetConditional(h, rounds > 0 ? 1u : 0u);
+}
+__global__ void k_mt_round_end(MatchState* s, int32_t rounds, cudaGraphConditionalHandle h, int use_h,
+                               unsigned long long body_kernels) {
+  s->kernels += body_kernels;
+  s->matched += s->now;
+  s->round += 1;
+  const bool more = s->now > 0 && s->round < rounds;
+  s->now = 0;
+  if (use_h) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+// a two-hop stage runs while at most 75% of the vertices are matched
+__global__ void k_mt_stage_begin(MatchState* s, int32_t n, cudaGraphConditionalHandle h, int use_h) {
+  s->nkeys = 0;
+  s->got = 0;
+  if (use_h) cudaGraphSetConditional(h, 4 * s->matched <= 3 * (int64_t)n ? 1u : 0u);
+}
+__global__ void k_mt_stage_end(MatchState* s, unsigned long long body_kernels) {
+  s->matched += s->got;
+  s->kernels += body_kernels;
+}
+
 unsigned mgrid(const Ctx& c, int64_t items_per_block, int64_t n) {
   int64_t g = (n + items_per_block - 1) / items_per_block;
   const int64_t cap = (int64_t)c.num_sms * 8;
@@ -248,10 +287,105 @@ int bits_of(int64_t x) {  // smallest b with x < 2^b
   return b;
 }
 
-int64_t read_count(Ctx& c, const int64_t* d) {
-  GM_CUDA(cudaMemcpyAsync(c.h_small, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
-  return c.h_small[0];
+MatchState* state_of(Ctx& c) {
+  if (!c.mstate) c.mstate = c.mem.make<MatchState>(1);
+  return static_cast<MatchState*>(c.mstate);
+}
+
+MatchGraph mview(const Level& L) { return MatchGraph{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+
+// one heavy-edge round: preferences, then mutual pairs counted into s->now
+void emit_round(Ctx& c, int lvl, cudaStream_t st) {
+  const Level& L = c.lv[lvl];
+  const int32_t n = L.n;
+  k_match_prefer<<<mgrid(c, kMThreads / kSubWarp, n), kMThreads, 0, st>>>(mview(L), c.C, c.lmax, c.cfg.seed, lvl,
+                                                                         c.req); count_launch();
+  k_match_mutual<<<mgrid(c, kMThreads, n), kMThreads, 0, st>>>(n, c.req, c.C, &state_of(c)->now); count_launch();
+}
+
+// one two-hop stage (its keys, their sort, the pairing), matched count into s->got
+void emit_stage(Ctx& c, int lvl, int stage, cudaStream_t st, unsigned long long* kcount) {
+  const Level& L = c.lv[lvl];
+  const int32_t n = L.n;
+  MatchState* s = state_of(c);
+  const int idbits = bits_of(n);
+  // group bits: a vertex id (leaves, relatives), 31 hash bits (twins), none (isolated)
+  const int gbits = stage == 2 ? 31 : stage == 4 ? 0 : idbits;
+  const unsigned gv = mgrid(c, kMThreads, n);
+  k_twohop_keys<<<gv, kMThreads, 0, st>>>(mview(L), c.C, stage, c.cfg.seed, idbits, c.sort.key[0], c.sort.val[0],
+                                          &s->nkeys); count_launch();
+  const int cur = radix_sort_pairs(c.sort, n, &s->nkeys, std::max(1, gbits + idbits), st,
+                                   kcount ? &c.cap : nullptr, kcount);
+  k_pair_groups<<<gv, kMThreads, 0, st>>>(c.sort.key[cur], c.sort.val[cur], &s->nkeys, idbits, mview(L), c.lmax,
+                                          stage == 2 ? 1 : 0, c.C, &s->got); count_launch();
+}
+
+// pairs and single vertices numbered by their smallest member into L.M
+void emit_number(Ctx& c, int lvl, cudaStream_t st) {
+  Level& L = c.lv[lvl];
+  const int32_t n = L.n;
+  scan(LoadRep{c.C}, StoreRank{c.rank}, n, nullptr, c.scan, st);
+  GM_CUDA(cudaMemcpyAsync(&state_of(c)->nc, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)),
+                          sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  k_match_number<<<mgrid(c, kMThreads, n), kMThreads, 0, st>>>(n, c.C, c.rank, L.M); count_launch();
+}
+
+// Captures the matching of one level: rounds in a WHILE node, each two-hop
+// stage in an IF node on the 75% rule, then the numbering.
+void build_match_graph(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
+  L.cgexec = nullptr;
+  MatchState* s = state_of(c);
+  cudaStream_t saved = c.st;
+  cudaStream_t cs = c.cap.s[0];
+  long long root = 0, body = 0;
+  long long* outer = set_capture_counter(&root);
+  GM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  c.cap.depth = 0;
+  c.st = cs;
+  try {
+    GM_CUDA(cudaMemsetAsync(c.C, 0xFF, (size_t)std::max(1, L.n) * sizeof(int32_t), cs));  // mate = -1
+    cudaGraphConditionalHandle h = cap_handle(cs, 0);
+    k_mt_init<<<1, 1, 0, cs>>>(s, c.cfg.match_rounds, h, 1); count_launch();
+    cap_cond(c.cap, cs, h, cudaGraphCondTypeWhile, [&](cudaStream_t bs) {
+      body = 0;
+      set_capture_counter(&body);
+      emit_round(c, lvl, bs);
+      k_mt_round_end<<<1, 1, 0, bs>>>(s, c.cfg.match_rounds, h, 1, (unsigned long long)body + 1); count_launch();
+      set_capture_counter(&root);
+    });
+    for (int stage = 1; stage <= 4; stage++) {
+      cudaGraphConditionalHandle hs = cap_handle(cs, 0);
+      k_mt_stage_begin<<<1, 1, 0, cs>>>(s, L.n, hs, 1); count_launch();
+      cap_cond(c.cap, cs, hs, cudaGraphCondTypeIf, [&](cudaStream_t bs) {
+        body = 0;
+        set_capture_counter(&body);
+        emit_stage(c, lvl, stage, bs, &s->kernels);
+        k_mt_stage_end<<<1, 1, 0, bs>>>(s, (unsigned long long)body + 1); count_launch();
+        set_capture_counter(&root);
+      });
+    }
+    emit_number(c, lvl, cs);
+    cudaGraph_t g = nullptr;
+    GM_CUDA(cudaStreamEndCapture(cs, &g));
+    c.cap.depth = -1;
+    c.st = saved;
+    set_capture_counter(outer);
+    cudaError_t e = cudaGraphInstantiate(&L.cgexec, g, 0);
+    cudaGraphDestroy(g);
+    GM_CUDA(e);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c.cap.depth = -1;
+    c.st = saved;
+    set_capture_counter(outer);
+    throw;
+  }
+  L.cg_root = root;
 }
 
 }  // namespace
@@ -262,42 +396,47 @@ int64_t read_count(Ctx& c, const int64_t* d) {
 int32_t match_level(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
   const int32_t n = L.n;
-  const MatchGraph g{n, L.xadj, L.adj, L.adjw, L.vw};
-  int32_t* mate = c.C;
-  int32_t* pref = c.req;
-  int64_t* ctr = c.counters + 6;     // matched in a round; keys of a stage
-  int64_t* got = c.counters + 7;     // matched in a stage
-  GM_CUDA(cudaMemsetAsync(mate, 0xFF, (size_t)std::max(1, n) * sizeof(int32_t), c.st));  // -1
-  const unsigned gs = mgrid(c, kMThreads / kSubWarp, n), gv = mgrid(c, kMThreads, n);
-  int64_t matched = 0;
+  MatchState* s = state_of(c);
+  if (!L.M) L.M = c.mem.make<int32_t>((size_t)std::max(1, n));
+  if (c.use_graphs && !c.prof) {
+    // the graph writes L.M, which a stalled level gives back, so its address is part of the key
+    const int64_t key[6] = {(int64_t)n, L.m, c.lmax, (int64_t)c.cfg.match_rounds, -1, (int64_t)(intptr_t)L.M};
+    bool same = L.cgexec != nullptr;
+    for (int i = 0; i < 6 && same; i++) same = L.cg_key[i] == key[i];
+    if (!same) {
+      build_match_graph(c, lvl);
+      for (int i = 0; i < 6; i++) L.cg_key[i] = key[i];
+    }
+    GM_CUDA(cudaGraphLaunch(L.cgexec, c.st));
+    GM_CUDA(cudaMemcpyAsync(c.h_small, &s->nc, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaMemcpyAsync(c.h_small + 1, &s->kernels, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+    add_launches(L.cg_root + (long long)c.h_small[1]);
+    return (int32_t)c.h_small[0];
+  }
+  // stream launches: the same kernels, the loop decisions taken on the host
+  auto read = [&](const int64_t* d) {
+    GM_CUDA(cudaMemcpyAsync(c.h_small, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+    return c.h_small[0];
+  };
+  GM_CUDA(cudaMemsetAsync(c.C, 0xFF, (size_t)std::max(1, n) * sizeof(int32_t), c.st));
+  k_mt_init<<<1, 1, 0, c.st>>>(s, c.cfg.match_rounds, 0, 0); count_launch();
   for (int32_t r = 0; r < c.cfg.match_rounds; r++) {
-    GM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int64_t), c.st));
-    k_match_prefer<<<gs, kMThreads, 0, c.st>>>(g, mate, c.lmax, c.cfg.seed, lvl, pref); count_launch();
-    k_match_mutual<<<gv, kMThreads, 0, c.st>>>(n, pref, mate, ctr); count_launch();
-    const int64_t now = read_count(c, ctr);
-    matched += now;
+    emit_round(c, lvl, c.st);
+    const int64_t now = read(&s->now);
+    k_mt_round_end<<<1, 1, 0, c.st>>>(s, c.cfg.match_rounds, 0, 0, 0); count_launch();
     if (now == 0) break;
   }
-  const int idbits = bits_of(n);
   for (int stage = 1; stage <= 4; stage++) {
-    if (4 * matched > 3 * (int64_t)n) break;
-    // group bits: a vertex id (leaves, relatives), 31 hash bits (twins), none (isolated)
-    const int gbits = stage == 2 ? 31 : stage == 4 ? 0 : idbits;
-    GM_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(int64_t), c.st));
-    k_twohop_keys<<<gv, kMThreads, 0, c.st>>>(g, mate, stage, c.cfg.seed, idbits, c.sort.key[0], c.sort.val[0],
-                                             ctr); count_launch();
-    const int cur = radix_sort_pairs(c.sort, n, ctr, std::max(1, gbits + idbits), c.st);
-    k_pair_groups<<<gv, kMThreads, 0, c.st>>>(c.sort.key[cur], c.sort.val[cur], ctr, idbits, g, c.lmax,
-                                             stage == 2 ? 1 : 0, mate, got); count_launch();
-    matched += read_count(c, got);
+    k_mt_stage_begin<<<1, 1, 0, c.st>>>(s, n, 0, 0); count_launch();
+    if (4 * read(&s->matched) > 3 * (int64_t)n) break;
+    emit_stage(c, lvl, stage, c.st, nullptr);
+    k_mt_stage_end<<<1, 1, 0, c.st>>>(s, 0); count_launch();
   }
-  // number pairs and singles by their smallest member
-  scan(LoadRep{mate}, StoreRank{c.rank}, n, nullptr, c.scan, c.st);
-  const int64_t nc = read_count(c, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(n)));
-  if (!L.M) L.M = c.mem.make<int32_t>((size_t)std::max(1, n));
-  k_match_number<<<gv, kMThreads, 0, c.st>>>(n, mate, c.rank, L.M); count_launch();
+  emit_number(c, lvl, c.st);
   GM_CUDA(cudaGetLastError());
-  return (int32_t)nc;
+  return (int32_t)read(&s->nc);
 }
 
 }  // namespace gm

@@ -128,3 +128,22 @@ def test_coarsener_config_validation():
     for bad in [dict(coarsener=2), dict(coarsener=-1), dict(coarsener=1, match_rounds=-1)]:
         with pytest.raises(G.MapError):
             make_ctx(g, (2, 2), (1, 10), **bad)
+
+
+def test_matching_graph_reuse_across_runs():
+    """Repeated runs replay the cached per-level matching graphs; every run
+    gives the oracle's result, in graph and in stream launch mode alike."""
+    g = I.rmat(13, 8, 0.57, 0.19, 0.19, 2)
+    hier, dist = (4, 8), (1, 10)
+    opi, oJ, _ = O.map_run(g, hier, dist, 0.03, oracle_params(coarsener=1))
+    for mode in (0, 1):
+        ctx = make_ctx(g, hier, dist, coarsener=1, launch_mode=mode)
+        try:
+            for _ in range(3):
+                pi = np.zeros(g.n, np.int32)
+                l0 = G.map_launch_count()
+                assert G.map_run(ctx, pi) == oJ
+                assert np.array_equal(pi, opi)
+                assert G.map_launch_count() > l0
+        finally:
+            G.map_destroy(ctx)
