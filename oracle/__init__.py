@@ -25,7 +25,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,6 +59,9 @@ def lib():
         _lib.orc_map_run.restype = C.c_int64
         _lib.orc_hash.restype = C.c_uint64
         _lib.orc_hash.argtypes = [C.c_uint64, C.c_uint64]
+        _lib.orc_adaptive_eps.restype = C.c_double
+        _lib.orc_adaptive_eps.argtypes = [C.c_double, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32]
+        _lib.orc_hm_run.restype = C.c_int64
     return _lib
 
 
@@ -228,4 +231,43 @@ def map_run(g, hier, dist_, eps: float, params: Optional[Params] = None):
     st = Stats()
     J = lib().orc_map_run(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw), _p(h), _p(d), l,
                           C.c_double(eps), C.byref(prm), _p(pi), C.byref(st))
+    return pi, int(J), st
+
+
+class HmStats(C.Structure):
+    _fields_ = [("calls", C.c_int64 * 16), ("first_eps", C.c_double * 16)]
+
+
+def adaptive_eps(eps: float, cV: int, cVp: int, k: int, kp: int, d: int) -> float:
+    """Eq. 2: ((1 + eps) k' c(V) / (k c(V')))^(1/d) - 1."""
+    return float(lib().orc_adaptive_eps(eps, cV, cVp, k, kp, d))
+
+
+def build_subgraph(g, part, b: int):
+    """Alg. 2: the subgraph induced by block b.  Returns ((n', xadj, adj, adjw, vw), M, m', w')."""
+    part = _i32(part)
+    xs = np.zeros(g.n + 1, np.int64)
+    cap = max(1, g.m_dir)
+    as_ = np.zeros(cap, np.int32)
+    ws = np.zeros(cap, np.int32)
+    vs = np.zeros(max(1, g.n), np.int32)
+    M = np.zeros(max(1, g.n), np.int32)
+    mo = C.c_int64(0)
+    wo = C.c_int64(0)
+    ns = lib().orc_build_subgraph(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw), _p(part),
+                                  C.c_int32(b), _p(xs), _p(as_), _p(ws), _p(vs), _p(M), C.byref(mo), C.byref(wo))
+    ns = int(ns)
+    ms = int(xs[ns])
+    sub = (ns, xs[:ns + 1].copy(), as_[:ms].copy(), ws[:ms].copy(), vs[:ns].copy())
+    return sub, M[:g.n].copy(), int(mo.value), int(wo.value)
+
+
+def hm_run(g, hier, dist_, eps: float, params: Optional[Params] = None):
+    """Hierarchical multisection (Alg. 3).  Returns (pi, J, HmStats)."""
+    h, d, l = _topo(hier, dist_)
+    prm = params or default_params()
+    pi = np.zeros(g.n, np.int32)
+    st = HmStats()
+    J = lib().orc_hm_run(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw), _p(h), _p(d), l,
+                         C.c_double(eps), C.byref(prm), _p(pi), C.byref(st))
     return pi, int(J), st

@@ -9,6 +9,7 @@
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -925,4 +926,145 @@ int64_t orc_map_run(int32_t n, const int64_t *xadj, const int32_t *adj, const in
   }
   free(P); free(L);
   return J;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Hierarchical multisection (GPU-HM, Section 4.1 "Hierarchical             */
+/* Multisection", Eq. 2, Alg. 2 and Alg. 3).                                 */
+/*                                                                           */
+/* Adaptive imbalance (Eq. 2): eps' = ((1+eps) k' c(V) / (k c(V')))^(1/d)-1, */
+/* with k' the number of PEs the subgraph ends up on and d the number of     */
+/* hierarchy levels still to partition, the current one included.           */
+/* ------------------------------------------------------------------------- */
+double orc_adaptive_eps(double eps, int64_t cV, int64_t cVp, int64_t k, int64_t kp, int32_t d) {
+  double ratio = (1.0 + eps) * (double)kp * (double)cV / ((double)k * (double)cVp);
+  return pow(ratio, 1.0 / (double)d) - 1.0;
+}
+
+/* Alg. 2: the subgraph induced by the vertices v with part[v] == b.  Phase  */
+/* 1 counts n', w' and m' (CSR entries); phase 2 numbers the members by a     */
+/* prefix sum of the indicator; phase 3 counts each member's neighbours in   */
+/* the block, prefix-sums them into the row pointer and copies the edges in  */
+/* adjacency order.  M[v] is v's id in the subgraph (-1 outside).  The       */
+/* output arrays hold n' + 1, m', m' and n' entries.  Returns n'.            */
+int32_t orc_build_subgraph(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                           const int32_t *vw, const int32_t *part, int32_t b, int64_t *xadj_s,
+                           int32_t *adj_s, int32_t *adjw_s, int32_t *vw_s, int32_t *M, int64_t *out_m,
+                           int64_t *out_w) {
+  /* phase 1 */
+  int32_t ns = 0;
+  int64_t ws = 0, ms = 0;
+  for (int32_t v = 0; v < n; v++)
+    if (part[v] == b) { ns++; ws += vw[v]; }
+  for (int32_t v = 0; v < n; v++)
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; e++)
+      if (part[v] == b && part[adj[e]] == b) ms++;
+  /* phase 2: exclusive prefix sum of the indicator */
+  int32_t run = 0;
+  for (int32_t v = 0; v < n; v++) {
+    if (part[v] == b) M[v] = run++;
+    else M[v] = -1;
+  }
+  /* phase 3 */
+  int64_t *D = (int64_t *)calloc((size_t)ns + 1, sizeof(int64_t));
+  for (int32_t v = 0; v < n; v++) {
+    if (part[v] != b) continue;
+    int64_t d = 0;
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) d += part[adj[e]] == b;
+    D[M[v]] = d;
+  }
+  xadj_s[0] = 0;
+  for (int32_t j = 0; j < ns; j++) xadj_s[j + 1] = xadj_s[j] + D[j];
+  for (int32_t v = 0; v < n; v++) {
+    if (part[v] != b) continue;
+    int64_t i = xadj_s[M[v]];
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
+      if (part[adj[e]] != b) continue;
+      adj_s[i] = M[adj[e]];
+      adjw_s[i] = adjw[e];
+      i++;
+    }
+    vw_s[M[v]] = vw[v];
+  }
+  free(D);
+  if (out_m) *out_m = ms;
+  if (out_w) *out_w = ws;
+  return ns;
+}
+
+typedef struct {
+  const int32_t *hier;
+  double eps;
+  int64_t cV, k;
+  const orc_params *prm;
+  int32_t *pi;
+  orc_hm_stats *st;
+} hm_job;
+
+/* Alg. 3, one call: partition G' into a_i blocks with the multilevel        */
+/* partitioner (the mapping pipeline on the one-level hierarchy a_i with      */
+/* distance 1, whose J is twice the edge cut) under eps' (clamped to          */
+/* [0, 1 - 10^-6]); at i = 1 the blocks are PEs, otherwise every block's      */
+/* induced subgraph is partitioned one level down.  Block b at level i adds   */
+/* b * a_1 ... a_{i-1} to the PE id (a_1 varies fastest).  orig maps the      */
+/* subgraph's vertices to the input graph's.                                  */
+static void hm_call(hm_job *J, int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                    const int32_t *vw, const int32_t *orig, int32_t i, int64_t base) {
+  if (n == 0) return;
+  int32_t a = J->hier[i - 1];
+  int64_t kp = 1;
+  for (int32_t j = 0; j < i; j++) kp *= J->hier[j];
+  int64_t below = kp / a;
+  int64_t cVp = 0;
+  for (int32_t v = 0; v < n; v++) cVp += vw[v];
+  double ep = orc_adaptive_eps(J->eps, J->cV, cVp, J->k, kp, i);
+  if (ep < 0.0) ep = 0.0;
+  if (ep > 0.999999) ep = 0.999999;
+  int32_t one = 1;
+  int32_t *part = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  orc_map_run(n, xadj, adj, adjw, vw, &a, &one, 1, ep, J->prm, part, NULL);
+  if (J->st) {
+    J->st->calls[i - 1]++;
+    if (J->st->calls[i - 1] == 1) J->st->first_eps[i - 1] = ep;
+  }
+  if (i == 1) {
+    for (int32_t v = 0; v < n; v++) J->pi[orig[v]] = (int32_t)(base + part[v]);
+    free(part);
+    return;
+  }
+  int64_t m = xadj[n];
+  int64_t *xs = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+  int32_t *as = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+  int32_t *ws = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+  int32_t *vs = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *M = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  int32_t *os = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+  for (int32_t b = 0; b < a; b++) {
+    int32_t ns = orc_build_subgraph(n, xadj, adj, adjw, vw, part, b, xs, as, ws, vs, M, NULL, NULL);
+    for (int32_t v = 0; v < n; v++)
+      if (M[v] >= 0) os[M[v]] = orig[v];
+    hm_call(J, ns, xs, as, ws, vs, os, i - 1, base + (int64_t)b * below);
+  }
+  free(xs); free(as); free(ws); free(vs); free(M); free(os); free(part);
+}
+
+int64_t orc_hm_run(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                   const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
+                   double eps, const orc_params *prm, int32_t *pi, orc_hm_stats *stats) {
+  hm_job J;
+  J.hier = hier;
+  J.eps = eps;
+  J.cV = 0;
+  for (int32_t v = 0; v < n; v++) J.cV += vw[v];
+  J.k = orc_num_pes(hier, levels);
+  J.prm = prm;
+  J.pi = pi;
+  J.st = stats;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  int32_t *orig = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  for (int32_t v = 0; v < n; v++) orig[v] = v;
+  hm_call(&J, n, xadj, adj, adjw, vw, orig, levels, 0);
+  free(orig);
+  int64_t maxw = 0;
+  return orc_objective(n, xadj, adj, adjw, vw, hier, dist, levels, pi, NULL, &maxw);
 }

@@ -100,4 +100,21 @@ int64_t orc_map_run(int32_t n, const int64_t *xadj, const int32_t *adj, const in
 
 uint64_t orc_hash(uint64_t seed, uint64_t x);
 
+/* Hierarchical multisection (GPU-HM, Eq. 2, Alg. 2, Alg. 3). */
+typedef struct {
+  int64_t calls[16];     /* partitioner calls per hierarchy level (index i - 1) */
+  double first_eps[16];  /* eps' of the first call at each level */
+} orc_hm_stats;
+
+double orc_adaptive_eps(double eps, int64_t cV, int64_t cVp, int64_t k, int64_t kp, int32_t d);
+
+int32_t orc_build_subgraph(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                           const int32_t *vw, const int32_t *part, int32_t b, int64_t *xadj_s,
+                           int32_t *adj_s, int32_t *adjw_s, int32_t *vw_s, int32_t *M, int64_t *out_m,
+                           int64_t *out_w);
+
+int64_t orc_hm_run(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                   const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
+                   double eps, const orc_params *prm, int32_t *pi, orc_hm_stats *stats);
+
 #endif
