@@ -75,10 +75,12 @@ def parse():
                     help="0: refinement / clustering loops as CUDA graphs; 1: stream launches")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="steps re-run with per-kernel CUDA events after the timed region")
-    ap.add_argument("--workload", default="rgg", choices=["rgg", "batch", "serve"],
+    ap.add_argument("--workload", default="rgg", choices=["rgg", "batch", "serve", "hm"],
                     help="rgg: the RGG 2^20 multilevel job (default); batch: 64 RGGs of 2^12..2^18 vertices, "
                          "10 fixed refinement rounds each, one persistent launch vs one job at a time; serve: "
-                         "a Poisson stream of mapping requests through the server")
+                         "a Poisson stream of mapping requests through the server; hm: hierarchical multisection "
+                         "(GPU-HM) of the RGG 2^20 workload")
+    ap.add_argument("--hm-workers", type=int, default=8, help="host threads partitioning one level's subgraphs")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-pool", type=int, default=24,
                     help="distinct requests generated; the stream cycles through them")
@@ -608,6 +610,74 @@ def run_serve(args, ws, rank, local):
     return 0
 
 
+def run_hm(args, ws, rank, local):
+    """Hierarchical multisection of the RGG workload: wall time of map_run_hm
+    (it synchronises; its partitioner calls run on several streams)."""
+    import torch
+    from paper_2510_12196_gb300 import gpumap as G
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.log2n)
+    g, t = w.graph, w.topo
+    stream = torch.cuda.current_stream(dev)
+    d_in = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adj, g.adjw, g.vw)]
+    cfg = G.map_config_default(w.seed)
+    cfg.coarsener = COARSENERS[args.coarsener]
+    ctx = G.map_create(*d_in, g.n, t.hier, t.dist, t.eps, cfg, stream=stream, inputs_on_device=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    Js = [G.map_run_hm(ctx, workers=args.hm_workers) for _ in range(max(0, args.warmup))]
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(getattr(props, "pci_bus_id", None))
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = G.map_launch_count()
+    times, parts, builds = [], [], []
+    for i in range(args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Js.append(G.map_run_hm(ctx, workers=args.hm_workers))
+        times.append(time.perf_counter() - t0)
+        st = G.map_hm_stats(ctx)
+        parts.append(st.ms_partition)
+        builds.append(st.ms_build)
+    launches = G.map_launch_count() - launches0
+    clocks = sampler.stop()
+    st = G.map_hm_stats(ctx)
+    G.map_destroy(ctx)
+    assert len(set(Js)) == 1, f"nondeterministic J: {set(Js)}"
+    ms = 1000 * sum(times) / len(times)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        t0 = time.perf_counter()
+        _, Jc, _ = O.hm_run(g, t.hier, t.dist, t.eps, O.default_params(w.seed) if args.coarsener == "lp" else
+                            _oracle_params_match(w.seed))
+        dt = time.perf_counter() - t0
+        assert Jc == Js[0], "oracle and GPU disagree on the hierarchical multisection"
+        cpu = {"value": 1000 * dt, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": "one complete hierarchical multisection of the workload (serial C oracle)"}
+    line = {"metric": "end-to-end map time (hierarchical multisection, GPU-HM)", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": config_of(w, {"method": "GPU-HM (Alg. 3), partitioner = the library's multilevel pipeline "
+                                              "on a_i with distance 1", "workers": args.hm_workers,
+                                    "calls_per_level": [st.calls[i] for i in range(st.levels)]}, args.coarsener),
+            "J": Js[0], "ms_partition": sum(parts) / len(parts), "ms_build": sum(builds) / len(builds),
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _oracle_params_match(seed):
+    import oracle as O
+    p = O.default_params(seed)
+    p.coarsener = 1
+    return p
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -617,6 +687,8 @@ def main():
         return run_batch(args, ws, rank, local)
     if args.workload == "serve" and args.impl == "ours":
         return run_serve(args, ws, rank, local)
+    if args.workload == "hm" and args.impl == "ours":
+        return run_hm(args, ws, rank, local)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     return run_ours(args, ws, rank, local)

@@ -222,6 +222,39 @@ GPUMAP_API map_status map_project(map_ctx* ctx, int32_t level);
 GPUMAP_API map_status map_run(map_ctx* ctx, int32_t* out_pi, int64_t* out_J);
 
 /* Statistics of the hierarchy and of the last map_run. */
+/* Hierarchical multisection (GPU-HM; Section 4.1 "Hierarchical Multisection",
+ * Eq. 2, Alg. 2, Alg. 3) of the context's input graph, instead of the
+ * integrated pipeline of map_run.  From the top level a_l down, every
+ * (sub)graph is partitioned into a_i blocks by the library's multilevel
+ * pipeline on the one-level hierarchy a_i with distance 1 (its J is twice the
+ * edge cut), under the adaptive imbalance of Eq. 2,
+ *   eps' = ((1+eps) k' c(V) / (k c(V')))^(1/d) - 1,
+ * k' = a_1...a_i, d = i, clamped to [0, 1 - 1e-6]; then the induced subgraph
+ * of every block (Alg. 2, vertices renumbered in ascending id) is partitioned
+ * one level down.  Block b at level i adds b * a_1...a_{i-1} to the PE id.
+ * workers: host threads, each on its own stream, partitioning the subgraphs of
+ * one level at the same time (0: 8); the result does not depend on it.
+ * The mapping replaces the input level's (map_get_mapping, map_objective).
+ * out_pi: host, n entries (may be NULL); out_J: J under the full hierarchy
+ * (may be NULL).  Synchronises.  The partitioner contexts allocate with
+ * cudaMallocAsync (a caller allocator in the config is not passed on).
+ * Errors: MAP_E_INVALID (workers < 0, more than 16 levels), the partitioner's
+ * status otherwise. */
+GPUMAP_API map_status map_run_hm(map_ctx* ctx, int32_t workers, int32_t* out_pi, int64_t* out_J);
+
+typedef struct {
+  int32_t levels;          /* hierarchy levels */
+  int32_t workers;         /* host threads used */
+  int64_t calls[16];       /* partitioner calls at hierarchy level i (index i - 1), empty subgraphs skipped */
+  double first_eps[16];    /* eps' of the first non-empty subgraph at each level */
+  double ms_partition;     /* wall time in the partitioner calls */
+  double ms_build;         /* wall time building the subgraphs (Alg. 2) */
+  double ms_total;
+} map_hm_stats_t;
+
+/* Statistics of the last map_run_hm on this context. */
+GPUMAP_API map_status map_hm_stats(map_ctx* ctx, map_hm_stats_t* out);
+
 GPUMAP_API map_status map_stats(map_ctx* ctx, map_stats_t* out);
 
 /* Kernel classes of the optional profiler. */

@@ -108,6 +108,8 @@ void build_topology(Ctx& c, const int32_t* hier, const int32_t* dist, int32_t le
     for (int b = t.s[i - 1]; b < t.s[i]; b++) t.dist_of_bit[b] = dist[i - 1];
   c.topo = t;
   c.k = (int32_t)k;
+  c.hier.assign(hier, hier + levels);
+  c.dist.assign(dist, dist + levels);
   c.code_of_pe.assign((size_t)k, 0);
   c.pe_of_code.assign((size_t)t.kc, -1);
   for (int64_t p = 0; p < k; p++) {
@@ -567,6 +569,38 @@ map_status map_run(map_ctx* ctx, int32_t* out_pi, int64_t* out_J) {
       for (int32_t v = 0; v < L.n; v++) out_pi[v] = c.pe_of_code[(size_t)out_pi[v]];
     }
     if (out_J) *out_J = J;
+  });
+}
+
+map_status map_run_hm(map_ctx* ctx, int32_t workers, int32_t* out_pi, int64_t* out_J) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (workers < 0) throw ApiError(MAP_E_INVALID, "workers must be >= 0");
+    hm_run(c, workers ? workers : 8, &c.hm);
+    int64_t J = 0, mw = 0;
+    objective(c, 0, &J, &mw);
+    if (out_pi) {
+      Level& L = c.lv[0];
+      GM_CUDA(cudaMemcpyAsync(out_pi, L.pi, (size_t)L.n * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+      sync(c);
+      for (int32_t v = 0; v < L.n; v++) out_pi[v] = c.pe_of_code[(size_t)out_pi[v]];
+    }
+    if (out_J) *out_J = J;
+  });
+}
+
+map_status map_hm_stats(map_ctx* ctx, map_hm_stats_t* out) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!out) throw ApiError(MAP_E_INVALID, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->levels = c.hm.levels;
+    out->workers = c.hm.workers;
+    for (int i = 0; i < 16; i++) {
+      out->calls[i] = c.hm.calls[i];
+      out->first_eps[i] = c.hm.first_eps[i];
+    }
+    out->ms_partition = c.hm.ms_partition;
+    out->ms_build = c.hm.ms_build;
+    out->ms_total = c.hm.ms_total;
   });
 }
 

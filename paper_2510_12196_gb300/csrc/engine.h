@@ -119,6 +119,15 @@ struct DevMem {
   }
 };
 
+// statistics of the last hierarchical multisection run (hm.cu)
+struct HmStats {
+  int32_t levels = 0;
+  int64_t calls[16] = {};
+  double first_eps[16] = {};
+  double ms_partition = 0, ms_build = 0, ms_total = 0;
+  int32_t workers = 0;
+};
+
 struct Ctx {
   cudaStream_t st = nullptr;
   map_config cfg{};
@@ -128,6 +137,8 @@ struct Ctx {
   int64_t lmax = 0;
   double eps = 0;
   std::vector<int32_t> code_of_pe, pe_of_code;
+  std::vector<int32_t> hier, dist;  // a_1..a_l, d_1..d_l as given
+  HmStats hm;
   int32_t* d_code_of_pe = nullptr;
   int32_t* d_pe_of_code = nullptr;
   std::vector<Level> lv;       // lv[0] = input graph
@@ -259,6 +270,9 @@ void validate_graph(Ctx& c);
 
 // match.cu
 int32_t match_level(Ctx& c, int lvl);  // two-hop matching of level lvl into its M; returns n_c
+
+// hm.cu: hierarchical multisection of the input graph into lv[0].pi (codes)
+void hm_run(Ctx& c, int32_t workers, HmStats* st);
 
 }  // namespace gm
 

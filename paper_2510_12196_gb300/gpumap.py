@@ -52,6 +52,12 @@ class MapStats(C.Structure):
                 ("device_bytes", C.c_int64), ("device_bytes_peak", C.c_int64)]
 
 
+class MapHmStats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("workers", C.c_int32), ("calls", C.c_int64 * 16),
+                ("first_eps", C.c_double * 16), ("ms_partition", C.c_double), ("ms_build", C.c_double),
+                ("ms_total", C.c_double)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "map_config_default": (None, [_P]),
@@ -78,6 +84,8 @@ _SIGS = {
     "map_project": (C.c_int, [_P, C.c_int32]),
     "map_run": (C.c_int, [_P, _P, _P]),
     "map_stats": (C.c_int, [_P, _P]),
+    "map_run_hm": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "map_hm_stats": (C.c_int, [_P, _P]),
     "map_profile_enable": (C.c_int, [_P, C.c_int32]),
     "map_profile_read": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
     "map_launch_count": (C.c_longlong, []),
@@ -324,6 +332,19 @@ def map_run(ctx, out_pi=None):
     J = C.c_int64()
     _check(ctx, lib().map_run(ctx, _ptr(out_pi), C.byref(J)), "map_run")
     return J.value
+
+
+def map_run_hm(ctx, out_pi=None, workers: int = 0):
+    """Hierarchical multisection (GPU-HM) of the context's input graph; returns J."""
+    J = C.c_int64()
+    _check(ctx, lib().map_run_hm(ctx, int(workers), _ptr(out_pi), C.byref(J)), "map_run_hm")
+    return J.value
+
+
+def map_hm_stats(ctx) -> MapHmStats:
+    s = MapHmStats()
+    _check(ctx, lib().map_hm_stats(ctx, C.byref(s)), "map_hm_stats")
+    return s
 
 
 def map_stats(ctx) -> MapStats:
