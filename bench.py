@@ -625,6 +625,7 @@ def run_hm(args, ws, rank, local):
     d_in = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adj, g.adjw, g.vw)]
     cfg = G.map_config_default(w.seed)
     cfg.coarsener = COARSENERS[args.coarsener]
+    cfg.launch_mode = args.launch_mode
     ctx = G.map_create(*d_in, g.n, t.hier, t.dist, t.eps, cfg, stream=stream, inputs_on_device=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     Js = [G.map_run_hm(ctx, workers=args.hm_workers) for _ in range(max(0, args.warmup))]
@@ -666,6 +667,8 @@ def run_hm(args, ws, rank, local):
                                               "on a_i with distance 1", "workers": args.hm_workers,
                                     "calls_per_level": [st.calls[i] for i in range(st.levels)]}, args.coarsener),
             "J": Js[0], "ms_partition": sum(parts) / len(parts), "ms_build": sum(builds) / len(builds),
+            "ms_level": [st.ms_level[i] for i in range(st.levels)],
+            "ms_calls": {"create": st.ms_create, "run": st.ms_run, "destroy": st.ms_destroy},
             "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
     return 0

@@ -250,6 +250,8 @@ typedef struct {
   double ms_partition;     /* wall time in the partitioner calls */
   double ms_build;         /* wall time building the subgraphs (Alg. 2) */
   double ms_total;
+  double ms_level[16];     /* wall time partitioning hierarchy level i (index i - 1) */
+  double ms_create, ms_run, ms_destroy;  /* context setup, pipeline, teardown, summed over the calls */
 } map_hm_stats_t;
 
 /* Statistics of the last map_run_hm on this context. */

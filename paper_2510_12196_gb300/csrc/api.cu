@@ -6,10 +6,40 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "engine.h"
 
 namespace gm {
+
+namespace {
+std::mutex g_pin_mu;
+std::vector<void*> g_pin_free;
+constexpr int kPinnedSlab = 16;  // blocks per cudaMallocHost
+}  // namespace
+
+void* pinned_get(size_t bytes) {
+  if (bytes > kPinnedBlock) throw std::runtime_error("pinned_get: request larger than a block");
+  {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      void* p = g_pin_free.back();
+      g_pin_free.pop_back();
+      return p;
+    }
+  }
+  void* slab = nullptr;
+  GM_CUDA(cudaMallocHost(&slab, kPinnedBlock * kPinnedSlab));
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  for (int i = 1; i < kPinnedSlab; i++) g_pin_free.push_back(static_cast<char*>(slab) + (size_t)i * kPinnedBlock);
+  return slab;
+}
+
+void pinned_put(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  g_pin_free.push_back(p);
+}
 
 void* DevMem::get(size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -318,11 +348,11 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
     // keep the context alive so that map_last_error can report; free memory now
     try {
       ctx->c.mem.release_all();
-      if (ctx->c.h_state) cudaFreeHost(ctx->c.h_state);
+      pinned_put(ctx->c.h_state);
       ctx->c.h_state = nullptr;
-      if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
+      pinned_put(ctx->c.h_cstate);
       ctx->c.h_cstate = nullptr;
-      if (ctx->c.h_small) cudaFreeHost(ctx->c.h_small);
+      pinned_put(ctx->c.h_small);
       ctx->c.h_small = nullptr;
       cudaStreamSynchronize(ctx->c.st);
       for (auto& cs : ctx->c.cap.s)
@@ -344,10 +374,10 @@ void map_destroy(map_ctx* ctx) {
     cudaStreamSynchronize(ctx->c.st);
     ctx->c.mem.release_all();
     cudaStreamSynchronize(ctx->c.st);
-    if (ctx->c.h_state) cudaFreeHost(ctx->c.h_state);
-    if (ctx->c.h_cstate) cudaFreeHost(ctx->c.h_cstate);
-    if (ctx->c.h_small) cudaFreeHost(ctx->c.h_small);
-    if (ctx->c.h_eng_job) cudaFreeHost(ctx->c.h_eng_job);
+    pinned_put(ctx->c.h_state);
+    pinned_put(ctx->c.h_cstate);
+    pinned_put(ctx->c.h_small);
+    pinned_put(ctx->c.h_eng_job);
     for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
     for (auto& L : ctx->c.lv) {
       drop_graph(L);
@@ -601,6 +631,10 @@ map_status map_hm_stats(map_ctx* ctx, map_hm_stats_t* out) {
     out->ms_partition = c.hm.ms_partition;
     out->ms_build = c.hm.ms_build;
     out->ms_total = c.hm.ms_total;
+    for (int i = 0; i < 16; i++) out->ms_level[i] = c.hm.ms_level[i];
+    out->ms_create = c.hm.ms_create;
+    out->ms_run = c.hm.ms_run;
+    out->ms_destroy = c.hm.ms_destroy;
   });
 }
 

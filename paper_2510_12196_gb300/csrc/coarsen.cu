@@ -1145,7 +1145,8 @@ int32_t device_max_vw(Ctx& c, const Level& L) {
 void coarsen_alloc(Ctx& c) {
   const size_t n = (size_t)std::max(1, c.n0);
   c.cstate = c.mem.make<ClusterState>(1);
-  if (!c.h_cstate) GM_CUDA(cudaMallocHost(&c.h_cstate, sizeof(ClusterState)));
+  static_assert(sizeof(ClusterState) <= kPinnedBlock, "pinned block too small");
+  if (!c.h_cstate) c.h_cstate = static_cast<ClusterState*>(pinned_get(sizeof(ClusterState)));
   c.C = c.mem.make<int32_t>(n);
   c.Wc = c.mem.make<int32_t>(n);
   c.ReqW = c.mem.make<int32_t>(n);

@@ -95,6 +95,13 @@ long long launch_count();
 void add_launches(long long n);
 long long* set_capture_counter(long long* p);
 
+// Small pinned host blocks (kPinnedBlock bytes) shared by all contexts.
+// cudaFreeHost synchronises the whole device, so a context returns its
+// blocks to a process-wide free list instead of freeing them.
+constexpr size_t kPinnedBlock = 4096;
+void* pinned_get(size_t bytes);
+void pinned_put(void* p);
+
 }  // namespace gm
 
 #define GM_CUDA(x)                                                          \

@@ -125,6 +125,8 @@ struct HmStats {
   int64_t calls[16] = {};
   double first_eps[16] = {};
   double ms_partition = 0, ms_build = 0, ms_total = 0;
+  double ms_level[16] = {};                     // wall time of each level's partitioning
+  double ms_create = 0, ms_run = 0, ms_destroy = 0;  // summed over the partitioner calls
   int32_t workers = 0;
 };
 

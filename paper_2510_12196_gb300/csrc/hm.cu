@@ -213,6 +213,7 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
   std::string err;
   map_status err_st = MAP_OK;
   std::vector<double> eps_of((size_t)S.cnt, 0.0);
+  double t_create = 0, t_run = 0, t_destroy = 0;
   auto job = [&](int32_t j, cudaStream_t stream) -> bool {
     const int64_t nj = S.voff[(size_t)j + 1] - S.voff[(size_t)j];
     if (nj == 0) return true;
@@ -228,8 +229,10 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
     cfg.alloc_user = nullptr;
     map_ctx* sub = nullptr;
     const int64_t v0 = S.voff[(size_t)j], e0 = S.eoff[(size_t)j];
+    const auto t0 = std::chrono::steady_clock::now();
     map_status r = map_create(S.X + v0 + j, S.A + e0, S.W + e0, S.VW + v0, (int32_t)nj, &a, &one, 1, ep, &cfg,
                               (void*)stream, 1, &sub);
+    const auto t1 = std::chrono::steady_clock::now();
     if (r == MAP_OK) r = map_run(sub, nullptr, nullptr);
     if (r == MAP_OK) {
       Ctx& sc = sub->c;
@@ -245,7 +248,14 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
               (sub ? map_last_error(sub) : map_last_error(nullptr));
       }
     }
+    const auto t2 = std::chrono::steady_clock::now();
     if (sub) map_destroy(sub);
+    {
+      std::lock_guard<std::mutex> g(mu);
+      t_create += std::chrono::duration<double, std::milli>(t1 - t0).count();
+      t_run += std::chrono::duration<double, std::milli>(t2 - t1).count();
+      t_destroy += ms_since(t2);
+    }
     return r == MAP_OK;
   };
   const int32_t T = std::max(1, std::min(workers, S.cnt));
@@ -286,6 +296,9 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
   }
   if (err_st != MAP_OK) throw ApiError(err_st, err);
   if (st) {
+    st->ms_create += t_create;
+    st->ms_run += t_run;
+    st->ms_destroy += t_destroy;
     st->calls[i - 1] = 0;
     for (int32_t j = 0; j < S.cnt; j++)
       if (S.voff[(size_t)j + 1] > S.voff[(size_t)j]) {
@@ -402,7 +415,10 @@ void hm_run(Ctx& c, int32_t workers, HmStats* st) {
       const int32_t a = c.hier[(size_t)i - 1];
       auto tp = std::chrono::steady_clock::now();
       partition_level(c, S, i, a, part, workers, st);
-      if (st) st->ms_partition += ms_since(tp);
+      if (st) {
+        st->ms_level[i - 1] = ms_since(tp);
+        st->ms_partition += st->ms_level[i - 1];
+      }
       if (i == 1) {
         k_hm_final<<<hgrid(c, n), kHThreads, 0, c.st>>>(n, S.ORIG, S.BASE, part, c.d_code_of_pe, L0.pi); count_launch();
         GM_CUDA(cudaGetLastError());

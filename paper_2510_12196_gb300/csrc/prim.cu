@@ -5,6 +5,7 @@
 
 namespace gm {
 
+
 static std::atomic<long long> g_launches{0};
 static thread_local long long* t_capture_counter = nullptr;
 // While a graph is being captured, launches are counted into the capture's

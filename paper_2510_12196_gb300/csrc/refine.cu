@@ -2517,8 +2517,9 @@ void refine_alloc(Ctx& c) {
   GM_CUDA(cudaMemsetAsync(c.lock, 0, n, c.st));
   GM_CUDA(cudaMemsetAsync(c.counters, 0, CNT_N * sizeof(int64_t), c.st));
   GM_CUDA(cudaMemsetAsync(c.state, 0, sizeof(RefineState), c.st));
-  if (!c.h_state) GM_CUDA(cudaMallocHost(&c.h_state, sizeof(RefineState)));
-  if (!c.h_small) GM_CUDA(cudaMallocHost(&c.h_small, 8 * sizeof(int64_t)));
+  static_assert(sizeof(RefineState) <= kPinnedBlock, "pinned block too small");
+  if (!c.h_state) c.h_state = static_cast<RefineState*>(pinned_get(sizeof(RefineState)));
+  if (!c.h_small) c.h_small = static_cast<int64_t*>(pinned_get(8 * sizeof(int64_t)));
   c.gbar = c.mem.make<GridBar>(1);
   GM_CUDA(cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.st));
   c.d_stats = c.mem.make<int64_t>(4);
@@ -2802,7 +2803,8 @@ static void engine_setup(Ctx& c) {
   c.eng_max_cluster = engine_max_clusters(kEngMaxCluster, 512) > 0 ? kEngMaxCluster : 8;
   if (!c.eng_job) {
     c.eng_job = c.mem.make<EngineJob>(1);
-    GM_CUDA(cudaMallocHost(&c.h_eng_job, sizeof(EngineJob)));
+    static_assert(sizeof(EngineJob) <= kPinnedBlock, "pinned block too small");
+    c.h_eng_job = pinned_get(sizeof(EngineJob));
   }
 }
 

@@ -55,7 +55,8 @@ class MapStats(C.Structure):
 class MapHmStats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("workers", C.c_int32), ("calls", C.c_int64 * 16),
                 ("first_eps", C.c_double * 16), ("ms_partition", C.c_double), ("ms_build", C.c_double),
-                ("ms_total", C.c_double)]
+                ("ms_total", C.c_double), ("ms_level", C.c_double * 16), ("ms_create", C.c_double),
+                ("ms_run", C.c_double), ("ms_destroy", C.c_double)]
 
 
 _P = C.c_void_p
