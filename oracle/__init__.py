@@ -36,7 +36,7 @@ class Params(C.Structure):
                 ("coarsest_factor", C.c_int32), ("cluster_iters", C.c_int32),
                 ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
                 ("stall_num", C.c_int32), ("stall_den", C.c_int32),
-                ("coarsener", C.c_int32), ("match_rounds", C.c_int32)]
+                ("coarsener", C.c_int32), ("match_rounds", C.c_int32), ("initial", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -61,6 +61,7 @@ void orc_default_params(orc_params *p) {
   p->stall_den = 10;
   p->coarsener = 0;
   p->match_rounds = 16;
+  p->initial = 0;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -907,7 +908,11 @@ int64_t orc_map_run(int32_t n, const int64_t *xadj, const int32_t *adj, const in
   int32_t **P = (int32_t **)calloc((size_t)nl, sizeof(int32_t *));
   for (int32_t l = 0; l < nl; l++) P[l] = (int32_t *)malloc((size_t)(L[l].n > 0 ? L[l].n : 1) * sizeof(int32_t));
   int32_t top = nl - 1;
-  orc_initial(L[top].n, L[top].xadj, L[top].adj, L[top].vw, k, P[top]);
+  if (prm->initial == 1) /* hierarchical multisection of the coarsest graph */
+    orc_hm_run(L[top].n, L[top].xadj, L[top].adj, L[top].adjw, L[top].vw, hier, dist, levels, eps, prm,
+               P[top], NULL);
+  else
+    orc_initial(L[top].n, L[top].xadj, L[top].adj, L[top].vw, k, P[top]);
   int64_t J = 0, maxw = 0;
   if (stats) { memset(stats, 0, sizeof(*stats)); stats->levels = nl; }
   for (int32_t l = top; l >= 0; l--) {
@@ -1052,12 +1057,14 @@ int64_t orc_hm_run(int32_t n, const int64_t *xadj, const int32_t *adj, const int
                    const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
                    double eps, const orc_params *prm, int32_t *pi, orc_hm_stats *stats) {
   hm_job J;
+  orc_params part = *prm; /* the partitioner starts from breadth-first chunks */
+  part.initial = 0;
   J.hier = hier;
   J.eps = eps;
   J.cV = 0;
   for (int32_t v = 0; v < n; v++) J.cV += vw[v];
   J.k = orc_num_pes(hier, levels);
-  J.prm = prm;
+  J.prm = &part;
   J.pi = pi;
   J.st = stats;
   if (stats) memset(stats, 0, sizeof(*stats));

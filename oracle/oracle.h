@@ -35,6 +35,8 @@ typedef struct {
   int32_t stall_num, stall_den; /* stop coarsening if n_c > 9/10 n */
   int32_t coarsener;         /* 0: label-propagation clustering, 1: two-hop matching (Section 4.2) */
   int32_t match_rounds;      /* heavy-edge matching: at most this many rounds per level: 16 */
+  int32_t initial;           /* mapping of the coarsest graph: 0: breadth-first chunks; 1: hierarchical
+                                multisection (Section 4.2, initial partitioning) */
 } orc_params;
 
 typedef struct {

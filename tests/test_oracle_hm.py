@@ -149,3 +149,36 @@ def test_balanced_and_every_pe_used():
     W = np.bincount(pi, weights=g.vw, minlength=k)
     assert W.max() <= O.lmax(int(g.vw.sum()), k, 0.03)
     assert (W > 0).all()
+
+
+def test_map_run_hm_initial_composes():
+    """With the hierarchical-multisection initial mapping, the pipeline is the
+    clustering chain, hm_run on the coarsest graph, then Alg. 6 on every level
+    after projection: recomposed here from the separately pinned pieces."""
+    g = I.rgg2d(1 << 13, I.rgg_radius(1 << 13, 12), 17, wmax=10)
+    hier, dist = (4, 8), (1, 10)
+    k = math.prod(hier)
+    prm = O.default_params()
+    prm.initial = 1
+    pi, J, st = O.map_run(g, hier, dist, 0.03, prm)
+    L = O.lmax(int(g.vw.sum()), k, 0.03)
+    chain, cur = [], g
+    while len(chain) + 1 < prm.max_levels and cur.n >= prm.coarsest_factor * k:
+        wcap = max(L // prm.cluster_cap_div, int(cur.vw.max()))
+        M, nc = O.cluster(cur, wcap, prm, level=len(chain))
+        if nc * prm.stall_den > prm.stall_num * cur.n:
+            break
+        chain.append((cur, M))
+        xc, ac, wc, vc = O.contract(cur, M, nc)
+        cur = I.Graph(nc, xc, ac, wc, vc)
+    assert len(chain) + 1 == st.levels >= 2
+    p0 = O.default_params()
+    p, _, _ = O.hm_run(cur, hier, dist, 0.03, p0)
+    p, Jl, _, _, _, _, _ = O.refine(cur, hier, dist, L, p, params=prm, level=len(chain))
+    for lvl in range(len(chain) - 1, -1, -1):
+        fg, M = chain[lvl]
+        p = O.project(M, p)
+        p, Jl, _, _, _, _, _ = O.refine(fg, hier, dist, L, p, params=prm, level=lvl)
+    assert np.array_equal(p, pi) and Jl == J
+    # and it differs from the breadth-first start
+    assert not np.array_equal(O.map_run(g, hier, dist, 0.03)[0], pi)
