@@ -61,7 +61,9 @@ typedef enum {
 
 /* Optional device allocator: alloc returns device memory usable on `stream`
  * (NULL on failure); free releases it.  Used for every device buffer of a
- * context when both are set, else cudaMallocAsync / cudaFreeAsync are used. */
+ * context when both are set, else cudaMallocAsync / cudaFreeAsync are used;
+ * then the device's default memory pool keeps up to 8 GiB of freed memory
+ * for reuse (its release threshold, set once per process and device). */
 typedef void* (*map_alloc_fn)(size_t bytes, void* user, void* stream);
 typedef void (*map_free_fn)(void* ptr, size_t bytes, void* user, void* stream);
 
@@ -98,6 +100,9 @@ typedef struct {
                             while at most 75% of the vertices are matched) */
   int32_t match_rounds;  /* heavy-edge matching rounds at most (each matches mutual preferences; stops early
                             when a round matches nothing) */
+  int32_t initial;       /* mapping of the coarsest graph: 0: breadth-first chunks (default); 1: hierarchical
+                            multisection (as map_run_hm, on the coarsest graph, its partitioner starting
+                            from breadth-first chunks; Section 4.2, initial partitioning) */
 } map_config;
 
 typedef struct {
@@ -254,8 +259,10 @@ typedef struct {
   double ms_create, ms_run, ms_destroy;  /* context setup, pipeline, teardown, summed over the calls */
 } map_hm_stats_t;
 
-/* Statistics of the last map_run_hm on this context. */
-GPUMAP_API map_status map_hm_stats(map_ctx* ctx, map_hm_stats_t* out);
+/* Statistics of the last map_run_hm (which = 0) or of the last initial
+ * mapping by hierarchical multisection inside map_run (which = 1,
+ * map_config.initial = 1) on this context. */
+GPUMAP_API map_status map_hm_stats(map_ctx* ctx, int32_t which, map_hm_stats_t* out);
 
 GPUMAP_API map_status map_stats(map_ctx* ctx, map_stats_t* out);
 

@@ -3,6 +3,7 @@
 // internal PE codes; every step of the path itself runs in the kernels of
 // refine.cu and coarsen.cu.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -39,6 +40,26 @@ void pinned_put(void* p) {
   if (!p) return;
   std::lock_guard<std::mutex> g(g_pin_mu);
   g_pin_free.push_back(p);
+}
+
+// Stream-ordered allocations come from the device's default memory pool,
+// which by default hands freed memory back to the system at every
+// synchronisation, so that the next context maps it again.  Keeping up to
+// kPoolKeepBytes of freed blocks in the pool makes creating and destroying
+// contexts cheap (serving, hierarchical multisection).  Once per device.
+constexpr uint64_t kPoolKeepBytes = 8ULL << 30;
+void keep_pool_memory(int dev) {
+  static std::atomic<unsigned long long> done{0};  // one bit per device
+  const unsigned long long bit = 1ULL << (dev & 63);
+  if (done.load() & bit) return;
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = kPoolKeepBytes;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+  } else {
+    cudaGetLastError();
+  }
+  done.fetch_or(bit);
 }
 
 void* DevMem::get(size_t bytes) {
@@ -239,6 +260,7 @@ void map_config_default(map_config* cfg) {
   cfg->stall_den = 10;
   cfg->coarsener = 0;
   cfg->match_rounds = 16;
+  cfg->initial = 0;
 }
 
 const char* map_status_string(map_status s) {
@@ -278,11 +300,12 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       throw ApiError(MAP_E_INVALID, "engine_max_n and grid_engine_max_n must be >= -1");
     if (c.cfg.coarsener < 0 || c.cfg.coarsener > 1 || c.cfg.match_rounds < 0)
       throw ApiError(MAP_E_INVALID, "coarsener must be 0 or 1 and match_rounds >= 0");
+    if (c.cfg.initial < 0 || c.cfg.initial > 1) throw ApiError(MAP_E_INVALID, "initial must be 0 or 1");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
-    for (auto& cs : c.cap.s) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     sort_init();
     GM_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.dev));
+    if (!c.cfg.alloc) keep_pool_memory(c.dev);
     c.mem.st = c.st;
     c.mem.afn = c.cfg.alloc;
     c.mem.ffn = c.cfg.free;
@@ -331,10 +354,18 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
     c.lv.push_back(L);
     c.d_code_of_pe = c.mem.make<int32_t>((size_t)c.k);
     c.d_pe_of_code = c.mem.make<int32_t>((size_t)c.topo.kc);
-    GM_CUDA(cudaMemcpyAsync(c.d_code_of_pe, c.code_of_pe.data(), (size_t)c.k * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, c.st));
-    GM_CUDA(cudaMemcpyAsync(c.d_pe_of_code, c.pe_of_code.data(), (size_t)c.topo.kc * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, c.st));
+    const size_t tk = (size_t)c.k * sizeof(int32_t), tc = (size_t)c.topo.kc * sizeof(int32_t);
+    const int32_t* src_k = c.code_of_pe.data();
+    const int32_t* src_c = c.pe_of_code.data();
+    if (tk + tc <= kPinnedBlock) {  // small tables travel from pinned memory (no shared staging buffer)
+      c.h_tables = pinned_get(tk + tc);
+      std::memcpy(c.h_tables, src_k, tk);
+      std::memcpy(static_cast<char*>(c.h_tables) + tk, src_c, tc);
+      src_k = static_cast<const int32_t*>(c.h_tables);
+      src_c = reinterpret_cast<const int32_t*>(static_cast<const char*>(c.h_tables) + tk);
+    }
+    GM_CUDA(cudaMemcpyAsync(c.d_code_of_pe, src_k, tk, cudaMemcpyHostToDevice, c.st));
+    GM_CUDA(cudaMemcpyAsync(c.d_pe_of_code, src_c, tc, cudaMemcpyHostToDevice, c.st));
     c.errword = reinterpret_cast<uint32_t*>(c.mem.make<int64_t>(1));
     alloc_sort(c);
     refine_alloc(c);
@@ -354,6 +385,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       ctx->c.h_cstate = nullptr;
       pinned_put(ctx->c.h_small);
       ctx->c.h_small = nullptr;
+      pinned_put(ctx->c.h_tables);
+      ctx->c.h_tables = nullptr;
       cudaStreamSynchronize(ctx->c.st);
       for (auto& cs : ctx->c.cap.s)
         if (cs) cudaStreamDestroy(cs);
@@ -378,6 +411,7 @@ void map_destroy(map_ctx* ctx) {
     pinned_put(ctx->c.h_cstate);
     pinned_put(ctx->c.h_small);
     pinned_put(ctx->c.h_eng_job);
+    pinned_put(ctx->c.h_tables);
     for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
     for (auto& L : ctx->c.lv) {
       drop_graph(L);
@@ -605,7 +639,7 @@ map_status map_run(map_ctx* ctx, int32_t* out_pi, int64_t* out_J) {
 map_status map_run_hm(map_ctx* ctx, int32_t workers, int32_t* out_pi, int64_t* out_J) {
   return guarded(ctx, [&](Ctx& c) {
     if (workers < 0) throw ApiError(MAP_E_INVALID, "workers must be >= 0");
-    hm_run(c, workers ? workers : 8, &c.hm);
+    hm_run(c, 0, workers ? workers : 8, &c.hm);
     int64_t J = 0, mw = 0;
     objective(c, 0, &J, &mw);
     if (out_pi) {
@@ -618,23 +652,25 @@ map_status map_run_hm(map_ctx* ctx, int32_t workers, int32_t* out_pi, int64_t* o
   });
 }
 
-map_status map_hm_stats(map_ctx* ctx, map_hm_stats_t* out) {
+map_status map_hm_stats(map_ctx* ctx, int32_t which, map_hm_stats_t* out) {
   return guarded(ctx, [&](Ctx& c) {
     if (!out) throw ApiError(MAP_E_INVALID, "out is NULL");
+    if (which < 0 || which > 1) throw ApiError(MAP_E_INVALID, "which must be 0 or 1");
+    const HmStats& h = which == 0 ? c.hm : c.hm_init;
     std::memset(out, 0, sizeof(*out));
-    out->levels = c.hm.levels;
-    out->workers = c.hm.workers;
+    out->levels = h.levels;
+    out->workers = h.workers;
     for (int i = 0; i < 16; i++) {
-      out->calls[i] = c.hm.calls[i];
-      out->first_eps[i] = c.hm.first_eps[i];
+      out->calls[i] = h.calls[i];
+      out->first_eps[i] = h.first_eps[i];
+      out->ms_level[i] = h.ms_level[i];
     }
-    out->ms_partition = c.hm.ms_partition;
-    out->ms_build = c.hm.ms_build;
-    out->ms_total = c.hm.ms_total;
-    for (int i = 0; i < 16; i++) out->ms_level[i] = c.hm.ms_level[i];
-    out->ms_create = c.hm.ms_create;
-    out->ms_run = c.hm.ms_run;
-    out->ms_destroy = c.hm.ms_destroy;
+    out->ms_partition = h.ms_partition;
+    out->ms_build = h.ms_build;
+    out->ms_total = h.ms_total;
+    out->ms_create = h.ms_create;
+    out->ms_run = h.ms_run;
+    out->ms_destroy = h.ms_destroy;
   });
 }
 

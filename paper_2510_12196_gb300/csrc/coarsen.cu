@@ -833,11 +833,12 @@ struct LoadTableSize {
   }
 };
 
+// read-backs go through the context's pinned block (slots 6 and 7 here):
+// a pageable copy stages through a driver buffer that concurrent contexts share
 int64_t read_i64(Ctx& c, const int64_t* d) {
-  int64_t h = 0;
-  GM_CUDA(cudaMemcpyAsync(&h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(c.h_small + 6, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
-  return h;
+  return c.h_small[6];
 }
 
 int bits_for(int64_t x) {  // smallest b with x < 2^b
@@ -847,9 +848,10 @@ int bits_for(int64_t x) {  // smallest b with x < 2^b
 }
 
 void check_err(Ctx& c) {
-  uint32_t e = 0;
-  GM_CUDA(cudaMemcpyAsync(&e, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
+  c.h_small[7] = 0;
+  GM_CUDA(cudaMemcpyAsync(c.h_small + 7, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
+  const uint32_t e = (uint32_t)(c.h_small[7] & 0xffffffffLL);
   if (e & ERR_TIMEOUT) throw ApiError(MAP_E_TIMEOUT, "a bounded device loop gave up");
   if (e) throw ApiError(MAP_E_INTERNAL, "device consistency check failed (flags " + std::to_string(e) + ")");
 }
@@ -922,6 +924,7 @@ void build_cluster_graph(Ctx& c, int lvl, int64_t wcap) {
   const int32_t n = L.n;
   const unsigned gv = grid_for(c, kThreads, n);
   cudaStream_t saved = c.st;
+  cap_streams(c);
   cudaStream_t cs = c.cap.s[0];
   long long root = 0, body = 0;
   long long* outer = set_capture_counter(&root);
@@ -1129,15 +1132,6 @@ __global__ void k_max_i32(int32_t n, const int32_t* __restrict__ a, int32_t* out
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
-int32_t device_max_vw(Ctx& c, const Level& L) {
-  int32_t* d = reinterpret_cast<int32_t*>(c.counters + 4);
-  GM_CUDA(cudaMemsetAsync(d, 0, sizeof(int64_t), c.st));
-  k_max_i32<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.vw, d); count_launch();
-  int32_t h = 0;
-  GM_CUDA(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
-  return h;
-}
 
 
 }  // namespace
@@ -1160,12 +1154,21 @@ void validate_graph(Ctx& c) {
   GM_CUDA(cudaMemsetAsync(c.errword, 0, sizeof(uint32_t), c.st));
   GM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), c.st));
   k_validate<<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.m, c.errword, sums); count_launch();
+  // the largest vertex weight in the same round trip
+  int32_t* dmax = reinterpret_cast<int32_t*>(c.counters + 4);
+  GM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int64_t), c.st));
+  k_max_i32<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.vw, dmax); count_launch();
   GM_CUDA(cudaGetLastError());
-  uint32_t e = 0;
-  unsigned long long h[2] = {0, 0};
-  GM_CUDA(cudaMemcpyAsync(&e, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+  int64_t* hs = c.h_small;  // pinned: [0] error flags, [1..2] sums, [3] largest weight
+  hs[0] = 0;
+  hs[3] = 0;
+  GM_CUDA(cudaMemcpyAsync(hs, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(hs + 1, sums, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(hs + 3, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
+  const uint32_t e = (uint32_t)(hs[0] & 0xffffffffLL);
+  const unsigned long long h[2] = {(unsigned long long)hs[1], (unsigned long long)hs[2]};
+  const int32_t hmax = (int32_t)(hs[3] & 0xffffffffLL);
   GM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), c.st));
   if (e) {
     std::string m = "invalid graph:";
@@ -1180,7 +1183,7 @@ void validate_graph(Ctx& c) {
   if (h[0] >= (1ULL << 31) || h[1] >= (1ULL << 31))
     throw ApiError(MAP_E_OVERFLOW, "sum of vertex weights and sum of edge weights must be < 2^31");
   c.cV = (int64_t)h[0];
-  L.max_vw = device_max_vw(c, L);
+  L.max_vw = hmax;
 }
 
 int32_t coarsen(Ctx& c) {
@@ -1207,6 +1210,10 @@ int32_t coarsen(Ctx& c) {
 
 void initial_map(Ctx& c) {
   Level& L = c.lv.back();
+  if (c.cfg.initial == 1) {  // hierarchical multisection of the coarsest graph
+    hm_run(c, (int)c.lv.size() - 1, 8, &c.hm_init);
+    return;
+  }
   const size_t smem = L.n <= kInitSmemN ? (size_t)3 * L.n * sizeof(int32_t) : 0;
   static std::atomic<unsigned long long> attr_done{0};  // one bit per device
   const unsigned long long bit = 1ULL << (c.dev & 63);

@@ -140,7 +140,8 @@ struct Ctx {
   double eps = 0;
   std::vector<int32_t> code_of_pe, pe_of_code;
   std::vector<int32_t> hier, dist;  // a_1..a_l, d_1..d_l as given
-  HmStats hm;
+  HmStats hm;       // the last map_run_hm
+  HmStats hm_init;  // the last initial mapping by hierarchical multisection
   int32_t* d_code_of_pe = nullptr;
   int32_t* d_pe_of_code = nullptr;
   std::vector<Level> lv;       // lv[0] = input graph
@@ -179,6 +180,7 @@ struct Ctx {
   RefineState* state = nullptr;
   RefineState* h_state = nullptr;  // pinned mirror
   int64_t* h_small = nullptr;      // pinned, a few values read back together
+  void* h_tables = nullptr;        // pinned staging of small PE code tables
   int64_t* d_stats = nullptr;      // device, per-level statistics
   int32_t* trace_kind = nullptr;
   int64_t* trace_J = nullptr;
@@ -270,11 +272,17 @@ void initial_map(Ctx& c);
 void project(Ctx& c, int lvl);
 void validate_graph(Ctx& c);
 
+// the context's capture streams, created on first use
+inline void cap_streams(Ctx& c) {
+  for (auto& cs : c.cap.s)
+    if (!cs) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+}
+
 // match.cu
 int32_t match_level(Ctx& c, int lvl);  // two-hop matching of level lvl into its M; returns n_c
 
-// hm.cu: hierarchical multisection of the input graph into lv[0].pi (codes)
-void hm_run(Ctx& c, int32_t workers, HmStats* st);
+// hm.cu: hierarchical multisection of level lvl's graph into its pi (codes)
+void hm_run(Ctx& c, int lvl, int32_t workers, HmStats* st);
 
 }  // namespace gm
 

@@ -227,6 +227,7 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
     cfg.alloc = nullptr;  // the partitioner contexts allocate stream-ordered themselves
     cfg.free = nullptr;
     cfg.alloc_user = nullptr;
+    cfg.initial = 0;  // the partitioner starts from its breadth-first chunks
     map_ctx* sub = nullptr;
     const int64_t v0 = S.voff[(size_t)j], e0 = S.eoff[(size_t)j];
     const auto t0 = std::chrono::steady_clock::now();
@@ -309,8 +310,7 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
 }
 
 // Builds the a children of every subgraph of S (Alg. 2 for all blocks at once).
-Stack build_children(Ctx& c, const Stack& S, int32_t i, int32_t a, const int32_t* part) {
-  const int32_t n = c.n0;
+Stack build_children(Ctx& c, int32_t n, const Stack& S, int32_t i, int32_t a, const int32_t* part) {
   const int64_t nchild = (int64_t)S.cnt * a;
   int64_t below = 1;
   for (int32_t j = 0; j + 1 < i; j++) below *= c.hier[(size_t)j];
@@ -380,7 +380,7 @@ Stack build_children(Ctx& c, const Stack& S, int32_t i, int32_t a, const int32_t
 
 }  // namespace
 
-void hm_run(Ctx& c, int32_t workers, HmStats* st) {
+void hm_run(Ctx& c, int lvl, int32_t workers, HmStats* st) {
   const auto t0 = std::chrono::steady_clock::now();
   const int32_t levels = (int32_t)c.hier.size();
   if (levels > 16) throw ApiError(MAP_E_INVALID, "hierarchical multisection supports at most 16 levels");
@@ -389,8 +389,8 @@ void hm_run(Ctx& c, int32_t workers, HmStats* st) {
     st->levels = levels;
     st->workers = workers;
   }
-  const int32_t n = c.n0;
-  Level& L0 = c.lv[0];
+  Level& L0 = c.lv[(size_t)lvl];
+  const int32_t n = L0.n;
   Stack S;
   S.cnt = 1;
   S.voff = {0, (int64_t)n};
@@ -425,7 +425,7 @@ void hm_run(Ctx& c, int32_t workers, HmStats* st) {
         break;
       }
       auto tb = std::chrono::steady_clock::now();
-      Stack C = build_children(c, S, i, a, part);
+      Stack C = build_children(c, n, S, i, a, part);
       free_stack(c, S);
       S = C;
       GM_CUDA(cudaStreamSynchronize(c.st));

@@ -338,6 +338,7 @@ void build_match_graph(Ctx& c, int lvl) {
   L.cgexec = nullptr;
   MatchState* s = state_of(c);
   cudaStream_t saved = c.st;
+  cap_streams(c);
   cudaStream_t cs = c.cap.s[0];
   long long root = 0, body = 0;
   long long* outer = set_capture_counter(&root);

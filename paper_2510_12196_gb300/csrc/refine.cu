@@ -10,6 +10,7 @@
 // higher-degree vertex gets a whole CTA with a dense shared-memory
 // connectivity array over the PE code space; per-level group sums of that
 // array give the gain of every candidate PE in O(levels).
+#include <atomic>
 #include <algorithm>
 #include <mutex>
 
@@ -2527,7 +2528,11 @@ void refine_alloc(Ctx& c) {
   if (smem > 48 * 1024) {
     GM_CUDA(cudaFuncSetAttribute(k_lp_gain_high, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
-  GM_CUDA(cudaFuncSetAttribute(k_reb_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_sort_smem()));
+  static std::atomic<unsigned long long> resolve_done{0};  // one bit per device
+  if (!(resolve_done.load() & (1ULL << (c.dev & 63)))) {
+    GM_CUDA(cudaFuncSetAttribute(k_reb_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_sort_smem()));
+    resolve_done.fetch_or(1ULL << (c.dev & 63));
+  }
   if (kc * sizeof(int32_t) > 48 * 1024) {
     GM_CUDA(cudaFuncSetAttribute(k_reb_select_high, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kc * sizeof(int32_t))));
@@ -2644,6 +2649,7 @@ static void build_refine_graph(Ctx& c, int lvl, int32_t rounds) {
   Level& L = c.lv[lvl];
   drop_graph(L);
   cudaStream_t saved = c.st;
+  cap_streams(c);
   cudaStream_t cs = c.cap.s[0];
   const CtlArgs ca = ctl_args(c);
   const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
@@ -2800,7 +2806,15 @@ int engine_max_clusters(int C, int te) {
 
 static void engine_setup(Ctx& c) {
   if (c.eng_max_cluster > 0) return;
-  c.eng_max_cluster = engine_max_clusters(kEngMaxCluster, 512) > 0 ? kEngMaxCluster : 8;
+  // the occupancy query is a property of the device: once per process
+  static std::atomic<int> cached[64];
+  const int d = c.dev & 63;
+  int v = cached[d].load();
+  if (v == 0) {
+    v = engine_max_clusters(kEngMaxCluster, 512) > 0 ? kEngMaxCluster : 8;
+    cached[d].store(v);
+  }
+  c.eng_max_cluster = v;
   if (!c.eng_job) {
     c.eng_job = c.mem.make<EngineJob>(1);
     static_assert(sizeof(EngineJob) <= kPinnedBlock, "pinned block too small");
@@ -2892,6 +2906,8 @@ static bool engine_grid_ok(Ctx& c, const Level& L) {
   const int64_t lim =
       c.cfg.grid_engine_max_n > 0 ? c.cfg.grid_engine_max_n : (c.cfg.grid_engine_max_n < 0 ? -1 : (1 << 18));
   if (!c.use_graphs || c.prof || L.n > lim || L.max_deg > kEngMaxDeg) return false;
+  static std::atomic<int> cached[64];  // a property of the device: once per process
+  if (c.eng_grid_blocks == 0) c.eng_grid_blocks = cached[c.dev & 63].load();
   if (c.eng_grid_blocks == 0) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine_grid<512>, kEngThreads, engine_smem(512)) !=
@@ -2903,6 +2919,7 @@ static bool engine_grid_ok(Ctx& c, const Level& L) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.dev);
     c.eng_grid_blocks = (coop && per_sm > 0) ? c.num_sms * per_sm : -1;
+    cached[c.dev & 63].store(c.eng_grid_blocks);
   }
   return c.eng_grid_blocks > 0;
 }

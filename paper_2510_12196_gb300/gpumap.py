@@ -42,7 +42,7 @@ class MapConfig(C.Structure):
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32),
                 ("grid_engine_max_n", C.c_int32), ("coarsener", C.c_int32),
-                ("match_rounds", C.c_int32)]
+                ("match_rounds", C.c_int32), ("initial", C.c_int32)]
 
 
 class MapStats(C.Structure):
@@ -86,7 +86,7 @@ _SIGS = {
     "map_run": (C.c_int, [_P, _P, _P]),
     "map_stats": (C.c_int, [_P, _P]),
     "map_run_hm": (C.c_int, [_P, C.c_int32, _P, _P]),
-    "map_hm_stats": (C.c_int, [_P, _P]),
+    "map_hm_stats": (C.c_int, [_P, C.c_int32, _P]),
     "map_profile_enable": (C.c_int, [_P, C.c_int32]),
     "map_profile_read": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
     "map_launch_count": (C.c_longlong, []),
@@ -342,9 +342,10 @@ def map_run_hm(ctx, out_pi=None, workers: int = 0):
     return J.value
 
 
-def map_hm_stats(ctx) -> MapHmStats:
+def map_hm_stats(ctx, which: int = 0) -> MapHmStats:
+    """which = 0: the last map_run_hm; 1: the last multisection initial mapping."""
     s = MapHmStats()
-    _check(ctx, lib().map_hm_stats(ctx, C.byref(s)), "map_hm_stats")
+    _check(ctx, lib().map_hm_stats(ctx, int(which), C.byref(s)), "map_hm_stats")
     return s
 
 

@@ -45,3 +45,24 @@ TOPOS = [((4, 8), (1, 10)), ((4, 8, 6), (1, 10, 100)), ((2, 3), (3, 7)), ((3,), 
 
 def g_graph_from_level(xadj, adj, w, vw):
     return I.Graph(len(vw), xadj, adj, w, vw)
+
+
+def map_run_compare(g, hier, dist, eps=0.03, seed=0x5EED0000, **over):
+    """map_run on the GPU against the oracle's pipeline with the same
+    settings: levels, per-level n, iterations, J and the final mapping."""
+    ctx = make_ctx(g, hier, dist, eps=eps, seed=seed, **over)
+    try:
+        pi = np.zeros(g.n, np.int32)
+        J = G.map_run(ctx, pi)
+        st = G.map_stats(ctx)
+    finally:
+        G.map_destroy(ctx)
+    fields = {f[0] for f in O.Params._fields_}  # execution settings do not reach the oracle
+    opi, oJ, ost = O.map_run(g, hier, dist, eps, oracle_params(seed, **{k: v for k, v in over.items() if k in fields}))
+    assert st.levels == ost.levels
+    assert [st.n[i] for i in range(st.levels)] == [ost.n[i] for i in range(ost.levels)]
+    assert [st.iters[i] for i in range(st.levels)] == [ost.iters[i] for i in range(ost.levels)]
+    assert [st.J[i] for i in range(st.levels)] == [ost.J[i] for i in range(ost.levels)]
+    assert J == oJ
+    assert np.array_equal(pi, opi)
+    return J

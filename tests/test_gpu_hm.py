@@ -75,3 +75,25 @@ def test_hm_invalid_workers():
             G.map_run_hm(ctx, workers=-1)
     finally:
         G.map_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["rgg15", "rmat13", "grid3d_match", "stream"])
+def test_map_run_hm_initial_parity(case):
+    """The integrated pipeline with the hierarchical-multisection initial
+    mapping of the coarsest graph, bit-identical to the oracle."""
+    from gpu_helpers import map_run_compare
+    if case == "rgg15":
+        map_run_compare(I.rgg2d(1 << 15, I.rgg_radius(1 << 15, 12), 3, wmax=10), (4, 8, 8), (1, 10, 100), initial=1)
+    elif case == "rmat13":
+        map_run_compare(I.rmat(13, 16, 0.57, 0.19, 0.19, 5), (4, 16), (1, 10), initial=1)
+    elif case == "grid3d_match":
+        map_run_compare(I.grid3d(32, 32, 16), (4, 16, 8), (1, 10, 100), initial=1, coarsener=1)
+    else:
+        map_run_compare(I.rgg2d(1 << 14, I.rgg_radius(1 << 14, 12), 4, wmax=10, shuffled=True), (4, 8, 6),
+                        (1, 10, 100), initial=1, launch_mode=1, engine_max_n=-1, grid_engine_max_n=-1)
+
+
+def test_map_run_hm_initial_rgg_2_20():
+    from gpu_helpers import map_run_compare
+    w = I.workload_rgg(20)
+    map_run_compare(w.graph, w.topo.hier, w.topo.dist, w.topo.eps, seed=w.seed, initial=1)
