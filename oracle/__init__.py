@@ -36,7 +36,8 @@ class Params(C.Structure):
                 ("coarsest_factor", C.c_int32), ("cluster_iters", C.c_int32),
                 ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
                 ("stall_num", C.c_int32), ("stall_den", C.c_int32),
-                ("coarsener", C.c_int32), ("match_rounds", C.c_int32), ("initial", C.c_int32)]
+                ("coarsener", C.c_int32), ("match_rounds", C.c_int32), ("initial", C.c_int32),
+                ("lp_relax_num", C.c_int32), ("lp_relax_den", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -126,8 +127,9 @@ def gain(g, hier, dist_, pi, v: int, q: int) -> int:
                               _p(pi), C.c_int32(v), C.c_int32(q)))
 
 
-def lp_step(g, hier, dist_, pi, lock):
-    """One Alg. 4 step.  Returns (new pi, new lock, pi', g, inX, moved, |M|)."""
+def lp_step(g, hier, dist_, pi, lock, relax=(0, 1)):
+    """One Alg. 4 step.  Returns (new pi, new lock, pi', g, inX, moved, |M|).
+    relax = (num, den) > (0, .): the relaxed filter -G < floor(num conn(v, P(v)) / den)."""
     h, d, l = _topo(hier, dist_)
     pi = _i32(pi).copy()
     lock = np.ascontiguousarray(lock, dtype=np.uint8).copy()
@@ -135,8 +137,9 @@ def lp_step(g, hier, dist_, pi, lock):
     gn = np.zeros(g.n, np.int64)
     inx = np.zeros(g.n, np.uint8)
     mv = np.zeros(g.n, np.uint8)
-    cnt = lib().orc_lp_step(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(h), _p(d), l,
-                            _p(pi), _p(lock), _p(pp), _p(gn), _p(inx), _p(mv))
+    cnt = lib().orc_lp_step_relaxed(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(h), _p(d), l,
+                                    _p(pi), _p(lock), _p(pp), _p(gn), _p(inx), _p(mv), C.c_int32(relax[0]),
+                                    C.c_int32(relax[1]))
     return pi, lock, pp, gn, inx, mv, int(cnt)
 
 

@@ -62,6 +62,8 @@ void orc_default_params(orc_params *p) {
   p->coarsener = 0;
   p->match_rounds = 16;
   p->initial = 0;
+  p->lp_relax_num = 0;
+  p->lp_relax_den = 1;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -182,11 +184,23 @@ static int64_t gain_from_conn(const conn_table *t, const int32_t *hier, const in
 /*     recomputed gain is >= 0.                                               */
 /*  3. P(v) <- P'(v) for v in M, simultaneously; lock = indicator of M.       */
 /* Vertices outside X report P'(v) = P(v), g(v) = 0.  Returns |M|.           */
+/*                                                                           */
+/* Relaxed filter (Section 4.2, the filter Jet uses; relax_num > 0): v also  */
+/* enters X with a negative best gain G when -G < floor(c conn(v, P(v))),    */
+/* c = relax_num / relax_den, conn(v, P(v)) the weight of v's edges into its */
+/* own block.                                                                */
 /* ------------------------------------------------------------------------- */
 int32_t orc_lp_step(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
                     const int32_t *hier, const int32_t *dist, int32_t levels,
                     int32_t *pi, uint8_t *lock, int32_t *pi_prime, int64_t *gain,
                     uint8_t *in_x, uint8_t *moved) {
+  return orc_lp_step_relaxed(n, xadj, adj, adjw, hier, dist, levels, pi, lock, pi_prime, gain, in_x, moved, 0, 1);
+}
+
+int32_t orc_lp_step_relaxed(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                            const int32_t *hier, const int32_t *dist, int32_t levels,
+                            int32_t *pi, uint8_t *lock, int32_t *pi_prime, int64_t *gain,
+                            uint8_t *in_x, uint8_t *moved, int32_t relax_num, int32_t relax_den) {
   int64_t k = orc_num_pes(hier, levels);
   conn_table t;
   t.conn = (int64_t *)calloc((size_t)k, sizeof(int64_t));
@@ -211,8 +225,11 @@ int32_t orc_lp_step(int32_t n, const int64_t *xadj, const int32_t *adj, const in
         best_g = G;
       }
     }
+    int64_t own = t.conn[pi[v]];
     conn_clear(&t);
-    if (best_q >= 0 && best_g >= 0) {
+    int admit = best_g >= 0;
+    if (!admit && relax_num > 0) admit = -best_g < ((int64_t)relax_num * own) / relax_den;
+    if (best_q >= 0 && admit) {
       in_x[v] = 1;
       pi_prime[v] = best_q;
       gain[v] = best_g;
@@ -447,7 +464,8 @@ int32_t orc_refine(int32_t n, const int64_t *xadj, const int32_t *adj, const int
     t++;
     int kind;
     if (cur_maxw <= lmax) {
-      orc_lp_step(n, xadj, adj, adjw, hier, dist, levels, cur, lock, pp, gn, inx, mv);
+      orc_lp_step_relaxed(n, xadj, adj, adjw, hier, dist, levels, cur, lock, pp, gn, inx, mv, prm->lp_relax_num,
+                          prm->lp_relax_den);
       iw = 0;
       kind = 0;
     } else if (iw < prm->weak_max) {

@@ -37,6 +37,8 @@ typedef struct {
   int32_t match_rounds;      /* heavy-edge matching: at most this many rounds per level: 16 */
   int32_t initial;           /* mapping of the coarsest graph: 0: breadth-first chunks; 1: hierarchical
                                 multisection (Section 4.2, initial partitioning) */
+  int32_t lp_relax_num, lp_relax_den; /* Alg. 4 filter: 0 = non-negative gains only (the paper's);
+                                          > 0: also -G < floor(num conn(v, P(v)) / den) (Jet's) */
 } orc_params;
 
 typedef struct {
@@ -66,6 +68,10 @@ int32_t orc_lp_step(int32_t n, const int64_t *xadj, const int32_t *adj, const in
                     const int32_t *hier, const int32_t *dist, int32_t levels,
                     int32_t *pi, uint8_t *lock, int32_t *pi_prime, int64_t *gain,
                     uint8_t *in_x, uint8_t *moved);
+int32_t orc_lp_step_relaxed(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                            const int32_t *hier, const int32_t *dist, int32_t levels,
+                            int32_t *pi, uint8_t *lock, int32_t *pi_prime, int64_t *gain,
+                            uint8_t *in_x, uint8_t *moved, int32_t relax_num, int32_t relax_den);
 
 int32_t orc_rebalance(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
                       const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,

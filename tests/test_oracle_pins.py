@@ -215,6 +215,52 @@ def test_lp_step_bruteforce(hier, dist):
         assert cnt == int(mv.sum())
 
 
+@pytest.mark.parametrize("relax", [(1, 4), (3, 4), (2, 1)])
+def test_lp_step_relaxed_filter_bruteforce(relax):
+    """Jet's relaxed filter: v enters X when its best gain G >= 0 or
+    -G < floor(c conn(v, P(v))), c = num/den, conn(v, P(v)) read here off the
+    dense weight matrix; the afterburner and the apply are unchanged.  Unit
+    distances keep gains on the scale of connectivities, so the relaxation
+    has something to admit."""
+    hier, dist = (4, 8), (1, 1)
+    D = dmat_from_tree(hier, dist)
+    k = D.shape[0]
+    num, den = relax
+    neg_in = 0
+    for i, g in enumerate(small_graphs(12, seed0=910)):
+        C = dense(g)
+        # a mapping with locality, so that own-block connectivity is common
+        pi = ((np.arange(g.n) * 4) // g.n).astype(np.int32)
+        flip = rand_pi(g.n, k, 50 + i)
+        pi = np.where(np.arange(g.n) % 3 == 0, flip, pi).astype(np.int32)
+        lock = np.zeros(g.n, np.uint8)
+        npi, nlock, pp, gn, inx, mv, cnt = O.lp_step(g, hier, dist, pi, lock, relax=relax)
+        for v in range(g.n):
+            nb = sorted({int(pi[u]) for u in np.nonzero(C[v])[0]} - {int(pi[v])})
+            if not nb:
+                assert not inx[v]
+                continue
+            bg, bq = max((_bf_gain(C, D, pi, v, q), -q) for q in nb)
+            own = int(sum(C[v, u] for u in range(g.n) if pi[u] == pi[v] and u != v))
+            admit = bg >= 0 or -bg < (num * own) // den
+            assert bool(inx[v]) == admit
+            if admit:
+                assert pp[v] == -bq and gn[v] == bg
+                neg_in += bg < 0
+        for v in range(g.n):
+            if not inx[v]:
+                assert not mv[v]
+                continue
+            st = pi.copy()
+            for u in np.nonzero(C[v])[0]:
+                if inx[u] and (gn[u] > gn[v] or (gn[u] == gn[v] and u < v)):
+                    st[u] = pp[u]
+            assert bool(mv[v]) == (_bf_gain(C, D, st, v, pp[v]) >= 0)
+        assert np.array_equal(npi, np.where(mv == 1, pp, pi))
+    if 4 * num >= 3 * den:
+        assert neg_in > 0  # the relaxation admitted negative moves somewhere
+
+
 def test_lp_independent_moves_exact_delta():
     """When the moved vertices are pairwise non-adjacent, J drops by exactly
     twice the sum of their Eq. 1 gains."""
