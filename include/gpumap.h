@@ -103,6 +103,11 @@ typedef struct {
   int32_t initial;       /* mapping of the coarsest graph: 0: breadth-first chunks (default); 1: hierarchical
                             multisection (as map_run_hm, on the coarsest graph, its partitioner starting
                             from breadth-first chunks; Section 4.2, initial partitioning) */
+  int32_t lp_relax_num;  /* Alg. 4 filter.  0 (default): only moves of gain G >= 0 enter X, as in the paper;
+                            > 0: also moves with -G < floor(lp_relax_num conn(v, P(v)) / lp_relax_den),
+                            conn(v, P(v)) = weight of v's edges inside its PE (the filter Section 4.2
+                            describes for Jet) */
+  int32_t lp_relax_den;  /* >= 1 (default 1) */
 } map_config;
 
 typedef struct {

@@ -261,6 +261,8 @@ void map_config_default(map_config* cfg) {
   cfg->coarsener = 0;
   cfg->match_rounds = 16;
   cfg->initial = 0;
+  cfg->lp_relax_num = 0;
+  cfg->lp_relax_den = 1;
 }
 
 const char* map_status_string(map_status s) {
@@ -301,6 +303,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
     if (c.cfg.coarsener < 0 || c.cfg.coarsener > 1 || c.cfg.match_rounds < 0)
       throw ApiError(MAP_E_INVALID, "coarsener must be 0 or 1 and match_rounds >= 0");
     if (c.cfg.initial < 0 || c.cfg.initial > 1) throw ApiError(MAP_E_INVALID, "initial must be 0 or 1");
+    if (c.cfg.lp_relax_num < 0 || c.cfg.lp_relax_den < 1)
+      throw ApiError(MAP_E_INVALID, "lp_relax_num must be >= 0 and lp_relax_den >= 1");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     sort_init();

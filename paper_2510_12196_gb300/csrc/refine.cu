@@ -223,16 +223,33 @@ __device__ __forceinline__ bool best_target(const Row& r, int deg, int32_t p, co
   return any;
 }
 
+// Alg. 4 filter: G >= 0, or with the relaxed filter (relax_num > 0) also
+// -G < floor(relax_num conn(v, P(v)) / relax_den).
+struct LpFilter {
+  int32_t num, den;
+  __device__ __forceinline__ bool admit(int64_t G, int64_t own) const {
+    return G >= 0 || (num > 0 && -G < ((int64_t)num * own) / den);
+  }
+};
+
+// weight of a row's entries inside PE p
+template <class Row>
+__device__ __forceinline__ int64_t row_own(const Row& r, int deg, int32_t p) {
+  int64_t s = 0;
+  for (int j = 0; j < deg; j++) s += r.code(j) == p ? r.weight(j) : 0;
+  return s;
+}
+
 // Sub-warp work queue of a staged tile: the lanes in `work` (vertices with a
 // neighbour outside their own PE) are served four at a time by 8-lane
 // sub-warps; each sub-warp evaluates T(q) for every distinct neighbouring PE
 // q != p of its vertex from the staged entries and keeps the minimum (lowest
-// code on ties).  out(lane, G = T(p) - T(q*), q*, p) runs on the sub-warp's
-// first lane.
+// code on ties).  out(lane, G = T(p) - T(q*), q*, p, conn(v, p)) runs on the
+// sub-warp's first lane; conn(v, p) is summed only when `own` is set (else 0).
 template <class Out>
 __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t, int32_t p, int64_t Tp,
                                                 const int32_t* sc, const int32_t* sw, const int32_t* sdist, int lane,
-                                                Out out) {
+                                                bool own, Out out) {
   const int sub = lane >> 3, sl = lane & 7;
   const int rounds = (__popc(work) + 3) / 4;
   for (int r = 0; r < rounds; r++) {
@@ -244,12 +261,15 @@ __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t
     const int64_t tp = __shfl_sync(0xffffffffu, Tp, s2);
     const int32_t* c = sc + (vb - t.E0);
     const int32_t* w = sw + (vb - t.E0);
-    int64_t bt = INT64_MAX;
+    int64_t bt = INT64_MAX, ow = 0;
     int32_t bc = INT32_MAX;
     if (src >= 0) {
       for (int j = sl; j < dg; j += kSubWarp) {
         const int32_t q = c[j];
-        if (q == pv) continue;
+        if (q == pv) {
+          ow += w[j];
+          continue;
+        }
         int64_t T = 0;
         for (int l = 0; l < dg; l++) T += (int64_t)w[l] * dcode(sdist, q, c[l]);
         if (T < bt || (T == bt && q < bc)) {
@@ -266,8 +286,9 @@ __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t
         bt = ot;
         bc = oc;
       }
+      if (own) ow += __shfl_xor_sync(0xffffffffu, ow, o);
     }
-    if (src >= 0 && sl == 0) out(src, tp - bt, bc, pv);
+    if (src >= 0 && sl == 0) out(src, tp - bt, bc, pv, ow);
   }
 }
 
@@ -278,7 +299,7 @@ __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_lp_gain_tile(GraphView g, const int32_t* __restrict__ pi,
                                                                uint8_t* __restrict__ lock, int32_t* __restrict__ pp,
                                                                int64_t* __restrict__ gain, uint8_t* __restrict__ inx,
-                                                               Topo topo, const RefineState* st) {
+                                                               Topo topo, LpFilter flt, const RefineState* st) {
   __shared__ int32_t sdist[32];
   __shared__ int32_t sc[kTileWarps][kTileE];
   __shared__ int32_t sw[kTileWarps][kTileE];
@@ -313,7 +334,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_lp_gain_tile(G
         int64_t bt;
         if (best_target(r, deg, p, sdist, bc, bt)) {
           const int64_t G = row_cost(r, deg, sdist, p) - bt;
-          if (G >= 0) {
+          if (flt.admit(G, flt.num > 0 ? row_own(r, deg, p) : 0)) {
             inx[t.v] = 1;
             pp[t.v] = bc;
             gain[t.v] = G;
@@ -329,10 +350,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_lp_gain_tile(G
     }
   done_lane:
     const unsigned work = __ballot_sync(0xffffffffu, cand);
-    tile_gain_queue(work, t, p, Tp, sc[warp], sw[warp], sdist, lane,
-                    [&](int src, int64_t G, int32_t bc, int32_t pv) {
+    tile_gain_queue(work, t, p, Tp, sc[warp], sw[warp], sdist, lane, flt.num > 0,
+                    [&](int src, int64_t G, int32_t bc, int32_t pv, int64_t own) {
                       const int64_t v = tile * kTileV + src;
-                      const bool in = G >= 0;
+                      const bool in = flt.admit(G, own);
                       inx[v] = in ? 1 : 0;
                       pp[v] = in ? bc : pv;
                       gain[v] = in ? G : 0;
@@ -394,7 +415,7 @@ __device__ __forceinline__ int64_t conn_T(const int32_t* tab, const Topo& topo, 
 __global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
                                                              const int32_t* __restrict__ pi, uint8_t* lock,
                                                              int32_t* pp, int64_t* gain, uint8_t* inx, Topo topo,
-                                                             GroupLayout gl, const RefineState* st) {
+                                                             GroupLayout gl, LpFilter flt, const RefineState* st) {
   extern __shared__ int32_t tab[];
   __shared__ int64_t sbt[32];
   __shared__ int32_t sbc[32];
@@ -447,7 +468,7 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const 
         }
       const int64_t Tp = conn_T(tab, topo, gl, p);
       const int64_t G = Tp - bt;
-      if (bc != INT32_MAX && G >= 0) {
+      if (bc != INT32_MAX && flt.admit(G, tab[p])) {
         inx[v] = 1;
         pp[v] = bc;
         gain[v] = G;
@@ -1363,13 +1384,14 @@ void launch_lp(Ctx& c, int lvl) {
   const unsigned gh = std::max(1, std::min(L.n_hi, c.num_sms * 8));
   c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
+  const LpFilter flt{c.cfg.lp_relax_num, c.cfg.lp_relax_den};
   k_lp_gain_tile<<<tile_grid(c, (const void*)k_lp_gain_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.lock, c.pp, c.gain, c.inx, c.topo,
-                                                                c.state); count_launch();
+                                                                flt, c.state); count_launch();
   // per vertex: xadj 8, P 4, lock 1, X 1, P' 4, g 8; per entry: adjacency 4, weight 4, gathered P(u) 4
   c.prof_end(ev, PK_LP_GAIN, 26 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
   if (L.n_hi)
     k_lp_gain_high<<<gh, kHiThreads, conn_smem(c), c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.lock, c.pp, c.gain, c.inx,
-                                                          c.topo, group_layout(c.topo), c.state); count_launch();
+                                                          c.topo, group_layout(c.topo), flt, c.state); count_launch();
   ev = c.prof_begin();
   k_lp_after_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.pp, c.gain, c.inx, c.lock, c.topo, c.state); count_launch();
   // the X flag of every vertex (the work on X itself is data dependent)
@@ -1493,6 +1515,7 @@ struct EngineJob {
   int32_t sigma_gap;
   int32_t level;
   int32_t rounds;
+  LpFilter flt;
 };
 
 struct PlainRow {  // neighbour PEs through plain loads (the mapping changes inside the launch)
@@ -2050,7 +2073,8 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
             const PlainRow r{g.adj + t.b, g.adjw + t.b, J.pi};
             int32_t bc;
             int64_t bt;
-            if (best_target(r, (int)(t.e - t.b), p, S.sdist, bc, bt) && Tp - bt >= 0) {
+            if (best_target(r, (int)(t.e - t.b), p, S.sdist, bc, bt) &&
+                J.flt.admit(Tp - bt, J.flt.num > 0 ? row_own(r, (int)(t.e - t.b), p) : 0)) {
               J.inx[t.v] = 1;
               J.pp[t.v] = bc;
               J.gain[t.v] = Tp - bt;
@@ -2064,10 +2088,10 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
           }
         }
         const unsigned work = __ballot_sync(0xffffffffu, cand);
-        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane,
-                        [&](int src, int64_t Gv, int32_t bc, int32_t pv) {
+        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane, J.flt.num > 0,
+                        [&](int src, int64_t Gv, int32_t bc, int32_t pv, int64_t own) {
           const int64_t v = tile * kTileV + src;
-          const bool in = Gv >= 0;
+          const bool in = J.flt.admit(Gv, own);
           J.inx[v] = in ? 1 : 0;
           J.pp[v] = in ? bc : pv;
           J.gain[v] = in ? Gv : 0;
@@ -2862,6 +2886,7 @@ static EngineJob engine_job(Ctx& c, int lvl, int32_t rounds) {
   j.seed = c.cfg.seed;
   j.k = c.k;
   j.sigma_gap = c.cfg.sigma_gap;
+  j.flt = LpFilter{c.cfg.lp_relax_num, c.cfg.lp_relax_den};
   j.level = lvl;
   j.rounds = rounds;
   return j;
