@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("cluster_cap_div", C.c_int32), ("max_levels", C.c_int32),
                 ("stall_num", C.c_int32), ("stall_den", C.c_int32),
                 ("coarsener", C.c_int32), ("match_rounds", C.c_int32), ("initial", C.c_int32),
-                ("lp_relax_num", C.c_int32), ("lp_relax_den", C.c_int32)]
+                ("lp_relax_num", C.c_int32), ("lp_relax_den", C.c_int32), ("reb_objective", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -144,16 +144,17 @@ def lp_step(g, hier, dist_, pi, lock, relax=(0, 1)):
 
 
 def rebalance(g, hier, dist_, lmax_: int, strong: bool, pi, sigma_gap: int = 100,
-              seed: int = 0x5EED0000, level: int = 0, t: int = 1):
-    """One weak / strong rebalancing step.  Returns (new pi, dest, moved, count)."""
+              seed: int = 0x5EED0000, level: int = 0, t: int = 1, objective: int = 0):
+    """One weak / strong rebalancing step (objective 0: cut gains, 1: Eq. 1's
+    J gains).  Returns (new pi, dest, moved, count)."""
     h, d, l = _topo(hier, dist_)
     pi = _i32(pi).copy()
     dest = np.zeros(g.n, np.int32)
     mv = np.zeros(g.n, np.uint8)
-    cnt = lib().orc_rebalance(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw),
-                              _p(h), _p(d), l, C.c_int64(lmax_), C.c_int32(int(strong)),
-                              C.c_int32(sigma_gap), C.c_uint64(seed), C.c_int32(level), C.c_int32(t),
-                              _p(pi), _p(dest), _p(mv))
+    cnt = lib().orc_rebalance_obj(C.c_int32(g.n), _p(g.xadj), _p(g.adj), _p(g.adjw), _p(g.vw),
+                                  _p(h), _p(d), l, C.c_int64(lmax_), C.c_int32(int(strong)),
+                                  C.c_int32(sigma_gap), C.c_uint64(seed), C.c_int32(level), C.c_int32(t),
+                                  _p(pi), _p(dest), _p(mv), C.c_int32(objective))
     return pi, dest, mv, int(cnt)
 
 

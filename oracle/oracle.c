@@ -64,6 +64,7 @@ void orc_default_params(orc_params *p) {
   p->initial = 0;
   p->lp_relax_num = 0;
   p->lp_relax_den = 1;
+  p->reb_objective = 0;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -294,7 +295,20 @@ int32_t orc_rebalance(int32_t n, const int64_t *xadj, const int32_t *adj, const 
                       const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
                       int64_t lmax, int32_t strong, int32_t sigma_gap, uint64_t seed,
                       int32_t level, int32_t t, int32_t *pi, int32_t *dest, uint8_t *moved) {
-  (void)dist;
+  return orc_rebalance_obj(n, xadj, adj, adjw, vw, hier, dist, levels, lmax, strong, sigma_gap, seed, level, t,
+                           pi, dest, moved, 0);
+}
+
+/* objective 1 (Section 4.2 tried it: the rebalancing adapted to J): the     */
+/* gain of moving v to b is Eq. 1's G_b(v) instead of the cut gain          */
+/* conn(v, b) - conn(v, A); the destination is the neighbouring block below  */
+/* sigma of largest G_b(v) (lowest id on ties), the random fallback's gain   */
+/* is G_q(v) of the drawn block q, and buckets are taken of that gain.       */
+int32_t orc_rebalance_obj(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                          const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
+                          int64_t lmax, int32_t strong, int32_t sigma_gap, uint64_t seed,
+                          int32_t level, int32_t t, int32_t *pi, int32_t *dest, uint8_t *moved,
+                          int32_t objective) {
   int64_t k = orc_num_pes(hier, levels);
   int64_t *W = (int64_t *)calloc((size_t)k, sizeof(int64_t));
   int64_t cV = 0;
@@ -331,18 +345,24 @@ int32_t orc_rebalance(int32_t n, const int64_t *xadj, const int32_t *adj, const 
     if (2 * k * (int64_t)vw[v] > 3 * (k * W[A] - cV)) continue;  /* heavy: > 1.5 (c(A) - c(V)/k) */
     conn_fill(&ct, xadj, adj, adjw, pi, v);
     int32_t best = -1;
+    int64_t bestG = 0;
     for (int32_t i = 0; i < ct.count; i++) {
       int32_t b = ct.list[i];
       if (b == A || W[b] > sigma) continue;
-      if (best < 0 || ct.conn[b] > ct.conn[best] || (ct.conn[b] == ct.conn[best] && b < best)) best = b;
+      if (objective == 1) {
+        int64_t G = gain_from_conn(&ct, hier, dist, levels, A, b);
+        if (best < 0 || G > bestG || (G == bestG && b < best)) { best = b; bestG = G; }
+      } else if (best < 0 || ct.conn[b] > ct.conn[best] || (ct.conn[b] == ct.conn[best] && b < best)) {
+        best = b;
+      }
     }
     int64_t g;
     if (best >= 0) {
-      g = ct.conn[best] - ct.conn[A];
+      g = objective == 1 ? bestG : ct.conn[best] - ct.conn[A];
     } else {
       if (nU == 0) { conn_clear(&ct); continue; }
       best = U[h_rebalance(seed, level, t, v) % (uint64_t)nU];
-      g = -ct.conn[A];
+      g = objective == 1 ? gain_from_conn(&ct, hier, dist, levels, A, best) : -ct.conn[A];
     }
     conn_clear(&ct);
     dest[v] = best;
@@ -469,13 +489,13 @@ int32_t orc_refine(int32_t n, const int64_t *xadj, const int32_t *adj, const int
       iw = 0;
       kind = 0;
     } else if (iw < prm->weak_max) {
-      orc_rebalance(n, xadj, adj, adjw, vw, hier, dist, levels, lmax, 0, prm->sigma_gap,
-                    prm->seed, level, t, cur, dst, mv);
+      orc_rebalance_obj(n, xadj, adj, adjw, vw, hier, dist, levels, lmax, 0, prm->sigma_gap,
+                    prm->seed, level, t, cur, dst, mv, prm->reb_objective);
       iw++;
       kind = 1;
     } else {
-      orc_rebalance(n, xadj, adj, adjw, vw, hier, dist, levels, lmax, 1, prm->sigma_gap,
-                    prm->seed, level, t, cur, dst, mv);
+      orc_rebalance_obj(n, xadj, adj, adjw, vw, hier, dist, levels, lmax, 1, prm->sigma_gap,
+                    prm->seed, level, t, cur, dst, mv, prm->reb_objective);
       iw = 0;
       kind = 2;
     }

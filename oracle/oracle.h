@@ -39,6 +39,7 @@ typedef struct {
                                 multisection (Section 4.2, initial partitioning) */
   int32_t lp_relax_num, lp_relax_den; /* Alg. 4 filter: 0 = non-negative gains only (the paper's);
                                           > 0: also -G < floor(num conn(v, P(v)) / den) (Jet's) */
+  int32_t reb_objective;     /* rebalancing gain: 0 = edge cut (the paper's), 1 = Eq. 1's J gain */
 } orc_params;
 
 typedef struct {
@@ -77,6 +78,11 @@ int32_t orc_rebalance(int32_t n, const int64_t *xadj, const int32_t *adj, const 
                       const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
                       int64_t lmax, int32_t strong, int32_t sigma_gap, uint64_t seed,
                       int32_t level, int32_t t, int32_t *pi, int32_t *dest, uint8_t *moved);
+int32_t orc_rebalance_obj(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
+                          const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,
+                          int64_t lmax, int32_t strong, int32_t sigma_gap, uint64_t seed,
+                          int32_t level, int32_t t, int32_t *pi, int32_t *dest, uint8_t *moved,
+                          int32_t objective);
 
 int32_t orc_refine(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *adjw,
                    const int32_t *vw, const int32_t *hier, const int32_t *dist, int32_t levels,

@@ -355,6 +355,68 @@ def test_rebalance_grid_reduces_overload():
     assert W2.max() <= max(L, W.max())
 
 
+def _loss_bucket(g):
+    if g > 0:
+        return 0
+    if g == 0:
+        return 1
+    return 2 + int(np.floor(np.log2(-g)))
+
+
+def test_rebalance_j_objective_bruteforce():
+    """Rebalancing adapted to J (Section 4.2): every eligible vertex of an
+    overloaded block gets the neighbouring destination below sigma of largest
+    J gain (dense objective difference, lowest id on ties), its bucket is
+    taken of that gain (of the drawn block's gain when no neighbour
+    qualifies), and each block moves the prefix of its eligible vertices in
+    (bucket, id) order that covers its excess."""
+    hier, dist = (2, 4), (1, 10)
+    D = dmat_from_tree(hier, dist)
+    k = D.shape[0]
+    checked = 0
+    for s in range(30):
+        g = I.erdos_renyi(36, 0.13, 1500 + s, wmax=5, vwmax=4)
+        C = dense(g)
+        pi = (I.splitmix64(70 + s, np.arange(g.n, dtype=np.uint64)) % np.uint64(13)).astype(np.int64)
+        pi = np.minimum(pi, k - 1).astype(np.int32)
+        cv = int(g.vw.sum())
+        L = O.lmax(cv, k, 0.03)
+        gap = 2
+        W = np.bincount(pi, weights=g.vw, minlength=k).astype(np.int64)
+        sigma = max(-(-cv // k), L - gap)
+        npi, dest, mv, cnt = O.rebalance(g, hier, dist, L, False, pi, sigma_gap=gap, seed=s, objective=1)
+        order = {}
+        for v in range(g.n):
+            A = int(pi[v])
+            if W[A] <= L or 2 * k * int(g.vw[v]) > 3 * (k * int(W[A]) - cv):
+                assert not mv[v]
+                continue
+            cand = sorted({int(pi[u]) for u in np.nonzero(C[v])[0]} - {A})
+            cand = [b for b in cand if W[b] <= sigma]
+            if cand:
+                gb, nb = max((_bf_gain(C, D, pi, v, b), -b) for b in cand)
+                b = -nb
+            else:
+                U = np.nonzero(W <= sigma)[0]
+                if len(U) == 0:
+                    continue
+                # the drawn block: U[h(level 0, t 1, v) mod |U|]
+                h = O.hash64(s, (3 << 60) | (1 << 32) | v)
+                b = int(U[h % len(U)])
+                gb = _bf_gain(C, D, pi, v, b)
+            if mv[v]:
+                assert dest[v] == b
+            order.setdefault(A, []).append((_loss_bucket(gb), v))
+        for A, lst in order.items():
+            pre = 0
+            for _, v in sorted(lst):
+                assert bool(mv[v]) == (pre < W[A] - L)
+                pre += int(g.vw[v])
+            checked += 1
+        assert np.array_equal(npi, np.where(mv == 1, dest, pi))
+    assert checked > 20
+
+
 # ----------------------------------------------------------------------------
 # Alg. 6
 # ----------------------------------------------------------------------------
