@@ -108,6 +108,9 @@ typedef struct {
                             conn(v, P(v)) = weight of v's edges inside its PE (the filter Section 4.2
                             describes for Jet) */
   int32_t lp_relax_den;  /* >= 1 (default 1) */
+  int32_t reb_objective; /* rebalancing gains: 0 (default): edge cut conn(v, q) - conn(v, P(v)), as the paper
+                            settles on; 1: Eq. 1's J gain G_q(v) for the destination choice and the loss
+                            buckets (the variant Section 4.2 reports trying) */
 } map_config;
 
 typedef struct {

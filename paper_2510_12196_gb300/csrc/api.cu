@@ -263,6 +263,7 @@ void map_config_default(map_config* cfg) {
   cfg->initial = 0;
   cfg->lp_relax_num = 0;
   cfg->lp_relax_den = 1;
+  cfg->reb_objective = 0;
 }
 
 const char* map_status_string(map_status s) {
@@ -305,6 +306,8 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
     if (c.cfg.initial < 0 || c.cfg.initial > 1) throw ApiError(MAP_E_INVALID, "initial must be 0 or 1");
     if (c.cfg.lp_relax_num < 0 || c.cfg.lp_relax_den < 1)
       throw ApiError(MAP_E_INVALID, "lp_relax_num must be >= 0 and lp_relax_den >= 1");
+    if (c.cfg.reb_objective < 0 || c.cfg.reb_objective > 1)
+      throw ApiError(MAP_E_INVALID, "reb_objective must be 0 or 1");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     sort_init();

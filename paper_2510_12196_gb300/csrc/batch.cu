@@ -77,6 +77,7 @@ struct map_batch {
   cudaEvent_t ev_in = nullptr, ev_done = nullptr;
   Schedule sched;
   bool tuned = false;
+  bool var = false;                // some job uses the refinement variants (512-entry tiles only)
   double tune_ms = 0.0;
   int32_t max_n = 0;
   int64_t sum_n = 0, sum_m = 0;
@@ -137,7 +138,7 @@ void jobs_wait_for(map_batch& b, cudaStream_t s) {
 
 void enqueue(map_batch& b, cudaStream_t s, const Schedule& sc) {
   GM_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(unsigned int), s));
-  engine_launch(s, b.d_jobs, (int)b.jobs.size(), b.d_queue, sc.C, sc.te, sc.ncl);
+  engine_launch(s, b.d_jobs, (int)b.jobs.size(), b.d_queue, sc.C, sc.te, sc.ncl, b.var);
   k_batch_collect<<<1, 256, 0, s>>>(b.d_states, (int32_t)b.jobs.size(), b.d_res); count_launch();
 }
 
@@ -196,6 +197,7 @@ Schedule autotune(map_batch& b) {
     std::vector<Schedule> cand;
     for (int te : {512, 256})
       for (int C : {1, 2, 4, 8, 16}) {
+        if (b.var && te != 512) continue;
         const Schedule sc = make_schedule(b, C, te);
         if (sc.C) cand.push_back(sc);
       }
@@ -281,7 +283,10 @@ map_status map_batch_create(map_ctx* const* jobs, int32_t njobs, const map_batch
       if (j->c.dev != B.dev) throw ApiError(MAP_E_INVALID, "job " + std::to_string(i) + " lives on another device");
       if (B.opts.level < 0 || B.opts.level >= (int)j->c.lv.size() || !j->c.lv[B.opts.level].pi)
         throw ApiError(MAP_E_STATE, "job " + std::to_string(i) + " has no level " + std::to_string(B.opts.level));
+      B.var = B.var || uses_variants(j->c.cfg);
     }
+    if (B.var && B.opts.tile_entries == 256)
+      throw ApiError(MAP_E_INVALID, "jobs with the refinement variants need tile_entries 0 or 512");
     GM_CUDA(cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking));
     GM_CUDA(cudaEventCreateWithFlags(&B.ev_in, cudaEventDisableTiming));
     GM_CUDA(cudaEventCreateWithFlags(&B.ev_done, cudaEventDisableTiming));

@@ -261,7 +261,11 @@ void classify_degrees(Ctx& c, int lvl);
 int engine_max_clusters(int C, int te);  // resident clusters of C CTAs (0: not launchable)
 size_t engine_job_bytes();
 bool engine_job_write(Ctx& c, int lvl, int32_t rounds, void* dst);  // false: level unsuited to the engine
-void engine_launch(cudaStream_t st, const void* d_jobs, int njobs, unsigned int* queue, int C, int te, int nclusters);
+// whether a configuration uses the refinement variants (relaxed filter, J gains in rebalancing)
+inline bool uses_variants(const map_config& cfg) { return cfg.lp_relax_num > 0 || cfg.reb_objective != 0; }
+// var: some job uses the refinement variants (needs te = 512)
+void engine_launch(cudaStream_t st, const void* d_jobs, int njobs, unsigned int* queue, int C, int te, int nclusters,
+                   bool var);
 bool barrier_selftest(cudaStream_t st);  // the bounded grid-barrier wait gives up and reports it
 void drop_graph(Level& L);
 

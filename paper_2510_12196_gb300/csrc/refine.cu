@@ -11,6 +11,7 @@
 // connectivity array over the PE code space; per-level group sums of that
 // array give the gain of every candidate PE in O(levels).
 #include <atomic>
+#include <type_traits>
 #include <algorithm>
 #include <mutex>
 
@@ -724,6 +725,8 @@ struct RebArgs {
   int64_t cV;
   int32_t k;
   uint64_t seed;
+  int32_t obj;   // 0: cut gains conn(v, q) - conn(v, A); 1: Eq. 1 gains T(A) - T(q)
+  Topo topo;     // distances for the J gains
 };
 
 __device__ __forceinline__ bool reb_eligible(const RebArgs& a, int32_t A, int32_t cv) {
@@ -736,7 +739,12 @@ __device__ __forceinline__ bool reb_eligible(const RebArgs& a, int32_t A, int32_
 __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const int32_t* __restrict__ pi, RebArgs a,
                                                              int32_t* __restrict__ dest, uint8_t* __restrict__ bkt,
                                                              uint8_t* __restrict__ elig, const RefineState* st) {
+  __shared__ int32_t sdist[32];
   if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  if (a.obj) {
+    load_sdist(sdist, a.topo);
+    __syncthreads();
+  }
   auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
   const int lane = tile.thread_rank();
   const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
@@ -767,8 +775,9 @@ __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const 
       if (c[r] == A) connA += w[r];
     }
     connA = tile_sum32(tile, connA);
-    // conn of each slot's block (only destinations below sigma are candidates)
-    int32_t cc[kSlots];
+    // score of each slot's block: conn(v, q), or -T(q) for the J gains (only
+    // destinations below sigma are candidates)
+    int64_t cc[kSlots];
 #pragma unroll
     for (int r = 0; r < kSlots; r++) cc[r] = 0;
     const int rows = (deg + kSubWarp - 1) / kSubWarp;
@@ -778,35 +787,59 @@ __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const 
       for (int j = 0; j < kSubWarp; j++) {
         const int32_t cs = tile.shfl(crr, j);
         const int32_t ws = tile.shfl(wrr, j);
+        if (a.obj) {
 #pragma unroll
-        for (int r = 0; r < kSlots; r++) cc[r] += (c[r] == cs) ? ws : 0;
+          for (int r = 0; r < kSlots; r++) cc[r] -= (int64_t)ws * dcode(sdist, c[r], cs);
+        } else {
+#pragma unroll
+          for (int r = 0; r < kSlots; r++) cc[r] += (c[r] == cs) ? ws : 0;
+        }
       }
     }
-    int32_t bconn = -1, bc = INT32_MAX;
+    bool found = false;
+    int64_t bconn = 0;
+    int32_t bc = INT32_MAX;
 #pragma unroll
     for (int r = 0; r < kSlots; r++) {
       if (c[r] == A || a.W[c[r]] > sigma) continue;
-      if (cc[r] > bconn || (cc[r] == bconn && c[r] < bc)) {
+      if (!found || cc[r] > bconn || (cc[r] == bconn && c[r] < bc)) {
         bconn = cc[r];
         bc = c[r];
+        found = true;
       }
     }
 #pragma unroll
     for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-      const int32_t ob = tile.shfl_xor(bconn, o);
+      const int64_t ob = tile.shfl_xor(bconn, o);
       const int32_t oc = tile.shfl_xor(bc, o);
-      if (ob > bconn || (ob == bconn && oc < bc)) {
+      const bool of = tile.shfl_xor(found, o);
+      if (of && (!found || ob > bconn || (ob == bconn && oc < bc))) {
         bconn = ob;
         bc = oc;
+        found = true;
       }
+    }
+    // the source block's score, and the drawn block's when no neighbour qualifies
+    int64_t sA = connA, sR = 0;
+    int32_t qr = -1;
+    if (!found && nU > 0) qr = a.U[h_rebalance(a.seed, level, t, (int32_t)v) % (uint64_t)nU];
+    if (a.obj) {
+      int64_t pa = 0, pr = 0;
+#pragma unroll
+      for (int r = 0; r < kSlots; r++) {
+        pa -= (int64_t)w[r] * dcode(sdist, A, c[r]);
+        if (qr >= 0) pr -= (int64_t)w[r] * dcode(sdist, qr, c[r]);
+      }
+      sA = tile_sum64(tile, pa);
+      sR = tile_sum64(tile, pr);
     }
     if (lane == 0) {
       int64_t gcut;
-      if (bconn >= 0) {
-        gcut = (int64_t)bconn - connA;
-      } else if (nU > 0) {
-        bc = a.U[h_rebalance(a.seed, level, t, (int32_t)v) % (uint64_t)nU];
-        gcut = -(int64_t)connA;
+      if (found) {
+        gcut = bconn - sA;
+      } else if (qr >= 0) {
+        bc = qr;
+        gcut = sR - sA;
       } else {
         elig[v] = 0;
         continue;
@@ -822,10 +855,11 @@ __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const 
 
 __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
                                                                 const int32_t* __restrict__ pi, RebArgs a, int32_t kc,
-                                                                int32_t* dest, uint8_t* bkt, uint8_t* elig,
-                                                                const RefineState* st) {
-  extern __shared__ int32_t tab[];
-  __shared__ int32_t sbb[32], sbc[32];
+                                                                GroupLayout gl, int32_t* dest, uint8_t* bkt,
+                                                                uint8_t* elig, const RefineState* st) {
+  extern __shared__ int32_t tab[];  // conn per PE code (and the level group sums for the J gains)
+  __shared__ int64_t sbb[32];
+  __shared__ int32_t sbc[32];
   if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
   const int64_t sigma = a.cnt[CNT_SIGMA];
   const int64_t nU = a.cnt[CNT_NU];
@@ -836,23 +870,31 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
       if (threadIdx.x == 0) elig[v] = 0;
       continue;
     }
-    for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) tab[b] = 0;
+    const int32_t total = a.obj ? gl.total : kc;
+    for (int32_t b = threadIdx.x; b < total; b += blockDim.x) tab[b] = 0;
     __syncthreads();
-    for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
-      atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
-    __syncthreads();
-    int32_t bconn = -1, bc = INT32_MAX;
+    if (a.obj) {
+      conn_build(g, v, pi, a.topo, gl, tab);
+    } else {
+      for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
+        atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
+      __syncthreads();
+    }
+    // score: conn(v, q), or -T(q) for the J gains; -1 / INT64_MIN: none
+    int64_t bconn = a.obj ? INT64_MIN : -1;
+    int32_t bc = INT32_MAX;
     for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) {
       const int32_t x = tab[b];
       if (x == 0 || b == A || a.W[b] > sigma) continue;
-      if (x > bconn || (x == bconn && b < bc)) {
-        bconn = x;
+      const int64_t sc = a.obj ? -conn_T(tab, a.topo, gl, b) : (int64_t)x;
+      if (sc > bconn || (sc == bconn && b < bc)) {
+        bconn = sc;
         bc = b;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const int32_t ob = __shfl_xor_sync(0xffffffffu, bconn, o);
+      const int64_t ob = __shfl_xor_sync(0xffffffffu, bconn, o);
       const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
       if (ob > bconn || (ob == bconn && oc < bc)) {
         bconn = ob;
@@ -870,14 +912,14 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
           bconn = sbb[w];
           bc = sbc[w];
         }
-      const int64_t connA = tab[A];
+      const int64_t sA = a.obj ? -conn_T(tab, a.topo, gl, A) : (int64_t)tab[A];
       int64_t gcut = 0;
       bool ok = true;
-      if (bconn >= 0) {
-        gcut = (int64_t)bconn - connA;
+      if (bc != INT32_MAX) {
+        gcut = bconn - sA;
       } else if (nU > 0) {
         bc = a.U[h_rebalance(a.seed, st->level, st->t, v) % (uint64_t)nU];
-        gcut = -connA;
+        gcut = (a.obj ? -conn_T(tab, a.topo, gl, bc) : 0) - sA;
       } else {
         ok = false;
       }
@@ -1415,12 +1457,15 @@ void launch_rebalance(Ctx& c, int lvl, bool prep_done = false) {
   if (!prep_done) {
     k_reb_prep<<<1, 1024, 0, c.st>>>(reb_prep_args(c), c.state); count_launch();
   }
-  RebArgs a{c.W, c.U, c.counters, c.tab, c.lmax, c.cV, c.k, c.cfg.seed};
+  RebArgs a{c.W, c.U, c.counters, c.tab, c.lmax, c.cV, c.k, c.cfg.seed, c.cfg.reb_objective, c.topo};
   k_reb_select_low<<<grid_for(c, kThreads / kSubWarp, n), kThreads, 0, c.st>>>(view(L), L.pi, a, c.dest, bucket,
                                                                                  c.elig, c.state); count_launch();
-  if (L.n_hi)
-    k_reb_select_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, (size_t)c.topo.kc * sizeof(int32_t),
-                        c.st>>>(view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, c.dest, bucket, c.elig, c.state); count_launch();
+  if (L.n_hi) {
+    const GroupLayout gl = group_layout(c.topo);
+    const size_t smem = (size_t)(c.cfg.reb_objective ? gl.total : c.topo.kc) * sizeof(int32_t);
+    k_reb_select_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, smem, c.st>>>(
+        view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state); count_launch();
+  }
   k_reb_cut<<<1, 1024, 0, c.st>>>(c.W, c.topo.kc, c.lmax, c.tab, c.bcut, c.rem, c.counters, c.state); count_launch();
   const int idbits = bits_for_n(n);
   const int bits = c.topo.code_bits + idbits;
@@ -1516,6 +1561,7 @@ struct EngineJob {
   int32_t level;
   int32_t rounds;
   LpFilter flt;
+  int32_t reb_obj;  // rebalancing gains: 0 cut, 1 Eq. 1
 };
 
 struct PlainRow {  // neighbour PEs through plain loads (the mapping changes inside the launch)
@@ -1724,19 +1770,27 @@ __device__ void eng_sort(const EngineJob& J, EngSmem& S, int32_t* dyn, int n, in
 
 // Alg. 5 destination of one vertex (thread level): edge-cut gain, lowest id
 // on ties, the random-block fallback; returns false if the vertex cannot move.
-__device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int64_t nU, int32_t t, int32_t& dst,
-                               int32_t& bucket) {
+template <bool kJ>
+__device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int64_t nU, int32_t t,
+                               const int32_t* sdist, int32_t& dst, int32_t& bucket) {
   const GraphView& g = J.g;
   const int32_t A = J.pi[v];
   const int64_t WA = J.W[A];
   if (WA <= J.lmax) return false;
   if (2 * (int64_t)J.k * g.vw[v] > 3 * ((int64_t)J.k * WA - J.cV)) return false;
   const int64_t b = g.xadj[v], e = g.xadj[v + 1];
-  int32_t connA = 0, bconn = -1, bc = INT32_MAX;
+  const PlainRow row{g.adj + b, g.adjw + b, J.pi};
+  const int deg = (int)(e - b);
+  // score: conn(v, q), or -T(q) for the J gains (kJ)
+  using Score = typename std::conditional<kJ, int64_t, int32_t>::type;
+  Score connA = 0, bconn = 0;
+  if constexpr (kJ) connA = -row_cost(row, deg, sdist, A);
+  int32_t bc = INT32_MAX;
+  bool found = false;
   for (int64_t x = b; x < e; x++) {
     const int32_t c = J.pi[g.adj[x]];
     if (c == A) {
-      connA += g.adjw[x];
+      if constexpr (!kJ) connA += g.adjw[x];
       continue;
     }
     if (J.W[c] > sigma) continue;
@@ -1747,19 +1801,26 @@ __device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int
         break;
       }
     if (seen) continue;
-    int32_t cc = 0;
-    for (int64_t y = x; y < e; y++) cc += (J.pi[g.adj[y]] == c) ? g.adjw[y] : 0;
-    if (cc > bconn || (cc == bconn && c < bc)) {
+    Score cc = 0;
+    if constexpr (kJ) {
+      cc = -row_cost(row, deg, sdist, c);
+    } else {
+      for (int64_t y = x; y < e; y++) cc += (J.pi[g.adj[y]] == c) ? g.adjw[y] : 0;
+    }
+    if (!found || cc > bconn || (cc == bconn && c < bc)) {
       bconn = cc;
       bc = c;
+      found = true;
     }
   }
   int64_t gcut;
-  if (bconn >= 0) {
+  if (found) {
     gcut = (int64_t)bconn - connA;
   } else if (nU > 0) {
     bc = J.U[h_rebalance(J.seed, J.level, t, v) % (uint64_t)nU];
-    gcut = -(int64_t)connA;
+    int64_t sr = 0;  // the drawn block is not a neighbour
+    if constexpr (kJ) sr = -row_cost(row, deg, sdist, bc);
+    gcut = sr - connA;
   } else {
     return false;
   }
@@ -1810,12 +1871,14 @@ __device__ __forceinline__ TileLane eng_stage(const EngineJob& J, const TileGrap
 // Alg. 5 destinations of the lanes in `work` (vertices of an overloaded block
 // that are not heavy) from their staged rows, four at a time by 8-lane
 // sub-warps: the neighbouring block q != A with W(q) <= sigma of largest
-// conn(v, q), lowest id on ties.  out(lane, A, best conn or -1, q, conn(v, A))
-// runs on the sub-warp's first lane.
-template <class Out>
+// score, lowest id on ties.  The score is conn(v, q) for the cut gains, or
+// -T(q) = -sum_u w D(q, P(u)) for the J gains (kJ).  out(lane, A, found, q,
+// score of A, score of q, staged codes, staged weights, degree) runs on the
+// sub-warp's first lane; the gain is the difference of the two scores.
+template <bool kJ, class Out>
 __device__ __forceinline__ void reb_tile_queue(unsigned work, const TileLane& tl, int32_t A, const int32_t* sc,
-                                               const int32_t* sw, const int64_t* W, int64_t sigma, int lane,
-                                               Out out) {
+                                               const int32_t* sw, const int64_t* W, int64_t sigma,
+                                               const int32_t* sdist, int lane, Out out) {
   const int sub = lane >> 3, sl = lane & 7;
   const int rounds = (__popc(work) + 3) / 4;
   for (int r = 0; r < rounds; r++) {
@@ -1826,41 +1889,81 @@ __device__ __forceinline__ void reb_tile_queue(unsigned work, const TileLane& tl
     const int32_t a = __shfl_sync(0xffffffffu, A, s2);
     const int32_t* c = sc + (vb - tl.E0);
     const int32_t* w = sw + (vb - tl.E0);
-    int32_t ca = 0, bconn = -1, bc = INT32_MAX;
-    if (src >= 0) {
-      for (int j = sl; j < dg; j += kSubWarp) {
-        const int32_t q = c[j];
-        if (q == a) {
-          ca += w[j];
-          continue;
-        }
-        if (W[q] > sigma) continue;
-        bool seen = false;
-        for (int l = 0; l < j; l++)
-          if (c[l] == q) {
-            seen = true;
-            break;
+    if constexpr (!kJ) {
+      int32_t ca = 0, bconn = -1, bc = INT32_MAX;
+      if (src >= 0) {
+        for (int j = sl; j < dg; j += kSubWarp) {
+          const int32_t q = c[j];
+          if (q == a) {
+            ca += w[j];
+            continue;
           }
-        if (seen) continue;
-        int32_t cc = 0;
-        for (int l = j; l < dg; l++) cc += (c[l] == q) ? w[l] : 0;
-        if (cc > bconn || (cc == bconn && q < bc)) {
-          bconn = cc;
-          bc = q;
+          if (W[q] > sigma) continue;
+          bool seen = false;
+          for (int l = 0; l < j; l++)
+            if (c[l] == q) {
+              seen = true;
+              break;
+            }
+          if (seen) continue;
+          int32_t cc = 0;
+          for (int l = j; l < dg; l++) cc += (c[l] == q) ? w[l] : 0;
+          if (cc > bconn || (cc == bconn && q < bc)) {
+            bconn = cc;
+            bc = q;
+          }
         }
       }
-    }
 #pragma unroll
-    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-      ca += __shfl_xor_sync(0xffffffffu, ca, o);
-      const int32_t oc = __shfl_xor_sync(0xffffffffu, bconn, o);
-      const int32_t oq = __shfl_xor_sync(0xffffffffu, bc, o);
-      if (oc > bconn || (oc == bconn && oq < bc)) {
-        bconn = oc;
-        bc = oq;
+      for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+        ca += __shfl_xor_sync(0xffffffffu, ca, o);
+        const int32_t oc = __shfl_xor_sync(0xffffffffu, bconn, o);
+        const int32_t oq = __shfl_xor_sync(0xffffffffu, bc, o);
+        if (oc > bconn || (oc == bconn && oq < bc)) {
+          bconn = oc;
+          bc = oq;
+        }
       }
+      if (src >= 0 && sl == 0) out(src, a, bconn >= 0, bc, (int64_t)ca, (int64_t)bconn, c, w, dg);
+    } else {
+      int64_t ca = 0, bconn = 0;
+      int32_t bc = INT32_MAX;
+      bool found = false;
+      if (src >= 0) {
+        for (int j = sl; j < dg; j += kSubWarp) {
+          const int32_t q = c[j];
+          ca -= (int64_t)w[j] * dcode(sdist, a, q);
+          if (q == a || W[q] > sigma) continue;
+          bool seen = false;
+          for (int l = 0; l < j; l++)
+            if (c[l] == q) {
+              seen = true;
+              break;
+            }
+          if (seen) continue;
+          int64_t cc = 0;
+          for (int l = 0; l < dg; l++) cc -= (int64_t)w[l] * dcode(sdist, q, c[l]);
+          if (!found || cc > bconn || (cc == bconn && q < bc)) {
+            bconn = cc;
+            bc = q;
+            found = true;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+        ca += __shfl_xor_sync(0xffffffffu, ca, o);
+        const int64_t oc = __shfl_xor_sync(0xffffffffu, bconn, o);
+        const int32_t oq = __shfl_xor_sync(0xffffffffu, bc, o);
+        const bool of = __shfl_xor_sync(0xffffffffu, found, o);
+        if (of && (!found || oc > bconn || (oc == bconn && oq < bc))) {
+          bconn = oc;
+          bc = oq;
+          found = true;
+        }
+      }
+      if (src >= 0 && sl == 0) out(src, a, found, bc, ca, bconn, c, w, dg);
     }
-    if (src >= 0 && sl == 0) out(src, a, bconn, bc, ca);
   }
 }
 
@@ -1967,7 +2070,9 @@ __device__ uint8_t* eng_resolve_local(const EngineJob& J, EngSmem& S, int32_t* a
 }
 
 // Alg. 6 on one job by the calling cluster (all its threads call it).
-template <int kTE, class Sync>
+// kVar: the job may use the refinement variants (relaxed filter, J gains in
+// rebalancing); the plain instantiation leaves their code out.
+template <int kTE, bool kVar, class Sync>
 __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int32_t* sc, int32_t* sw,
                                const EngGeom& eg, const Sync& sy) {
   const GraphView g = J.g;
@@ -2074,7 +2179,8 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
             int32_t bc;
             int64_t bt;
             if (best_target(r, (int)(t.e - t.b), p, S.sdist, bc, bt) &&
-                J.flt.admit(Tp - bt, J.flt.num > 0 ? row_own(r, (int)(t.e - t.b), p) : 0)) {
+                (kVar ? J.flt.admit(Tp - bt, J.flt.num > 0 ? row_own(r, (int)(t.e - t.b), p) : 0)
+                      : Tp - bt >= 0)) {
               J.inx[t.v] = 1;
               J.pp[t.v] = bc;
               J.gain[t.v] = Tp - bt;
@@ -2088,10 +2194,10 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
           }
         }
         const unsigned work = __ballot_sync(0xffffffffu, cand);
-        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane, J.flt.num > 0,
+        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane, kVar && J.flt.num > 0,
                         [&](int src, int64_t Gv, int32_t bc, int32_t pv, int64_t own) {
           const int64_t v = tile * kTileV + src;
-          const bool in = J.flt.admit(Gv, own);
+          const bool in = kVar ? J.flt.admit(Gv, own) : Gv >= 0;
           J.inx[v] = in ? 1 : 0;
           J.pp[v] = in ? bc : pv;
           J.gain[v] = in ? Gv : 0;
@@ -2164,7 +2270,12 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       const TileLane tl = stage_tile<kTE>(tg, tile * kTileV, lane, sc, sw, PlainGather{J.pi});
       if (cand && !tl.staged) {  // oversized tile: this lane alone, from global memory
         int32_t dst, bk;
-        const bool ok = eng_reb_select(J, (int32_t)v, sigma, nU, t, dst, bk);
+        bool ok;
+        if constexpr (kVar)
+          ok = J.reb_obj != 0 ? eng_reb_select<true>(J, (int32_t)v, sigma, nU, t, S.sdist, dst, bk)
+                              : eng_reb_select<false>(J, (int32_t)v, sigma, nU, t, S.sdist, dst, bk);
+        else
+          ok = eng_reb_select<false>(J, (int32_t)v, sigma, nU, t, S.sdist, dst, bk);
         J.elig[v] = ok ? 1 : 0;
         if (ok) {
           J.dest[v] = dst;
@@ -2174,17 +2285,20 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         cand = false;
       }
       const unsigned work = __ballot_sync(0xffffffffu, cand);
-      reb_tile_queue(work, tl, A, sc, sw, J.W, sigma, lane,
-                     [&](int src, int32_t a, int32_t bconn, int32_t bc, int32_t ca) {
+      auto reb_out = [&](int src, int32_t a, bool found, int32_t bc, int64_t sa, int64_t sb, const int32_t* rc,
+                         const int32_t* rw, int dg) {
                        const int64_t u = tile * kTileV + src;
                        int64_t gcut;
                        int32_t dst;
-                       if (bconn >= 0) {
-                         gcut = (int64_t)bconn - ca;
+                       if (found) {
+                         gcut = sb - sa;
                          dst = bc;
                        } else if (nU > 0) {
                          dst = J.U[h_rebalance(J.seed, J.level, t, u) % (uint64_t)nU];
-                         gcut = -(int64_t)ca;
+                         int64_t sr = 0;  // the drawn block is not a neighbour: conn 0, or -T(q)
+                         if (kVar && J.reb_obj)
+                           for (int l = 0; l < dg; l++) sr -= (int64_t)rw[l] * dcode(S.sdist, dst, rc[l]);
+                         gcut = sr - sa;
                        } else {
                          J.elig[u] = 0;
                          return;
@@ -2195,7 +2309,11 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
                        J.bkt[u] = (uint8_t)bk;
                        atomicAdd((unsigned long long*)&J.tab[(int64_t)a * kBuckets + bk],
                                  (unsigned long long)(int64_t)g.vw[u]);
-                     });
+                     };
+      if (kVar && J.reb_obj != 0)
+        reb_tile_queue<true>(work, tl, A, sc, sw, J.W, sigma, S.sdist, lane, reb_out);
+      else
+        reb_tile_queue<false>(work, tl, A, sc, sw, J.W, sigma, S.sdist, lane, reb_out);
       __syncwarp();
     }
     sy.sync();
@@ -2407,7 +2525,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
   for (int64_t v = gt; v < n; v += GT) J.pi[v] = J.best[v];
 }
 
-template <int kTE>
+template <int kTE, bool kVar>
 __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __restrict__ jobs, int32_t njobs,
                                                           unsigned int* queue) {
   __shared__ EngSmem S;
@@ -2428,7 +2546,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
   int32_t* sw = sc + kTE;
   if (!queue) {  // one job per cluster
     const int32_t jid = (int32_t)(blockIdx.x / csize);
-    if (jid < njobs) engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg, ClusterSync{});
+    if (jid < njobs) engine_run_job<kTE, kVar>(jobs[jid], S, eng_dyn, sc, sw, eg, ClusterSync{});
     return;
   }
   // persistent clusters: the next job from the queue (jobs in the order given)
@@ -2438,14 +2556,14 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
     const int32_t jid = *cl.map_shared_rank(&job_slot, 0);
     eng_sync();
     if (jid >= njobs) break;
-    engine_run_job<kTE>(jobs[jid], S, eng_dyn, sc, sw, eg, ClusterSync{});
+    engine_run_job<kTE, kVar>(jobs[jid], S, eng_dyn, sc, sw, eg, ClusterSync{});
   }
 }
 
 // The same engine over the whole grid (cooperative launch, one block per SM):
 // for levels too large for one cluster, whose graph-launched iterations are
 // dominated by launch gaps.
-template <int kTE>
+template <int kTE, bool kVar>
 __global__ void __launch_bounds__(kEngThreads, 1) k_engine_grid(const EngineJob* __restrict__ job, GridBar* bar) {
   __shared__ EngSmem S;
   __shared__ unsigned int bar_flag;
@@ -2460,7 +2578,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine_grid(const EngineJob*
   eg.GW = (int64_t)gridDim.x * (blockDim.x >> 5);
   int32_t* sc = eng_dyn + warp * 2 * kTE;
   int32_t* sw = sc + kTE;
-  engine_run_job<kTE>(*job, S, eng_dyn, sc, sw, eg, GridSync{bar, &bar_flag, gridDim.x});
+  engine_run_job<kTE, kVar>(*job, S, eng_dyn, sc, sw, eg, GridSync{bar, &bar_flag, gridDim.x});
 }
 
 // Self-test of the bounded grid barrier: a barrier that waits for one more
@@ -2508,6 +2626,18 @@ CtlArgs ctl_args(Ctx& c) {
 }
 }  // namespace
 
+// Raises a kernel's dynamic shared memory limit to at least `bytes`.  The
+// attribute belongs to the process, so contexts of different sizes must
+// never lower it under one another: it only grows.
+static void raise_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes at{};
+  GM_CUDA(cudaFuncGetAttributes(&at, fn));
+  if ((size_t)at.maxDynamicSharedSizeBytes < bytes)
+    GM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
 void refine_alloc(Ctx& c) {
   const size_t n = (size_t)std::max(1, c.n0);
   const size_t kc = (size_t)c.topo.kc;
@@ -2549,20 +2679,15 @@ void refine_alloc(Ctx& c) {
   GM_CUDA(cudaMemsetAsync(c.gbar, 0, sizeof(GridBar), c.st));
   c.d_stats = c.mem.make<int64_t>(4);
   const size_t smem = conn_smem(c);
-  if (smem > 48 * 1024) {
-    GM_CUDA(cudaFuncSetAttribute(k_lp_gain_high, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
+  if (smem > 48 * 1024) raise_smem((const void*)k_lp_gain_high, smem);
   static std::atomic<unsigned long long> resolve_done{0};  // one bit per device
   if (!(resolve_done.load() & (1ULL << (c.dev & 63)))) {
     GM_CUDA(cudaFuncSetAttribute(k_reb_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_sort_smem()));
     resolve_done.fetch_or(1ULL << (c.dev & 63));
   }
-  if (kc * sizeof(int32_t) > 48 * 1024) {
-    GM_CUDA(cudaFuncSetAttribute(k_reb_select_high, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kc * sizeof(int32_t))));
-    GM_CUDA(cudaFuncSetAttribute(k_block_weights, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kc * sizeof(int32_t))));
-  }
+  const size_t reb_smem = (size_t)(c.cfg.reb_objective ? group_layout(c.topo).total : kc) * sizeof(int32_t);
+  if (reb_smem > 48 * 1024) raise_smem((const void*)k_reb_select_high, reb_smem);
+  if (kc * sizeof(int32_t) > 48 * 1024) raise_smem((const void*)k_block_weights, kc * sizeof(int32_t));
 }
 
 void compute_block_weights(Ctx& c, int lvl) {
@@ -2776,7 +2901,14 @@ static int engine_cluster(Ctx& c, const Level& L) {
 }
 
 using EngineKernel = void (*)(const EngineJob*, int32_t, unsigned int*);
-static EngineKernel engine_kernel(int te) { return te == 256 ? k_engine<256> : k_engine<512>; }
+// the variants exist for 512-entry tiles only
+static EngineKernel engine_kernel(int te, bool var = false) {
+  if (var) return k_engine<512, true>;
+  return te == 256 ? k_engine<256, false> : k_engine<512, false>;
+}
+using GridKernel = void (*)(const EngineJob*, GridBar*);
+static GridKernel grid_kernel(bool var) { return var ? k_engine_grid<512, true> : k_engine_grid<512, false>; }
+
 // dynamic shared memory: the warps' staging arrays, or the two key / value
 // buffers of the single-CTA sort (used at other times)
 static size_t engine_smem(int te) {
@@ -2807,11 +2939,13 @@ static void engine_attributes() {
   GM_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (dev < 0 || dev >= 256 || done[dev]) return;
-  GM_CUDA(cudaFuncSetAttribute(k_engine_grid<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(512)));
-  for (int te : {256, 512}) {
-    GM_CUDA(cudaFuncSetAttribute(engine_kernel(te), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(te)));
-    if (cudaFuncSetAttribute(engine_kernel(te), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-      cudaGetLastError();
+  for (bool var : {false, true})
+    GM_CUDA(cudaFuncSetAttribute(grid_kernel(var), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(512)));
+  for (int v = 0; v < 3; v++) {
+    const int te = v == 0 ? 256 : 512;
+    const EngineKernel k = engine_kernel(te, v == 2);
+    GM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)engine_smem(te)));
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
   }
   done[dev] = true;
 }
@@ -2887,6 +3021,7 @@ static EngineJob engine_job(Ctx& c, int lvl, int32_t rounds) {
   j.k = c.k;
   j.sigma_gap = c.cfg.sigma_gap;
   j.flt = LpFilter{c.cfg.lp_relax_num, c.cfg.lp_relax_den};
+  j.reb_obj = c.cfg.reb_objective;
   j.level = lvl;
   j.rounds = rounds;
   return j;
@@ -2903,18 +3038,20 @@ bool engine_job_write(Ctx& c, int lvl, int32_t rounds, void* dst) {
 }
 
 void engine_launch(cudaStream_t st, const void* d_jobs, int njobs, unsigned int* queue, int C, int te,
-                   int nclusters) {
+                   int nclusters, bool var) {
   engine_attributes();
+  if (var && te != 512) throw ApiError(MAP_E_INTERNAL, "the engine's variant build uses 512-entry tiles");
   cudaLaunchAttribute attr{};
   cudaLaunchConfig_t cfg = engine_config(C, te, (unsigned)(C * nclusters), st, &attr);
-  GM_CUDA(cudaLaunchKernelEx(&cfg, engine_kernel(te), static_cast<const EngineJob*>(d_jobs), (int32_t)njobs, queue));
+  GM_CUDA(cudaLaunchKernelEx(&cfg, engine_kernel(te, var), static_cast<const EngineJob*>(d_jobs), (int32_t)njobs,
+                             queue));
   count_launch();
 }
 
 static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, int64_t* maxw, int32_t* iters) {
   *static_cast<EngineJob*>(c.h_eng_job) = engine_job(c, lvl, rounds);
   GM_CUDA(cudaMemcpyAsync(c.eng_job, c.h_eng_job, sizeof(EngineJob), cudaMemcpyHostToDevice, c.st));
-  engine_launch(c.st, c.eng_job, 1, nullptr, C, 512, 1);
+  engine_launch(c.st, c.eng_job, 1, nullptr, C, 512, 1, uses_variants(c.cfg));
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
   const RefineState h = *c.h_state;
@@ -2935,12 +3072,16 @@ static bool engine_grid_ok(Ctx& c, const Level& L) {
   if (c.eng_grid_blocks == 0) c.eng_grid_blocks = cached[c.dev & 63].load();
   if (c.eng_grid_blocks == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine_grid<512>, kEngThreads, engine_smem(512)) !=
-            cudaSuccess ||
-        per_sm < 1) {
-      cudaGetLastError();
-      per_sm = 0;
+    for (bool var : {false, true}) {  // both builds must fit the cooperative grid
+      int ps = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, grid_kernel(var), kEngThreads, engine_smem(512)) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        ps = 0;
+      }
+      per_sm = var ? std::min(per_sm, ps) : ps;
     }
+    if (per_sm < 1) per_sm = 0;
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.dev);
     c.eng_grid_blocks = (coop && per_sm > 0) ? c.num_sms * per_sm : -1;
@@ -2963,7 +3104,7 @@ static void refine_engine_grid(Ctx& c, int lvl, int32_t rounds, int64_t* J, int6
   attr.val.cooperative = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  GM_CUDA(cudaLaunchKernelEx(&cfg, k_engine_grid<512>, static_cast<const EngineJob*>(c.eng_job),
+  GM_CUDA(cudaLaunchKernelEx(&cfg, grid_kernel(uses_variants(c.cfg)), static_cast<const EngineJob*>(c.eng_job),
                              static_cast<GridBar*>(c.gbar)));
   count_launch();
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));

@@ -43,7 +43,7 @@ class MapConfig(C.Structure):
                 ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32),
                 ("grid_engine_max_n", C.c_int32), ("coarsener", C.c_int32),
                 ("match_rounds", C.c_int32), ("initial", C.c_int32), ("lp_relax_num", C.c_int32),
-                ("lp_relax_den", C.c_int32)]
+                ("lp_relax_den", C.c_int32), ("reb_objective", C.c_int32)]
 
 
 class MapStats(C.Structure):
