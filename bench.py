@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--initial", default="bfs", choices=["bfs", "hm"],
                     help="mapping of the coarsest graph: bfs: breadth-first chunks (default); hm: hierarchical "
                          "multisection (Section 4.2, initial partitioning)")
+    ap.add_argument("--lp-relax", default="0/1",
+                    help="relaxed label-propagation filter c = num/den (0/1: the paper's G >= 0 filter)")
+    ap.add_argument("--reb-objective", default="cut", choices=["cut", "j"],
+                    help="rebalancing gains: cut (the paper's) or j (Eq. 1)")
     ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1],
                     help="0: refinement / clustering loops as CUDA graphs; 1: stream launches")
     ap.add_argument("--profile-steps", type=int, default=3,
@@ -110,10 +114,18 @@ COARSENERS = {"lp": 0, "match": 1}
 INITIALS = {"bfs": 0, "hm": 1}
 
 
-def config_of(w, extra=None, coarsener="lp", initial="bfs"):
+def variant_settings(args):
+    """(lp_relax_num, lp_relax_den, reb_objective) of the command line."""
+    num, den = (int(x) for x in args.lp_relax.split("/"))
+    return num, den, 1 if args.reb_objective == "j" else 0
+
+
+def config_of(w, extra=None, coarsener="lp", initial="bfs", variants=(0, 1, 0)):
     g, t = w.graph, w.topo
     tail = "" if coarsener == "lp" else " two-hop-matching-coarsener"
     tail += "" if initial == "bfs" else " multisection-initial-mapping"
+    tail += "" if variants[0] == 0 else f" relaxed-lp-filter-{variants[0]}/{variants[1]}"
+    tail += "" if variants[2] == 0 else " j-objective-rebalancing"
     cfg = {"workload": f"rgg2d n=2^{int(np.log2(g.n))} mean-degree-12 edge-weights-1..10 "
                        f"H={':'.join(map(str, t.hier))} D={':'.join(map(str, t.dist))} eps={t.eps} full-multilevel"
                        + tail,
@@ -209,12 +221,13 @@ def kernel_hash(kernel="k_eval_tile"):
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ----------------------------------------------------------------------------
-def oracle_run(w, samples, coarsener="lp", initial="bfs"):
+def oracle_run(w, samples, coarsener="lp", initial="bfs", variants=(0, 1, 0)):
     import oracle as O
     g, t = w.graph, w.topo
     prm = O.default_params(w.seed)
     prm.coarsener = COARSENERS[coarsener]
     prm.initial = INITIALS[initial]
+    prm.lp_relax_num, prm.lp_relax_den, prm.reb_objective = variants
     times, last = [], None
     for _ in range(samples):
         t0 = time.perf_counter()
@@ -232,14 +245,15 @@ def run_reference(args, ws, rank):
         return 0
     w = workload(args.log2n)
     for _ in range(max(0, args.warmup)):
-        oracle_run(w, 1, args.coarsener, args.initial)
-    times, er, J = oracle_run(w, max(1, args.steps), args.coarsener, args.initial)
+        oracle_run(w, 1, args.coarsener, args.initial, variant_settings(args))
+    times, er, J = oracle_run(w, max(1, args.steps), args.coarsener, args.initial, variant_settings(args))
     tot = sum(times)
     val = er * len(times) / tot
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": len(times), "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": config_of(w, coarsener=args.coarsener, initial=args.initial), "J": J,
+            "data": "synthetic", "config": config_of(w, coarsener=args.coarsener, initial=args.initial,
+                                                     variants=variant_settings(args)), "J": J,
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "the full workload per step (complete multilevel run)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -270,6 +284,7 @@ def run_ours(args, ws, rank, local):
     cfg.launch_mode = args.launch_mode
     cfg.coarsener = COARSENERS[args.coarsener]
     cfg.initial = INITIALS[args.initial]
+    cfg.lp_relax_num, cfg.lp_relax_den, cfg.reb_objective = variant_settings(args)
     ctx = G.map_create(*d_in, g.n, t.hier, t.dist, t.eps, cfg, stream=stream, inputs_on_device=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     Js = []
@@ -372,7 +387,7 @@ def run_ours(args, ws, rank, local):
     G.map_destroy(ctx)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        times, er_c, Jc = oracle_run(w, args.cpu_samples, args.coarsener, args.initial)
+        times, er_c, Jc = oracle_run(w, args.cpu_samples, args.coarsener, args.initial, variant_settings(args))
         assert er_c == er and Jc == Js[0], "oracle and GPU disagree on the bench workload"
         cpu = {"value": er * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the full workload, {len(times)} complete runs (serial C oracle)",
@@ -382,7 +397,8 @@ def run_ours(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": config_of(w, {"levels": levels, "refine_rounds": [st.iters[i] for i in range(levels)],
-                                        "edge_rounds_per_step": er}, args.coarsener, args.initial),
+                                        "edge_rounds_per_step": er}, args.coarsener, args.initial,
+                                       variant_settings(args)),
                 "J": Js[0], "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(launches), "kernels": prof,
                 "phase_ms": {"coarsen": st.ms_coarsen, "initial": st.ms_initial, "refine": st.ms_refine,
