@@ -283,7 +283,8 @@ enum {
   MAP_K_SORT = 4,      /* radix-sort scatter passes */
   MAP_K_EVAL_CTL = 5,  /* J evaluation launches that only close an LP or weak step (exact change of J
                           already accumulated): the controller, no CSR pass */
-  MAP_K_COUNT = 6
+  MAP_K_MATCH = 6,     /* heavy-edge preference of the matching coarsener (one round) */
+  MAP_K_COUNT = 7
 };
 
 /* Enables (1) or disables (0) CUDA-event timing of the kernel classes above

@@ -62,7 +62,7 @@ struct ClusterState {
 
 // Kernel classes timed by the optional CUDA-event profiler.
 enum : int32_t { PK_LP_GAIN = 0, PK_LP_AFTER = 1, PK_EVAL = 2, PK_CLUSTER = 3, PK_SORT = 4, PK_EVAL_CTL = 5,
-                 PK_COUNT = 6 };
+                 PK_MATCH = 6, PK_COUNT = 7 };
 
 struct ProfRec {
   cudaEvent_t a, b;

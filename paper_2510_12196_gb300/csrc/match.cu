@@ -298,8 +298,13 @@ MatchGraph mview(const Level& L) { return MatchGraph{L.n, L.xadj, L.adj, L.adjw,
 void emit_round(Ctx& c, int lvl, cudaStream_t st) {
   const Level& L = c.lv[lvl];
   const int32_t n = L.n;
+  c.prof_level = lvl;
+  cudaEvent_t ev = c.prof_begin();
   k_match_prefer<<<mgrid(c, kMThreads / kSubWarp, n), kMThreads, 0, st>>>(mview(L), c.C, c.lmax, c.cfg.seed, lvl,
                                                                          c.req); count_launch();
+  // per vertex: xadj 8, mate 4, c(v) 4, p 4; per entry: adjacency 4, weight 4, mate(u) 4, c(u) 4 (every row
+  // read in full: an upper bound after the first round, when matched vertices skip theirs)
+  c.prof_end(ev, PK_MATCH, 20 * (int64_t)n + 16 * L.m);
   k_match_mutual<<<mgrid(c, kMThreads, n), kMThreads, 0, st>>>(n, c.req, c.C, &state_of(c)->now); count_launch();
 }
 

@@ -356,7 +356,8 @@ def map_stats(ctx) -> MapStats:
     return s
 
 
-KERNEL_CLASSES = {0: "lp_gain", 1: "lp_after", 2: "eval_J", 3: "cluster", 4: "radix_sort", 5: "eval_J_close"}
+KERNEL_CLASSES = {0: "lp_gain", 1: "lp_after", 2: "eval_J", 3: "cluster", 4: "radix_sort", 5: "eval_J_close",
+                  6: "match_prefer"}
 
 
 def map_profile_enable(ctx, enable: bool = True) -> None:
