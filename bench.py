@@ -46,15 +46,18 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per algorithmic byte of a kernel class from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the input
 # graph of the RGG 2^20 workload;
-# profiles/k_eval_tile_k_lp_gain_tile_k_cluster_tile_rgg2e20_level0.md),
+# profiles/k_eval_tile_k_lp_gain_tile_k_cluster_tile_rgg2e20_level0.md and
+# profiles/k_match_prefer_rgg2e20_level0.md),
 # valid only while the kernel's source hash matches.
 TRAFFIC = {
-    "eval_J": {"kernel": "k_eval_tile", "kernel_hash": "1a257be59f189df2", "dram_bytes": 116094720,
-               "alg_bytes": 163348488, "dram_per_alg_byte": 116094720 / 163348488},
-    "lp_gain": {"kernel": "k_lp_gain_tile", "kernel_hash": "7f557cd3d5da71f0", "dram_bytes": 119368448,
-                "alg_bytes": 178028552, "dram_per_alg_byte": 119368448 / 178028552},
-    "cluster": {"kernel": "k_cluster_tile", "kernel_hash": "bc5de036b3a742be", "dram_bytes": 130340864,
-                "alg_bytes": 167542792, "dram_per_alg_byte": 130340864 / 167542792},
+    "eval_J": {"kernel": "k_eval_tile", "kernel_hash": "28b7db6eed622687", "dram_bytes": 116894208,
+               "alg_bytes": 163348488, "dram_per_alg_byte": 116894208 / 163348488},
+    "lp_gain": {"kernel": "k_lp_gain_tile", "kernel_hash": "836479d11fdfe6e0", "dram_bytes": 119705600,
+                "alg_bytes": 178028552, "dram_per_alg_byte": 119705600 / 178028552},
+    "cluster": {"kernel": "k_cluster_tile", "kernel_hash": "959fc8c19c9378f4", "dram_bytes": 130333952,
+                "alg_bytes": 167542792, "dram_per_alg_byte": 130333952 / 167542792},
+    "match_prefer": {"kernel": "k_match_prefer", "kernel_hash": "1163769f774c5448", "dram_bytes": 121675776,
+                     "alg_bytes": 221992288, "dram_per_alg_byte": 121675776 / 221992288},
 }
 
 
@@ -94,7 +97,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--probe", action="store_true",
                     help="one map_run, then one label-propagation step and one J evaluation on the input "
-                         "graph inside the NVTX range 'probe' (for ncu captures of single launches)")
+                         "graph inside the NVTX range 'probe', the coarsening again inside 'probe_coarsen' and "
+                         "the matching coarsening inside 'probe_match' (for ncu captures of single launches)")
     return ap.parse_args()
 
 
@@ -204,11 +208,11 @@ def measured_peak():
 
 def kernel_hash(kernel="k_eval_tile"):
     """Hash of the source of one kernel: its definition (launch bounds and
-    body, from refine.cu or coarsen.cu), the row helper, the tile staging and
-    common.cuh."""
+    body, from refine.cu, coarsen.cu or match.cu), the row helper, the tile
+    staging and common.cuh."""
     import re
     csrc = os.path.join(ROOT, "paper_2510_12196_gb300", "csrc")
-    text = "".join(open(os.path.join(csrc, f)).read() for f in ("refine.cu", "coarsen.cu"))
+    text = "".join(open(os.path.join(csrc, f)).read() for f in ("refine.cu", "coarsen.cu", "match.cu"))
     h = hashlib.sha256()
     for name in (kernel, "row_cost"):
         m = re.search(r"\n[^\n]*\b" + name + r"\(.*?\n}\n", text, re.S)
@@ -433,9 +437,18 @@ def run_probe(args, local):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     G.map_destroy(ctx)
+    # the matching coarsener on the same graph (its first launches are level 0's heavy-edge rounds)
+    cfg.coarsener = 1
+    ctx = G.map_create(g.xadj, g.adj, g.adjw, g.vw, g.n, t.hier, t.dist, t.eps, cfg)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("probe_match")
+    nl = G.map_coarsen(ctx)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    G.map_destroy(ctx)
     print(json.dumps({"probe": "coarsening (range probe_coarsen); lp_step + objective on level 0 after "
-                               "map_run (range probe)", "J_map": J, "moved": moved,
-                      "J_after_step": J2, "n": g.n, "m_dir": g.m_dir}))
+                               "map_run (range probe); matching coarsening (range probe_match)", "J_map": J,
+                      "moved": moved, "J_after_step": J2, "n": g.n, "m_dir": g.m_dir, "match_levels": nl}))
     return 0
 
 

@@ -43,17 +43,44 @@ __device__ __forceinline__ uint64_t h_nbr(uint64_t seed, int32_t u) {
   return mix64(seed, (5ULL << 60) | (uint64_t)(uint32_t)u);
 }
 
-// candidate (w, c, u) of vertex v better than (bw, bc, bu)?
-__device__ __forceinline__ bool rate_better(int64_t w, int64_t c, int32_t u, int64_t bw, int64_t bc, int32_t bu,
-                                            int32_t v, uint64_t seed, int32_t level) {
-  if (u < 0) return false;
-  if (bu < 0) return true;
-  const unsigned __int128 lhs = (unsigned __int128)(uint64_t)(w * w) * (uint64_t)bc;
-  const unsigned __int128 rhs = (unsigned __int128)(uint64_t)(bw * bw) * (uint64_t)c;
-  if (lhs != rhs) return lhs > rhs;
+// Compares the exp*2 ratings ww1 / c1 and ww2 / c2 (ww = w^2) exactly:
+// ww1 c2 against ww2 c1 in 128 bits; -1, 0 or 1.
+__device__ __forceinline__ int rating_cmp(uint64_t ww1, uint64_t c1, uint64_t ww2, uint64_t c2) {
+  if (c1 == c2) return ww1 == ww2 ? 0 : (ww1 > ww2 ? 1 : -1);
+  const uint64_t lo1 = ww1 * c2, hi1 = __umul64hi(ww1, c2);
+  const uint64_t lo2 = ww2 * c1, hi2 = __umul64hi(ww2, c1);
+  if (hi1 != hi2) return hi1 > hi2 ? 1 : -1;
+  return lo1 == lo2 ? 0 : (lo1 > lo2 ? 1 : -1);
+}
+
+// A vertex's best candidate so far: rating ww / c, the neighbour u and the
+// noise hash of the edge (computed on the first tie only).
+struct Pref {
+  uint64_t ww, c, h;
+  int32_t u;
+  bool hk;
+};
+
+// Offers neighbour (ww, c, u) of v: larger rating, then smaller edge hash,
+// then smaller u.
+__device__ __forceinline__ void pref_offer(Pref& b, uint64_t ww, uint64_t c, int32_t u, int32_t v, uint64_t seed,
+                                           int32_t level) {
+  if (b.u < 0) {
+    b = Pref{ww, c, 0, u, false};
+    return;
+  }
+  const int r = rating_cmp(ww, c, b.ww, b.c);
+  if (r > 0) {
+    b = Pref{ww, c, 0, u, false};
+    return;
+  }
+  if (r < 0) return;
+  if (!b.hk) {
+    b.h = h_edge(seed, level, min(v, b.u), max(v, b.u));
+    b.hk = true;
+  }
   const uint64_t hu = h_edge(seed, level, min(v, u), max(v, u));
-  const uint64_t hb = h_edge(seed, level, min(v, bu), max(v, bu));
-  return hu < hb || (hu == hb && u < bu);
+  if (hu < b.h || (hu == b.h && u < b.u)) b = Pref{ww, c, hu, u, true};
 }
 
 __global__ void __launch_bounds__(kMThreads) k_match_prefer(MatchGraph g, const int32_t* __restrict__ mate,
@@ -68,8 +95,7 @@ __global__ void __launch_bounds__(kMThreads) k_match_prefer(MatchGraph g, const 
     const int64_t v0 = w0 + (first - wfirst);
     const bool free_v = v0 < g.n && mate[v0] < 0;
     const int32_t v = (int32_t)v0;
-    int64_t bw = 0, bc = 0;
-    int32_t bu = -1;
+    Pref b{0, 0, 0, -1, false};
     if (free_v) {
       const int64_t cv = g.vw[v];
       for (int64_t x = g.xadj[v] + sl; x < g.xadj[v + 1]; x += kSubWarp) {
@@ -77,26 +103,27 @@ __global__ void __launch_bounds__(kMThreads) k_match_prefer(MatchGraph g, const 
         if (mate[u] >= 0) continue;
         const int64_t cu = g.vw[u];
         if (cv + cu > lmax) continue;
-        const int64_t w = g.adjw[x];
-        if (rate_better(w, cu, u, bw, bc, bu, v, seed, level)) {
-          bw = w;
-          bc = cu;
-          bu = u;
-        }
+        const uint64_t w = (uint64_t)g.adjw[x];
+        pref_offer(b, w * w, (uint64_t)cu, u, v, seed, level);
       }
+      if (b.u >= 0 && !b.hk) b.h = h_edge(seed, level, min(v, b.u), max(v, b.u));
     }
+    // sub-warp reduction on (rating, hash, u), hashes known
 #pragma unroll
     for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-      const int64_t ow = __shfl_xor_sync(0xffffffffu, bw, o);
-      const int64_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
-      const int32_t ou = __shfl_xor_sync(0xffffffffu, bu, o);
-      if (rate_better(ow, oc, ou, bw, bc, bu, v, seed, level)) {
-        bw = ow;
-        bc = oc;
-        bu = ou;
+      const uint64_t oww = __shfl_xor_sync(0xffffffffu, b.ww, o);
+      const uint64_t oc = __shfl_xor_sync(0xffffffffu, b.c, o);
+      const uint64_t oh = __shfl_xor_sync(0xffffffffu, b.h, o);
+      const int32_t ou = __shfl_xor_sync(0xffffffffu, b.u, o);
+      if (ou < 0) continue;
+      bool take = b.u < 0;
+      if (!take) {
+        const int r = rating_cmp(oww, oc, b.ww, b.c);
+        take = r > 0 || (r == 0 && (oh < b.h || (oh == b.h && ou < b.u)));
       }
+      if (take) b = Pref{oww, oc, oh, ou, true};
     }
-    if (sl == 0 && v0 < g.n) pref[v] = free_v ? bu : -1;
+    if (sl == 0 && v0 < g.n) pref[v] = free_v ? b.u : -1;
   }
 }
 
