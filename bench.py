@@ -85,11 +85,11 @@ def parse():
                     help="0: refinement / clustering loops as CUDA graphs; 1: stream launches")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="steps re-run with per-kernel CUDA events after the timed region")
-    ap.add_argument("--workload", default="rgg", choices=["rgg", "batch", "serve", "hm"],
+    ap.add_argument("--workload", default="rgg", choices=["rgg", "rmat", "batch", "serve", "hm"],
                     help="rgg: the RGG 2^20 multilevel job (default); batch: 64 RGGs of 2^12..2^18 vertices, "
                          "10 fixed refinement rounds each, one persistent launch vs one job at a time; serve: "
                          "a Poisson stream of mapping requests through the server; hm: hierarchical multisection "
-                         "(GPU-HM) of the RGG 2^20 workload")
+                         "(GPU-HM) of the RGG 2^20 workload; rmat: the R-MAT scale-22 full map (4:16:8)")
     ap.add_argument("--hm-workers", type=int, default=8, help="host threads partitioning one level's subgraphs")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-pool", type=int, default=24,
@@ -109,8 +109,10 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(log2n):
+def workload(log2n, kind="rgg"):
     from paper_2510_12196_gb300 import inputs as I
+    if kind == "rmat":
+        return I.workload_rmat(22)
     return I.workload_rgg(log2n)
 
 
@@ -130,11 +132,16 @@ def config_of(w, extra=None, coarsener="lp", initial="bfs", variants=(0, 1, 0)):
     tail += "" if initial == "bfs" else " multisection-initial-mapping"
     tail += "" if variants[0] == 0 else f" relaxed-lp-filter-{variants[0]}/{variants[1]}"
     tail += "" if variants[2] == 0 else " j-objective-rebalancing"
-    cfg = {"workload": f"rgg2d n=2^{int(np.log2(g.n))} mean-degree-12 edge-weights-1..10 "
-                       f"H={':'.join(map(str, t.hier))} D={':'.join(map(str, t.dist))} eps={t.eps} full-multilevel"
-                       + tail,
-           "n": g.n, "m_undirected": g.m, "m_dir": g.m_dir, "k": t.k, "seed": w.seed,
-           "l2": "flushed between timed steps (512 MiB write); the CSR (~112 MB) is below the 129 MB L2",
+    if w.name.startswith("rmat"):
+        fam = (f"rmat scale 22 edge-factor 16 (a,b,c)=(.57,.19,.19) self-loops/duplicates removed, unit weights "
+               f"n={g.n} ")
+        l2 = "flushed between timed steps (512 MiB write); the CSR is larger than the 129 MB L2"
+    else:
+        fam = f"rgg2d n=2^{int(np.log2(g.n))} mean-degree-12 edge-weights-1..10 "
+        l2 = "flushed between timed steps (512 MiB write); the CSR (~112 MB) is below the 129 MB L2"
+    cfg = {"workload": fam + f"H={':'.join(map(str, t.hier))} D={':'.join(map(str, t.dist))} eps={t.eps} "
+                             "full-multilevel" + tail,
+           "n": g.n, "m_undirected": g.m, "m_dir": g.m_dir, "k": t.k, "seed": w.seed, "l2": l2,
            "parallelism": "replicas"}
     if extra:
         cfg.update(extra)
@@ -247,7 +254,7 @@ def oracle_run(w, samples, coarsener="lp", initial="bfs", variants=(0, 1, 0)):
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    w = workload(args.log2n)
+    w = workload(args.log2n, args.workload)
     for _ in range(max(0, args.warmup)):
         oracle_run(w, 1, args.coarsener, args.initial, variant_settings(args))
     times, er, J = oracle_run(w, max(1, args.steps), args.coarsener, args.initial, variant_settings(args))
@@ -280,7 +287,7 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    w = workload(args.log2n)
+    w = workload(args.log2n, args.workload)
     g, t = w.graph, w.topo
     stream = torch.cuda.current_stream(dev)
     d_in = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adj, g.adjw, g.vw)]
@@ -361,6 +368,23 @@ def run_ours(args, ws, rank, local):
             "avg_launch_us": 1000 * tv["ms"] / max(1, tv["launches"]),
             "all_levels_GBps": tall["bytes"] / (tall["ms"] / 1000.0) / 1e9 if tall["ms"] > 0 else 0.0}
 
+    # refinement rounds on the input graph against both per-round byte models
+    # (compulsory streams 37 m_dir + 58 n; strict CSR-twice minimum 16 m_dir + 58 n)
+    r0 = st.iters[0]
+    ms0 = st.ms_refine_level[0]
+    refine_round = None
+    if r0 > 0 and ms0 > 0:
+        us = 1000.0 * ms0 / r0
+        alg_b = 37 * g.m_dir + 58 * g.n
+        strict_b = 16 * g.m_dir + 58 * g.n
+        refine_round = {"level": 0, "rounds": int(r0), "us_per_round": us,
+                        "alg_bytes": alg_b, "alg_GBps": alg_b / us / 1e3, "alg_frac": alg_b / us / 1e3 / peak,
+                        "strict_bytes": strict_b, "strict_GBps": strict_b / us / 1e3,
+                        "strict_frac": strict_b / us / 1e3 / peak, "peak": peak,
+                        "scope": "host wall time of Alg. 6 on the input graph in the last timed step (graph "
+                                 "launches, result read-back), over its iterations: label-propagation and "
+                                 "rebalancing rounds together"}
+
     # end to end through the C ABI with host buffers (pinned), P read back
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
@@ -403,7 +427,8 @@ def run_ours(args, ws, rank, local):
                 "config": config_of(w, {"levels": levels, "refine_rounds": [st.iters[i] for i in range(levels)],
                                         "edge_rounds_per_step": er}, args.coarsener, args.initial,
                                        variant_settings(args)),
-                "J": Js[0], "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "J": Js[0], "e2e": e2e, "roofline": roof, "refine_round": refine_round, "cpu_baseline": cpu,
+                "clocks": clocks,
                 "gpu_launches": int(launches), "kernels": prof,
                 "phase_ms": {"coarsen": st.ms_coarsen, "initial": st.ms_initial, "refine": st.ms_refine,
                              "project": st.ms_project}}

@@ -122,6 +122,7 @@ typedef struct {
   double ms_coarsen, ms_initial, ms_refine, ms_project;  /* host wall time per phase */
   int64_t device_bytes;    /* device memory held by the context */
   int64_t device_bytes_peak; /* largest device memory the context has held */
+  double ms_refine_level[65]; /* host wall time of Alg. 6 on each level (map_run; ends with a synchronisation) */
 } map_stats_t;
 
 /* Fills *cfg with the defaults listed above (seed 0x5EED0000, no allocator). */

@@ -627,10 +627,12 @@ map_status map_run(map_ctx* ctx, int32_t* out_pi, int64_t* out_J) {
       t0 = now_ms();
       int32_t it = 0;
       refine(c, l, -1, &J, &mw, &it);
-      c.ms_refine += now_ms() - t0;
+      const double dt = now_ms() - t0;
+      c.ms_refine += dt;
       if (l <= 64) {
         c.iters[l] = it;
         c.Jlev[l] = J;
+        c.ms_level[l] = dt;
       }
     }
     if (out_pi) {
@@ -691,6 +693,7 @@ map_status map_stats(map_ctx* ctx, map_stats_t* out) {
       out->m_dir[l] = c.lv[l].m;
       out->J[l] = c.Jlev[l];
       out->iters[l] = c.iters[l];
+      out->ms_refine_level[l] = c.ms_level[l];
     }
     out->ms_coarsen = c.ms_coarsen;
     out->ms_initial = c.ms_initial;

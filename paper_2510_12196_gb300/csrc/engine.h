@@ -242,6 +242,7 @@ struct Ctx {
   double ms_coarsen = 0, ms_initial = 0, ms_refine = 0, ms_project = 0;
   int32_t iters[65] = {0};
   int64_t Jlev[65] = {0};
+  double ms_level[65] = {0};
 };
 
 // api.cu: error text of the last failed context-free call on this thread

@@ -50,7 +50,8 @@ class MapStats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("n", C.c_int32 * 65), ("m_dir", C.c_int64 * 65),
                 ("J", C.c_int64 * 65), ("iters", C.c_int32 * 65), ("ms_coarsen", C.c_double),
                 ("ms_initial", C.c_double), ("ms_refine", C.c_double), ("ms_project", C.c_double),
-                ("device_bytes", C.c_int64), ("device_bytes_peak", C.c_int64)]
+                ("device_bytes", C.c_int64), ("device_bytes_peak", C.c_int64),
+                ("ms_refine_level", C.c_double * 65)]
 
 
 class MapHmStats(C.Structure):
