@@ -1214,6 +1214,7 @@ void initial_map(Ctx& c) {
     hm_run(c, (int)c.lv.size() - 1, 8, &c.hm_init);
     return;
   }
+  if (L.n > kInitSmemN && initial_map_large(c)) return;
   const size_t smem = L.n <= kInitSmemN ? (size_t)3 * L.n * sizeof(int32_t) : 0;
   static std::atomic<unsigned long long> attr_done{0};  // one bit per device
   const unsigned long long bit = 1ULL << (c.dev & 63);

@@ -283,6 +283,10 @@ inline void cap_streams(Ctx& c) {
     if (!cs) GM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
 }
 
+// initial.cu: breadth-first initial mapping of a large coarsest graph over the whole GPU; false when
+// its component labelling did not settle within its round limit (the caller then runs the one-CTA kernel)
+bool initial_map_large(Ctx& c);
+
 // match.cu
 int32_t match_level(Ctx& c, int lvl);  // two-hop matching of level lvl into its M; returns n_c
 
