@@ -450,11 +450,13 @@ int32_t orc_rebalance_obj(int32_t n, const int64_t *xadj, const int32_t *adj, co
 /* ------------------------------------------------------------------------- */
 /* Alg. 6, overall refinement: label propagation while balanced, else up to */
 /* weak_max weak rebalancing steps followed by a strong one; the best        */
-/* mapping is kept.  Readings: both tests of lines 17-18 compare against the */
-/* best J before line 17 updates it; a feasible P' always replaces an         */
-/* infeasible best (and resets the patience counter, as a balance gain does  */
-/* on line 21).  rounds >= 0 runs exactly that many iterations (no early     */
-/* exit); rounds < 0 uses the patience rule.  trace_kind records 0 = label   */
+/* mapping is kept.  Readings: after a feasible move, the "better than the   */
+/* best" test and the "better than phi times the best" test both compare     */
+/* against the best J before the first of them replaces it; a feasible P'    */
+/* always replaces an infeasible best (and resets the patience counter, as   */
+/* a smaller maximum imbalance does).  rounds >= 0 runs exactly that many    */
+/* iterations (no early exit); rounds < 0 uses the patience rule.            */
+/* trace_kind records 0 = label                                              */
 /* propagation, 1 = weak, 2 = strong per iteration; trace_J / trace_maxw the */
 /* objective and maximum block weight after it.                              */
 /* ------------------------------------------------------------------------- */

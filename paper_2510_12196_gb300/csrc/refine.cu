@@ -1235,8 +1235,9 @@ __device__ __forceinline__ int64_t block_max_w(const int64_t* __restrict__ W, in
   return mx;
 }
 
-// One Alg. 6 decision (thread 0): lines 16-21 on J and the maximum block
-// weight of P', the patience test, and the kind of the next step.
+// One Alg. 6 decision (thread 0): the best-mapping and patience updates on
+// J and the maximum block weight of P' after a move, and the kind of the next
+// step.
 __device__ void control_step(RefineState* s, int64_t mx, int64_t J, const CtlArgs& a, int phase,
                              cudaGraphConditionalHandle h_loop, int use_handle) {
   if (phase == 1 && s->done) {
