@@ -267,8 +267,8 @@ int32_t orc_lp_step_relaxed(int32_t n, const int64_t *xadj, const int32_t *adj, 
 }
 
 /* ------------------------------------------------------------------------- */
-/* Alg. 5 (weak) and the strong variant, with the edge-cut loss of Section   */
-/* 4.2 ("we use the standard rebalancing that minimizes edge-cut").          */
+/* Alg. 5 (weak) and the strong variant, with the edge-cut loss that Section */
+/* 4.2 settles on (its J-based variant is objective 1 below).                */
 /* ------------------------------------------------------------------------- */
 typedef struct { int64_t a, b, c; int32_t v; } key4;
 
