@@ -22,6 +22,7 @@
 
 #include "engine.h"
 #include "tile.cuh"
+#include "mid.cuh"
 
 namespace gm {
 
@@ -44,6 +45,15 @@ inline unsigned tile_grid(Ctx& c, const void* fn, int64_t n) {
   const int64_t tiles = (n + kTileV - 1) / kTileV;
   int64_t g = (tiles + kTileWarps - 1) / kTileWarps;
   const int64_t cap = (int64_t)c.num_sms * c.resident_blocks(fn, kTileThreads, 0);
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// Grid of a mid-degree kernel (one warp per vertex of the high-degree list).
+inline unsigned mid_grid(Ctx& c, const void* fn, size_t smem, int64_t n_hi) {
+  int64_t g = (n_hi + kMidWarps - 1) / kMidWarps;
+  const int64_t cap = (int64_t)c.num_sms * c.resident_blocks(fn, kMidThreads, smem);
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (unsigned)g;
@@ -329,11 +339,14 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t t) {
   return x ^ (x >> 15);
 }
 
-__global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+// Vertices of degree > kMidDeg: `sel` lists their positions in hi[].
+__global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const int32_t* __restrict__ hi,
+                                                             const int32_t* __restrict__ sel, int32_t n_sel,
                                                              const int64_t* __restrict__ hoff, int32_t* hkey,
                                                              int32_t* hval, ClusterArgs a, uint32_t* err) {
   __shared__ Cand sb[32];
-  for (int32_t idx = blockIdx.x; idx < n_hi; idx += gridDim.x) {
+  for (int32_t j = blockIdx.x; j < n_sel; j += gridDim.x) {
+    const int32_t idx = sel[j];
     const int32_t v = hi[idx];
     const int64_t deg = g.xadj[v + 1] - g.xadj[v];
     if (!cluster_active(a, v, deg)) {
@@ -390,6 +403,115 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const 
       cluster_request(a, v, own, best.t, g.vw[v]);
     }
     __syncthreads();
+  }
+}
+
+// Vertices of degree in (kLowDeg, kMidDeg]: one warp per vertex.  Each lane
+// keeps its (at most kMidPer) entries in registers; the labels are summed in
+// the warp's open-addressing table in shared memory (at most kMidDeg + 1
+// keys in kMidSlots slots), and only the slots used are reset afterwards.
+// The rating is the one of k_cluster_high: the largest weight, then the
+// smaller tie-hash, then the smaller label, own cluster included.
+constexpr int kMidSlots = 512;
+static_assert(kMidSlots >= 2 * (kMidDeg + 1), "mid-degree table at most half full");
+
+__device__ __forceinline__ int32_t mid_insert(int32_t* K, int32_t* V, int32_t t, int32_t w) {
+  uint32_t h = slot_hash(t) & (uint32_t)(kMidSlots - 1);
+  for (int probe = 0; probe < kMidSlots; probe++) {
+    const int32_t prev = atomicCAS(&K[h], -1, t);
+    if (prev == -1 || prev == t) {
+      atomicAdd(&V[h], w);
+      return (int32_t)h;
+    }
+    h = (h + 1) & (uint32_t)(kMidSlots - 1);
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(kMidThreads) k_cluster_mid(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                             ClusterArgs a, uint32_t* err) {
+  __shared__ int32_t sk[kMidWarps][kMidSlots];
+  __shared__ int32_t sv[kMidWarps][kMidSlots];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* K = sk[warp];
+  int32_t* V = sv[warp];
+  for (int s = lane; s < kMidSlots; s += 32) {
+    K[s] = -1;
+    V[s] = 0;
+  }
+  __syncwarp();
+  for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
+    const int32_t v = hi[i];
+    const int64_t beg = g.xadj[v];
+    const int64_t deg = g.xadj[v + 1] - beg;
+    if (deg > kMidDeg) continue;
+    if (!cluster_active(a, v, deg)) {
+      if (lane == 0) a.req[v] = -1;
+      continue;
+    }
+    const int32_t own = a.C[v];
+    int32_t t[kMidPer], w[kMidPer], hs[kMidPer];
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++) {
+      const int j = lane + 32 * r;
+      t[r] = j < deg ? g.adj[beg + j] : -1;
+      w[r] = j < deg ? g.adjw[beg + j] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++) t[r] = t[r] >= 0 ? a.C[t[r]] : -1;
+    // the own cluster is a candidate even without an edge into it (weight 0)
+    const int32_t ho = lane == 0 ? mid_insert(K, V, own, 0) : -1;
+    bool lost = lane == 0 && ho < 0;
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++) {
+      hs[r] = t[r] >= 0 ? mid_insert(K, V, t[r], w[r]) : -1;
+      lost |= t[r] >= 0 && hs[r] < 0;
+    }
+    if (lost) atomicOr(err, ERR_CAPACITY);
+    __syncwarp();
+    int32_t bs = ho >= 0 ? V[ho] : -1;
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++)
+      if (hs[r] >= 0) bs = max(bs, V[hs[r]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bs = max(bs, __shfl_xor_sync(0xffffffffu, bs, o));
+    // among the labels with the best weight: the smallest (tie-hash, label)
+    uint64_t bh = ~0ULL;
+    int32_t bt = INT32_MAX;
+    auto consider = [&](int32_t slot) {
+      if (slot < 0 || V[slot] != bs) return;
+      const int32_t x = K[slot];
+      const uint64_t h = h_tie(a.seed, a.level, x);
+      if (h < bh || (h == bh && x < bt)) {
+        bh = h;
+        bt = x;
+      }
+    };
+    consider(ho);
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++) consider(hs[r]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t oh = __shfl_xor_sync(0xffffffffu, bh, o);
+      const int32_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      if (oh < bh || (oh == bh && ot < bt)) {
+        bh = oh;
+        bt = ot;
+      }
+    }
+    __syncwarp();
+    if (ho >= 0) {
+      K[ho] = -1;
+      V[ho] = 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++)
+      if (hs[r] >= 0) {
+        K[hs[r]] = -1;
+        V[hs[r]] = 0;
+      }
+    __syncwarp();
+    if (lane == 0) cluster_request(a, v, own, bt, g.vw[v]);
   }
 }
 
@@ -900,9 +1022,14 @@ void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
   k_cluster_tile<<<tile_grid(c, (const void*)k_cluster_tile, n), kTileThreads, 0, c.st>>>(view(L), a); count_launch();
   // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
   c.prof_end(ev, PK_CLUSTER, 16 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
-  if (L.n_hi)
-    k_cluster_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
-        view(L), L.hi, L.n_hi, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
+  if (L.n_hi > L.n_huge) {
+    k_cluster_mid<<<mid_grid(c, (const void*)k_cluster_mid, 0, L.n_hi), kMidThreads, 0, c.st>>>(view(L), L.hi,
+                                                                                                L.n_hi, a, c.errword);
+    count_launch();
+  }
+  if (L.n_huge)
+    k_cluster_high<<<std::max(1, std::min(L.n_huge, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
+        view(L), L.hi, L.huge, L.n_huge, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
   k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag, c.cfg.seed, lvl, c.sort.key[0],
                                                 c.sort.val[0], c.cstate); count_launch();
   // contested requests: compaction in id order, stable sort by (target,
@@ -1020,7 +1147,8 @@ int32_t cluster_level(Ctx& c, int lvl) {
   ClusterState* cs = c.cstate;
   bool graph_ran = false;
   if (c.use_graphs && !c.prof) {
-    const int64_t key[6] = {(int64_t)L.n, L.m, (int64_t)L.n_hi, L.hi_slots, wcap, (int64_t)(intptr_t)c.hkey};
+    const int64_t key[6] = {(int64_t)L.n, L.m, (int64_t)L.n_hi | ((int64_t)L.n_huge << 32), L.hi_slots, wcap,
+                            (int64_t)(intptr_t)c.hkey};
     bool same = L.cgexec != nullptr;
     for (int i = 0; i < 6 && same; i++) same = L.cg_key[i] == key[i];
     if (!same) {
@@ -1075,7 +1203,7 @@ void free_level(Ctx& c, Level& L) {
   if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
   L.cgexec = nullptr;
   for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
-                  (void*)L.hi_off, (void*)L.M})
+                  (void*)L.huge, (void*)L.hi_off, (void*)L.M})
     if (p) c.mem.put(p);
   L = Level{};
 }

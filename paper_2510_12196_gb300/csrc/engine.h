@@ -84,6 +84,8 @@ struct Level {
   int32_t n_hi = 0;
   int64_t m_hi = 0;            // CSR entries of the high-degree vertices
   int64_t max_deg = 0;         // largest degree (0 when n_hi == 0, i.e. at most kLowDeg)
+  int32_t* huge = nullptr;     // positions in hi of the vertices of degree > kMidDeg, ascending
+  int32_t n_huge = 0;
   int64_t* hi_off = nullptr;   // hash-table offsets of the high-degree vertices (n_hi + 1)
   int64_t hi_slots = 0;
   int32_t max_vw = 0;
@@ -91,6 +93,7 @@ struct Level {
   cudaGraphExec_t gexec = nullptr;
   int32_t g_rounds = -2;
   int32_t g_nhi = -1;
+  int32_t g_nhuge = -1;
   long long g_root = 0;  // kernel nodes outside the conditional bodies
   // instantiated clustering graph of this level and its key
   cudaGraphExec_t cgexec = nullptr;

@@ -7,9 +7,10 @@
 // sub-warp that keeps its (up to 32) neighbour PEs and edge weights in
 // registers; gains of every neighbouring PE are evaluated by shuffles, so the
 // per-vertex connectivity table of Section 4.2 never leaves registers.  A
-// higher-degree vertex gets a whole CTA with a dense shared-memory
-// connectivity array over the PE code space; per-level group sums of that
-// array give the gain of every candidate PE in O(levels).
+// vertex of degree 33..255 gets one warp with its own dense shared-memory
+// connectivity array over the PE code space, and a larger one a whole CTA
+// with one such array; per-level group sums of that array give the gain of
+// every candidate PE in O(levels).
 #include <atomic>
 #include <type_traits>
 #include <algorithm>
@@ -17,6 +18,7 @@
 
 #include "engine.h"
 #include "tile.cuh"
+#include "mid.cuh"
 
 namespace gm {
 
@@ -172,8 +174,39 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_eval_tile(Grap
   eval_finish(Jacc, ec);
 }
 
+// The high-degree kernels below come in two forms: one warp per vertex of
+// degree <= kMidDeg (`_mid`, over the whole list hi[] of degree > kLowDeg,
+// skipping the larger ones) and one CTA per vertex (`_high`, over the
+// positions `sel` in hi[], or all of hi[] when sel is null).
+__device__ __forceinline__ int32_t hi_vertex(const int32_t* hi, const int32_t* sel, int32_t j) {
+  return hi[sel ? sel[j] : j];
+}
+
+// J contribution of the vertices of degree in (kLowDeg, kMidDeg], one warp per vertex.
+__global__ void __launch_bounds__(kMidThreads) k_eval_mid(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                          const int32_t* __restrict__ pi, Topo topo, int64_t* Jacc,
+                                                          const RefineState* st, int phase) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  if (incremental_j(st, phase)) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
+    const int32_t v = hi[i];
+    const int64_t b = g.xadj[v], e = g.xadj[v + 1];
+    if (e - b > kMidDeg) continue;
+    const int32_t p = pi[v];
+    for (int64_t x = b + lane; x < e; x += 32) acc += (int64_t)g.adjw[x] * dcode(sdist, p, pi[g.adj[x]]);
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
+}
+
 // J contribution of the high-degree vertices (one CTA per vertex).
-__global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+__global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int32_t* __restrict__ hi,
+                                                          const int32_t* __restrict__ sel, int32_t n_sel,
                                                           const int32_t* __restrict__ pi, Topo topo, int64_t* Jacc,
                                                           const RefineState* st, int phase) {
   __shared__ int32_t sdist[32];
@@ -182,8 +215,8 @@ __global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int
   load_sdist(sdist, topo);
   __syncthreads();
   int64_t acc = 0;
-  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
-    const int32_t v = hi[i];
+  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
+    const int32_t v = hi_vertex(hi, sel, i);
     const int32_t p = pi[v];
     for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
       acc += (int64_t)g.adjw[e] * dcode(sdist, p, pi[g.adj[e]]);
@@ -413,7 +446,8 @@ __device__ __forceinline__ int64_t conn_T(const int32_t* tab, const Topo& topo, 
   return T;
 }
 
-__global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+__global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const int32_t* __restrict__ hi,
+                                                             const int32_t* __restrict__ sel, int32_t n_sel,
                                                              const int32_t* __restrict__ pi, uint8_t* lock,
                                                              int32_t* pp, int64_t* gain, uint8_t* inx, Topo topo,
                                                              GroupLayout gl, LpFilter flt, const RefineState* st) {
@@ -421,8 +455,8 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const 
   __shared__ int64_t sbt[32];
   __shared__ int32_t sbc[32];
   if (!kind_is(st, 1 << KIND_LP)) return;
-  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
-    const int32_t v = hi[i];
+  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
+    const int32_t v = hi_vertex(hi, sel, i);
     const int32_t p = pi[v];
     if (lock[v]) {
       __syncthreads();
@@ -483,6 +517,116 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const 
   }
 }
 
+// Per-warp dense connectivity table of one mid-degree vertex: each lane's
+// entries (PE codes q[r], weights w[r]; q < 0 for none) are added to conn at
+// ct[q] and, with `groups`, to the level group sums ct[off_i + (q >> s_i)]
+// (the layout of conn_build), by shared-memory atomics.  With `add` false it
+// undoes that (stores zeros at the same slots) once the table has been read.
+__device__ __forceinline__ void mid_table(int32_t* ct, const int32_t (&q)[kMidPer], const int32_t (&w)[kMidPer],
+                                          const Topo& topo, const GroupLayout& gl, bool groups, bool add) {
+#pragma unroll
+  for (int r = 0; r < kMidPer; r++) {
+    if (q[r] < 0) continue;
+    if (add) atomicAdd(&ct[q[r]], w[r]);
+    else ct[q[r]] = 0;
+    if (groups)
+      for (int i = 1; i <= topo.levels; i++) {
+        int32_t* slot = &ct[gl.off[i] + (q[r] >> topo.s[i])];
+        if (add) atomicAdd(slot, w[r]);
+        else *slot = 0;
+      }
+  }
+}
+
+// Loads a mid-degree row into registers: PE codes of the neighbours (-1 past
+// the row) and edge weights; all loads of a stage are issued before any use.
+__device__ __forceinline__ void mid_row(const GraphView& g, const int32_t* __restrict__ pi, int64_t beg, int64_t deg,
+                                        int lane, int32_t (&q)[kMidPer], int32_t (&w)[kMidPer]) {
+#pragma unroll
+  for (int r = 0; r < kMidPer; r++) {
+    const int j = lane + 32 * r;
+    q[r] = j < deg ? g.adj[beg + j] : -1;
+    w[r] = j < deg ? g.adjw[beg + j] : 0;
+  }
+#pragma unroll
+  for (int r = 0; r < kMidPer; r++) q[r] = q[r] >= 0 ? pi[q[r]] : -1;
+}
+
+// Alg. 4 step 1 for the vertices of degree in (kLowDeg, kMidDeg]: one warp
+// per vertex with its own dense table (conn and level group sums) in shared
+// memory; the candidates are the PEs of the row's entries (conn > 0), so the
+// argmin of T over them equals k_lp_gain_high's scan of the code space.
+__global__ void __launch_bounds__(kMidThreads) k_lp_gain_mid(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                             const int32_t* __restrict__ pi, uint8_t* lock,
+                                                             int32_t* pp, int64_t* gain, uint8_t* inx, Topo topo,
+                                                             GroupLayout gl, LpFilter flt, const RefineState* st) {
+  extern __shared__ int32_t mtab[];
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* ct = mtab + (int64_t)warp * gl.total;
+  for (int32_t b = lane; b < gl.total; b += 32) ct[b] = 0;
+  __syncwarp();
+  for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
+    const int32_t v = hi[i];
+    const int64_t beg = g.xadj[v];
+    const int64_t deg = g.xadj[v + 1] - beg;
+    if (deg > kMidDeg) continue;
+    const int32_t p = pi[v];
+    const bool locked = lock[v] != 0;
+    __syncwarp();  // every lane has read the lock before lane 0 clears it
+    if (locked) {
+      if (lane == 0) {
+        inx[v] = 0;
+        pp[v] = p;
+        gain[v] = 0;
+        lock[v] = 0;
+      }
+      continue;
+    }
+    int32_t q[kMidPer], w[kMidPer];
+    mid_row(g, pi, beg, deg, lane, q, w);
+    mid_table(ct, q, w, topo, gl, true, true);
+    __syncwarp();
+    int64_t bt = INT64_MAX;
+    int32_t bc = INT32_MAX;
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++) {
+      if (q[r] < 0 || q[r] == p) continue;
+      const int64_t T = conn_T(ct, topo, gl, q[r]);
+      if (T < bt || (T == bt && q[r] < bc)) {
+        bt = T;
+        bc = q[r];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ot < bt || (ot == bt && oc < bc)) {
+        bt = ot;
+        bc = oc;
+      }
+    }
+    const int64_t Tp = conn_T(ct, topo, gl, p);
+    const int64_t own = ct[p];
+    __syncwarp();
+    mid_table(ct, q, w, topo, gl, true, false);
+    __syncwarp();
+    if (lane == 0) {
+      const int64_t G = bc != INT32_MAX ? Tp - bt : 0;
+      if (bc != INT32_MAX && flt.admit(G, own)) {
+        inx[v] = 1;
+        pp[v] = bc;
+        gain[v] = G;
+      } else {
+        inx[v] = 0;
+        pp[v] = p;
+        gain[v] = 0;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Alg. 4 step 2: gain under the approximate future state given by ord
 // ---------------------------------------------------------------------------
@@ -524,7 +668,38 @@ __global__ void __launch_bounds__(kThreads) k_lp_after_low(GraphView g, const in
   }
 }
 
-__global__ void __launch_bounds__(kHiThreads) k_lp_after_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+// Alg. 4 step 2 for the vertices of degree in (kLowDeg, kMidDeg], one warp per vertex.
+__global__ void __launch_bounds__(kMidThreads) k_lp_after_mid(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                              const int32_t* __restrict__ pi,
+                                                              const int32_t* __restrict__ pp,
+                                                              const int64_t* __restrict__ gain,
+                                                              const uint8_t* __restrict__ inx, uint8_t* lock,
+                                                              Topo topo, const RefineState* st) {
+  __shared__ int32_t sdist[32];
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
+    const int32_t v = hi[i];
+    if (!inx[v]) continue;
+    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
+    if (end - beg > kMidDeg) continue;
+    const int32_t p = pi[v], q = pp[v];
+    const int64_t gv = gain[v];
+    int64_t s = 0;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      const int32_t b = future_block(g.adj[e], v, gv, pi, pp, gain, inx);
+      s += (int64_t)g.adjw[e] * (dcode(sdist, p, b) - dcode(sdist, q, b));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && s >= 0) lock[v] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kHiThreads) k_lp_after_high(GraphView g, const int32_t* __restrict__ hi,
+                                                              const int32_t* __restrict__ sel, int32_t n_sel,
                                                               const int32_t* __restrict__ pi,
                                                               const int32_t* __restrict__ pp,
                                                               const int64_t* __restrict__ gain,
@@ -535,8 +710,8 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_after_high(GraphView g, const
   if (!kind_is(st, 1 << KIND_LP)) return;
   load_sdist(sdist, topo);
   __syncthreads();
-  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
-    const int32_t v = hi[i];
+  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
+    const int32_t v = hi_vertex(hi, sel, i);
     if (!inx[v]) continue;
     const int32_t p = pi[v], q = pp[v];
     const int64_t gv = gain[v];
@@ -605,9 +780,34 @@ __global__ void __launch_bounds__(kThreads) k_delta_low(GraphView g, const int32
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
 }
 
-// movers of degree > kLowDeg: one CTA per vertex
+// movers of degree in (kLowDeg, kMidDeg]: one warp per vertex
 template <class Mv>
-__global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+__global__ void __launch_bounds__(kMidThreads) k_delta_mid(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                           const int32_t* __restrict__ pi, Mv mv, Topo topo,
+                                                           int64_t* Jacc, const RefineState* st, int kind) {
+  __shared__ int32_t sdist[32];
+  __shared__ int64_t sm[33];
+  if (st->kind != kind) return;
+  load_sdist(sdist, topo);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
+    const int32_t v = hi[i];
+    if (!mv.moved(v)) continue;
+    const int64_t b = g.xadj[v], e = g.xadj[v + 1];
+    if (e - b > kMidDeg) continue;
+    const int32_t ov = pi[v], nv = mv.target(v);
+    for (int64_t x = b + lane; x < e; x += 32) acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[x], g.adjw[x]);
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
+}
+
+// movers of larger degree: one CTA per vertex
+template <class Mv>
+__global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, const int32_t* __restrict__ hi,
+                                                           const int32_t* __restrict__ sel, int32_t n_sel,
                                                            const int32_t* __restrict__ pi, Mv mv, Topo topo,
                                                            int64_t* Jacc, const RefineState* st, int kind) {
   __shared__ int32_t sdist[32];
@@ -616,8 +816,8 @@ __global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, const in
   load_sdist(sdist, topo);
   __syncthreads();
   int64_t acc = 0;
-  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
-    const int32_t v = hi[i];
+  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
+    const int32_t v = hi_vertex(hi, sel, i);
     if (!mv.moved(v)) continue;
     const int32_t ov = pi[v], nv = mv.target(v);
     for (int64_t x = g.xadj[v] + threadIdx.x; x < g.xadj[v + 1]; x += blockDim.x)
@@ -853,7 +1053,90 @@ __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const 
   }
 }
 
-__global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+// Alg. 5 destination for the vertices of degree in (kLowDeg, kMidDeg]: one
+// warp per vertex with its own dense table in shared memory (conn per PE code,
+// plus the level group sums for the J gains); candidates are the PEs of the
+// row's entries, as in k_reb_select_high.
+__global__ void __launch_bounds__(kMidThreads) k_reb_select_mid(GraphView g, const int32_t* __restrict__ hi, int32_t n_hi,
+                                                                const int32_t* __restrict__ pi, RebArgs a, int32_t kc,
+                                                                GroupLayout gl, int32_t* dest, uint8_t* bkt,
+                                                                uint8_t* elig, const RefineState* st) {
+  extern __shared__ int32_t mtab[];
+  if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t total = a.obj ? gl.total : kc;
+  const bool groups = a.obj != 0;
+  int32_t* ct = mtab + (int64_t)warp * total;
+  for (int32_t b = lane; b < total; b += 32) ct[b] = 0;
+  __syncwarp();
+  const int64_t sigma = a.cnt[CNT_SIGMA];
+  const int64_t nU = a.cnt[CNT_NU];
+  for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
+    const int32_t v = hi[i];
+    const int64_t beg = g.xadj[v];
+    const int64_t deg = g.xadj[v + 1] - beg;
+    if (deg > kMidDeg) continue;
+    const int32_t A = pi[v];
+    if (!reb_eligible(a, A, g.vw[v])) {
+      if (lane == 0) elig[v] = 0;
+      continue;
+    }
+    int32_t q[kMidPer], w[kMidPer];
+    mid_row(g, pi, beg, deg, lane, q, w);
+    mid_table(ct, q, w, a.topo, gl, groups, true);
+    __syncwarp();
+    // score: conn(v, q), or -T(q) for the J gains; -1 / INT64_MIN: none
+    int64_t bconn = a.obj ? INT64_MIN : -1;
+    int32_t bc = INT32_MAX;
+#pragma unroll
+    for (int r = 0; r < kMidPer; r++) {
+      const int32_t b = q[r];
+      if (b < 0 || b == A || a.W[b] > sigma) continue;
+      const int64_t sc = a.obj ? -conn_T(ct, a.topo, gl, b) : (int64_t)ct[b];
+      if (sc > bconn || (sc == bconn && b < bc)) {
+        bconn = sc;
+        bc = b;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int64_t ob = __shfl_xor_sync(0xffffffffu, bconn, o);
+      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (ob > bconn || (ob == bconn && oc < bc)) {
+        bconn = ob;
+        bc = oc;
+      }
+    }
+    int64_t gcut = 0;
+    bool ok = true;
+    if (lane == 0) {
+      const int64_t sA = a.obj ? -conn_T(ct, a.topo, gl, A) : (int64_t)ct[A];
+      if (bc != INT32_MAX) {
+        gcut = bconn - sA;
+      } else if (nU > 0) {
+        bc = a.U[h_rebalance(a.seed, st->level, st->t, v) % (uint64_t)nU];
+        gcut = (a.obj ? -conn_T(ct, a.topo, gl, bc) : 0) - sA;
+      } else {
+        ok = false;
+      }
+    }
+    __syncwarp();
+    mid_table(ct, q, w, a.topo, gl, groups, false);
+    __syncwarp();
+    if (lane == 0) {
+      if (ok) {
+        const int32_t bk = loss_bucket(gcut);
+        dest[v] = bc;
+        bkt[v] = (uint8_t)bk;
+        atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
+      }
+      elig[v] = ok ? 1 : 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, const int32_t* __restrict__ hi,
+                                                                const int32_t* __restrict__ sel, int32_t n_sel,
                                                                 const int32_t* __restrict__ pi, RebArgs a, int32_t kc,
                                                                 GroupLayout gl, int32_t* dest, uint8_t* bkt,
                                                                 uint8_t* elig, const RefineState* st) {
@@ -863,8 +1146,8 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
   if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
   const int64_t sigma = a.cnt[CNT_SIGMA];
   const int64_t nU = a.cnt[CNT_NU];
-  for (int32_t i = blockIdx.x; i < n_hi; i += gridDim.x) {
-    const int32_t v = hi[i];
+  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
+    const int32_t v = hi_vertex(hi, sel, i);
     const int32_t A = pi[v];
     if (!reb_eligible(a, A, g.vw[v])) {
       if (threadIdx.x == 0) elig[v] = 0;
@@ -1391,6 +1674,21 @@ inline unsigned grid_for(const Ctx& c, int64_t items_per_block, int64_t n) {
 
 size_t conn_smem(const Ctx& c) { return (size_t)group_layout(c.topo).total * sizeof(int32_t); }
 
+// Grid of a mid-degree kernel (one warp per vertex of the high-degree list).
+inline unsigned mid_grid(Ctx& c, const void* fn, size_t smem, int64_t n_hi) {
+  int64_t g = (n_hi + kMidWarps - 1) / kMidWarps;
+  const int64_t cap = (int64_t)c.num_sms * c.resident_blocks(fn, kMidThreads, smem);
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// The dense per-warp tables of the mid-degree LP gain and rebalancing kernels
+// fit in shared memory (else the CTA-per-vertex kernels take every vertex of
+// degree > kLowDeg).
+inline bool mid_tables(const Ctx& c) { return group_layout(c.topo).total <= kMidTableMax; }
+inline size_t mid_table_smem(int32_t words) { return (size_t)kMidWarps * words * sizeof(int32_t); }
+
 // J of the current mapping of a level; with `ec`, the last block of the
 // low-degree pass also takes the Alg. 6 decision (the high-degree pass runs
 // first so that J is complete then).
@@ -1399,9 +1697,13 @@ size_t conn_smem(const Ctx& c) { return (size_t)group_layout(c.topo).total * siz
 void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr, bool full = true) {
   Level& L = c.lv[lvl];
   c.prof_level = lvl;
-  if (L.n_hi)
-    k_eval_high<<<std::min(L.n_hi, c.num_sms * 8), kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc,
-                                                                         ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
+  if (L.n_hi > L.n_huge) {
+    k_eval_mid<<<mid_grid(c, (const void*)k_eval_mid, 0, L.n_hi), kMidThreads, 0, c.st>>>(
+        view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc, ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
+  }
+  if (L.n_huge)
+    k_eval_high<<<std::min(L.n_huge, c.num_sms * 8), kHiThreads, 0, c.st>>>(
+        view(L), L.hi, L.huge, L.n_huge, L.pi, c.topo, c.Jacc, ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
   cudaEvent_t ev = c.prof_begin();
   const EvalCtl none{nullptr, nullptr, nullptr, CtlArgs{}, 0, 0, 0};
   k_eval_tile<<<tile_grid(c, (const void*)k_eval_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc,
@@ -1416,15 +1718,24 @@ void launch_delta(Ctx& c, int lvl, Mv mv, int kind) {
   Level& L = c.lv[lvl];
   k_delta_low<Mv><<<grid_for(c, kThreads / kSubWarp, L.n), kThreads, 0, c.st>>>(view(L), L.pi, mv, c.topo, c.Jacc,
                                                                                  c.state, kind); count_launch();
-  if (L.n_hi)
-    k_delta_high<Mv><<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
+  if (L.n_hi > L.n_huge) {
+    k_delta_mid<Mv><<<mid_grid(c, (const void*)k_delta_mid<Mv>, 0, L.n_hi), kMidThreads, 0, c.st>>>(
         view(L), L.hi, L.n_hi, L.pi, mv, c.topo, c.Jacc, c.state, kind); count_launch();
+  }
+  if (L.n_huge)
+    k_delta_high<Mv><<<std::max(1, std::min(L.n_huge, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
+        view(L), L.hi, L.huge, L.n_huge, L.pi, mv, c.topo, c.Jacc, c.state, kind); count_launch();
 }
 
 void launch_lp(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
   const unsigned gl = grid_for(c, kThreads / kSubWarp, L.n);
-  const unsigned gh = std::max(1, std::min(L.n_hi, c.num_sms * 8));
+  const bool mid_tab = mid_tables(c);
+  const GroupLayout glay = group_layout(c.topo);
+  // vertices of degree > kLowDeg left to the CTA-per-vertex kernels
+  const int32_t* gsel = mid_tab ? L.huge : nullptr;
+  const int32_t ng = mid_tab ? L.n_huge : L.n_hi;
+  const unsigned gh = std::max(1, std::min(L.n_huge, c.num_sms * 8));
   c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
   const LpFilter flt{c.cfg.lp_relax_num, c.cfg.lp_relax_den};
@@ -1432,16 +1743,25 @@ void launch_lp(Ctx& c, int lvl) {
                                                                 flt, c.state); count_launch();
   // per vertex: xadj 8, P 4, lock 1, X 1, P' 4, g 8; per entry: adjacency 4, weight 4, gathered P(u) 4
   c.prof_end(ev, PK_LP_GAIN, 26 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
-  if (L.n_hi)
-    k_lp_gain_high<<<gh, kHiThreads, conn_smem(c), c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.lock, c.pp, c.gain, c.inx,
-                                                          c.topo, group_layout(c.topo), flt, c.state); count_launch();
+  if (mid_tab && L.n_hi > L.n_huge) {
+    const size_t sm = mid_table_smem(glay.total);
+    k_lp_gain_mid<<<mid_grid(c, (const void*)k_lp_gain_mid, sm, L.n_hi), kMidThreads, sm, c.st>>>(
+        view(L), L.hi, L.n_hi, L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state); count_launch();
+  }
+  if (ng)
+    k_lp_gain_high<<<std::max(1, std::min(ng, c.num_sms * 8)), kHiThreads, conn_smem(c), c.st>>>(
+        view(L), L.hi, gsel, ng, L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state); count_launch();
   ev = c.prof_begin();
   k_lp_after_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.pp, c.gain, c.inx, c.lock, c.topo, c.state); count_launch();
   // the X flag of every vertex (the work on X itself is data dependent)
   c.prof_end(ev, PK_LP_AFTER, (int64_t)(L.n - L.n_hi));
-  if (L.n_hi)
-    k_lp_after_high<<<gh, kHiThreads, 0, c.st>>>(view(L), L.hi, L.n_hi, L.pi, c.pp, c.gain, c.inx, c.lock, c.topo,
-                                                 c.state); count_launch();
+  if (L.n_hi > L.n_huge) {
+    k_lp_after_mid<<<mid_grid(c, (const void*)k_lp_after_mid, 0, L.n_hi), kMidThreads, 0, c.st>>>(
+        view(L), L.hi, L.n_hi, L.pi, c.pp, c.gain, c.inx, c.lock, c.topo, c.state); count_launch();
+  }
+  if (L.n_huge)
+    k_lp_after_high<<<gh, kHiThreads, 0, c.st>>>(view(L), L.hi, L.huge, L.n_huge, L.pi, c.pp, c.gain, c.inx, c.lock,
+                                                 c.topo, c.state); count_launch();
   launch_delta(c, lvl, LpMoves{c.lock, c.pp}, KIND_LP);
   k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.state); count_launch();
 }
@@ -1463,9 +1783,20 @@ void launch_rebalance(Ctx& c, int lvl, bool prep_done = false) {
                                                                                  c.elig, c.state); count_launch();
   if (L.n_hi) {
     const GroupLayout gl = group_layout(c.topo);
-    const size_t smem = (size_t)(c.cfg.reb_objective ? gl.total : c.topo.kc) * sizeof(int32_t);
-    k_reb_select_high<<<std::max(1, std::min(L.n_hi, c.num_sms * 8)), kHiThreads, smem, c.st>>>(
-        view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state); count_launch();
+    const int32_t words = c.cfg.reb_objective ? gl.total : c.topo.kc;
+    const size_t smem = (size_t)words * sizeof(int32_t);
+    const bool mid_tab = mid_tables(c);
+    if (mid_tab && L.n_hi > L.n_huge) {
+      const size_t sm = mid_table_smem(words);
+      k_reb_select_mid<<<mid_grid(c, (const void*)k_reb_select_mid, sm, L.n_hi), kMidThreads, sm, c.st>>>(
+          view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state); count_launch();
+    }
+    const int32_t ng = mid_tab ? L.n_huge : L.n_hi;
+    if (ng) {
+      k_reb_select_high<<<std::max(1, std::min(ng, c.num_sms * 8)), kHiThreads, smem, c.st>>>(
+          view(L), L.hi, mid_tab ? L.huge : nullptr, ng, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state);
+      count_launch();
+    }
   }
   k_reb_cut<<<1, 1024, 0, c.st>>>(c.W, c.topo.kc, c.lmax, c.tab, c.bcut, c.rem, c.counters, c.state); count_launch();
   const int idbits = bits_for_n(n);
@@ -2790,6 +3121,7 @@ void drop_graph(Level& L) {
   L.gexec = nullptr;
   L.g_rounds = -2;
   L.g_nhi = -1;
+  L.g_nhuge = -1;
 }
 
 // Captures one level's whole Alg. 6 run as a graph: initial J / weights, then
@@ -2873,12 +3205,14 @@ static void build_refine_graph(Ctx& c, int lvl, int32_t rounds) {
   }
   L.g_rounds = rounds;
   L.g_nhi = L.n_hi;
+  L.g_nhuge = L.n_huge;
   L.g_root = root;
 }
 
 static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
   Level& L = c.lv[lvl];
-  if (!L.gexec || L.g_rounds != rounds || L.g_nhi != L.n_hi) build_refine_graph(c, lvl, rounds);
+  if (!L.gexec || L.g_rounds != rounds || L.g_nhi != L.n_hi || L.g_nhuge != L.n_huge)
+    build_refine_graph(c, lvl, rounds);
   GM_CUDA(cudaGraphLaunch(L.gexec, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
@@ -3163,14 +3497,24 @@ void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t*
 
 // high-degree vertex list of a level (ascending ids)
 namespace {
+// Degree classes counted by one scan: the low 32 bits count the vertices of
+// degree > kLowDeg, the high 32 bits those of degree > kMidDeg (a subset).
 struct LoadHigh {
   const int64_t* xadj;
-  __device__ int64_t operator()(int64_t v) const { return (xadj[v + 1] - xadj[v] > kLowDeg) ? 1 : 0; }
+  __device__ int64_t operator()(int64_t v) const {
+    const int64_t d = xadj[v + 1] - xadj[v];
+    return (d > kLowDeg ? 1 : 0) + (d > kMidDeg ? (1LL << 32) : 0);
+  }
 };
+// hi[] gets every vertex of degree > kLowDeg; huge[] the positions in hi[] of
+// those of degree > kMidDeg
 struct StoreHigh {
   int32_t* out;
+  int32_t* huge;
   __device__ void operator()(int64_t v, int64_t e, int64_t x) const {
-    if (x) out[e] = (int32_t)v;
+    const int32_t pos = (int32_t)(e & 0xffffffffLL);
+    if (x & 1) out[pos] = (int32_t)v;
+    if (x >> 32) huge[e >> 32] = pos;
   }
 };
 
@@ -3203,7 +3547,8 @@ __global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const
 void classify_degrees(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
   if (!L.hi) L.hi = c.mem.make<int32_t>((size_t)std::max(1, L.n));
-  scan(LoadHigh{L.xadj}, StoreHigh{L.hi}, L.n, nullptr, c.scan, c.st);
+  if (!L.huge) L.huge = c.mem.make<int32_t>((size_t)std::max(1, L.n));
+  scan(LoadHigh{L.xadj}, StoreHigh{L.hi, L.huge}, L.n, nullptr, c.scan, c.st);
   unsigned long long* st = reinterpret_cast<unsigned long long*>(c.d_stats);
   GM_CUDA(cudaMemsetAsync(st, 0, 3 * sizeof(int64_t), c.st));
   const int64_t blocks = std::min<int64_t>(((int64_t)L.n + 255) / 256, (int64_t)c.num_sms * 8);
@@ -3213,7 +3558,8 @@ void classify_degrees(Ctx& c, int lvl) {
                           cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_small + 1, st, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
-  L.n_hi = (int32_t)c.h_small[0];
+  L.n_hi = (int32_t)(c.h_small[0] & 0xffffffffLL);
+  L.n_huge = (int32_t)(c.h_small[0] >> 32);
   L.m_hi = c.h_small[1];
   L.max_deg = c.h_small[2];
   L.max_vw = (int32_t)c.h_small[3];
