@@ -727,6 +727,8 @@ __global__ void k_coarse_vw(int32_t n, const int32_t* __restrict__ M, const int3
 // each lane finds the row of its entry among the 32 row starts.  A first walk
 // counts the warp's valid entries, the block reserves one range for its eight
 // warps with a single atomic, and a second walk (gathers now cached) writes.
+// Rows of degree > kMidDeg are jumped over (k_contract_keys_big takes them),
+// so that no warp walks a hub's row alone while the rest of its block waits.
 __device__ __forceinline__ int contract_owner(int64_t x, int64_t b, int last) {
   // largest lane L <= last with row start(L) <= x (starts are non-decreasing)
   int lo = 0;
@@ -739,6 +741,19 @@ __device__ __forceinline__ int contract_owner(int64_t x, int64_t b, int last) {
   return lo;
 }
 
+// First entry at or after x0 that lies outside the rows of the lanes in
+// `big` (E1 if none; warp-uniform, as x0 is).  The row holding x0 < E1 ends
+// after x0, so every step advances.
+__device__ __forceinline__ int64_t contract_skip(int64_t x0, int64_t E1, int64_t b, int64_t e, int last,
+                                                 unsigned big) {
+  while (big && x0 < E1) {
+    const int o = contract_owner(x0, b, last);
+    if (!((big >> o) & 1u)) break;
+    x0 = __shfl_sync(0xffffffffu, e, o);
+  }
+  return x0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_contract_keys(GraphView g, const int32_t* __restrict__ M, int bits,
                                                             uint64_t* key, int32_t* val, int64_t* valid) {
   constexpr int kWarps = kThreads / 32;
@@ -749,25 +764,28 @@ __global__ void __launch_bounds__(kThreads) k_contract_keys(GraphView g, const i
   const int64_t ntiles = ((int64_t)g.n + 31) / 32;
   for (int64_t bt = blockIdx.x; bt * kWarps < ntiles; bt += gridDim.x) {
     const int64_t tile = bt * kWarps + warp;
-    int64_t E0 = 0, E1 = 0, b = 0;
+    int64_t E0 = 0, E1 = 0, b = 0, e = 0;
     int32_t mv = 0;
     int last = 0;
+    unsigned big = 0;
     if (tile < ntiles) {  // warp-uniform
       const int64_t v = tile * 32 + lane;
       last = (int)min((int64_t)31, (int64_t)g.n - 1 - tile * 32);
       const bool vv = v < g.n;
       b = vv ? g.xadj[v] : 0;
-      const int64_t e = vv ? g.xadj[v + 1] : 0;
+      e = vv ? g.xadj[v + 1] : 0;
       mv = vv ? M[v] : 0;
       E0 = __shfl_sync(0xffffffffu, b, 0);
       E1 = __shfl_sync(0xffffffffu, e, last);
+      big = __ballot_sync(0xffffffffu, e - b > kMidDeg);
     }
     unsigned long long cnt = 0;
-    for (int64_t x0 = E0; x0 < E1; x0 += 32) {
+    for (int64_t x0 = contract_skip(E0, E1, b, e, last, big); x0 < E1;
+         x0 = contract_skip(x0 + 32, E1, b, e, last, big)) {
       const int64_t x = x0 + lane;
       const int o = contract_owner(x, b, last);
       const int32_t mo = __shfl_sync(0xffffffffu, mv, o);
-      const bool ok = x < E1 && M[g.adj[x]] != mo;
+      const bool ok = x < E1 && !((big >> o) & 1u) && M[g.adj[x]] != mo;
       cnt += __popc(__ballot_sync(0xffffffffu, ok));
     }
     if (lane == 0) wcnt[warp] = cnt;
@@ -783,11 +801,12 @@ __global__ void __launch_bounds__(kThreads) k_contract_keys(GraphView g, const i
     }
     __syncthreads();
     unsigned long long pos = bbase + wcnt[warp];
-    for (int64_t x0 = E0; x0 < E1; x0 += 32) {
+    for (int64_t x0 = contract_skip(E0, E1, b, e, last, big); x0 < E1;
+         x0 = contract_skip(x0 + 32, E1, b, e, last, big)) {
       const int64_t x = x0 + lane;
       const int o = contract_owner(x, b, last);
       const int32_t mo = __shfl_sync(0xffffffffu, mv, o);
-      const int32_t mu = x < E1 ? M[g.adj[x]] : mo;
+      const int32_t mu = (x < E1 && !((big >> o) & 1u)) ? M[g.adj[x]] : mo;
       const bool ok = mu != mo;
       const unsigned bal = __ballot_sync(0xffffffffu, ok);
       if (ok) {
@@ -825,6 +844,44 @@ struct LoadValid32 {
   const int64_t* d_valid;
   __device__ int64_t operator()(int64_t i) const { return i < *d_valid ? val[i] : 0; }
 };
+
+// Keys of the rows of degree > kMidDeg (one CTA per row; `sel` lists their
+// positions in hi[]): the block counts its row's valid entries, reserves one
+// range with a single atomic, and its warps fill it through a shared cursor.
+__global__ void __launch_bounds__(kThreads) k_contract_keys_big(GraphView g, const int32_t* __restrict__ hi,
+                                                                const int32_t* __restrict__ sel, int32_t n_sel,
+                                                                const int32_t* __restrict__ M, int bits, uint64_t* key,
+                                                                int32_t* val, int64_t* valid) {
+  __shared__ unsigned long long sm[33];
+  __shared__ unsigned long long cursor;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int32_t j = blockIdx.x; j < n_sel; j += gridDim.x) {
+    const int32_t v = hi[sel[j]];
+    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
+    const int32_t mo = M[v];
+    unsigned long long cnt = 0;
+    for (int64_t x = beg + threadIdx.x; x < end; x += blockDim.x) cnt += M[g.adj[x]] != mo ? 1 : 0;
+    cnt = block_sum(cnt, sm);
+    if (threadIdx.x == 0) cursor = cnt ? atomicAdd((unsigned long long*)valid, cnt) : 0ULL;
+    __syncthreads();
+    for (int64_t x0 = beg; x0 < end; x0 += blockDim.x) {  // same trip count in every warp
+      const int64_t x = x0 + threadIdx.x;
+      const int32_t mu = x < end ? M[g.adj[x]] : mo;
+      const bool ok = mu != mo;
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      unsigned long long p = 0;
+      if (lane == 0 && bal) p = atomicAdd(&cursor, (unsigned long long)__popc(bal));
+      p = __shfl_sync(0xffffffffu, p, 0);
+      if (ok) {
+        const unsigned long long q = p + __popc(bal & lt);
+        key[q] = ((uint64_t)(uint32_t)mo << bits) | (uint32_t)mu;
+        val[q] = g.adjw[x];
+      }
+    }
+    __syncthreads();  // cursor and sm are rewritten for the next row
+  }
+}
 
 __global__ void k_copy_i64(const int64_t* src, int64_t* dst) { *dst = *src; }
 
@@ -1236,6 +1293,10 @@ void contract_level(Ctx& c, int lvl, int32_t nc, Level* spare) {
   if (m > 0) {
     k_contract_keys<<<grid_for(c, kThreads, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
                                                                        c.sort.val[0], d_valid); count_launch();
+    if (F.n_huge) {
+      k_contract_keys_big<<<std::max(1, std::min(F.n_huge, c.num_sms * 8)), kThreads, 0, c.st>>>(
+          view(F), F.hi, F.huge, F.n_huge, F.M, bits, c.sort.key[0], c.sort.val[0], d_valid); count_launch();
+    }
     c.prof_level = lvl;
     cudaEvent_t ev = c.prof_begin();
     const int cur = radix_sort_pairs(c.sort, m, d_valid, 2 * bits, c.st);  // the valid keys only
