@@ -52,10 +52,10 @@ L2_FLUSH_BYTES = 512 << 20
 TRAFFIC = {
     "eval_J": {"kernel": "k_eval_tile", "kernel_hash": "28b7db6eed622687", "dram_bytes": 116894208,
                "alg_bytes": 163348488, "dram_per_alg_byte": 116894208 / 163348488},
-    "lp_gain": {"kernel": "k_lp_gain_tile", "kernel_hash": "836479d11fdfe6e0", "dram_bytes": 119705600,
-                "alg_bytes": 178028552, "dram_per_alg_byte": 119705600 / 178028552},
-    "cluster": {"kernel": "k_cluster_tile", "kernel_hash": "959fc8c19c9378f4", "dram_bytes": 130333952,
-                "alg_bytes": 167542792, "dram_per_alg_byte": 130333952 / 167542792},
+    "lp_gain": {"kernel": "k_lp_gain_tile", "kernel_hash": "dd953e2062dfbd76", "dram_bytes": 120026880,
+                "alg_bytes": 178028552, "dram_per_alg_byte": 120026880 / 178028552},
+    "cluster": {"kernel": "k_cluster_tile", "kernel_hash": "02325cea3dd5d1e9", "dram_bytes": 129711872,
+                "alg_bytes": 167542792, "dram_per_alg_byte": 129711872 / 167542792},
     "match_prefer": {"kernel": "k_match_prefer", "kernel_hash": "1163769f774c5448", "dram_bytes": 121675776,
                      "alg_bytes": 221992288, "dram_per_alg_byte": 121675776 / 221992288},
 }

@@ -199,52 +199,14 @@ struct GatherLabel {
   __device__ __forceinline__ int32_t operator()(int32_t u) const { return C[u]; }
 };
 
-// Best cluster of one vertex: the largest edge weight into a neighbouring
-// cluster or its own, ties to the smaller tie-hash, then the smaller label.
-// Hashes are computed only when scores tie (same total order).
-template <class Row>
-__device__ __forceinline__ int32_t best_cluster(const Row& r, int deg, int32_t own, const ClusterArgs& a) {
-  int32_t so = 0;
-  for (int j = 0; j < deg; j++) so += (r.code(j) == own) ? r.weight(j) : 0;
-  int32_t bt = own, bs = so;
-  uint64_t bh = 0;
-  bool bh_known = false;
-  for (int j = 0; j < deg; j++) {
-    const int32_t t = r.code(j);
-    if (t == own) continue;
-    bool seen = false;
-    for (int l = 0; l < j; l++)
-      if (r.code(l) == t) {
-        seen = true;
-        break;
-      }
-    if (seen) continue;
-    int32_t sc = 0;
-    for (int l = j; l < deg; l++) sc += (r.code(l) == t) ? r.weight(l) : 0;
-    if (sc < bs) continue;
-    if (sc > bs) {
-      bs = sc;
-      bt = t;
-      bh_known = false;
-      continue;
-    }
-    if (!bh_known) {
-      bh = h_tie(a.seed, a.level, bt);
-      bh_known = true;
-    }
-    const uint64_t h = h_tie(a.seed, a.level, t);
-    if (h < bh || (h == bh && t < bt)) {
-      bt = t;
-      bh = h;
-    }
-  }
-  return bt;
-}
-
 // Clustering ratings for the low-degree vertices.  Warp tiles stage the
 // neighbour labels; the active vertices of a tile are then rated four at a
 // time by 8-lane sub-warps reading the staged entries from shared memory.
-__global__ void __launch_bounds__(kTileThreads) k_cluster_tile(GraphView g, ClusterArgs a) {
+// In a tile whose CSR range exceeds the staging capacity (a high-degree row
+// inside, as on power-law graphs) each sub-warp first copies its vertex's
+// row (at most kLowDeg entries) into its quarter of the warp's buffer.
+static_assert(kTileE / 4 >= kLowDeg, "a sub-warp's quarter of the staging buffer holds one low-degree row");
+__global__ void __launch_bounds__(kTileThreads, 9) k_cluster_tile(GraphView g, ClusterArgs a) {
   __shared__ int32_t sc[kTileWarps][kTileE];
   __shared__ int32_t sw[kTileWarps][kTileE];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -258,19 +220,25 @@ __global__ void __launch_bounds__(kTileThreads) k_cluster_tile(GraphView g, Clus
     const bool active = low && cluster_active(a, (int32_t)t.v, deg);
     int32_t own = active ? a.C[t.v] : -1;
     if (low && !active) a.req[t.v] = -1;
-    if (active && !t.staged) {  // oversized tile: this lane alone, from global memory
-      const int32_t best =
-          best_cluster(GlobalRow<GatherLabel>{g.adj + t.b, g.adjw + t.b, GatherLabel{a.C}}, deg, own, a);
-      cluster_request(a, (int32_t)t.v, own, best, g.vw[t.v]);
-    }
-    const unsigned work = __ballot_sync(0xffffffffu, active && t.staged);
+    const unsigned work = __ballot_sync(0xffffffffu, active);
     const int rounds = (__popc(work) + 3) / 4;
     for (int r = 0; r < rounds; r++) {
       const int src = tile_worker(work, r, sub);
       const int s2 = src < 0 ? 0 : src;
-      const int off = (int)(__shfl_sync(0xffffffffu, t.b, s2) - t.E0);
-      const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - __shfl_sync(0xffffffffu, t.b, s2));
+      const int64_t vb = __shfl_sync(0xffffffffu, t.b, s2);
+      int off = (int)(vb - t.E0);
+      const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - vb);
       const int32_t ow = __shfl_sync(0xffffffffu, own, s2);
+      if (!t.staged) {  // warp-uniform
+        off = sub * (kTileE / 4);
+        __syncwarp();  // the previous round has read this quarter
+        if (src >= 0)
+          for (int j = sl; j < dg; j += kSubWarp) {
+            sc[warp][off + j] = a.C[g.adj[vb + j]];
+            sw[warp][off + j] = g.adjw[vb + j];
+          }
+        __syncwarp();
+      }
       const int32_t* c = sc[warp] + off;
       const int32_t* w = sw[warp] + off;
       // best (score, tie-hash, label) over this lane's candidates; the hash

@@ -280,10 +280,28 @@ __device__ __forceinline__ int64_t row_own(const Row& r, int deg, int32_t p) {
 // q != p of its vertex from the staged entries and keeps the minimum (lowest
 // code on ties).  out(lane, G = T(p) - T(q*), q*, p, conn(v, p)) runs on the
 // sub-warp's first lane; conn(v, p) is summed only when `own` is set (else 0).
-template <class Out>
+// In a tile whose range was not staged (it exceeds the buffer capacity
+// `cap`), each sub-warp first copies its vertex's row into its quarter of
+// the buffer with `load`.
+struct RowLoader {
+  const int32_t* __restrict__ adj;
+  const int32_t* __restrict__ adjw;
+  const int32_t* __restrict__ pi;
+  __device__ __forceinline__ void operator()(int64_t vb, int dg, int sl, int32_t* c, int32_t* w) const {
+    for (int j = sl; j < dg; j += kSubWarp) {
+      c[j] = pi[adj[vb + j]];
+      w[j] = adjw[vb + j];
+    }
+  }
+};
+struct NoRowLoader {  // callers that never queue a vertex of an unstaged tile
+  __device__ __forceinline__ void operator()(int64_t, int, int, int32_t*, int32_t*) const {}
+};
+
+template <class Load, class Out>
 __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t, int32_t p, int64_t Tp,
-                                                const int32_t* sc, const int32_t* sw, const int32_t* sdist, int lane,
-                                                bool own, Out out) {
+                                                int32_t* sc, int32_t* sw, int cap, Load load,
+                                                const int32_t* sdist, int lane, bool own, Out out) {
   const int sub = lane >> 3, sl = lane & 7;
   const int rounds = (__popc(work) + 3) / 4;
   for (int r = 0; r < rounds; r++) {
@@ -293,8 +311,15 @@ __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t
     const int dg = (int)(__shfl_sync(0xffffffffu, t.e, s2) - vb);
     const int32_t pv = __shfl_sync(0xffffffffu, p, s2);
     const int64_t tp = __shfl_sync(0xffffffffu, Tp, s2);
-    const int32_t* c = sc + (vb - t.E0);
-    const int32_t* w = sw + (vb - t.E0);
+    int64_t off = vb - t.E0;
+    if (!t.staged) {  // warp-uniform
+      off = sub * (cap / 4);
+      __syncwarp();  // the previous round has read this quarter
+      if (src >= 0) load(vb, dg, sl, sc + off, sw + off);
+      __syncwarp();
+    }
+    const int32_t* c = sc + off;
+    const int32_t* w = sw + off;
     int64_t bt = INT64_MAX, ow = 0;
     int32_t bc = INT32_MAX;
     if (src >= 0) {
@@ -329,7 +354,8 @@ __device__ __forceinline__ void tile_gain_queue(unsigned work, const TileLane& t
 // Alg. 4 step 1 for the low-degree vertices.  Warp tiles stage the
 // neighbour PEs; each lane checks its own vertex (T(P(v)), any neighbour
 // outside P(v)); the vertices with candidates are then evaluated four at a
-// time by 8-lane sub-warps from the staged entries.
+// time by 8-lane sub-warps from the staged entries (in a tile too long to
+// stage, from the row each sub-warp copies into shared memory first).
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_lp_gain_tile(GraphView g, const int32_t* __restrict__ pi,
                                                                uint8_t* __restrict__ lock, int32_t* __restrict__ pp,
                                                                int64_t* __restrict__ gain, uint8_t* __restrict__ inx,
@@ -362,29 +388,22 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_lp_gain_tile(G
         for (int j = 0; j < deg; j++) cand |= c[j] != p;
         if (cand)
           for (int j = 0; j < deg; j++) Tp += (int64_t)w[j] * dcode(sdist, p, c[j]);
-      } else {  // oversized tile: this lane alone, from global memory
-        const GlobalRow<GatherPi> r{g.adj + t.b, g.adjw + t.b, GatherPi{pi}};
-        int32_t bc;
-        int64_t bt;
-        if (best_target(r, deg, p, sdist, bc, bt)) {
-          const int64_t G = row_cost(r, deg, sdist, p) - bt;
-          if (flt.admit(G, flt.num > 0 ? row_own(r, deg, p) : 0)) {
-            inx[t.v] = 1;
-            pp[t.v] = bc;
-            gain[t.v] = G;
-            goto done_lane;
-          }
+      } else {  // oversized tile: the lane check from global memory; a sub-warp stages the row below
+        for (int j = 0; j < deg; j++) {
+          const int32_t q = pi[g.adj[t.b + j]];
+          cand |= q != p;
+          Tp += (int64_t)g.adjw[t.b + j] * dcode(sdist, p, q);
         }
       }
-      if (!cand) {  // locked, no neighbour outside P(v), or the global path found no move
+      if (!cand) {  // locked, or no neighbour outside P(v)
         inx[t.v] = 0;
         pp[t.v] = p;
         gain[t.v] = 0;
       }
     }
-  done_lane:
     const unsigned work = __ballot_sync(0xffffffffu, cand);
-    tile_gain_queue(work, t, p, Tp, sc[warp], sw[warp], sdist, lane, flt.num > 0,
+    tile_gain_queue(work, t, p, Tp, sc[warp], sw[warp], kTileE, RowLoader{g.adj, g.adjw, pi}, sdist, lane,
+                    flt.num > 0,
                     [&](int src, int64_t G, int32_t bc, int32_t pv, int64_t own) {
                       const int64_t v = tile * kTileV + src;
                       const bool in = flt.admit(G, own);
@@ -2526,7 +2545,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
           }
         }
         const unsigned work = __ballot_sync(0xffffffffu, cand);
-        tile_gain_queue(work, t, p, Tp, sc, sw, S.sdist, lane, kVar && J.flt.num > 0,
+        tile_gain_queue(work, t, p, Tp, sc, sw, kTE, NoRowLoader{}, S.sdist, lane, kVar && J.flt.num > 0,
                         [&](int src, int64_t Gv, int32_t bc, int32_t pv, int64_t own) {
           const int64_t v = tile * kTileV + src;
           const bool in = kVar ? J.flt.admit(Gv, own) : Gv >= 0;
