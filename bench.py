@@ -102,6 +102,24 @@ def parse():
     return ap.parse_args()
 
 
+def slowest_rank(pg, x, dev):
+    """The largest x over the ranks (a job's time is its slowest rank's);
+    x itself without a process group.  dev: where the reduction tensor lives
+    (the rank's GPU under NCCL, "cpu" under gloo)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ranks, seconds):
+    """Whole-job throughput: the units every rank processed (each rank maps
+    its own replica of the workload: weak scaling) over the job's time."""
+    return units_per_rank * ranks / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -343,11 +361,8 @@ def run_ours(args, ws, rank, local):
                     "level0": {"launches": l0, "ms": ms0, "bytes": by0}}
     G.map_profile_enable(ctx, 0)
     assert len(set(Js)) == 1, f"nondeterministic J: {set(Js)}"
-    if pg:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = er * args.steps * ws / (total_ms / 1000.0)
+    total_ms = slowest_rank(pg, total_ms, dev)
+    value = job_throughput(er * args.steps, ws, total_ms / 1000.0)
 
     # roofline of the dominant profiled kernel (largest device time over the
     # job), on its launches over the input graph (the coarser levels fit in L2)
@@ -404,11 +419,8 @@ def run_ours(args, ws, rank, local):
             if i > 0:  # first one warms the allocator
                 e2e_t.append(dt)
         e2e_s = sum(e2e_t)
-        if pg:
-            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = {"value": er * len(e2e_t) * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": hbytes,
+        e2e_s = slowest_rank(pg, e2e_s, dev)
+        e2e = {"value": job_throughput(er * len(e2e_t), ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": hbytes,
                "d2h_bytes_per_step": g.n * 4, "ms_per_step": 1000 * e2e_s / len(e2e_t),
                "path": "map_create(host CSR) + map_run + download of P + map_destroy"}
 
