@@ -383,6 +383,8 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const 
 constexpr int kMidSlots = 512;
 static_assert(kMidSlots >= 2 * (kMidDeg + 1), "mid-degree table at most half full");
 
+// Adds weight w to label t's slot (claimed on first use); returns the slot,
+// or -1 if the table were full (excluded by the bound above).
 __device__ __forceinline__ int32_t mid_insert(int32_t* K, int32_t* V, int32_t t, int32_t w) {
   uint32_t h = slot_hash(t) & (uint32_t)(kMidSlots - 1);
   for (int probe = 0; probe < kMidSlots; probe++) {
