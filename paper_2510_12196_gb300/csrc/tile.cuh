@@ -9,7 +9,9 @@
 // xadj -> adjacency -> gather is paid once per tile instead of once per
 // vertex, which is what bounds a per-vertex pass over a low-degree graph.
 // Tiles whose range exceeds kTileE entries (a high-degree vertex inside, or a
-// dense tile) are processed by each lane straight from global memory.
+// dense tile) are not staged: the J pass reads each lane's row straight from
+// global memory, and the clustering and gain kernels let each 8-lane sub-warp
+// copy the row of the vertex it serves into its quarter of the buffer.
 #pragma once
 
 #include "common.cuh"
