@@ -294,6 +294,39 @@ def erdos_renyi(n: int, p: float, seed: int, wmax: int = 1, vwmax: int = 1) -> G
     return csr_from_pairs(n, u, v, w, vw=vw, name=f"er_n{n}")
 
 
+DEGREE_MIX_EXACT = (32, 33, 255, 256)
+
+
+def degree_mix(seed: int = 21) -> Graph:
+    """A 1,600-vertex graph whose degrees straddle the bounds of the
+    per-vertex paths (32 and 255): a dense core 0..399 (degrees ~160), six
+    hubs 400..405 (degrees 300..700), a sparse rest 406..1595 (degrees ~7)
+    and the vertices 1596..1599 of degree exactly 32, 33, 255 and 256.  Edge
+    weights 1..9, vertex weights 1..4 (numpy's PCG64 stream of `seed`)."""
+    rng = np.random.default_rng(seed)
+    n, core, hub0, sparse0, exact0 = 1600, 400, 400, 406, 1596
+    pairs = []
+    iu, ju = np.triu_indices(core, 1)
+    keep = rng.random(iu.size) < 0.4
+    pairs.append(np.stack([iu[keep], ju[keep]], 1))
+    for h in range(hub0, sparse0):
+        deg = int(rng.integers(300, 701))
+        nb = rng.choice(np.setdiff1d(np.arange(exact0), [h]), size=deg, replace=False)
+        pairs.append(np.stack([np.full(deg, h), nb], 1))
+    ns = exact0 - sparse0
+    iu, ju = np.triu_indices(ns, 1)
+    keep = rng.random(iu.size) < 0.004
+    pairs.append(np.stack([iu[keep] + sparse0, ju[keep] + sparse0], 1))
+    for i, deg in enumerate(DEGREE_MIX_EXACT):
+        nb = rng.choice(np.arange(sparse0, exact0), size=deg, replace=False)
+        pairs.append(np.stack([np.full(deg, exact0 + i), nb], 1))
+    p = np.concatenate(pairs).astype(np.int64)
+    p = np.unique(np.stack([p.min(1), p.max(1)], 1), axis=0)
+    w = rng.integers(1, 10, size=len(p))
+    vw = rng.integers(1, 5, size=n).astype(np.int32)
+    return csr_from_pairs(n, p[:, 0], p[:, 1], w, vw, name="degree_mix")
+
+
 def random_mapping(n: int, k: int, seed: int) -> np.ndarray:
     """Pi_0(v) = SplitMix64(seed ^ v) mod k."""
     return (splitmix64(seed, np.arange(n, dtype=np.uint64)) % _U64(k)).astype(np.int32)

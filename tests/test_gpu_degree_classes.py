@@ -20,40 +20,17 @@ pytestmark = pytest.mark.gpu
 # gains and rebalancing destinations take the CTA-per-vertex kernels for all
 # vertices of degree > 32.
 TOPOS = [((4, 8), (1, 10)), ((4, 8, 6), (1, 10, 100)), ((2, 4, 16, 8), (1, 10, 100, 1000))]
-EXACT = (32, 33, 255, 256)
+EXACT = I.DEGREE_MIX_EXACT
 
 
 def degree_mix_graph(seed=21):
-    """1,600 vertices: a dense core 0..399 (degrees ~160), six hubs 400..405
-    (degrees 300..700), a sparse rest 406..1595 (degrees ~7) and the vertices
-    1596..1599 of degree exactly 32, 33, 255 and 256.  Edge weights 1..9,
-    vertex weights 1..4."""
-    rng = np.random.default_rng(seed)
-    n, core, hub0, sparse0, exact0 = 1600, 400, 400, 406, 1596
-    pairs = []
-    iu, ju = np.triu_indices(core, 1)
-    keep = rng.random(iu.size) < 0.4
-    pairs.append(np.stack([iu[keep], ju[keep]], 1))
-    for h in range(hub0, sparse0):
-        deg = int(rng.integers(300, 701))
-        nb = rng.choice(np.setdiff1d(np.arange(exact0), [h]), size=deg, replace=False)
-        pairs.append(np.stack([np.full(deg, h), nb], 1))
-    ns = exact0 - sparse0
-    iu, ju = np.triu_indices(ns, 1)
-    keep = rng.random(iu.size) < 0.004
-    pairs.append(np.stack([iu[keep] + sparse0, ju[keep] + sparse0], 1))
-    for i, deg in enumerate(EXACT):
-        nb = rng.choice(np.arange(sparse0, exact0), size=deg, replace=False)
-        pairs.append(np.stack([np.full(deg, exact0 + i), nb], 1))
-    p = np.concatenate(pairs).astype(np.int64)
-    p = np.unique(np.stack([p.min(1), p.max(1)], 1), axis=0)
-    w = rng.integers(1, 10, size=len(p))
-    vw = rng.integers(1, 5, size=n).astype(np.int32)
-    g = I.csr_from_pairs(n, p[:, 0], p[:, 1], w, vw, name="degree_mix")
+    """The seeded degree-mix graph (inputs.degree_mix), with its degree
+    classes checked."""
+    g = I.degree_mix(seed)
     deg = np.diff(g.xadj)
-    assert list(deg[exact0:]) == list(EXACT)
-    assert (deg[:core] > 32).all() and (deg[:core] <= 255).all()
-    assert (deg[hub0:sparse0] > 255).all()
+    assert list(deg[1596:]) == list(EXACT)
+    assert (deg[:400] > 32).all() and (deg[:400] <= 255).all()
+    assert (deg[400:406] > 255).all()
     return g
 
 
