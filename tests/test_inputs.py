@@ -56,3 +56,14 @@ def test_batch_and_serve_recipes():
         assert w.topo.k in (32, 256, 512, 1024)
     t = I.poisson_arrivals(1000, 0.005, 1)
     assert np.all(np.diff(t) > 0) and 0.004 < t[-1] / 1000 < 0.006
+
+
+def test_degree_mix_classes():
+    g = I.degree_mix()
+    deg = np.diff(g.xadj)
+    assert g.n == 1600 and list(deg[1596:]) == list(I.DEGREE_MIX_EXACT)
+    assert ((deg[:400] > 32) & (deg[:400] <= 255)).all() and (deg[400:406] > 255).all()
+    assert (deg[406:1596] <= 32).all()
+    I.check_graph(g)
+    h = I.degree_mix()
+    assert np.array_equal(g.adj, h.adj) and np.array_equal(g.adjw, h.adjw) and np.array_equal(g.vw, h.vw)
