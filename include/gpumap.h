@@ -285,7 +285,14 @@ enum {
   MAP_K_EVAL_CTL = 5,  /* J evaluation launches that only close an LP or weak step (exact change of J
                           already accumulated): the controller, no CSR pass */
   MAP_K_MATCH = 6,     /* heavy-edge preference of the matching coarsener (one round) */
-  MAP_K_COUNT = 7
+  MAP_K_CLUSTER_MID = 7,   /* clustering rating, one warp per vertex of degree 33..255 (bytes: the
+                              active half of the rows, expected) */
+  MAP_K_CLUSTER_HIGH = 8,  /* clustering rating, one CTA per vertex of degree > 255 (same model) */
+  MAP_K_EVAL_MID = 9,      /* objective J, degree 33..255 */
+  MAP_K_EVAL_HIGH = 10,    /* objective J, degree > 255 */
+  MAP_K_LP_GAIN_MID = 11,  /* Alg. 4 step 1, degree 33..255 */
+  MAP_K_LP_GAIN_HIGH = 12, /* Alg. 4 step 1, the vertices the per-warp tables do not take */
+  MAP_K_COUNT = 13
 };
 
 /* Enables (1) or disables (0) CUDA-event timing of the kernel classes above
@@ -325,7 +332,11 @@ GPUMAP_API long long map_launch_count(void);
  * contents; each call clears what must start at zero.  Calls that overlap on
  * the GPU (several streams or host threads) race on it: serialise them.  The
  * first call on a device looks up the array's address with that device
- * current; make that first call before any stream capture on the device. */
+ * current and keeps it for the process; make that first call before any
+ * stream capture on the device.  A cudaDeviceReset invalidates the kept
+ * address: do not call this entry point on a device after resetting it.
+ * Rows are clamped to [0, xadj[n]): a malformed xadj cannot make it read
+ * outside adjncy / adjwgt. */
 GPUMAP_API map_status map_objective_noalloc(const int64_t* xadj, const int32_t* adjncy, const int32_t* adjwgt,
                                             const int32_t* vwgt, int32_t n, const int32_t* pi, const int32_t* hier,
                                             const int32_t* dist, int32_t levels, int64_t* out, void* stream);
@@ -360,8 +371,9 @@ GPUMAP_API map_status map_selftest_barrier_timeout(void* stream);
  * Limits: all contexts on the current device, no context twice, and no
  * vertex of degree > 128 on the refined level (MAP_E_INVALID: refine such a
  * job with map_refine).  The batch keeps pointers into the contexts: destroy
- * it before them, and do not run map_coarsen on a job (which may move its
- * level buffers) while the batch exists.  The launch is asynchronous on the
+ * it before them.  map_coarsen and map_run (which coarsens) may move a job's
+ * level buffers: after either ran on a job, map_batch_launch returns
+ * MAP_E_STATE; build a new batch.  The launch is asynchronous on the
  * stream given at creation; it waits for the jobs' pending work on their own
  * streams, and their later work waits for it.  map_batch_results
  * synchronises and returns the jobs' best J, maximum block weight and

@@ -66,6 +66,7 @@ struct map_batch {
   cudaStream_t st = nullptr;       // caller's stream
   cudaStream_t cap = nullptr;      // private stream for capture and tuning
   std::vector<int32_t> order;      // job indices, largest first
+  std::vector<uint64_t> gens;      // each job's level generation when the batch was built
   void* d_jobs = nullptr;          // engine job descriptors in `order`
   RefineState** d_states = nullptr;
   JobResult* d_res = nullptr;
@@ -313,6 +314,8 @@ map_status map_batch_create(map_ctx* const* jobs, int32_t njobs, const map_batch
       B.sum_m += L.m;
     }
     for (int32_t i = 0; i < njobs; i++) hs[i] = B.jobs[i]->c.state;
+    B.gens.resize(njobs);
+    for (int32_t i = 0; i < njobs; i++) B.gens[i] = B.jobs[i]->c.level_gen;
     GM_CUDA(cudaMalloc(&B.d_jobs, jb * njobs));
     GM_CUDA(cudaMalloc(&B.d_states, sizeof(RefineState*) * njobs));
     GM_CUDA(cudaMalloc(&B.d_res, sizeof(JobResult) * njobs));
@@ -335,6 +338,13 @@ map_status map_batch_create(map_ctx* const* jobs, int32_t njobs, const map_batch
 map_status map_batch_launch(map_batch* b) {
   return batch_guard(b, [&](map_batch& B) {
     GM_CUDA(cudaSetDevice(B.dev));
+    // the job descriptors and the captured graph hold pointers into the
+    // jobs' level buffers, which a coarsening (map_coarsen, map_run) may move
+    for (size_t i = 0; i < B.jobs.size(); i++)
+      if (B.jobs[i]->c.level_gen != B.gens[i])
+        throw ApiError(MAP_E_STATE, "job " + std::to_string(i) +
+                                        " was coarsened after the batch was built (map_coarsen or map_run); "
+                                        "destroy the batch and build a new one");
     if (!B.tuned) {
       // the jobs' mappings must be in place before tuning or capture
       wait_for_jobs(B, B.cap);

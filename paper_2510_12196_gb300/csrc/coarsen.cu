@@ -1049,14 +1049,23 @@ void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
   k_cluster_tile<<<tile_grid(c, (const void*)k_cluster_tile, n), kTileThreads, 0, c.st>>>(view(L), a); count_launch();
   // per vertex: xadj 8, C 4, request 4 (+ hash, no memory); per entry: adjacency 4, weight 4, C(u) 4
   c.prof_end(ev, PK_CLUSTER, 16 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
+  // mid / high classes: xadj (8) of every listed vertex; the active half (the
+  // sub-round's hash bit) also reads C and writes its request (8) and
+  // streams its row (12 per entry): expected bytes
   if (L.n_hi > L.n_huge) {
+    const int64_t nv = L.n_hi - L.n_huge, me = L.m_hi - L.m_huge;
+    ev = c.prof_begin();
     k_cluster_mid<<<mid_grid(c, (const void*)k_cluster_mid, 0, L.n_hi), kMidThreads, 0, c.st>>>(view(L), L.hi,
                                                                                                 L.n_hi, a, c.errword);
     count_launch();
+    c.prof_end(ev, PK_CLUSTER_MID, 8 * nv + (8 * nv + 12 * me) / 2);
   }
-  if (L.n_huge)
+  if (L.n_huge) {
+    ev = c.prof_begin();
     k_cluster_high<<<std::max(1, std::min(L.n_huge, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
         view(L), L.hi, L.huge, L.n_huge, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
+    c.prof_end(ev, PK_CLUSTER_HIGH, 8 * (int64_t)L.n_huge + (8 * (int64_t)L.n_huge + 12 * L.m_huge) / 2);
+  }
   k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag, c.cfg.seed, lvl, c.sort.key[0],
                                                 c.sort.val[0], c.cstate); count_launch();
   // contested requests: compaction in id order, stable sort by (target,
@@ -1380,6 +1389,7 @@ void validate_graph(Ctx& c) {
 }
 
 int32_t coarsen(Ctx& c) {
+  c.level_gen++;
   // previous coarse levels are kept as spares: repeated runs on the same
   // graph rebuild identical levels into the same buffers
   std::vector<Level> spare(c.lv.begin() + 1, c.lv.end());

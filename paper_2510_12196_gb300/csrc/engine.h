@@ -62,7 +62,8 @@ struct ClusterState {
 
 // Kernel classes timed by the optional CUDA-event profiler.
 enum : int32_t { PK_LP_GAIN = 0, PK_LP_AFTER = 1, PK_EVAL = 2, PK_CLUSTER = 3, PK_SORT = 4, PK_EVAL_CTL = 5,
-                 PK_MATCH = 6, PK_COUNT = 7 };
+                 PK_MATCH = 6, PK_CLUSTER_MID = 7, PK_CLUSTER_HIGH = 8, PK_EVAL_MID = 9, PK_EVAL_HIGH = 10,
+                 PK_LP_GAIN_MID = 11, PK_LP_GAIN_HIGH = 12, PK_COUNT = 13 };
 
 struct ProfRec {
   cudaEvent_t a, b;
@@ -83,6 +84,7 @@ struct Level {
   int32_t* hi = nullptr;       // vertices of degree > kLowDeg, ascending
   int32_t n_hi = 0;
   int64_t m_hi = 0;            // CSR entries of the high-degree vertices
+  int64_t m_huge = 0;          // CSR entries of the vertices of degree > kMidDeg
   int64_t max_deg = 0;         // largest degree (0 when n_hi == 0, i.e. at most kLowDeg)
   int32_t* huge = nullptr;     // positions in hi of the vertices of degree > kMidDeg, ascending
   int32_t n_huge = 0;
@@ -190,6 +192,9 @@ struct Ctx {
   int64_t* trace_maxw = nullptr;
   int32_t trace_cap = 4096;
   int32_t last_iters = 0;
+  // bumped by every coarsening (coarse level buffers may be freed and
+  // reallocated): a batch built on this context refuses to launch after it
+  uint64_t level_gen = 0;
 
   // sort / scan scratch
   SortBufs sort;

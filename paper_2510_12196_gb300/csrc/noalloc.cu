@@ -17,8 +17,10 @@
 // uses it.  Calls whose work overlaps on the GPU (different streams, or
 // several host threads) race on the array and give wrong results: serialise
 // them.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress, with that device current) and caches it; make that
-// first call before any stream capture on the device.
+// (cudaGetSymbolAddress, with that device current) and keeps it for the
+// process; make that first call before any stream capture on the device.
+// A cudaDeviceReset invalidates the kept address: the entry point must not be
+// used on a device after it was reset.
 #include <mutex>
 #include <string>
 
@@ -63,7 +65,9 @@ __global__ void k_na_clear(NoAllocScratch* s, Topo t, Hier h) {
 }
 
 // J and block weights: one 8-lane sub-warp per vertex (any degree); mapping
-// entries or neighbours outside their range are skipped.
+// entries or neighbours outside their range are skipped, and every row is
+// clamped to [0, xadj[n]) so that a malformed xadj cannot read outside the
+// adjacency arrays.
 __global__ void __launch_bounds__(kNaThreads) k_na_eval(int32_t n, const int64_t* __restrict__ xadj,
                                                         const int32_t* __restrict__ adj,
                                                         const int32_t* __restrict__ adjw,
@@ -77,12 +81,14 @@ __global__ void __launch_bounds__(kNaThreads) k_na_eval(int32_t n, const int64_t
   const int lane = tile.thread_rank();
   const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
   int64_t acc = 0;
+  const int64_t m = xadj[n];
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < n; v += nsw) {
     const int32_t pv = pi[v];
     if (pv < 0 || pv >= t.k) continue;
     const int32_t cv = s->code[pv];
     if (lane == 0) atomicAdd((unsigned long long*)&s->W[cv], (unsigned long long)(int64_t)vw[v]);
-    for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += kSubWarp) {
+    const int64_t eb = max(xadj[v], (int64_t)0), ee = min(xadj[v + 1], m);
+    for (int64_t e = eb + lane; e < ee; e += kSubWarp) {
       const int32_t u = adj[e];
       if (u < 0 || u >= n) continue;
       const int32_t pu = pi[u];

@@ -1716,14 +1716,21 @@ inline size_t mid_table_smem(int32_t words) { return (size_t)kMidWarps * words *
 void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr, bool full = true) {
   Level& L = c.lv[lvl];
   c.prof_level = lvl;
+  cudaEvent_t ev = nullptr;
+  // per vertex xadj (8) + P(v) (4), per entry adjacency (4) + weight (4) + P(u) (4), per degree class
   if (L.n_hi > L.n_huge) {
+    if (full) ev = c.prof_begin();
     k_eval_mid<<<mid_grid(c, (const void*)k_eval_mid, 0, L.n_hi), kMidThreads, 0, c.st>>>(
         view(L), L.hi, L.n_hi, L.pi, c.topo, c.Jacc, ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
+    if (full) c.prof_end(ev, PK_EVAL_MID, 12 * (int64_t)(L.n_hi - L.n_huge) + 12 * (L.m_hi - L.m_huge));
   }
-  if (L.n_huge)
+  if (L.n_huge) {
+    if (full) ev = c.prof_begin();
     k_eval_high<<<std::min(L.n_huge, c.num_sms * 8), kHiThreads, 0, c.st>>>(
         view(L), L.hi, L.huge, L.n_huge, L.pi, c.topo, c.Jacc, ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
-  cudaEvent_t ev = c.prof_begin();
+    if (full) c.prof_end(ev, PK_EVAL_HIGH, 12 * (int64_t)L.n_huge + 12 * L.m_huge);
+  }
+  ev = c.prof_begin();
   const EvalCtl none{nullptr, nullptr, nullptr, CtlArgs{}, 0, 0, 0};
   k_eval_tile<<<tile_grid(c, (const void*)k_eval_tile, L.n), kTileThreads, 0, c.st>>>(view(L), L.pi, c.topo, c.Jacc,
                                                                                        ec ? *ec : none); count_launch();
@@ -1764,12 +1771,18 @@ void launch_lp(Ctx& c, int lvl) {
   c.prof_end(ev, PK_LP_GAIN, 26 * (int64_t)(L.n - L.n_hi) + 12 * (L.m - L.m_hi));
   if (mid_tab && L.n_hi > L.n_huge) {
     const size_t sm = mid_table_smem(glay.total);
+    ev = c.prof_begin();
     k_lp_gain_mid<<<mid_grid(c, (const void*)k_lp_gain_mid, sm, L.n_hi), kMidThreads, sm, c.st>>>(
         view(L), L.hi, L.n_hi, L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state); count_launch();
+    c.prof_end(ev, PK_LP_GAIN_MID, 26 * (int64_t)(L.n_hi - L.n_huge) + 12 * (L.m_hi - L.m_huge));
   }
-  if (ng)
+  if (ng) {
+    const int64_t me = mid_tab ? L.m_huge : L.m_hi;
+    ev = c.prof_begin();
     k_lp_gain_high<<<std::max(1, std::min(ng, c.num_sms * 8)), kHiThreads, conn_smem(c), c.st>>>(
         view(L), L.hi, gsel, ng, L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state); count_launch();
+    c.prof_end(ev, PK_LP_GAIN_HIGH, 26 * (int64_t)ng + 12 * me);
+  }
   ev = c.prof_begin();
   k_lp_after_low<<<gl, kThreads, 0, c.st>>>(view(L), L.pi, c.pp, c.gain, c.inx, c.lock, c.topo, c.state); count_launch();
   // the X flag of every vertex (the work on X itself is data dependent)
@@ -3539,10 +3552,11 @@ struct StoreHigh {
 
 __global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const int32_t* __restrict__ vw,
                               unsigned long long* out) {
-  unsigned long long mhi = 0, mdeg = 0, mvw = 0;
+  unsigned long long mhi = 0, mdeg = 0, mvw = 0, mhuge = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long d = (unsigned long long)(xadj[v + 1] - xadj[v]);
     if (d > (unsigned long long)kLowDeg) mhi += d;
+    if (d > (unsigned long long)kMidDeg) mhuge += d;
     mdeg = d > mdeg ? d : mdeg;
     const unsigned long long w = (unsigned long long)vw[v];
     mvw = w > mvw ? w : mvw;
@@ -3550,6 +3564,7 @@ __global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mhi += __shfl_xor_sync(0xffffffffu, mhi, o);
+    mhuge += __shfl_xor_sync(0xffffffffu, mhuge, o);
     const unsigned long long y = __shfl_xor_sync(0xffffffffu, mdeg, o);
     mdeg = y > mdeg ? y : mdeg;
     const unsigned long long z = __shfl_xor_sync(0xffffffffu, mvw, o);
@@ -3559,6 +3574,7 @@ __global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const
     if (mhi) atomicAdd(&out[0], mhi);
     if (mdeg) atomicMax(&out[1], mdeg);
     if (mvw) atomicMax(&out[2], mvw);
+    if (mhuge) atomicAdd(&out[3], mhuge);
   }
 }
 }  // namespace
@@ -3569,19 +3585,20 @@ void classify_degrees(Ctx& c, int lvl) {
   if (!L.huge) L.huge = c.mem.make<int32_t>((size_t)std::max(1, L.n));
   scan(LoadHigh{L.xadj}, StoreHigh{L.hi, L.huge}, L.n, nullptr, c.scan, c.st);
   unsigned long long* st = reinterpret_cast<unsigned long long*>(c.d_stats);
-  GM_CUDA(cudaMemsetAsync(st, 0, 3 * sizeof(int64_t), c.st));
+  GM_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), c.st));
   const int64_t blocks = std::min<int64_t>(((int64_t)L.n + 255) / 256, (int64_t)c.num_sms * 8);
   k_level_stats<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, c.st>>>(L.n, L.xadj, L.vw, st); count_launch();
-  // count of high-degree vertices and the three statistics, one synchronisation
+  // count of high-degree vertices and the four statistics, one synchronisation
   GM_CUDA(cudaMemcpyAsync(c.h_small, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
                           cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaMemcpyAsync(c.h_small + 1, st, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(c.h_small + 1, st, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
   L.n_hi = (int32_t)(c.h_small[0] & 0xffffffffLL);
   L.n_huge = (int32_t)(c.h_small[0] >> 32);
   L.m_hi = c.h_small[1];
   L.max_deg = c.h_small[2];
   L.max_vw = (int32_t)c.h_small[3];
+  L.m_huge = c.h_small[4];
 }
 
 }  // namespace gm

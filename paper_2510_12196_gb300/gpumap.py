@@ -358,7 +358,14 @@ def map_stats(ctx) -> MapStats:
 
 
 KERNEL_CLASSES = {0: "lp_gain", 1: "lp_after", 2: "eval_J", 3: "cluster", 4: "radix_sort", 5: "eval_J_close",
-                  6: "match_prefer"}
+                  6: "match_prefer", 7: "cluster_mid", 8: "cluster_high", 9: "eval_J_mid", 10: "eval_J_high",
+                  11: "lp_gain_mid", 12: "lp_gain_high"}
+# the kernel each profiled class times
+KERNEL_OF_CLASS = {"lp_gain": "k_lp_gain_tile", "lp_after": "k_lp_after_low", "eval_J": "k_eval_tile",
+                   "cluster": "k_cluster_tile", "radix_sort": "radix-sort passes (k_sort_hist + k_sort_scatter)",
+                   "eval_J_close": "k_eval_tile (controller only)", "match_prefer": "k_match_prefer",
+                   "cluster_mid": "k_cluster_mid", "cluster_high": "k_cluster_high", "eval_J_mid": "k_eval_mid",
+                   "eval_J_high": "k_eval_high", "lp_gain_mid": "k_lp_gain_mid", "lp_gain_high": "k_lp_gain_high"}
 
 
 def map_profile_enable(ctx, enable: bool = True) -> None:

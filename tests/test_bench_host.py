@@ -91,3 +91,29 @@ def test_config_names_the_workload():
     assert cfg["levels"] == 2 and "flushed" in cfg["l2"]
     assert (cfg["n"], cfg["m_dir"], cfg["k"]) == (w.graph.n, w.graph.m_dir, 256)
     assert cfg["parallelism"] == "replicas"
+
+
+def test_units_per_step_and_grid_config():
+    """A multilevel step maps the input graph once (its undirected edges);
+    the grid step is 10 fixed rounds over all its edges."""
+    w = I.workload_grid64()
+    assert bench.units_per_step(w) == 8064 * 10
+    cfg = bench.config_of(w)
+    assert "64x64" in cfg["workload"] and "10 fixed refinement rounds" in cfg["workload"]
+    assert "L2" in cfg["l2"] and cfg["rounds"] == 10
+    r = I.workload_rmat(10)
+    assert bench.units_per_step(r) == r.graph.m
+    assert "rmat scale 10" in bench.config_of(r)["workload"]
+
+
+def test_cpu_sample_is_bounded_for_rmat_only():
+    class A:
+        rmat_scale, cpu_sample_scale, log2n = 22, 11, 12
+    big = I.workload_rmat(12)  # stands in for the scale-22 workload (only its name is read)
+    s, text = bench.cpu_sample(A, big)
+    assert s.name.startswith("rmat_s11") and "scale 11" in text and s.graph.n == 1 << 11
+    g = I.workload_rgg(12)
+    s, text = bench.cpu_sample(A, g)
+    assert s is g and "full workload" in text
+    s, text = bench.cpu_sample(A, I.workload_grid64())
+    assert "10 fixed refinement rounds" in text

@@ -155,6 +155,35 @@ def test_batch_coarse_level_jobs():
             G.map_destroy(c)
 
 
+def test_batch_refuses_after_coarsening():
+    """A coarsening (map_coarsen, or map_run, which coarsens) may move a job's
+    level buffers, which the batch's descriptors and graph point into: the
+    next launch is refused with MAP_E_STATE instead of replaying on them."""
+    jobs = _jobs([5000, 7000], seed0=0x5EED1500)
+    ctxs = _make(jobs)
+    try:
+        for c, (_, _, _, p0) in zip(ctxs, jobs):
+            G.map_set_mapping(c, 0, p0)
+        b = G.map_batch_create(ctxs, G.map_batch_opts_default(rounds=3, autotune=0))
+        try:
+            G.map_batch_launch(b)
+            G.map_batch_results(b, len(ctxs))
+            G.map_coarsen(ctxs[1])
+            with pytest.raises(G.MapError) as e:
+                G.map_batch_launch(b)
+            assert e.value.status == 6
+        finally:
+            G.map_batch_destroy(b)
+        # a batch built afterwards runs
+        b = G.map_batch_create(ctxs, G.map_batch_opts_default(rounds=3, autotune=0))
+        G.map_batch_launch(b)
+        G.map_batch_results(b, len(ctxs))
+        G.map_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
 def test_batch_errors():
     jobs = _jobs([500, 600], seed0=0x5EED1400)
     ctxs = _make(jobs)

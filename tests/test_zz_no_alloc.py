@@ -3,13 +3,15 @@
 map_objective_noalloc serves callers that cannot or must not allocate device
 memory (the CUDA allocation calls may synchronise the whole device; some
 callers live under a fixed memory budget of their own pool).  It must return
-exactly what map_objective returns, also when called twice in a row: the
-second call reuses the shared scratch array and must not see the first
-call's block weights or J.  This file is collected last on purpose.
+exactly what map_objective returns, and what the CPU oracle computes, also
+when called twice in a row: the second call reuses the shared scratch array
+and must not see the first call's block weights or J.  This file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2510_12196_gb300 import gpumap as G
 from paper_2510_12196_gb300 import inputs as I
 
@@ -37,6 +39,8 @@ def test_noalloc_objective_matches_map_objective_twice(hier, dist):
     pis = [I.random_mapping(g.n, k, 1), ((np.arange(g.n) * k) // g.n).astype(np.int32)]
     for pi in pis:
         want = _context_objective(g, hier, dist, pi)
+        oJ, omx, _ = O.objective(g, hier, dist, pi)
+        assert want == (oJ, omx)
         pi_d = torch.from_numpy(pi).cuda()
         G.map_objective_noalloc(*dev, g.n, pi_d, hier, dist, out)
         torch.cuda.synchronize()
