@@ -154,20 +154,6 @@ __global__ void k_iota(int32_t* a, int64_t n) {
 // ---------------------------------------------------------------------------
 // clustering
 // ---------------------------------------------------------------------------
-struct Cand {
-  int32_t score;
-  int32_t t;
-  uint64_t h;
-};
-// a better than b: larger score, then smaller tie-hash, then smaller label
-__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
-  if (a.t < 0) return false;
-  if (b.t < 0) return true;
-  if (a.score != b.score) return a.score > b.score;
-  if (a.h != b.h) return a.h < b.h;
-  return a.t < b.t;
-}
-
 struct ClusterArgs {
   const int32_t* C;      // labels (snapshot)
   const int32_t* Wc;     // cluster weights (snapshot)
@@ -299,78 +285,297 @@ __global__ void __launch_bounds__(kTileThreads, 9) k_cluster_tile(GraphView g, C
   }
 }
 
-// one CTA per high-degree vertex, open-addressing table in global memory
-// (shared-memory tables for rows up to 2047 entries were measured slower on
-// R-MAT: fewer resident blocks, same-label atomics serialised on chip)
 __device__ __forceinline__ uint32_t slot_hash(int32_t t) {
   uint32_t x = (uint32_t)t * 0x9E3779B1u;
   return x ^ (x >> 15);
 }
 
-// Vertices of degree > kMidDeg: `sel` lists their positions in hi[].
-__global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, const int32_t* __restrict__ hi,
-                                                             const int32_t* __restrict__ sel, int32_t n_sel,
-                                                             const int64_t* __restrict__ hoff, int32_t* hkey,
-                                                             int32_t* hval, ClusterArgs a, uint32_t* err) {
-  __shared__ Cand sb[32];
-  for (int32_t j = blockIdx.x; j < n_sel; j += gridDim.x) {
-    const int32_t idx = sel[j];
-    const int32_t v = hi[idx];
-    const int64_t deg = g.xadj[v + 1] - g.xadj[v];
-    if (!cluster_active(a, v, deg)) {
-      if (threadIdx.x == 0) a.req[v] = -1;
-      continue;
+// Vertices of degree > kMidDeg (up to 1.6e5 entries on R-MAT scale 22).
+// Each row is rated in an open-addressing table (next power of two >= 2
+// (deg + 1) slots, at least 64, linear probing) of 64-bit words, (label <<
+// 32) | summed weight: a new label costs one compare-and-swap, a repeated one
+// a compare-and-swap and an add (the weight sum of a row stays below 2^31, so
+// it never carries into the label).  The own cluster is inserted with weight
+// 0.  The decision takes the largest weight, then the smaller tie-hash, then
+// the smaller label, and puts every slot back to empty.
+//  * rows of at most kSmemRowDeg entries: the whole row on one CTA, its
+//    table in shared memory (no global atomics);
+//  * larger rows: their entries, flattened in huge[] order, are cut into
+//    chunks of kHubChunk entries that the CTAs of one wave take in turn, the
+//    table in global memory.  A second launch reads the table back in the
+//    same chunks (each chunk takes the slots in proportion to its share of
+//    the row's entries) and stores each slice's best label; a third combines
+//    the slices of every row and files its request.
+constexpr unsigned long long kEmptySlot = ~0ULL;
+constexpr int64_t kSmemRowDeg = 2047;
+constexpr uint32_t kSmemSlots = 4096;  // >= 2 (kSmemRowDeg + 1)
+static_assert(kSmemSlots >= 2 * (kSmemRowDeg + 1), "shared-memory row table at most half full");
+
+// Inserts from slot h on (`probes` already made).
+__device__ __forceinline__ bool hub_insert_from(unsigned long long* T, uint32_t mask, int32_t t, int32_t w, uint32_t h,
+                                                uint32_t probes) {
+  const unsigned long long key = (unsigned long long)(uint32_t)t << 32;
+  for (uint32_t probe = probes; probe <= mask; probe++) {
+    const unsigned long long prev = atomicCAS(&T[h], kEmptySlot, key | (uint32_t)w);
+    if (prev == kEmptySlot) return true;
+    if ((prev >> 32) == (uint32_t)t) {
+      if (w) atomicAdd(&T[h], (unsigned long long)(uint32_t)w);
+      return true;
     }
-    const int64_t base = hoff[idx];
-    const int32_t size = (int32_t)(hoff[idx + 1] - base);
-    const uint32_t mask = (uint32_t)size - 1u;
-    int32_t* K = hkey + base;
-    int32_t* V = hval + base;
-    for (int32_t s = threadIdx.x; s < size; s += blockDim.x) {
-      K[s] = -1;
-      V[s] = 0;
-    }
-    __syncthreads();
-    const int32_t own = a.C[v];
-    const int64_t beg = g.xadj[v];
-    for (int64_t e = beg - 1 + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x) {
-      const int32_t t = (e < beg) ? own : a.C[g.adj[e]];
-      const int32_t w = (e < beg) ? 0 : g.adjw[e];
-      uint32_t h = slot_hash(t) & mask;
-      bool placed = false;
-      for (int32_t probe = 0; probe < size; probe++) {
-        const int32_t prev = atomicCAS(&K[h], -1, t);
-        if (prev == -1 || prev == t) {
-          atomicAdd(&V[h], w);
-          placed = true;
-          break;
-        }
-        h = (h + 1) & mask;
-      }
-      if (!placed) atomicOr(err, ERR_CAPACITY);
-    }
-    __syncthreads();
-    Cand best{0, -1, 0};
-    for (int32_t s = threadIdx.x; s < size; s += blockDim.x) {
-      const int32_t t = K[s];
-      if (t < 0) continue;
-      Cand x{V[s], t, h_tie(a.seed, a.level, t)};
-      if (better(x, best)) best = x;
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+__device__ __forceinline__ bool hub_insert(unsigned long long* T, uint32_t mask, int32_t t, int32_t w) {
+  return hub_insert_from(T, mask, t, w, slot_hash(t) & mask, 0);
+}
+
+// entries a thread keeps in flight
+constexpr int kHubBatch = 4;
+
+// Inserts the CSR entries [e0, e1) of a row (labels gathered from C) with
+// stride blockDim.x: per thread kHubBatch entries at a time, whose loads,
+// label gathers and first compare-and-swaps are each issued before any
+// result is used; only collisions with another label probe on.  Returns
+// false if a table overflowed.
+__device__ __forceinline__ bool hub_insert_range(const GraphView& g, const int32_t* __restrict__ C, int64_t e0,
+                                                 int64_t e1, unsigned long long* T, uint32_t mask) {
+  bool ok = true;
+  for (int64_t f0 = e0; f0 < e1; f0 += (int64_t)blockDim.x * kHubBatch) {
+    int32_t t[kHubBatch], w[kHubBatch];
+    uint32_t h[kHubBatch];
+    unsigned long long prev[kHubBatch];
+#pragma unroll
+    for (int b = 0; b < kHubBatch; b++) {
+      const int64_t e = f0 + (int64_t)b * blockDim.x + threadIdx.x;
+      t[b] = e < e1 ? g.adj[e] : -1;
+      w[b] = e < e1 ? g.adjw[e] : 0;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      Cand x{__shfl_xor_sync(0xffffffffu, best.score, o), __shfl_xor_sync(0xffffffffu, best.t, o),
-             __shfl_xor_sync(0xffffffffu, best.h, o)};
-      if (better(x, best)) best = x;
+    for (int b = 0; b < kHubBatch; b++) t[b] = t[b] >= 0 ? C[t[b]] : -1;
+#pragma unroll
+    for (int b = 0; b < kHubBatch; b++) {
+      h[b] = slot_hash(t[b]) & mask;
+      prev[b] = t[b] >= 0 ? atomicCAS(&T[h[b]], kEmptySlot, ((unsigned long long)(uint32_t)t[b] << 32) | (uint32_t)w[b])
+                          : kEmptySlot;
     }
-    if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-        if (better(sb[w], best)) best = sb[w];
-      cluster_request(a, v, own, best.t, g.vw[v]);
+#pragma unroll
+    for (int b = 0; b < kHubBatch; b++) {
+      if (t[b] < 0 || prev[b] == kEmptySlot) continue;
+      if ((prev[b] >> 32) == (uint32_t)t[b]) {
+        if (w[b]) atomicAdd(&T[h[b]], (unsigned long long)(uint32_t)w[b]);
+      } else {
+        ok &= hub_insert_from(T, mask, t[b], w[b], (h[b] + 1) & mask, 1);
+      }
     }
-    __syncthreads();
+  }
+  return ok;
+}
+
+struct HubScratch {
+  int32_t bs[kHiThreads / 32];
+  uint64_t bh[kHiThreads / 32];
+  int32_t bt[kHiThreads / 32];
+};
+
+// The best label of the slots T[s0, s1) of a row table (kGlobal: read from
+// L2, where other CTAs' atomics were performed): the largest weight, then
+// the smaller tie-hash, then the smaller label, in two passes so that only
+// labels of the largest weight are hashed; every slot is put back to empty.
+// All threads of the CTA call it; thread 0 receives the result (bs = -1 for
+// no label); ends with a barrier.
+template <bool kGlobal>
+__device__ __forceinline__ void table_best(unsigned long long* T, uint32_t s0, uint32_t s1, const ClusterArgs& a,
+                                           HubScratch& sx, int32_t& out_bs, uint64_t& out_bh, int32_t& out_bt) {
+  int32_t bs = -1;
+#pragma unroll 4
+  for (uint32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const unsigned long long x = kGlobal ? __ldcg(T + s) : T[s];
+    if (x != kEmptySlot) bs = max(bs, (int32_t)(uint32_t)x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bs = max(bs, __shfl_xor_sync(0xffffffffu, bs, o));
+  if ((threadIdx.x & 31) == 0) sx.bs[threadIdx.x >> 5] = bs;
+  __syncthreads();
+  bs = sx.bs[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) bs = max(bs, sx.bs[w]);
+  uint64_t bh = ~0ULL;
+  int32_t bt = INT32_MAX;
+#pragma unroll 4
+  for (uint32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const unsigned long long x = kGlobal ? __ldcg(T + s) : T[s];
+    if (x == kEmptySlot) continue;
+    T[s] = kEmptySlot;
+    if ((int32_t)(uint32_t)x != bs) continue;
+    const int32_t t = (int32_t)(x >> 32);
+    const uint64_t h = h_tie(a.seed, a.level, t);
+    if (h < bh || (h == bh && t < bt)) {
+      bh = h;
+      bt = t;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t oh = __shfl_xor_sync(0xffffffffu, bh, o);
+    const int32_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+    if (oh < bh || (oh == bh && ot < bt)) {
+      bh = oh;
+      bt = ot;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sx.bh[threadIdx.x >> 5] = bh;
+    sx.bt[threadIdx.x >> 5] = bt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+      if (sx.bh[w] < bh || (sx.bh[w] == bh && sx.bt[w] < bt)) {
+        bh = sx.bh[w];
+        bt = sx.bt[w];
+      }
+    out_bs = bs;
+    out_bh = bh;
+    out_bt = bt;
+  }
+  __syncthreads();
+}
+
+// The larger rows' slice results: per chunk two slots (0: the large row
+// holding the chunk's first entry, 1: a large row starting inside the chunk;
+// a row of at least kSmemRowDeg + 1 >= kHubChunk entries leaves room for no
+// other), each ((weight << 32) | label, tie-hash).
+__device__ __forceinline__ int64_t part_slot(int64_t ch, int64_t rb) {
+  return 4 * ch + (rb >= ch * kHubChunk ? 2 : 0);
+}
+
+// Dynamic chunk tickets: thread 0 draws the next chunk for the CTA.  The
+// last CTA to leave resets the counters for the next launch (every CTA's
+// final draw precedes its exit count).
+__device__ __forceinline__ int64_t next_chunk(unsigned long long* ctr, int64_t* s_ch) {
+  if (threadIdx.x == 0) *s_ch = (int64_t)atomicAdd(&ctr[0], 1ULL);
+  __syncthreads();
+  const int64_t ch = *s_ch;
+  __syncthreads();
+  return ch;
+}
+__device__ __forceinline__ void leave_chunks(unsigned long long* ctr) {
+  if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1ULL) == gridDim.x - 1) {
+    ctr[0] = 0;
+    ctr[1] = 0;
+  }
+}
+
+// Sub-round step 1 for the rows of degree > kMidDeg: the rows on the
+// shared-memory path are rated and decided here; the larger rows only insert.
+__global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRows hr,
+                                                             const int64_t* __restrict__ hoff,
+                                                             unsigned long long* htab, ClusterArgs a,
+                                                             unsigned long long* ctr, uint32_t* err) {
+  __shared__ unsigned long long stab[kSmemSlots];
+  __shared__ HubScratch sx;
+  __shared__ int32_t s_bs, s_bt;
+  __shared__ uint64_t s_bh;
+  __shared__ int64_t s_ch;
+  for (uint32_t s = threadIdx.x; s < kSmemSlots; s += blockDim.x) stab[s] = kEmptySlot;
+  __syncthreads();
+  const int64_t m_hub = hr.pre[hr.n_huge];
+  for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
+      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
+      if (rb >= ce) break;
+      const int64_t deg = re - rb;
+      const bool first = rb >= cb;  // this chunk holds the row's first entry
+      // a row on the shared-memory path belongs to the chunk of its first entry
+      if (deg <= kSmemRowDeg && !first) continue;
+      const int32_t idx = hr.huge[r];
+      const int32_t v = hr.hi[idx];
+      if (!cluster_active(a, v, deg)) {
+        if (first && threadIdx.x == 0) a.req[v] = -1;
+        continue;
+      }
+      const int32_t own = a.C[v];
+      const int64_t x0 = g.xadj[v] - rb;  // CSR position of flat entry f: x0 + f
+      bool ok = true;
+      if (deg <= kSmemRowDeg) {
+        uint32_t size = 64;
+        while (size < 2 * (uint32_t)(deg + 1)) size <<= 1;
+        if (threadIdx.x == 0) ok = hub_insert(stab, size - 1, own, 0);
+        ok &= hub_insert_range(g, a.C, x0 + rb, x0 + re, stab, size - 1);
+        if (!ok) atomicOr(err, ERR_CAPACITY);
+        __syncthreads();
+        table_best<false>(stab, 0, size, a, sx, s_bs, s_bh, s_bt);
+        if (threadIdx.x == 0) cluster_request(a, v, own, s_bt, g.vw[v]);
+        continue;
+      }
+      const int64_t base = hoff[idx];
+      const uint32_t mask = (uint32_t)(hoff[idx + 1] - base) - 1u;
+      unsigned long long* T = htab + base;
+      if (first && threadIdx.x == 0) ok = hub_insert(T, mask, own, 0);
+      ok &= hub_insert_range(g, a.C, x0 + max(rb, cb), x0 + min(re, ce), T, mask);
+      if (!ok) atomicOr(err, ERR_CAPACITY);
+    }
+  }
+  leave_chunks(ctr);
+}
+
+// Sub-round step 2: every chunk reads back its slice of each larger row it
+// overlaps (slots [S (f0 - rb) / deg, S (f1 - rb) / deg) of the row's S
+// slots for its entries [f0, f1)), empties it and stores the slice's best.
+__global__ void __launch_bounds__(kHiThreads) k_cluster_giant(HubRows hr, const int64_t* __restrict__ hoff,
+                                                              unsigned long long* htab, unsigned long long* part,
+                                                              ClusterArgs a, unsigned long long* ctr) {
+  __shared__ HubScratch sx;
+  __shared__ int32_t s_bs, s_bt;
+  __shared__ uint64_t s_bh;
+  __shared__ int64_t s_ch;
+  const int64_t m_hub = hr.pre[hr.n_huge];
+  for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
+      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
+      if (rb >= ce) break;
+      const int64_t deg = re - rb;
+      if (deg <= kSmemRowDeg) continue;
+      const int32_t idx = hr.huge[r];
+      if (!cluster_active(a, hr.hi[idx], deg)) continue;
+      const int64_t base = hoff[idx];
+      const int64_t S = hoff[idx + 1] - base;
+      const uint32_t s0 = (uint32_t)(S * (max(rb, cb) - rb) / deg), s1 = (uint32_t)(S * (min(re, ce) - rb) / deg);
+      table_best<true>(htab + base, s0, s1, a, sx, s_bs, s_bh, s_bt);
+      if (threadIdx.x == 0) {
+        const int64_t p = part_slot(ch, rb);
+        part[p] = ((unsigned long long)(uint32_t)s_bs << 32) | (uint32_t)s_bt;
+        part[p + 1] = s_bh;
+      }
+    }
+  }
+  leave_chunks(ctr);
+}
+
+// Sub-round step 3: per active larger row (one thread each), the best of its
+// slices, then its request.
+__global__ void k_cluster_giant_finish(HubRows hr, const unsigned long long* __restrict__ part, const int32_t* vw,
+                                       ClusterArgs a) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < hr.n_huge; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
+    if (re - rb <= kSmemRowDeg) continue;
+    const int32_t v = hr.hi[hr.huge[r]];
+    if (!cluster_active(a, v, re - rb)) continue;
+    int32_t bs = -1, bt = INT32_MAX;
+    uint64_t bh = ~0ULL;
+    for (int64_t ch = rb / kHubChunk; ch <= (re - 1) / kHubChunk; ch++) {
+      const int64_t p = part_slot(ch, rb);
+      const int32_t s = (int32_t)(part[p] >> 32), t = (int32_t)(uint32_t)part[p];
+      const uint64_t h = part[p + 1];
+      if (s > bs || (s == bs && (h < bh || (h == bh && t < bt)))) {
+        bs = s;
+        bt = t;
+        bh = h;
+      }
+    }
+    cluster_request(a, v, a.C[v], bt, vw[v]);
   }
 }
 
@@ -1062,8 +1267,18 @@ void launch_subround(Ctx& c, int lvl, int32_t r, int64_t wcap) {
   }
   if (L.n_huge) {
     ev = c.prof_begin();
-    k_cluster_high<<<std::max(1, std::min(L.n_huge, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
-        view(L), L.hi, L.huge, L.n_huge, L.hi_off, c.hkey, c.hval, a, c.errword); count_launch();
+    const HubRows hr = hub_rows(L);
+    // one wave of resident CTAs over the chunks
+    const int64_t res = (int64_t)c.num_sms * c.resident_blocks((const void*)k_cluster_high, kHiThreads, 0);
+    const unsigned gh = (unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, res));
+    k_cluster_high<<<gh, kHiThreads, 0, c.st>>>(view(L), hr, L.hi_off, c.htab, a, c.hub_ctr, c.errword);
+    count_launch();
+    const int64_t res2 = (int64_t)c.num_sms * c.resident_blocks((const void*)k_cluster_giant, kHiThreads, 0);
+    k_cluster_giant<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, res2)), kHiThreads, 0, c.st>>>(
+        hr, L.hi_off, c.htab, L.hub_part, a, c.hub_ctr); count_launch();
+    k_cluster_giant_finish<<<grid_for(c, kThreads, L.n_huge), kThreads, 0, c.st>>>(hr, L.hub_part, L.vw, a);
+    count_launch();
+    // the three launches of the class together
     c.prof_end(ev, PK_CLUSTER_HIGH, 8 * (int64_t)L.n_huge + (8 * (int64_t)L.n_huge + 12 * L.m_huge) / 2);
   }
   k_cluster_classify<<<gv, kThreads, 0, c.st>>>(n, c.req, c.Wc, c.ReqW, wcap, flag, c.cfg.seed, lvl, c.sort.key[0],
@@ -1172,24 +1387,28 @@ int32_t cluster_level(Ctx& c, int lvl) {
     GM_CUDA(cudaMemcpyAsync(L.hi_off + L.n_hi, c.scan.tile_sums + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice,
                             c.st));
     L.hi_slots = read_i64(c, L.hi_off + L.n_hi);
-    if (L.hi_slots > c.hcap) {
-      if (c.hkey) c.mem.put(c.hkey);
-      if (c.hval) c.mem.put(c.hval);
-      c.hcap = L.hi_slots;
-      c.hkey = c.mem.make<int32_t>((size_t)c.hcap);
-      c.hval = c.mem.make<int32_t>((size_t)c.hcap);
+    if (L.n_huge) {
+      if (L.hi_slots > c.hcap) {
+        if (c.htab) c.mem.put(c.htab);
+        c.hcap = L.hi_slots;
+        c.htab = c.mem.make<unsigned long long>((size_t)c.hcap);
+        c.htab_clean = false;
+      }
+      // every sub-round leaves the tables empty; after a failure they are cleared again
+      if (!c.htab_clean) GM_CUDA(cudaMemsetAsync(c.htab, 0xFF, (size_t)c.hcap * sizeof(unsigned long long), c.st));
+      c.htab_clean = false;
     }
   }
   ClusterState* cs = c.cstate;
   bool graph_ran = false;
   if (c.use_graphs && !c.prof) {
-    const int64_t key[6] = {(int64_t)L.n, L.m, (int64_t)L.n_hi | ((int64_t)L.n_huge << 32), L.hi_slots, wcap,
-                            (int64_t)(intptr_t)c.hkey};
+    const int64_t key[8] = {(int64_t)L.n, L.m, (int64_t)L.n_hi | ((int64_t)L.n_huge << 32), L.hi_slots, wcap,
+                            (int64_t)(intptr_t)c.htab, (int64_t)(intptr_t)L.hub_chunk, L.n_hub_chunks};
     bool same = L.cgexec != nullptr;
-    for (int i = 0; i < 6 && same; i++) same = L.cg_key[i] == key[i];
+    for (int i = 0; i < 8 && same; i++) same = L.cg_key[i] == key[i];
     if (!same) {
       build_cluster_graph(c, lvl, wcap);
-      for (int i = 0; i < 6; i++) L.cg_key[i] = key[i];
+      for (int i = 0; i < 8; i++) L.cg_key[i] = key[i];
     }
     GM_CUDA(cudaGraphLaunch(L.cgexec, c.st));
     // read back with the cluster count below (kernel accounting only)
@@ -1230,6 +1449,7 @@ int32_t cluster_level(Ctx& c, int lvl) {
   const uint32_t e = (uint32_t)(c.h_small[1] & 0xffffffffLL);
   if (e & ERR_TIMEOUT) throw ApiError(MAP_E_TIMEOUT, "a bounded device loop gave up");
   if (e) throw ApiError(MAP_E_INTERNAL, "device consistency check failed (flags " + std::to_string(e) + ")");
+  c.htab_clean = true;
   return (int32_t)nc;
 }
 
@@ -1239,7 +1459,8 @@ void free_level(Ctx& c, Level& L) {
   if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
   L.cgexec = nullptr;
   for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
-                  (void*)L.huge, (void*)L.hi_off, (void*)L.M})
+                  (void*)L.huge, (void*)L.hi_off, (void*)L.M, (void*)L.hub_pre, (void*)L.hub_chunk,
+                  (void*)L.hub_part})
     if (p) c.mem.put(p);
   L = Level{};
 }
@@ -1339,6 +1560,8 @@ void coarsen_alloc(Ctx& c) {
   c.ReqW = c.mem.make<int32_t>(n);
   c.req = c.mem.make<int32_t>(n);
   c.rank = c.mem.make<int32_t>(2 * n + 2);
+  c.hub_ctr = c.mem.make<unsigned long long>(2);
+  GM_CUDA(cudaMemsetAsync(c.hub_ctr, 0, 2 * sizeof(unsigned long long), c.st));
 }
 
 void validate_graph(Ctx& c) {

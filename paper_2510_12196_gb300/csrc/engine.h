@@ -90,6 +90,15 @@ struct Level {
   int32_t n_huge = 0;
   int64_t* hi_off = nullptr;   // hash-table offsets of the high-degree vertices (n_hi + 1)
   int64_t hi_slots = 0;
+  // the CSR entries of the vertices of degree > kMidDeg, flattened in huge[]
+  // order and cut into chunks of kHubChunk entries (clustering):
+  int64_t* hub_pre = nullptr;    // exclusive prefix of their degrees (n_huge + 1)
+  int32_t* hub_chunk = nullptr;  // per chunk: the huge[] index of the row holding its first entry
+  // per chunk, two slots (the large row holding its first entry, the large
+  // row starting inside it): a clustering slice result, 16 bytes each
+  unsigned long long* hub_part = nullptr;
+  int64_t hub_chunk_cap = 0;
+  int64_t n_hub_chunks = 0;
   int32_t max_vw = 0;
   // instantiated Alg. 6 graph of this level and what it was captured for
   cudaGraphExec_t gexec = nullptr;
@@ -99,9 +108,22 @@ struct Level {
   long long g_root = 0;  // kernel nodes outside the conditional bodies
   // instantiated clustering graph of this level and its key
   cudaGraphExec_t cgexec = nullptr;
-  int64_t cg_key[6] = {0, 0, 0, 0, 0, 0};
+  int64_t cg_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long cg_root = 0;
 };
+
+// Device view of the flattened entries of the rows of degree > kMidDeg.
+struct HubRows {
+  const int32_t* __restrict__ hi;
+  const int32_t* __restrict__ huge;
+  int32_t n_huge;
+  const int64_t* __restrict__ pre;    // n_huge + 1
+  const int32_t* __restrict__ chunk;  // first row of each chunk
+  int64_t nchunks;
+};
+inline HubRows hub_rows(const Level& L) {
+  return HubRows{L.hi, L.huge, L.n_huge, L.hub_pre, L.hub_chunk, L.n_hub_chunks};
+}
 
 struct DevMem {
   map_alloc_fn afn = nullptr;
@@ -208,9 +230,15 @@ struct Ctx {
   int32_t* ReqW = nullptr;      // requested weight per target [n0]
   int32_t* req = nullptr;       // requested target per vertex [n0]
   int32_t* rank = nullptr;      // label -> coarse id [2 n0 + 2]
-  int32_t* hkey = nullptr;      // hash tables of high-degree vertices
-  int32_t* hval = nullptr;
+  // chunk tickets of the hub clustering kernels: {next chunk, CTAs done},
+  // zero between launches (the last CTA of a launch resets them)
+  unsigned long long* hub_ctr = nullptr;
+  // hash tables of the vertices of degree > kMidDeg during clustering: one
+  // 64-bit word per slot, (label << 32) | summed weight, all slots empty
+  // (~0) between sub-rounds
+  unsigned long long* htab = nullptr;
   int64_t hcap = 0;
+  bool htab_clean = false;
   uint32_t* errword = nullptr;
   ClusterState* cstate = nullptr;
   ClusterState* h_cstate = nullptr;  // pinned mirror

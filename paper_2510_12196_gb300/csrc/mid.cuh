@@ -18,5 +18,7 @@ constexpr int kMidThreads = kMidWarps * 32;
 // bound (in 32-bit words) of one warp's dense connectivity table (PE codes and
 // level group sums): kMidWarps tables stay within 48 KB of shared memory
 constexpr int kMidTableMax = 1536;
+// entries per chunk when the rows of degree > kMidDeg are spread over CTAs
+constexpr int64_t kHubChunk = 2048;
 
 }  // namespace gm

@@ -204,22 +204,40 @@ __global__ void __launch_bounds__(kMidThreads) k_eval_mid(GraphView g, const int
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
 }
 
-// J contribution of the high-degree vertices (one CTA per vertex).
-__global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, const int32_t* __restrict__ hi,
-                                                          const int32_t* __restrict__ sel, int32_t n_sel,
-                                                          const int32_t* __restrict__ pi, Topo topo, int64_t* Jacc,
-                                                          const RefineState* st, int phase) {
+// J contribution of the vertices of degree > kMidDeg: their entries,
+// flattened in huge[] order, are taken in chunks of kHubChunk by the CTAs of
+// one wave (every entry's term is independent), so no CTA waits on a hub's
+// whole row; each thread follows the row of its own entries.
+__global__ void __launch_bounds__(kHiThreads) k_eval_high(GraphView g, HubRows hr, const int32_t* __restrict__ pi,
+                                                          Topo topo, int64_t* Jacc, const RefineState* st, int phase) {
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
   if (incremental_j(st, phase)) return;
   load_sdist(sdist, topo);
   __syncthreads();
+  const int64_t m_hub = hr.pre[hr.n_huge];
   int64_t acc = 0;
-  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
-    const int32_t v = hi_vertex(hi, sel, i);
-    const int32_t p = pi[v];
-    for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
+  for (int64_t ch = blockIdx.x; ch < hr.nchunks; ch += gridDim.x) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    int32_t r = hr.chunk[ch];
+    int64_t re = hr.pre[r + 1], x0 = 0;
+    int32_t p = 0;
+    bool have = false;
+    for (int64_t f = cb + threadIdx.x; f < ce; f += blockDim.x) {
+      while (f >= re) {
+        r++;
+        re = hr.pre[r + 1];
+        have = false;
+      }
+      if (!have) {
+        const int32_t v = hr.hi[hr.huge[r]];
+        x0 = g.xadj[v] - hr.pre[r];
+        p = pi[v];
+        have = true;
+      }
+      const int64_t e = x0 + f;
       acc += (int64_t)g.adjw[e] * dcode(sdist, p, pi[g.adj[e]]);
+    }
   }
   acc = block_sum(acc, sm);
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
@@ -823,24 +841,46 @@ __global__ void __launch_bounds__(kMidThreads) k_delta_mid(GraphView g, const in
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
 }
 
-// movers of larger degree: one CTA per vertex
+// movers of degree > kMidDeg: the flattened hub entries in chunks of
+// kHubChunk over the CTAs of one wave (as k_eval_high); the entries of rows
+// that do not move are skipped
 template <class Mv>
-__global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, const int32_t* __restrict__ hi,
-                                                           const int32_t* __restrict__ sel, int32_t n_sel,
-                                                           const int32_t* __restrict__ pi, Mv mv, Topo topo,
-                                                           int64_t* Jacc, const RefineState* st, int kind) {
+__global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, HubRows hr, const int32_t* __restrict__ pi,
+                                                           Mv mv, Topo topo, int64_t* Jacc, const RefineState* st,
+                                                           int kind) {
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
   if (st->kind != kind) return;
   load_sdist(sdist, topo);
   __syncthreads();
+  const int64_t m_hub = hr.pre[hr.n_huge];
   int64_t acc = 0;
-  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
-    const int32_t v = hi_vertex(hi, sel, i);
-    if (!mv.moved(v)) continue;
-    const int32_t ov = pi[v], nv = mv.target(v);
-    for (int64_t x = g.xadj[v] + threadIdx.x; x < g.xadj[v + 1]; x += blockDim.x)
-      acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[x], g.adjw[x]);
+  for (int64_t ch = blockIdx.x; ch < hr.nchunks; ch += gridDim.x) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    int32_t r = hr.chunk[ch];
+    int64_t re = hr.pre[r + 1], x0 = 0;
+    int32_t ov = 0, nv = 0;
+    int state = 0;  // 0: row not looked at, 1: a mover, 2: stays
+    for (int64_t f = cb + threadIdx.x; f < ce; f += blockDim.x) {
+      while (f >= re) {
+        r++;
+        re = hr.pre[r + 1];
+        state = 0;
+      }
+      if (state == 0) {
+        const int32_t v = hr.hi[hr.huge[r]];
+        state = 2;
+        if (mv.moved(v)) {
+          state = 1;
+          x0 = g.xadj[v] - hr.pre[r];
+          ov = pi[v];
+          nv = mv.target(v);
+        }
+      }
+      if (state != 1) continue;
+      const int64_t e = x0 + f;
+      acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[e], g.adjw[e]);
+    }
   }
   acc = block_sum(acc, sm);
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
@@ -1726,8 +1766,9 @@ void launch_eval(Ctx& c, int lvl, const EvalCtl* ec = nullptr, bool full = true)
   }
   if (L.n_huge) {
     if (full) ev = c.prof_begin();
-    k_eval_high<<<std::min(L.n_huge, c.num_sms * 8), kHiThreads, 0, c.st>>>(
-        view(L), L.hi, L.huge, L.n_huge, L.pi, c.topo, c.Jacc, ec ? ec->s : nullptr, ec ? ec->phase : 0); count_launch();
+    k_eval_high<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, (int64_t)c.num_sms * 8)), kHiThreads,
+                  0, c.st>>>(view(L), hub_rows(L), L.pi, c.topo, c.Jacc, ec ? ec->s : nullptr, ec ? ec->phase : 0);
+    count_launch();
     if (full) c.prof_end(ev, PK_EVAL_HIGH, 12 * (int64_t)L.n_huge + 12 * L.m_huge);
   }
   ev = c.prof_begin();
@@ -1749,8 +1790,9 @@ void launch_delta(Ctx& c, int lvl, Mv mv, int kind) {
         view(L), L.hi, L.n_hi, L.pi, mv, c.topo, c.Jacc, c.state, kind); count_launch();
   }
   if (L.n_huge)
-    k_delta_high<Mv><<<std::max(1, std::min(L.n_huge, c.num_sms * 8)), kHiThreads, 0, c.st>>>(
-        view(L), L.hi, L.huge, L.n_huge, L.pi, mv, c.topo, c.Jacc, c.state, kind); count_launch();
+    k_delta_high<Mv><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, (int64_t)c.num_sms * 8)),
+                       kHiThreads, 0, c.st>>>(view(L), hub_rows(L), L.pi, mv, c.topo, c.Jacc, c.state, kind);
+  if (L.n_huge) count_launch();
 }
 
 void launch_lp(Ctx& c, int lvl) {
@@ -3579,6 +3621,56 @@ __global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const
 }
 }  // namespace
 
+namespace {
+// Chunk map of the flattened hub entries: chunk c starts in the row r with
+// pre[r] <= c * kHubChunk < pre[r + 1].
+__global__ void k_hub_chunks(int32_t n_huge, const int64_t* __restrict__ pre, int32_t* chunk) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_huge; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c0 = (pre[r] + kHubChunk - 1) / kHubChunk, c1 = (pre[r + 1] + kHubChunk - 1) / kHubChunk;
+    for (int64_t c = c0; c < c1; c++) chunk[c] = (int32_t)r;
+  }
+}
+
+struct LoadHubDeg {
+  const int32_t* hi;
+  const int32_t* huge;
+  const int64_t* xadj;
+  __device__ int64_t operator()(int64_t j) const {
+    const int32_t v = hi[huge[j]];
+    return xadj[v + 1] - xadj[v];
+  }
+};
+
+// The flattened entries of the rows of degree > kMidDeg (in huge[] order)
+// and their chunk map, so that kernels can spread those rows over CTAs.
+void prepare_hubs(Ctx& c, Level& L) {
+  if (!L.n_huge) {
+    L.n_hub_chunks = 0;
+    return;
+  }
+  if (!L.hub_pre) L.hub_pre = c.mem.make<int64_t>((size_t)L.n + 1);
+  const int64_t nch = (L.m_huge + kHubChunk - 1) / kHubChunk;
+  if (!L.hub_chunk || L.hub_chunk_cap < nch + 1) {
+    // captured graphs hold the old pointers
+    drop_graph(L);
+    if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
+    L.cgexec = nullptr;
+    if (L.hub_chunk) c.mem.put(L.hub_chunk);
+    if (L.hub_part) c.mem.put(L.hub_part);
+    L.hub_chunk_cap = nch + 1;
+    L.hub_chunk = c.mem.make<int32_t>((size_t)L.hub_chunk_cap);
+    L.hub_part = c.mem.make<unsigned long long>((size_t)L.hub_chunk_cap * 4);
+  }
+  scan(LoadHubDeg{L.hi, L.huge, L.xadj}, StoreExcl{L.hub_pre}, L.n_huge, nullptr, c.scan, c.st);
+  const int64_t tiles = std::max<int64_t>(1, scan_tiles(L.n_huge));
+  GM_CUDA(cudaMemcpyAsync(L.hub_pre + L.n_huge, c.scan.tile_sums + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                          c.st));
+  k_hub_chunks<<<grid_for(c, kThreads, L.n_huge), kThreads, 0, c.st>>>(L.n_huge, L.hub_pre, L.hub_chunk);
+  count_launch();
+  L.n_hub_chunks = nch;
+}
+}  // namespace
+
 void classify_degrees(Ctx& c, int lvl) {
   Level& L = c.lv[lvl];
   if (!L.hi) L.hi = c.mem.make<int32_t>((size_t)std::max(1, L.n));
@@ -3599,6 +3691,7 @@ void classify_degrees(Ctx& c, int lvl) {
   L.max_deg = c.h_small[2];
   L.max_vw = (int32_t)c.h_small[3];
   L.m_huge = c.h_small[4];
+  prepare_hubs(c, L);
 }
 
 }  // namespace gm
