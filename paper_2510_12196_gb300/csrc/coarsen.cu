@@ -449,23 +449,6 @@ __device__ __forceinline__ int64_t part_slot(int64_t ch, int64_t rb) {
   return 4 * ch + (rb >= ch * kHubChunk ? 2 : 0);
 }
 
-// Dynamic chunk tickets: thread 0 draws the next chunk for the CTA.  The
-// last CTA to leave resets the counters for the next launch (every CTA's
-// final draw precedes its exit count).
-__device__ __forceinline__ int64_t next_chunk(unsigned long long* ctr, int64_t* s_ch) {
-  if (threadIdx.x == 0) *s_ch = (int64_t)atomicAdd(&ctr[0], 1ULL);
-  __syncthreads();
-  const int64_t ch = *s_ch;
-  __syncthreads();
-  return ch;
-}
-__device__ __forceinline__ void leave_chunks(unsigned long long* ctr) {
-  if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1ULL) == gridDim.x - 1) {
-    ctr[0] = 0;
-    ctr[1] = 0;
-  }
-}
-
 // Sub-round step 1 for the rows of degree > kMidDeg: the rows on the
 // shared-memory path are rated and decided here; the larger rows only insert.
 __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRows hr,
@@ -1460,7 +1443,7 @@ void free_level(Ctx& c, Level& L) {
   L.cgexec = nullptr;
   for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
                   (void*)L.huge, (void*)L.hi_off, (void*)L.M, (void*)L.hub_pre, (void*)L.hub_chunk,
-                  (void*)L.hub_part})
+                  (void*)L.hub_part, (void*)L.hub_sidx, (void*)L.hub_split, (void*)L.hub_gtab})
     if (p) c.mem.put(p);
   L = Level{};
 }

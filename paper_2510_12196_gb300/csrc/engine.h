@@ -97,6 +97,16 @@ struct Level {
   // per chunk, two slots (the large row holding its first entry, the large
   // row starting inside it): a clustering slice result, 16 bytes each
   unsigned long long* hub_part = nullptr;
+  // rows of degree > hub_split_deg whose connectivity tables are summed over
+  // chunks (LP gains, rebalancing selection): per huge[] row its index among
+  // them (-1: rated whole), their list, and n_split x kc partial tables (zero
+  // between uses)
+  int32_t* hub_sidx = nullptr;
+  int32_t* hub_split = nullptr;
+  int32_t* hub_gtab = nullptr;
+  int32_t n_split = 0;
+  int64_t hub_gtab_cap = 0;
+  int64_t hub_split_deg = 0;
   int64_t hub_chunk_cap = 0;
   int64_t n_hub_chunks = 0;
   int32_t max_vw = 0;

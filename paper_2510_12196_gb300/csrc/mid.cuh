@@ -20,5 +20,26 @@ constexpr int kMidThreads = kMidWarps * 32;
 constexpr int kMidTableMax = 1536;
 // entries per chunk when the rows of degree > kMidDeg are spread over CTAs
 constexpr int64_t kHubChunk = 2048;
+// rows rated by one CTA whole (PE-code tables); larger rows sum chunk tables
+constexpr int64_t kSplitDeg = 4096;
+// bound of the per-level partial tables of the larger rows (else rated whole)
+constexpr int64_t kSplitTableBytes = 1LL << 30;
+
+// Dynamic chunk tickets: thread 0 draws the next chunk for the CTA.  The
+// last CTA to leave resets the counters for the next launch (every CTA's
+// final draw precedes its exit count).
+__device__ __forceinline__ int64_t next_chunk(unsigned long long* ctr, int64_t* s_ch) {
+  if (threadIdx.x == 0) *s_ch = (int64_t)atomicAdd(&ctr[0], 1ULL);
+  __syncthreads();
+  const int64_t ch = *s_ch;
+  __syncthreads();
+  return ch;
+}
+__device__ __forceinline__ void leave_chunks(unsigned long long* ctr) {
+  if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1ULL) == gridDim.x - 1) {
+    ctr[0] = 0;
+    ctr[1] = 0;
+  }
+}
 
 }  // namespace gm

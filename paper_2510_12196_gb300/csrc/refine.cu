@@ -452,11 +452,14 @@ __host__ inline GroupLayout group_layout(const Topo& t) {
 
 // Fills conn[0, kc) (already zeroed) with the edge weights of v per neighbour
 // PE and the level group sums after it.  Returns T(P(v)) summed over the block.
-__device__ void conn_build(const GraphView& g, int32_t v, const int32_t* __restrict__ pi, const Topo& topo,
-                           const GroupLayout& gl, int32_t* tab) {
-  for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x)
-    atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
-  __syncthreads();
+// conn of the CSR entries [e0, e1) added into tab[code] (shared memory).
+__device__ __forceinline__ void conn_add(const GraphView& g, int64_t e0, int64_t e1, const int32_t* __restrict__ pi,
+                                         int32_t* tab) {
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
+}
+
+// The level group sums of a complete conn table (layout of GroupLayout).
+__device__ void conn_groups(const Topo& topo, const GroupLayout& gl, int32_t* tab) {
   for (int i = 1; i <= topo.levels; i++) {
     const int32_t cnt = topo.kc >> topo.s[i];
     const int32_t sh = topo.s[i] - topo.s[i - 1];
@@ -471,6 +474,13 @@ __device__ void conn_build(const GraphView& g, int32_t v, const int32_t* __restr
   }
 }
 
+__device__ void conn_build(const GraphView& g, int32_t v, const int32_t* __restrict__ pi, const Topo& topo,
+                           const GroupLayout& gl, int32_t* tab) {
+  conn_add(g, g.xadj[v], g.xadj[v + 1], pi, tab);
+  __syncthreads();
+  conn_groups(topo, gl, tab);
+}
+
 // sum_b conn(b) D(q, b) from the group sums (Eq. 1 regrouped by level).
 __device__ __forceinline__ int64_t conn_T(const int32_t* tab, const Topo& topo, const GroupLayout& gl, int32_t q) {
   int64_t T = 0;
@@ -481,6 +491,58 @@ __device__ __forceinline__ int64_t conn_T(const int32_t* tab, const Topo& topo, 
     prev = cur;
   }
   return T;
+}
+
+// Alg. 4 step 1 for vertex v (current PE code p) from its complete table
+// (conn over the PE codes and the level group sums): the neighbouring PE
+// q != p of smallest T(q) (lowest code on ties), the filter, the outputs.
+// All threads of the CTA call it; ends with a barrier.
+__device__ __forceinline__ void lp_hub_decide(const int32_t* tab, const Topo& topo, const GroupLayout& gl,
+                                              const LpFilter& flt, int32_t v, int32_t p, int32_t* pp, int64_t* gain,
+                                              uint8_t* inx, int64_t* sbt, int32_t* sbc) {
+  int64_t bt = INT64_MAX;
+  int32_t bc = INT32_MAX;
+  for (int32_t q = threadIdx.x; q < topo.kc; q += blockDim.x) {
+    if (q == p || tab[q] == 0) continue;
+    const int64_t T = conn_T(tab, topo, gl, q);
+    if (T < bt || (T == bt && q < bc)) {
+      bt = T;
+      bc = q;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
+    const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+    if (ot < bt || (ot == bt && oc < bc)) {
+      bt = ot;
+      bc = oc;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sbt[threadIdx.x >> 5] = bt;
+    sbc[threadIdx.x >> 5] = bc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+      if (sbt[w] < bt || (sbt[w] == bt && sbc[w] < bc)) {
+        bt = sbt[w];
+        bc = sbc[w];
+      }
+    const int64_t Tp = conn_T(tab, topo, gl, p);
+    const int64_t G = Tp - bt;
+    if (bc != INT32_MAX && flt.admit(G, tab[p])) {
+      inx[v] = 1;
+      pp[v] = bc;
+      gain[v] = G;
+    } else {
+      inx[v] = 0;
+      pp[v] = p;
+      gain[v] = 0;
+    }
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const int32_t* __restrict__ hi,
@@ -508,49 +570,7 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_gain_high(GraphView g, const 
     for (int32_t b = threadIdx.x; b < gl.total; b += blockDim.x) tab[b] = 0;
     __syncthreads();
     conn_build(g, v, pi, topo, gl, tab);
-    int64_t bt = INT64_MAX;
-    int32_t bc = INT32_MAX;
-    for (int32_t q = threadIdx.x; q < topo.kc; q += blockDim.x) {
-      if (q == p || tab[q] == 0) continue;
-      const int64_t T = conn_T(tab, topo, gl, q);
-      if (T < bt || (T == bt && q < bc)) {
-        bt = T;
-        bc = q;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const int64_t ot = __shfl_xor_sync(0xffffffffu, bt, o);
-      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
-      if (ot < bt || (ot == bt && oc < bc)) {
-        bt = ot;
-        bc = oc;
-      }
-    }
-    if ((threadIdx.x & 31) == 0) {
-      sbt[threadIdx.x >> 5] = bt;
-      sbc[threadIdx.x >> 5] = bc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-        if (sbt[w] < bt || (sbt[w] == bt && sbc[w] < bc)) {
-          bt = sbt[w];
-          bc = sbc[w];
-        }
-      const int64_t Tp = conn_T(tab, topo, gl, p);
-      const int64_t G = Tp - bt;
-      if (bc != INT32_MAX && flt.admit(G, tab[p])) {
-        inx[v] = 1;
-        pp[v] = bc;
-        gain[v] = G;
-      } else {
-        inx[v] = 0;
-        pp[v] = p;
-        gain[v] = 0;
-      }
-    }
-    __syncthreads();
+    lp_hub_decide(tab, topo, gl, flt, v, p, pp, gain, inx, sbt, sbc);
   }
 }
 
@@ -1194,6 +1214,70 @@ __global__ void __launch_bounds__(kMidThreads) k_reb_select_mid(GraphView g, con
   }
 }
 
+// Rebalancing selection for eligible vertex v of block A from its complete
+// table (conn over the PE codes, plus the level group sums for the J gains):
+// the best destination below sigma among the neighbouring blocks (the drawn
+// block of U if none), its loss bucket, and the per-(block, bucket) weight
+// totals.  All threads of the CTA call it; ends with a barrier.
+__device__ __forceinline__ void reb_hub_decide(const int32_t* tab, const RebArgs& a, int32_t kc, const GroupLayout& gl,
+                                               int32_t v, int32_t A, int32_t cv, int32_t* dest, uint8_t* bkt,
+                                               uint8_t* elig, const RefineState* st, int64_t* sbb, int32_t* sbc) {
+  const int64_t sigma = a.cnt[CNT_SIGMA];
+  const int64_t nU = a.cnt[CNT_NU];
+  // score: conn(v, q), or -T(q) for the J gains; -1 / INT64_MIN: none
+  int64_t bconn = a.obj ? INT64_MIN : -1;
+  int32_t bc = INT32_MAX;
+  for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) {
+    const int32_t x = tab[b];
+    if (x == 0 || b == A || a.W[b] > sigma) continue;
+    const int64_t sc = a.obj ? -conn_T(tab, a.topo, gl, b) : (int64_t)x;
+    if (sc > bconn || (sc == bconn && b < bc)) {
+      bconn = sc;
+      bc = b;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t ob = __shfl_xor_sync(0xffffffffu, bconn, o);
+    const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
+    if (ob > bconn || (ob == bconn && oc < bc)) {
+      bconn = ob;
+      bc = oc;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sbb[threadIdx.x >> 5] = bconn;
+    sbc[threadIdx.x >> 5] = bc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+      if (sbb[w] > bconn || (sbb[w] == bconn && sbc[w] < bc)) {
+        bconn = sbb[w];
+        bc = sbc[w];
+      }
+    const int64_t sA = a.obj ? -conn_T(tab, a.topo, gl, A) : (int64_t)tab[A];
+    int64_t gcut = 0;
+    bool ok = true;
+    if (bc != INT32_MAX) {
+      gcut = bconn - sA;
+    } else if (nU > 0) {
+      bc = a.U[h_rebalance(a.seed, st->level, st->t, v) % (uint64_t)nU];
+      gcut = (a.obj ? -conn_T(tab, a.topo, gl, bc) : 0) - sA;
+    } else {
+      ok = false;
+    }
+    if (ok) {
+      const int32_t bk = loss_bucket(gcut);
+      dest[v] = bc;
+      bkt[v] = (uint8_t)bk;
+      atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)cv);
+    }
+    elig[v] = ok ? 1 : 0;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, const int32_t* __restrict__ hi,
                                                                 const int32_t* __restrict__ sel, int32_t n_sel,
                                                                 const int32_t* __restrict__ pi, RebArgs a, int32_t kc,
@@ -1203,8 +1287,6 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
   __shared__ int64_t sbb[32];
   __shared__ int32_t sbc[32];
   if (!kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG))) return;
-  const int64_t sigma = a.cnt[CNT_SIGMA];
-  const int64_t nU = a.cnt[CNT_NU];
   for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
     const int32_t v = hi_vertex(hi, sel, i);
     const int32_t A = pi[v];
@@ -1222,60 +1304,150 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
         atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
       __syncthreads();
     }
-    // score: conn(v, q), or -T(q) for the J gains; -1 / INT64_MIN: none
-    int64_t bconn = a.obj ? INT64_MIN : -1;
-    int32_t bc = INT32_MAX;
-    for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) {
-      const int32_t x = tab[b];
-      if (x == 0 || b == A || a.W[b] > sigma) continue;
-      const int64_t sc = a.obj ? -conn_T(tab, a.topo, gl, b) : (int64_t)x;
-      if (sc > bconn || (sc == bconn && b < bc)) {
-        bconn = sc;
-        bc = b;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const int64_t ob = __shfl_xor_sync(0xffffffffu, bconn, o);
-      const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, o);
-      if (ob > bconn || (ob == bconn && oc < bc)) {
-        bconn = ob;
-        bc = oc;
-      }
-    }
-    if ((threadIdx.x & 31) == 0) {
-      sbb[threadIdx.x >> 5] = bconn;
-      sbc[threadIdx.x >> 5] = bc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-        if (sbb[w] > bconn || (sbb[w] == bconn && sbc[w] < bc)) {
-          bconn = sbb[w];
-          bc = sbc[w];
-        }
-      const int64_t sA = a.obj ? -conn_T(tab, a.topo, gl, A) : (int64_t)tab[A];
-      int64_t gcut = 0;
-      bool ok = true;
-      if (bc != INT32_MAX) {
-        gcut = bconn - sA;
-      } else if (nU > 0) {
-        bc = a.U[h_rebalance(a.seed, st->level, st->t, v) % (uint64_t)nU];
-        gcut = (a.obj ? -conn_T(tab, a.topo, gl, bc) : 0) - sA;
-      } else {
-        ok = false;
-      }
-      if (ok) {
-        const int32_t bk = loss_bucket(gcut);
-        dest[v] = bc;
-        bkt[v] = (uint8_t)bk;
-        atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
-      }
-      elig[v] = ok ? 1 : 0;
-    }
-    __syncthreads();
+    reb_hub_decide(tab, a, kc, gl, v, A, g.vw[v], dest, bkt, elig, st, sbb, sbc);
   }
 }
+
+// Connectivity-table kernels over the rows of degree > kMidDeg, spread over
+// CTAs by chunk tickets (the table over the PE codes does not grow with the
+// degree; the work does).  A row of at most split_deg entries is rated whole
+// by the CTA that draws the chunk holding its first entry.  A larger row is
+// rated in two launches: every chunk adds the conn of its entries into the
+// row's global partial table, then one CTA per row reads the table back
+// (emptying it), adds the level group sums and decides.  The policy P gives
+// the table width, whether group sums are needed, which vertices take part
+// and the decision.
+struct LpHubPolicy {  // Alg. 4 step 1
+  const int32_t* pi;
+  uint8_t* lock;
+  int32_t* pp;
+  int64_t* gain;
+  uint8_t* inx;
+  Topo topo;
+  GroupLayout gl;
+  LpFilter flt;
+  const RefineState* st;
+  __device__ bool run() const { return kind_is(st, 1 << KIND_LP); }
+  __device__ const Topo& topo_of() const { return topo; }
+  __device__ int32_t topo_kc() const { return topo.kc; }
+  __device__ int32_t words() const { return gl.total; }
+  __device__ bool groups() const { return true; }
+  __device__ bool want(int32_t v) const { return lock[v] == 0; }
+  // a locked vertex keeps its PE, and its lock ends with this step
+  __device__ void skip(int32_t v) const {
+    inx[v] = 0;
+    pp[v] = pi[v];
+    gain[v] = 0;
+    lock[v] = 0;
+  }
+  __device__ void decide(const int32_t* tab, int32_t v, int32_t cv, int64_t* sb, int32_t* sc) const {
+    lp_hub_decide(tab, topo, gl, flt, v, pi[v], pp, gain, inx, sb, sc);
+  }
+};
+struct RebHubPolicy {  // rebalancing selection
+  const int32_t* pi;
+  const int32_t* vw;
+  RebArgs a;
+  GroupLayout gl;
+  int32_t* dest;
+  uint8_t* bkt;
+  uint8_t* elig;
+  const RefineState* st;
+  __device__ bool run() const { return kind_is(st, (1 << KIND_WEAK) | (1 << KIND_STRONG)); }
+  __device__ const Topo& topo_of() const { return a.topo; }
+  __device__ int32_t topo_kc() const { return a.topo.kc; }
+  __device__ int32_t words() const { return a.obj ? gl.total : a.topo.kc; }
+  __device__ bool groups() const { return a.obj != 0; }
+  __device__ bool want(int32_t v) const { return reb_eligible(a, pi[v], vw[v]); }
+  __device__ void skip(int32_t v) const { elig[v] = 0; }
+  __device__ void decide(const int32_t* tab, int32_t v, int32_t cv, int64_t* sb, int32_t* sc) const {
+    reb_hub_decide(tab, a, a.topo.kc, gl, v, pi[v], cv, dest, bkt, elig, st, sb, sc);
+  }
+};
+
+template <class P>
+__global__ void __launch_bounds__(kHiThreads) k_hub_tab(GraphView g, HubRows hr, P pol, int64_t split_deg,
+                                                        const int32_t* __restrict__ sidx, int32_t* gtab,
+                                                        unsigned long long* ctr) {
+  extern __shared__ int32_t tab[];
+  __shared__ int64_t sb[32];
+  __shared__ int32_t sc[32];
+  __shared__ int64_t s_ch;
+  if (!pol.run()) return;
+  const int32_t words = pol.words(), kc = pol.topo_kc();
+  for (int32_t b = threadIdx.x; b < words; b += blockDim.x) tab[b] = 0;
+  __syncthreads();
+  const int64_t m_hub = hr.pre[hr.n_huge];
+  for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
+      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
+      if (rb >= ce) break;
+      const bool split = re - rb > split_deg;
+      if (!split && rb < cb) continue;  // rated whole by the chunk of its first entry
+      const int32_t v = hr.hi[hr.huge[r]];
+      const bool w = pol.want(v);
+      __syncthreads();  // every thread has read what want() reads before skip() writes it
+      if (!w) {
+        if (!split && threadIdx.x == 0) pol.skip(v);
+        continue;
+      }
+      const int64_t x0 = g.xadj[v] - rb;
+      if (!split) {
+        conn_add(g, x0 + rb, x0 + re, pol.pi, tab);
+        __syncthreads();
+        if (pol.groups()) conn_groups(pol.topo_of(), pol.gl, tab);
+        pol.decide(tab, v, g.vw[v], sb, sc);
+      } else {
+        conn_add(g, x0 + max(rb, cb), x0 + min(re, ce), pol.pi, tab);
+        __syncthreads();
+        int32_t* G = gtab + (int64_t)sidx[r] * kc;
+        for (int32_t b = threadIdx.x; b < kc; b += blockDim.x)
+          if (tab[b]) atomicAdd(&G[b], tab[b]);
+        __syncthreads();
+      }
+      for (int32_t b = threadIdx.x; b < words; b += blockDim.x) tab[b] = 0;
+      __syncthreads();
+    }
+  }
+  leave_chunks(ctr);
+}
+
+// The larger rows, one CTA each (tickets): the summed table, then the decision.
+template <class P>
+__global__ void __launch_bounds__(kHiThreads) k_hub_tab_finish(GraphView g, HubRows hr, P pol,
+                                                               const int32_t* __restrict__ split, int32_t n_split,
+                                                               int32_t* gtab, unsigned long long* ctr) {
+  extern __shared__ int32_t tab[];
+  __shared__ int64_t sb[32];
+  __shared__ int32_t sc[32];
+  __shared__ int64_t s_j;
+  if (!pol.run()) return;
+  const int32_t words = pol.words(), kc = pol.topo_kc();
+  for (int32_t b = threadIdx.x; b < words; b += blockDim.x) tab[b] = 0;
+  __syncthreads();
+  for (int64_t j = next_chunk(ctr, &s_j); j < n_split; j = next_chunk(ctr, &s_j)) {
+    const int32_t v = hr.hi[hr.huge[split[j]]];
+    const bool w = pol.want(v);
+    __syncthreads();
+    if (!w) {  // nothing was added to its table
+      if (threadIdx.x == 0) pol.skip(v);
+      continue;
+    }
+    int32_t* G = gtab + j * kc;
+    for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) {
+      tab[b] = G[b];
+      G[b] = 0;
+    }
+    __syncthreads();
+    if (pol.groups()) conn_groups(pol.topo_of(), pol.gl, tab);
+    pol.decide(tab, v, g.vw[v], sb, sc);
+    for (int32_t b = threadIdx.x; b < words; b += blockDim.x) tab[b] = 0;
+    __syncthreads();
+  }
+  leave_chunks(ctr);
+}
+
 
 // Compaction stores for the sort inputs.
 struct LoadFlag2 {
@@ -1748,6 +1920,24 @@ inline unsigned mid_grid(Ctx& c, const void* fn, size_t smem, int64_t n_hi) {
 inline bool mid_tables(const Ctx& c) { return group_layout(c.topo).total <= kMidTableMax; }
 inline size_t mid_table_smem(int32_t words) { return (size_t)kMidWarps * words * sizeof(int32_t); }
 
+// The two launches of a hub table kernel (the second only for rows summed
+// over chunks), each one wave of resident CTAs drawing tickets.
+template <class P>
+void launch_hub_tab(Ctx& c, Level& L, const P& pol, size_t smem) {
+  const void* f1 = (const void*)k_hub_tab<P>;
+  const int64_t r1 = (int64_t)c.num_sms * c.resident_blocks(f1, kHiThreads, smem);
+  k_hub_tab<P><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, r1)), kHiThreads, smem, c.st>>>(
+      view(L), hub_rows(L), pol, L.hub_split_deg, L.hub_sidx, L.hub_gtab, c.hub_ctr);
+  count_launch();
+  if (L.n_split) {
+    const void* f2 = (const void*)k_hub_tab_finish<P>;
+    const int64_t r2 = (int64_t)c.num_sms * c.resident_blocks(f2, kHiThreads, smem);
+    k_hub_tab_finish<P><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_split, r2)), kHiThreads, smem, c.st>>>(
+        view(L), hub_rows(L), pol, L.hub_split, L.n_split, L.hub_gtab, c.hub_ctr);
+    count_launch();
+  }
+}
+
 // J of the current mapping of a level; with `ec`, the last block of the
 // low-degree pass also takes the Alg. 6 decision (the high-degree pass runs
 // first so that J is complete then).
@@ -1821,8 +2011,13 @@ void launch_lp(Ctx& c, int lvl) {
   if (ng) {
     const int64_t me = mid_tab ? L.m_huge : L.m_hi;
     ev = c.prof_begin();
-    k_lp_gain_high<<<std::max(1, std::min(ng, c.num_sms * 8)), kHiThreads, conn_smem(c), c.st>>>(
-        view(L), L.hi, gsel, ng, L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state); count_launch();
+    if (mid_tab) {
+      const LpHubPolicy pol{L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state};
+      launch_hub_tab(c, L, pol, (size_t)glay.total * sizeof(int32_t));
+    } else {
+      k_lp_gain_high<<<std::max(1, std::min(ng, c.num_sms * 8)), kHiThreads, conn_smem(c), c.st>>>(
+          view(L), L.hi, gsel, ng, L.pi, c.lock, c.pp, c.gain, c.inx, c.topo, glay, flt, c.state); count_launch();
+    }
     c.prof_end(ev, PK_LP_GAIN_HIGH, 26 * (int64_t)ng + 12 * me);
   }
   ev = c.prof_begin();
@@ -1866,9 +2061,12 @@ void launch_rebalance(Ctx& c, int lvl, bool prep_done = false) {
           view(L), L.hi, L.n_hi, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state); count_launch();
     }
     const int32_t ng = mid_tab ? L.n_huge : L.n_hi;
-    if (ng) {
+    if (ng && mid_tab) {
+      const RebHubPolicy pol{L.pi, L.vw, a, gl, c.dest, bucket, c.elig, c.state};
+      launch_hub_tab(c, L, pol, smem);
+    } else if (ng) {
       k_reb_select_high<<<std::max(1, std::min(ng, c.num_sms * 8)), kHiThreads, smem, c.st>>>(
-          view(L), L.hi, mid_tab ? L.huge : nullptr, ng, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state);
+          view(L), L.hi, nullptr, ng, L.pi, a, c.topo.kc, gl, c.dest, bucket, c.elig, c.state);
       count_launch();
     }
   }
@@ -3631,6 +3829,24 @@ __global__ void k_hub_chunks(int32_t n_huge, const int64_t* __restrict__ pre, in
   }
 }
 
+struct LoadSplit {
+  const int32_t* hi;
+  const int32_t* huge;
+  const int64_t* xadj;
+  __device__ int64_t operator()(int64_t j) const {
+    const int32_t v = hi[huge[j]];
+    return xadj[v + 1] - xadj[v] > kSplitDeg ? 1 : 0;
+  }
+};
+struct StoreSplit {
+  int32_t* sidx;
+  int32_t* list;
+  __device__ void operator()(int64_t j, int64_t e, int64_t x) const {
+    sidx[j] = x ? (int32_t)e : -1;
+    if (x) list[e] = (int32_t)j;
+  }
+};
+
 struct LoadHubDeg {
   const int32_t* hi;
   const int32_t* huge;
@@ -3640,6 +3856,13 @@ struct LoadHubDeg {
     return xadj[v + 1] - xadj[v];
   }
 };
+
+// one device value read back through the context's pinned block (slot 5)
+int64_t read_i64_at(Ctx& c, const int64_t* d) {
+  GM_CUDA(cudaMemcpyAsync(c.h_small + 5, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaStreamSynchronize(c.st));
+  return c.h_small[5];
+}
 
 // The flattened entries of the rows of degree > kMidDeg (in huge[] order)
 // and their chunk map, so that kernels can spread those rows over CTAs.
@@ -3668,6 +3891,26 @@ void prepare_hubs(Ctx& c, Level& L) {
   k_hub_chunks<<<grid_for(c, kThreads, L.n_huge), kThreads, 0, c.st>>>(L.n_huge, L.hub_pre, L.hub_chunk);
   count_launch();
   L.n_hub_chunks = nch;
+  // the rows whose PE-code tables are summed over chunks
+  if (!L.hub_sidx) L.hub_sidx = c.mem.make<int32_t>((size_t)std::max(1, L.n));
+  if (!L.hub_split) L.hub_split = c.mem.make<int32_t>((size_t)std::max(1, L.n));
+  scan(LoadSplit{L.hi, L.huge, L.xadj}, StoreSplit{L.hub_sidx, L.hub_split}, L.n_huge, nullptr, c.scan, c.st);
+  int64_t ns = read_i64_at(c, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n_huge)));
+  const int64_t need = ns * c.topo.kc;
+  if (need * (int64_t)sizeof(int32_t) > kSplitTableBytes) {
+    ns = 0;  // too many: every row is rated whole
+    L.hub_split_deg = INT64_MAX;
+  } else {
+    L.hub_split_deg = kSplitDeg;
+  }
+  L.n_split = (int32_t)ns;
+  if (ns && L.hub_gtab_cap < need) {
+    drop_graph(L);
+    if (L.hub_gtab) c.mem.put(L.hub_gtab);
+    L.hub_gtab_cap = need;
+    L.hub_gtab = c.mem.make<int32_t>((size_t)need);
+    GM_CUDA(cudaMemsetAsync(L.hub_gtab, 0, (size_t)need * sizeof(int32_t), c.st));
+  }
 }
 }  // namespace
 
