@@ -1443,7 +1443,8 @@ void free_level(Ctx& c, Level& L) {
   L.cgexec = nullptr;
   for (void* p : {(void*)L.xadj, (void*)L.adj, (void*)L.adjw, (void*)L.vw, (void*)L.pi, (void*)L.hi,
                   (void*)L.huge, (void*)L.hi_off, (void*)L.M, (void*)L.hub_pre, (void*)L.hub_chunk,
-                  (void*)L.hub_part, (void*)L.hub_sidx, (void*)L.hub_split, (void*)L.hub_gtab})
+                  (void*)L.hub_part, (void*)L.hub_sidx, (void*)L.hub_split, (void*)L.hub_gtab,
+                  (void*)L.hub_acc})
     if (p) c.mem.put(p);
   L = Level{};
 }

@@ -101,6 +101,7 @@ struct Level {
   // chunks (LP gains, rebalancing selection): per huge[] row its index among
   // them (-1: rated whole), their list, and n_split x kc partial tables (zero
   // between uses)
+  int64_t* hub_acc = nullptr;    // per huge[] row: a sum over chunks (zero between uses)
   int32_t* hub_sidx = nullptr;
   int32_t* hub_split = nullptr;
   int32_t* hub_gtab = nullptr;

@@ -57,7 +57,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t* __re
 }
 
 // Stable scatter: within a tile, items are ordered (warp, item, lane), which is
-// the global index order; ranks among equal digits follow that order.
+// the global index order; ranks among equal digits follow that order.  The
+// tile is first placed in digit order in shared memory, then written out so
+// that consecutive threads write consecutive positions of a digit's run
+// (coalesced stores instead of one scattered store per item).
+constexpr size_t kScatterSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(int32_t));
+static_assert(kSortThreads == 256, "one digit per thread in the tile's digit scan");
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* __restrict__ kin,
                                                                const int32_t* __restrict__ vin,
                                                                uint64_t* __restrict__ kout,
@@ -65,8 +70,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
                                                                const int64_t* d_n, int shift,
                                                                const int64_t* __restrict__ hist_off,
                                                                int64_t max_tiles, int64_t skip_upto) {
+  extern __shared__ __align__(16) unsigned char scatter_raw[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(scatter_raw);      // [kSortTile]
+  int32_t* sv = reinterpret_cast<int32_t*>(sk + kSortTile);      // [kSortTile]
   __shared__ int32_t wcnt[kSortWarps][256];
   __shared__ int64_t goff[256];
+  __shared__ int32_t tstart[256];
+  __shared__ int32_t sm32[33];
   const int64_t n = load_count(d_n, max_n);
   if (n <= skip_upto) return;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -97,6 +107,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
     rank[j] = valid ? r : -1;
   }
   __syncthreads();
+  // per digit: the warps' offsets within the digit, and the digit's count
+  int32_t dcount = 0;
   for (int d = threadIdx.x; d < 256; d += kSortThreads) {
     int32_t run = 0;
 #pragma unroll
@@ -105,16 +117,29 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
       wcnt[ww][d] = run;
       run += t;
     }
+    dcount = run;
   }
+  // digit starts within the tile (kSortThreads == 256: one digit per thread)
+  int32_t total;
+  const int32_t ex = block_exclusive_scan(dcount, sm32, &total);
+  tstart[threadIdx.x] = ex;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kSortItems; j++) {
     if (rank[j] >= 0) {
-      int d = (int)((k[j] >> shift) & 255u);
-      int64_t pos = goff[d] + wcnt[w][d] + rank[j];
-      kout[pos] = k[j];
-      vout[pos] = v[j];
+      const int d = (int)((k[j] >> shift) & 255u);
+      const int p = tstart[d] + wcnt[w][d] + rank[j];
+      sk[p] = k[j];
+      sv[p] = v[j];
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < total; i += kSortThreads) {
+    const uint64_t key = sk[i];
+    const int d = (int)((key >> shift) & 255u);
+    const int64_t pos = goff[d] + (i - tstart[d]);
+    kout[pos] = key;
+    vout[pos] = sv[i];
   }
 }
 
@@ -153,6 +178,7 @@ void sort_init() {
   const unsigned long long bit = 1ULL << (dev & 63);
   if (done.load() & bit) return;
   cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_sort_smem());
+  cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
   done.fetch_or(bit);
 }
 
@@ -181,7 +207,7 @@ static void sort_passes(SortBufs& b, int64_t max_n, const int64_t* d_n, int bits
   for (int shift = 0; shift < bits; shift += 8) {
     k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], max_n, d_n, shift, b.hist, tiles, skip); count_launch();
     scan(LoadI64{b.hist}, StoreExcl{b.hist_off}, 256 * tiles, nullptr, b.scan, st);
-    k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(b.key[cur], b.val[cur], b.key[cur ^ 1],
+    k_sort_scatter<<<(unsigned)tiles, kSortThreads, kScatterSmem, st>>>(b.key[cur], b.val[cur], b.key[cur ^ 1],
                                                              b.val[cur ^ 1], max_n, d_n, shift, b.hist_off,
                                                              tiles, skip); count_launch();
     cur ^= 1;

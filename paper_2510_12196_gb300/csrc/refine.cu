@@ -755,30 +755,53 @@ __global__ void __launch_bounds__(kMidThreads) k_lp_after_mid(GraphView g, const
   }
 }
 
-__global__ void __launch_bounds__(kHiThreads) k_lp_after_high(GraphView g, const int32_t* __restrict__ hi,
-                                                              const int32_t* __restrict__ sel, int32_t n_sel,
-                                                              const int32_t* __restrict__ pi,
-                                                              const int32_t* __restrict__ pp,
-                                                              const int64_t* __restrict__ gain,
-                                                              const uint8_t* __restrict__ inx, uint8_t* lock,
-                                                              Topo topo, const RefineState* st) {
+// Alg. 4 step 2 for the vertices of degree > kMidDeg in X: their entries,
+// flattened in huge[] order, in chunks drawn by the CTAs of one wave; each
+// chunk adds its part of a row's recomputed gain into the row's accumulator,
+// and k_lp_after_hub_finish sets the locks (the moves that stay
+// non-negative) and clears the accumulators.
+__global__ void __launch_bounds__(kHiThreads) k_lp_after_hub(GraphView g, HubRows hr, const int32_t* __restrict__ pi,
+                                                             const int32_t* __restrict__ pp,
+                                                             const int64_t* __restrict__ gain,
+                                                             const uint8_t* __restrict__ inx, int64_t* acc, Topo topo,
+                                                             const RefineState* st, unsigned long long* ctr) {
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
+  __shared__ int64_t s_ch;
   if (!kind_is(st, 1 << KIND_LP)) return;
   load_sdist(sdist, topo);
   __syncthreads();
-  for (int32_t i = blockIdx.x; i < n_sel; i += gridDim.x) {
-    const int32_t v = hi_vertex(hi, sel, i);
-    if (!inx[v]) continue;
-    const int32_t p = pi[v], q = pp[v];
-    const int64_t gv = gain[v];
-    int64_t s = 0;
-    for (int64_t e = g.xadj[v] + threadIdx.x; e < g.xadj[v + 1]; e += blockDim.x) {
-      const int32_t b = future_block(g.adj[e], v, gv, pi, pp, gain, inx);
-      s += (int64_t)g.adjw[e] * (dcode(sdist, p, b) - dcode(sdist, q, b));
+  const int64_t m_hub = hr.pre[hr.n_huge];
+  for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
+      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
+      if (rb >= ce) break;
+      const int32_t v = hr.hi[hr.huge[r]];
+      if (!inx[v]) continue;
+      const int32_t p = pi[v], q = pp[v];
+      const int64_t gv = gain[v];
+      const int64_t x0 = g.xadj[v] - rb;
+      int64_t s = 0;
+      for (int64_t e = x0 + max(rb, cb) + threadIdx.x; e < x0 + min(re, ce); e += blockDim.x) {
+        const int32_t b = future_block(g.adj[e], v, gv, pi, pp, gain, inx);
+        s += (int64_t)g.adjw[e] * (dcode(sdist, p, b) - dcode(sdist, q, b));
+      }
+      s = block_sum(s, sm);
+      if (threadIdx.x == 0 && s) atomicAdd((unsigned long long*)&acc[r], (unsigned long long)s);
     }
-    s = block_sum(s, sm);
-    if (threadIdx.x == 0 && s >= 0) lock[v] = 1;
+  }
+  leave_chunks(ctr);
+}
+
+__global__ void k_lp_after_hub_finish(HubRows hr, const uint8_t* __restrict__ inx, int64_t* acc, uint8_t* lock,
+                                      const RefineState* st) {
+  if (!kind_is(st, 1 << KIND_LP)) return;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < hr.n_huge; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = hr.hi[hr.huge[r]];
+    if (!inx[v]) continue;
+    if (acc[r] >= 0) lock[v] = 1;
+    acc[r] = 0;
   }
 }
 
@@ -1318,6 +1341,8 @@ __global__ void __launch_bounds__(kHiThreads) k_reb_select_high(GraphView g, con
 // the table width, whether group sums are needed, which vertices take part
 // and the decision.
 struct LpHubPolicy {  // Alg. 4 step 1
+  // skip() clears the lock that want() reads: a barrier between them
+  static constexpr bool kWantBarrier = true;
   const int32_t* pi;
   uint8_t* lock;
   int32_t* pp;
@@ -1345,6 +1370,7 @@ struct LpHubPolicy {  // Alg. 4 step 1
   }
 };
 struct RebHubPolicy {  // rebalancing selection
+  static constexpr bool kWantBarrier = false;
   const int32_t* pi;
   const int32_t* vw;
   RebArgs a;
@@ -1387,7 +1413,7 @@ __global__ void __launch_bounds__(kHiThreads) k_hub_tab(GraphView g, HubRows hr,
       if (!split && rb < cb) continue;  // rated whole by the chunk of its first entry
       const int32_t v = hr.hi[hr.huge[r]];
       const bool w = pol.want(v);
-      __syncthreads();  // every thread has read what want() reads before skip() writes it
+      if (P::kWantBarrier) __syncthreads();  // every thread has read what want() reads before skip() writes it
       if (!w) {
         if (!split && threadIdx.x == 0) pol.skip(v);
         continue;
@@ -1429,7 +1455,7 @@ __global__ void __launch_bounds__(kHiThreads) k_hub_tab_finish(GraphView g, HubR
   for (int64_t j = next_chunk(ctr, &s_j); j < n_split; j = next_chunk(ctr, &s_j)) {
     const int32_t v = hr.hi[hr.huge[split[j]]];
     const bool w = pol.want(v);
-    __syncthreads();
+    if (P::kWantBarrier) __syncthreads();
     if (!w) {  // nothing was added to its table
       if (threadIdx.x == 0) pol.skip(v);
       continue;
@@ -1993,7 +2019,6 @@ void launch_lp(Ctx& c, int lvl) {
   // vertices of degree > kLowDeg left to the CTA-per-vertex kernels
   const int32_t* gsel = mid_tab ? L.huge : nullptr;
   const int32_t ng = mid_tab ? L.n_huge : L.n_hi;
-  const unsigned gh = std::max(1, std::min(L.n_huge, c.num_sms * 8));
   c.prof_level = lvl;
   cudaEvent_t ev = c.prof_begin();
   const LpFilter flt{c.cfg.lp_relax_num, c.cfg.lp_relax_den};
@@ -2028,9 +2053,15 @@ void launch_lp(Ctx& c, int lvl) {
     k_lp_after_mid<<<mid_grid(c, (const void*)k_lp_after_mid, 0, L.n_hi), kMidThreads, 0, c.st>>>(
         view(L), L.hi, L.n_hi, L.pi, c.pp, c.gain, c.inx, c.lock, c.topo, c.state); count_launch();
   }
-  if (L.n_huge)
-    k_lp_after_high<<<gh, kHiThreads, 0, c.st>>>(view(L), L.hi, L.huge, L.n_huge, L.pi, c.pp, c.gain, c.inx, c.lock,
-                                                 c.topo, c.state); count_launch();
+  if (L.n_huge) {
+    const int64_t res = (int64_t)c.num_sms * c.resident_blocks((const void*)k_lp_after_hub, kHiThreads, 0);
+    k_lp_after_hub<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, res)), kHiThreads, 0, c.st>>>(
+        view(L), hub_rows(L), L.pi, c.pp, c.gain, c.inx, L.hub_acc, c.topo, c.state, c.hub_ctr);
+    count_launch();
+    k_lp_after_hub_finish<<<grid_for(c, kThreads, L.n_huge), kThreads, 0, c.st>>>(hub_rows(L), c.inx, L.hub_acc,
+                                                                                c.lock, c.state);
+    count_launch();
+  }
   launch_delta(c, lvl, LpMoves{c.lock, c.pp}, KIND_LP);
   k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.state); count_launch();
 }
@@ -3891,6 +3922,10 @@ void prepare_hubs(Ctx& c, Level& L) {
   k_hub_chunks<<<grid_for(c, kThreads, L.n_huge), kThreads, 0, c.st>>>(L.n_huge, L.hub_pre, L.hub_chunk);
   count_launch();
   L.n_hub_chunks = nch;
+  if (!L.hub_acc) {
+    L.hub_acc = c.mem.make<int64_t>((size_t)std::max(1, L.n));
+    GM_CUDA(cudaMemsetAsync(L.hub_acc, 0, (size_t)std::max(1, L.n) * sizeof(int64_t), c.st));
+  }
   // the rows whose PE-code tables are summed over chunks
   if (!L.hub_sidx) L.hub_sidx = c.mem.make<int32_t>((size_t)std::max(1, L.n));
   if (!L.hub_split) L.hub_split = c.mem.make<int32_t>((size_t)std::max(1, L.n));
