@@ -1049,108 +1049,129 @@ __global__ void __launch_bounds__(kThreads) k_reb_select_low(GraphView g, const 
   }
   auto tile = cg::tiled_partition<kSubWarp>(cg::this_thread_block());
   const int lane = tile.thread_rank();
-  const int64_t nsw = ((int64_t)gridDim.x * blockDim.x) / kSubWarp;
+  const int wl = threadIdx.x & 31, sub = wl / kSubWarp;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t sigma = a.cnt[CNT_SIGMA];
   const int64_t nU = a.cnt[CNT_NU];
   const int32_t level = st->level, t = st->t;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSubWarp; v < g.n; v += nsw) {
-    const int64_t beg = g.xadj[v];
-    const int deg = (int)(g.xadj[v + 1] - beg);
-    if (deg > kLowDeg) continue;
-    const int32_t A = pi[v];
-    if (!reb_eligible(a, A, g.vw[v])) {
-      if (lane == 0) elig[v] = 0;
-      continue;
-    }
-    int32_t c[kSlots], w[kSlots];
-    int32_t connA = 0;
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) {
-      const int idx = lane + kSubWarp * r;
-      if (idx < deg) {
-        c[r] = pi[g.adj[beg + idx]];
-        w[r] = g.adjw[beg + idx];
-      } else {
-        c[r] = A;
-        w[r] = 0;
-      }
-      if (c[r] == A) connA += w[r];
-    }
-    connA = tile_sum32(tile, connA);
-    // score of each slot's block: conn(v, q), or -T(q) for the J gains (only
-    // destinations below sigma are candidates)
-    int64_t cc[kSlots];
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) cc[r] = 0;
-    const int rows = (deg + kSubWarp - 1) / kSubWarp;
-    for (int rr = 0; rr < rows; rr++) {
-      const int32_t crr = pick(c, rr);
-      const int32_t wrr = pick(w, rr);
-      for (int j = 0; j < kSubWarp; j++) {
-        const int32_t cs = tile.shfl(crr, j);
-        const int32_t ws = tile.shfl(wrr, j);
-        if (a.obj) {
-#pragma unroll
-          for (int r = 0; r < kSlots; r++) cc[r] -= (int64_t)ws * dcode(sdist, c[r], cs);
-        } else {
-#pragma unroll
-          for (int r = 0; r < kSlots; r++) cc[r] += (c[r] == cs) ? ws : 0;
-        }
+  // 32 vertices per warp: each lane checks its vertex's eligibility (most
+  // are not: their blocks are not overloaded), then the eligible ones are
+  // served four at a time by the 8-lane sub-warps
+  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < g.n; base += nwarps * 32) {
+    const int64_t vl = base + wl;
+    bool want = false;
+    int64_t beg_l = 0;
+    int deg_l = 0;
+    int32_t A_l = 0;
+    if (vl < g.n) {
+      beg_l = g.xadj[vl];
+      deg_l = (int)(g.xadj[vl + 1] - beg_l);
+      if (deg_l <= kLowDeg) {
+        A_l = pi[vl];
+        want = reb_eligible(a, A_l, g.vw[vl]);
+        if (!want) elig[vl] = 0;
       }
     }
-    bool found = false;
-    int64_t bconn = 0;
-    int32_t bc = INT32_MAX;
-#pragma unroll
-    for (int r = 0; r < kSlots; r++) {
-      if (c[r] == A || a.W[c[r]] > sigma) continue;
-      if (!found || cc[r] > bconn || (cc[r] == bconn && c[r] < bc)) {
-        bconn = cc[r];
-        bc = c[r];
-        found = true;
-      }
-    }
-#pragma unroll
-    for (int o = kSubWarp / 2; o > 0; o >>= 1) {
-      const int64_t ob = tile.shfl_xor(bconn, o);
-      const int32_t oc = tile.shfl_xor(bc, o);
-      const bool of = tile.shfl_xor(found, o);
-      if (of && (!found || ob > bconn || (ob == bconn && oc < bc))) {
-        bconn = ob;
-        bc = oc;
-        found = true;
-      }
-    }
-    // the source block's score, and the drawn block's when no neighbour qualifies
-    int64_t sA = connA, sR = 0;
-    int32_t qr = -1;
-    if (!found && nU > 0) qr = a.U[h_rebalance(a.seed, level, t, (int32_t)v) % (uint64_t)nU];
-    if (a.obj) {
-      int64_t pa = 0, pr = 0;
+    const unsigned work = __ballot_sync(0xffffffffu, want);
+    const int rounds = (__popc(work) + 3) / 4;
+    for (int rnd = 0; rnd < rounds; rnd++) {
+      const int src = tile_worker(work, rnd, sub);
+      const int s2 = src < 0 ? 0 : src;
+      const int64_t v = base + s2;
+      const int64_t beg = __shfl_sync(0xffffffffu, beg_l, s2);
+      const int deg = __shfl_sync(0xffffffffu, deg_l, s2);
+      const int32_t A = __shfl_sync(0xffffffffu, A_l, s2);
+      if (src < 0) continue;
+      int32_t c[kSlots], w[kSlots];
+      int32_t connA = 0;
 #pragma unroll
       for (int r = 0; r < kSlots; r++) {
-        pa -= (int64_t)w[r] * dcode(sdist, A, c[r]);
-        if (qr >= 0) pr -= (int64_t)w[r] * dcode(sdist, qr, c[r]);
+        const int idx = lane + kSubWarp * r;
+        if (idx < deg) {
+          c[r] = pi[g.adj[beg + idx]];
+          w[r] = g.adjw[beg + idx];
+        } else {
+          c[r] = A;
+          w[r] = 0;
+        }
+        if (c[r] == A) connA += w[r];
       }
-      sA = tile_sum64(tile, pa);
-      sR = tile_sum64(tile, pr);
-    }
-    if (lane == 0) {
-      int64_t gcut;
-      if (found) {
-        gcut = bconn - sA;
-      } else if (qr >= 0) {
-        bc = qr;
-        gcut = sR - sA;
-      } else {
-        elig[v] = 0;
-        continue;
+      connA = tile_sum32(tile, connA);
+      // score of each slot's block: conn(v, q), or -T(q) for the J gains (only
+      // destinations below sigma are candidates)
+      int64_t cc[kSlots];
+#pragma unroll
+      for (int r = 0; r < kSlots; r++) cc[r] = 0;
+      const int rows = (deg + kSubWarp - 1) / kSubWarp;
+      for (int rr = 0; rr < rows; rr++) {
+        const int32_t crr = pick(c, rr);
+        const int32_t wrr = pick(w, rr);
+        for (int j = 0; j < kSubWarp; j++) {
+          const int32_t cs = tile.shfl(crr, j);
+          const int32_t ws = tile.shfl(wrr, j);
+          if (a.obj) {
+#pragma unroll
+            for (int r = 0; r < kSlots; r++) cc[r] -= (int64_t)ws * dcode(sdist, c[r], cs);
+          } else {
+#pragma unroll
+            for (int r = 0; r < kSlots; r++) cc[r] += (c[r] == cs) ? ws : 0;
+          }
+        }
       }
-      const int32_t bk = loss_bucket(gcut);
-      dest[v] = bc;
-      bkt[v] = (uint8_t)bk;
-      elig[v] = 1;
-      atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
+      bool found = false;
+      int64_t bconn = 0;
+      int32_t bc = INT32_MAX;
+#pragma unroll
+      for (int r = 0; r < kSlots; r++) {
+        if (c[r] == A || a.W[c[r]] > sigma) continue;
+        if (!found || cc[r] > bconn || (cc[r] == bconn && c[r] < bc)) {
+          bconn = cc[r];
+          bc = c[r];
+          found = true;
+        }
+      }
+#pragma unroll
+      for (int o = kSubWarp / 2; o > 0; o >>= 1) {
+        const int64_t ob = tile.shfl_xor(bconn, o);
+        const int32_t oc = tile.shfl_xor(bc, o);
+        const bool of = tile.shfl_xor(found, o);
+        if (of && (!found || ob > bconn || (ob == bconn && oc < bc))) {
+          bconn = ob;
+          bc = oc;
+          found = true;
+        }
+      }
+      // the source block's score, and the drawn block's when no neighbour qualifies
+      int64_t sA = connA, sR = 0;
+      int32_t qr = -1;
+      if (!found && nU > 0) qr = a.U[h_rebalance(a.seed, level, t, (int32_t)v) % (uint64_t)nU];
+      if (a.obj) {
+        int64_t pa = 0, pr = 0;
+#pragma unroll
+        for (int r = 0; r < kSlots; r++) {
+          pa -= (int64_t)w[r] * dcode(sdist, A, c[r]);
+          if (qr >= 0) pr -= (int64_t)w[r] * dcode(sdist, qr, c[r]);
+        }
+        sA = tile_sum64(tile, pa);
+        sR = tile_sum64(tile, pr);
+      }
+      if (lane == 0) {
+        int64_t gcut;
+        if (found) {
+          gcut = bconn - sA;
+        } else if (qr >= 0) {
+          bc = qr;
+          gcut = sR - sA;
+        } else {
+          elig[v] = 0;
+          continue;
+        }
+        const int32_t bk = loss_bucket(gcut);
+        dest[v] = bc;
+        bkt[v] = (uint8_t)bk;
+        elig[v] = 1;
+        atomicAdd((unsigned long long*)&a.tab[(int64_t)A * kBuckets + bk], (unsigned long long)(int64_t)g.vw[v]);
+      }
     }
   }
 }
