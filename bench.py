@@ -57,13 +57,13 @@ L2_FLUSH_BYTES = 512 << 20
 # profiles/k_match_prefer_rgg2e20_level0.md),
 # valid only while the kernel's source hash matches.
 TRAFFIC = {
-    ("rgg2d", "eval_J"): {"kernel": "k_eval_tile", "kernel_hash": "2b622cbccb68f6b2", "dram_bytes": 116894208,
+    ("rgg2d", "eval_J"): {"kernel": "k_eval_tile", "kernel_hash": "920bb3b5b48138c4", "dram_bytes": 116894208,
                "alg_bytes": 163348488, "dram_per_alg_byte": 116894208 / 163348488},
-    ("rgg2d", "lp_gain"): {"kernel": "k_lp_gain_tile", "kernel_hash": "75079966d06ef483", "dram_bytes": 120026880,
+    ("rgg2d", "lp_gain"): {"kernel": "k_lp_gain_tile", "kernel_hash": "6b701f37fb0860d6", "dram_bytes": 120026880,
                 "alg_bytes": 178028552, "dram_per_alg_byte": 120026880 / 178028552},
-    ("rgg2d", "cluster"): {"kernel": "k_cluster_tile", "kernel_hash": "c83ea5cbfe58bf26", "dram_bytes": 129711872,
-                "alg_bytes": 167542792, "dram_per_alg_byte": 129711872 / 167542792},
-    ("rgg2d", "match_prefer"): {"kernel": "k_match_prefer", "kernel_hash": "736b33187751ac30", "dram_bytes": 121675776,
+    ("rgg2d", "cluster"): {"kernel": "k_cluster_tile", "kernel_hash": "03b2663e5efeed5a", "dram_bytes": 129838592,
+                           "alg_bytes": 167542792, "dram_per_alg_byte": 129838592 / 167542792},
+    ("rgg2d", "match_prefer"): {"kernel": "k_match_prefer", "kernel_hash": "8f3c2a530fe7cd2d", "dram_bytes": 121675776,
                      "alg_bytes": 221992288, "dram_per_alg_byte": 121675776 / 221992288},
 }
 
@@ -281,16 +281,28 @@ def _code_only(src):
 def kernel_hash(kernel="k_eval_tile"):
     """Hash of the code (comments left out) of one kernel: its definition
     (launch bounds and body, from refine.cu, coarsen.cu or match.cu), the row
-    helper, the tile staging and common.cuh."""
+    helper, the tile-staging functions of tile.cuh that it calls, and
+    common.cuh."""
     import re
     csrc = os.path.join(ROOT, "paper_2510_12196_gb300", "csrc")
     text = "".join(open(os.path.join(csrc, f)).read() for f in ("refine.cu", "coarsen.cu", "match.cu"))
+    tile = open(os.path.join(csrc, "tile.cuh")).read()
+
+    def body(src, name):
+        m = re.search(r"\n[^\n]*\b" + name + r"\(.*?\n}\n", src, re.S)
+        return m.group(0) if m else ""
+
     h = hashlib.sha256()
-    for name in (kernel, "row_cost"):
-        m = re.search(r"\n[^\n]*\b" + name + r"\(.*?\n}\n", text, re.S)
-        h.update(_code_only(m.group(0) if m else "").encode())
-    for f in ("tile.cuh", "common.cuh"):
-        h.update(_code_only(open(os.path.join(csrc, f)).read()).encode())
+    kbody = body(text, kernel)
+    for part in (kbody, body(text, "row_cost")):
+        h.update(_code_only(part).encode())
+    # the staging helpers and constants of tile.cuh: constants always, each
+    # function only if the kernel names it
+    h.update(_code_only("\n".join(l for l in tile.split("\n") if l.startswith("constexpr"))).encode())
+    for fn in ("stage_tile", "stage_tile_packed", "tile_worker", "tile_worker_ranked"):
+        if re.search(r"\b" + fn + r"\b", kbody):
+            h.update(_code_only(body(tile, fn)).encode())
+    h.update(_code_only(open(os.path.join(csrc, "common.cuh")).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -193,23 +193,23 @@ struct GatherLabel {
 // row (at most kLowDeg entries) into its quarter of the warp's buffer.
 static_assert(kTileE / 4 >= kLowDeg, "a sub-warp's quarter of the staging buffer holds one low-degree row");
 __global__ void __launch_bounds__(kTileThreads, 9) k_cluster_tile(GraphView g, ClusterArgs a) {
-  __shared__ int32_t sc[kTileWarps][kTileE];
-  __shared__ int32_t sw[kTileWarps][kTileE];
+  __shared__ int2 scw[kTileWarps][kTileE];  // (label, weight) per staged entry
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane >> 3, sl = lane & 7;
   const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
   const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
   for (int64_t tile = (int64_t)blockIdx.x * kTileWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kTileWarps) {
-    const TileLane t = stage_tile(tg, tile * kTileV, lane, sc[warp], sw[warp], GatherLabel{a.C});
+    const TileLane t = stage_tile_packed(tg, tile * kTileV, lane, scw[warp], GatherLabel{a.C});
     const int deg = (int)(t.e - t.b);
     const bool low = t.v < g.n && deg <= kLowDeg;
     const bool active = low && cluster_active(a, (int32_t)t.v, deg);
     int32_t own = active ? a.C[t.v] : -1;
     if (low && !active) a.req[t.v] = -1;
     const unsigned work = __ballot_sync(0xffffffffu, active);
+    const int rank = __popc(work & ((1u << lane) - 1u));
     const int rounds = (__popc(work) + 3) / 4;
     for (int r = 0; r < rounds; r++) {
-      const int src = tile_worker(work, r, sub);
+      const int src = tile_worker_ranked(work, rank, r, sub, lane);
       const int s2 = src < 0 ? 0 : src;
       const int64_t vb = __shfl_sync(0xffffffffu, t.b, s2);
       int off = (int)(vb - t.E0);
@@ -219,14 +219,10 @@ __global__ void __launch_bounds__(kTileThreads, 9) k_cluster_tile(GraphView g, C
         off = sub * (kTileE / 4);
         __syncwarp();  // the previous round has read this quarter
         if (src >= 0)
-          for (int j = sl; j < dg; j += kSubWarp) {
-            sc[warp][off + j] = a.C[g.adj[vb + j]];
-            sw[warp][off + j] = g.adjw[vb + j];
-          }
+          for (int j = sl; j < dg; j += kSubWarp) scw[warp][off + j] = make_int2(a.C[g.adj[vb + j]], g.adjw[vb + j]);
         __syncwarp();
       }
-      const int32_t* c = sc[warp] + off;
-      const int32_t* w = sw[warp] + off;
+      const int2* cw = scw[warp] + off;
       // best (score, tie-hash, label) over this lane's candidates; the hash
       // of the current best is computed once, on the first tie
       int32_t bs = 0, bt = -1, so = 0;
@@ -234,11 +230,16 @@ __global__ void __launch_bounds__(kTileThreads, 9) k_cluster_tile(GraphView g, C
       bool bhk = false;
       if (src >= 0) {
         for (int j = sl; j < dg; j += kSubWarp) {
-          const int32_t cj = c[j];
-          so += (cj == ow) ? w[j] : 0;
+          const int2 xj = cw[j];
+          const int32_t cj = xj.x;
+          so += (cj == ow) ? xj.y : 0;
           if (cj == ow || cj == bt) continue;
           int32_t scj = 0;
-          for (int l = 0; l < dg; l++) scj += (c[l] == cj) ? w[l] : 0;
+#pragma unroll 4
+          for (int l = 0; l < dg; l++) {
+            const int2 x = cw[l];
+            scj += (x.x == cj) ? x.y : 0;
+          }
           if (bt < 0 || scj > bs) {
             bs = scj;
             bt = cj;

@@ -98,6 +98,55 @@ __device__ __forceinline__ TileLane stage_tile(const TileGraph& g, int64_t v0, i
   return t;
 }
 
+// As stage_tile, with each staged entry one 64-bit word (value, weight) in
+// scw: a scan over a staged row then costs one shared load per entry.
+template <int kTE = kTileE, class Gather>
+__device__ __forceinline__ TileLane stage_tile_packed(const TileGraph& g, int64_t v0, int lane, int2* scw,
+                                                      Gather gather) {
+  TileLane t;
+  t.v = v0 + lane;
+  const bool valid = t.v < g.n;
+  t.b = valid ? g.xadj[t.v] : 0;
+  t.e = valid ? g.xadj[t.v + 1] : 0;
+  const int last = (int)min((int64_t)31, (int64_t)g.n - 1 - v0);
+  t.E0 = __shfl_sync(0xffffffffu, t.b, 0);
+  const int64_t E1 = __shfl_sync(0xffffffffu, t.e, last);
+  const int64_t span = E1 - t.E0;
+  t.staged = span <= kTE;
+  if (t.staged) {
+    constexpr int kQ = kTE / 32;
+    int32_t u[kQ], w[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+      const int jj = q * 32 + lane;
+      u[q] = (jj < span) ? g.adj[t.E0 + jj] : 0;
+      w[q] = (jj < span) ? g.adjw[t.E0 + jj] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+      const int jj = q * 32 + lane;
+      if (jj < span) u[q] = gather(u[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+      const int jj = q * 32 + lane;
+      if (jj < span) scw[jj] = make_int2(u[q], w[q]);
+    }
+  }
+  __syncwarp();
+  return t;
+}
+
+// Worker of sub-warp `sub` in round r of a tile whose lanes with `work` set
+// are served four at a time in lane order: the lane of rank 4 r + sub among
+// the set bits (-1 if none).  `rank` is the lane's own rank among them.
+__device__ __forceinline__ int tile_worker_ranked(unsigned work, int rank, int round, int sub, int lane) {
+  const bool mine = ((work >> lane) & 1u) && (rank >> 2) == round;
+  unsigned m = __ballot_sync(0xffffffffu, mine);
+  for (int k = 0; k < sub && m; k++) m &= m - 1;
+  return m ? __ffs(m) - 1 : -1;
+}
+
 // Work queue of one warp tile: the lanes with `work` set are served four at a
 // time, one per 8-lane sub-warp.  For the r-th round, sub-warp s takes the
 // worker of rank 4r + s.  Returns the source lane of this lane's sub-warp
