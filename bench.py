@@ -536,7 +536,11 @@ def run_ours(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": config_of(w, {"levels": levels, "level_n": [st.n[i] for i in range(levels)],
-                                        "refine_rounds": [st.iters[i] for i in range(levels)]},
+                                        "refine_rounds": [st.iters[i] for i in range(levels)],
+                                        "schedule": {"mid_deg": [st.mid_deg[i] for i in range(levels)],
+                                                     "split_deg": [st.split_deg[i] for i in range(levels)],
+                                                     "autotuned": [st.tuned[i] for i in range(levels)],
+                                                     "tune_ms": st.ms_tune}},
                                     args.coarsener, args.initial, variant_settings(args)),
                 "edge_rounds_per_s": job_throughput(er * args.steps, ws, total_ms / 1000.0),
                 "J": Js[0], "e2e": e2e, "roofline": roof, "refine_round": refine_round, "cpu_baseline": cpu,

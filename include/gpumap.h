@@ -111,6 +111,13 @@ typedef struct {
   int32_t reb_objective; /* rebalancing gains: 0 (default): edge cut conn(v, q) - conn(v, P(v)), as the paper
                             settles on; 1: Eq. 1's J gain G_q(v) for the destination choice and the loss
                             buckets (the variant Section 4.2 reports trying) */
+  int32_t mid_deg;       /* per-vertex split: vertices of degree 33..mid_deg get one warp each, larger ones the
+                            hub kernels (chunks of their entries over the CTAs).  0 (default): chosen per
+                            level by the autotuner (timing 255, 128 and 64 on levels whose rows of degree
+                            > 32 hold at least 2^20 entries, else 255); 33..255: fixed */
+  int32_t split_deg;     /* hub rows of more entries than this sum per-chunk connectivity tables over CTAs,
+                            smaller ones are rated whole by one CTA.  0 (default): autotuned with mid_deg
+                            (4096, 2048, 16384; else 4096); > 0: fixed */
 } map_config;
 
 typedef struct {
@@ -123,6 +130,10 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int64_t device_bytes_peak; /* largest device memory the context has held */
   double ms_refine_level[65]; /* host wall time of Alg. 6 on each level (map_run; ends with a synchronisation) */
+  int32_t mid_deg[65];     /* per-vertex split in force on each level (map_config.mid_deg) */
+  int32_t split_deg[65];   /* hub split bound in force on each level (INT32_MAX: every hub row rated whole) */
+  int32_t tuned[65];       /* 1: chosen by the autotuner; 0: defaults or the config's */
+  double ms_tune;          /* host wall time the autotuner has spent on this context */
 } map_stats_t;
 
 /* Fills *cfg with the defaults listed above (seed 0x5EED0000, no allocator). */

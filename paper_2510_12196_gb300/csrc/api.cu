@@ -264,6 +264,8 @@ void map_config_default(map_config* cfg) {
   cfg->lp_relax_num = 0;
   cfg->lp_relax_den = 1;
   cfg->reb_objective = 0;
+  cfg->mid_deg = 0;
+  cfg->split_deg = 0;
 }
 
 const char* map_status_string(map_status s) {
@@ -308,6 +310,9 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       throw ApiError(MAP_E_INVALID, "lp_relax_num must be >= 0 and lp_relax_den >= 1");
     if (c.cfg.reb_objective < 0 || c.cfg.reb_objective > 1)
       throw ApiError(MAP_E_INVALID, "reb_objective must be 0 or 1");
+    if (c.cfg.mid_deg != 0 && (c.cfg.mid_deg <= kLowDeg || c.cfg.mid_deg > kMidDeg))
+      throw ApiError(MAP_E_INVALID, "mid_deg must be 0 (autotuned) or in 33..255");
+    if (c.cfg.split_deg < 0) throw ApiError(MAP_E_INVALID, "split_deg must be 0 (autotuned) or positive");
     c.st = (cudaStream_t)stream;
     GM_CUDA(cudaGetDevice(&c.dev));
     sort_init();
@@ -694,7 +699,11 @@ map_status map_stats(map_ctx* ctx, map_stats_t* out) {
       out->J[l] = c.Jlev[l];
       out->iters[l] = c.iters[l];
       out->ms_refine_level[l] = c.ms_level[l];
+      out->mid_deg[l] = c.lv[l].mid_deg;
+      out->split_deg[l] = (int32_t)std::min<int64_t>(c.lv[l].hub_split_deg, INT32_MAX);
+      out->tuned[l] = c.lv[l].tuned;
     }
+    out->ms_tune = c.ms_tune;
     out->ms_coarsen = c.ms_coarsen;
     out->ms_initial = c.ms_initial;
     out->ms_refine = c.ms_refine;

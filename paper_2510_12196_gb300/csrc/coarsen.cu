@@ -37,8 +37,9 @@ struct GraphView {
   const int32_t* __restrict__ adj;
   const int32_t* __restrict__ adjw;
   const int32_t* __restrict__ vw;
+  int32_t mid_deg;  // rows of degree in (kLowDeg, mid_deg] get one warp; larger ones the hub kernels
 };
-inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw, L.mid_deg}; }
 
 // Persistent grid of a warp-tile kernel: one wave of resident blocks.
 inline unsigned tile_grid(Ctx& c, const void* fn, int64_t n) {
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(kMidThreads) k_cluster_mid(GraphView g, const 
     const int32_t v = hi[i];
     const int64_t beg = g.xadj[v];
     const int64_t deg = g.xadj[v + 1] - beg;
-    if (deg > kMidDeg) continue;
+    if (deg > g.mid_deg) continue;
     if (!cluster_active(a, v, deg)) {
       if (lane == 0) a.req[v] = -1;
       continue;
@@ -936,7 +937,7 @@ __global__ void __launch_bounds__(kThreads) k_contract_keys(GraphView g, const i
       mv = vv ? M[v] : 0;
       E0 = __shfl_sync(0xffffffffu, b, 0);
       E1 = __shfl_sync(0xffffffffu, e, last);
-      big = __ballot_sync(0xffffffffu, e - b > kMidDeg);
+      big = __ballot_sync(0xffffffffu, e - b > g.mid_deg);
     }
     unsigned long long cnt = 0;
     for (int64_t x0 = contract_skip(E0, E1, b, e, last, big); x0 < E1;

@@ -10,6 +10,7 @@
 #include "../../include/gpumap.h"
 #include "common.cuh"
 #include "prim.cuh"
+#include "mid.cuh"
 
 namespace gm {
 
@@ -84,7 +85,10 @@ struct Level {
   int32_t* hi = nullptr;       // vertices of degree > kLowDeg, ascending
   int32_t n_hi = 0;
   int64_t m_hi = 0;            // CSR entries of the high-degree vertices
-  int64_t m_huge = 0;          // CSR entries of the vertices of degree > kMidDeg
+  int64_t m_huge = 0;          // CSR entries of the vertices of degree > mid_deg
+  int32_t mid_deg = kMidDeg;   // warp-per-vertex bound of this level (autotuned, <= kMidDeg)
+  int64_t split_req = kSplitDeg;  // hub split bound asked for (hub_split_deg: the one in force)
+  int32_t tuned = 0;           // 1: (mid_deg, split_req) chosen by timing, 0: defaults or the config's
   int64_t max_deg = 0;         // largest degree (0 when n_hi == 0, i.e. at most kLowDeg)
   int32_t* huge = nullptr;     // positions in hi of the vertices of degree > kMidDeg, ascending
   int32_t n_huge = 0;
@@ -287,6 +291,8 @@ struct Ctx {
 
   // stats
   double ms_coarsen = 0, ms_initial = 0, ms_refine = 0, ms_project = 0;
+  double ms_tune = 0;             // host wall time the schedule autotuner spent
+  RefineState* probe_state = nullptr;  // kind = LP, for the autotuner's timing probe
   int32_t iters[65] = {0};
   int64_t Jlev[65] = {0};
   double ms_level[65] = {0};

@@ -12,6 +12,7 @@
 // with one such array; per-level group sums of that array give the gain of
 // every candidate PE in O(levels).
 #include <atomic>
+#include <chrono>
 #include <type_traits>
 #include <algorithm>
 #include <mutex>
@@ -33,9 +34,10 @@ struct GraphView {
   const int32_t* __restrict__ adj;
   const int32_t* __restrict__ adjw;
   const int32_t* __restrict__ vw;
+  int32_t mid_deg;  // rows of degree in (kLowDeg, mid_deg] get one warp; larger ones the hub kernels
 };
 
-inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw}; }
+inline GraphView view(const Level& L) { return GraphView{L.n, L.xadj, L.adj, L.adjw, L.vw, L.mid_deg}; }
 
 __host__ __device__ inline int bits_for_n(int64_t x) {  // smallest b with x <= 2^b
   int b = 0;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kMidThreads) k_eval_mid(GraphView g, const int
   for (int64_t i = (int64_t)blockIdx.x * kMidWarps + warp; i < n_hi; i += (int64_t)gridDim.x * kMidWarps) {
     const int32_t v = hi[i];
     const int64_t b = g.xadj[v], e = g.xadj[v + 1];
-    if (e - b > kMidDeg) continue;
+    if (e - b > g.mid_deg) continue;
     const int32_t p = pi[v];
     for (int64_t x = b + lane; x < e; x += 32) acc += (int64_t)g.adjw[x] * dcode(sdist, p, pi[g.adj[x]]);
   }
@@ -627,7 +629,7 @@ __global__ void __launch_bounds__(kMidThreads) k_lp_gain_mid(GraphView g, const 
     const int32_t v = hi[i];
     const int64_t beg = g.xadj[v];
     const int64_t deg = g.xadj[v + 1] - beg;
-    if (deg > kMidDeg) continue;
+    if (deg > g.mid_deg) continue;
     const int32_t p = pi[v];
     const bool locked = lock[v] != 0;
     __syncwarp();  // every lane has read the lock before lane 0 clears it
@@ -741,7 +743,7 @@ __global__ void __launch_bounds__(kMidThreads) k_lp_after_mid(GraphView g, const
     const int32_t v = hi[i];
     if (!inx[v]) continue;
     const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
-    if (end - beg > kMidDeg) continue;
+    if (end - beg > g.mid_deg) continue;
     const int32_t p = pi[v], q = pp[v];
     const int64_t gv = gain[v];
     int64_t s = 0;
@@ -876,7 +878,7 @@ __global__ void __launch_bounds__(kMidThreads) k_delta_mid(GraphView g, const in
     const int32_t v = hi[i];
     if (!mv.moved(v)) continue;
     const int64_t b = g.xadj[v], e = g.xadj[v + 1];
-    if (e - b > kMidDeg) continue;
+    if (e - b > g.mid_deg) continue;
     const int32_t ov = pi[v], nv = mv.target(v);
     for (int64_t x = b + lane; x < e; x += 32) acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[x], g.adjw[x]);
   }
@@ -1198,7 +1200,7 @@ __global__ void __launch_bounds__(kMidThreads) k_reb_select_mid(GraphView g, con
     const int32_t v = hi[i];
     const int64_t beg = g.xadj[v];
     const int64_t deg = g.xadj[v + 1] - beg;
-    if (deg > kMidDeg) continue;
+    if (deg > g.mid_deg) continue;
     const int32_t A = pi[v];
     if (!reb_eligible(a, A, g.vw[v])) {
       if (lane == 0) elig[v] = 0;
@@ -3321,6 +3323,8 @@ void refine_alloc(Ctx& c) {
   c.evctr = reinterpret_cast<unsigned int*>(c.mem.make<int64_t>(1));
   GM_CUDA(cudaMemsetAsync(c.evctr, 0, sizeof(int64_t), c.st));
   c.state = c.mem.make<RefineState>(1);
+  c.probe_state = c.mem.make<RefineState>(1);
+  GM_CUDA(cudaMemsetAsync(c.probe_state, 0, sizeof(RefineState), c.st));  // kind 0 = KIND_LP
   c.trace_kind = c.mem.make<int32_t>(c.trace_cap);
   c.trace_J = c.mem.make<int64_t>(c.trace_cap);
   c.trace_maxw = c.mem.make<int64_t>(c.trace_cap);
@@ -3825,13 +3829,14 @@ namespace {
 // degree > kLowDeg, the high 32 bits those of degree > kMidDeg (a subset).
 struct LoadHigh {
   const int64_t* xadj;
+  int32_t mid_deg;
   __device__ int64_t operator()(int64_t v) const {
     const int64_t d = xadj[v + 1] - xadj[v];
-    return (d > kLowDeg ? 1 : 0) + (d > kMidDeg ? (1LL << 32) : 0);
+    return (d > kLowDeg ? 1 : 0) + (d > mid_deg ? (1LL << 32) : 0);
   }
 };
 // hi[] gets every vertex of degree > kLowDeg; huge[] the positions in hi[] of
-// those of degree > kMidDeg
+// those of degree > mid_deg
 struct StoreHigh {
   int32_t* out;
   int32_t* huge;
@@ -3843,12 +3848,12 @@ struct StoreHigh {
 };
 
 __global__ void k_level_stats(int32_t n, const int64_t* __restrict__ xadj, const int32_t* __restrict__ vw,
-                              unsigned long long* out) {
+                              int32_t mid_deg, unsigned long long* out) {
   unsigned long long mhi = 0, mdeg = 0, mvw = 0, mhuge = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long d = (unsigned long long)(xadj[v + 1] - xadj[v]);
     if (d > (unsigned long long)kLowDeg) mhi += d;
-    if (d > (unsigned long long)kMidDeg) mhuge += d;
+    if (d > (unsigned long long)mid_deg) mhuge += d;
     mdeg = d > mdeg ? d : mdeg;
     const unsigned long long w = (unsigned long long)vw[v];
     mvw = w > mvw ? w : mvw;
@@ -3885,9 +3890,10 @@ struct LoadSplit {
   const int32_t* hi;
   const int32_t* huge;
   const int64_t* xadj;
+  int64_t split_deg;
   __device__ int64_t operator()(int64_t j) const {
     const int32_t v = hi[huge[j]];
-    return xadj[v + 1] - xadj[v] > kSplitDeg ? 1 : 0;
+    return xadj[v + 1] - xadj[v] > split_deg ? 1 : 0;
   }
 };
 struct StoreSplit {
@@ -3916,9 +3922,10 @@ int64_t read_i64_at(Ctx& c, const int64_t* d) {
   return c.h_small[5];
 }
 
-// The flattened entries of the rows of degree > kMidDeg (in huge[] order)
-// and their chunk map, so that kernels can spread those rows over CTAs.
-void prepare_hubs(Ctx& c, Level& L) {
+// The flattened entries of the rows of degree > mid_deg (in huge[] order)
+// and their chunk map, so that kernels can spread those rows over CTAs;
+// rows above split_deg sum per-chunk PE tables.
+void prepare_hubs(Ctx& c, Level& L, int64_t split_deg) {
   if (!L.n_huge) {
     L.n_hub_chunks = 0;
     return;
@@ -3950,14 +3957,15 @@ void prepare_hubs(Ctx& c, Level& L) {
   // the rows whose PE-code tables are summed over chunks
   if (!L.hub_sidx) L.hub_sidx = c.mem.make<int32_t>((size_t)std::max(1, L.n));
   if (!L.hub_split) L.hub_split = c.mem.make<int32_t>((size_t)std::max(1, L.n));
-  scan(LoadSplit{L.hi, L.huge, L.xadj}, StoreSplit{L.hub_sidx, L.hub_split}, L.n_huge, nullptr, c.scan, c.st);
+  scan(LoadSplit{L.hi, L.huge, L.xadj, split_deg}, StoreSplit{L.hub_sidx, L.hub_split}, L.n_huge, nullptr, c.scan,
+       c.st);
   int64_t ns = read_i64_at(c, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n_huge)));
   const int64_t need = ns * c.topo.kc;
   if (need * (int64_t)sizeof(int32_t) > kSplitTableBytes) {
     ns = 0;  // too many: every row is rated whole
     L.hub_split_deg = INT64_MAX;
   } else {
-    L.hub_split_deg = kSplitDeg;
+    L.hub_split_deg = split_deg;
   }
   L.n_split = (int32_t)ns;
   if (ns && L.hub_gtab_cap < need) {
@@ -3970,15 +3978,18 @@ void prepare_hubs(Ctx& c, Level& L) {
 }
 }  // namespace
 
-void classify_degrees(Ctx& c, int lvl) {
-  Level& L = c.lv[lvl];
+// Degree classes of a level with the warp-per-vertex bound mid_deg and the
+// hub split bound split_deg.
+void classify_with(Ctx& c, Level& L, int32_t mid_deg, int64_t split_deg) {
   if (!L.hi) L.hi = c.mem.make<int32_t>((size_t)std::max(1, L.n));
   if (!L.huge) L.huge = c.mem.make<int32_t>((size_t)std::max(1, L.n));
-  scan(LoadHigh{L.xadj}, StoreHigh{L.hi, L.huge}, L.n, nullptr, c.scan, c.st);
+  L.mid_deg = mid_deg;
+  scan(LoadHigh{L.xadj, mid_deg}, StoreHigh{L.hi, L.huge}, L.n, nullptr, c.scan, c.st);
   unsigned long long* st = reinterpret_cast<unsigned long long*>(c.d_stats);
   GM_CUDA(cudaMemsetAsync(st, 0, 4 * sizeof(int64_t), c.st));
   const int64_t blocks = std::min<int64_t>(((int64_t)L.n + 255) / 256, (int64_t)c.num_sms * 8);
-  k_level_stats<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, c.st>>>(L.n, L.xadj, L.vw, st); count_launch();
+  k_level_stats<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, c.st>>>(L.n, L.xadj, L.vw, mid_deg, st);
+  count_launch();
   // count of high-degree vertices and the four statistics, one synchronisation
   GM_CUDA(cudaMemcpyAsync(c.h_small, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
                           cudaMemcpyDeviceToHost, c.st));
@@ -3990,7 +4001,138 @@ void classify_degrees(Ctx& c, int lvl) {
   L.max_deg = c.h_small[2];
   L.max_vw = (int32_t)c.h_small[3];
   L.m_huge = c.h_small[4];
-  prepare_hubs(c, L);
+  prepare_hubs(c, L, split_deg);
+}
+
+namespace {
+// The schedule autotuner.  A level whose rows of degree > kLowDeg hold at
+// least kTuneMinEntries entries gets its warp-per-vertex bound mid_deg
+// (candidates 255, 128, 64: which rows a warp takes and which the hub
+// kernels) and its hub split bound (candidates 4096, 2048, 16384: which hub
+// rows one CTA rates whole and which sum per-chunk tables) chosen by timing a
+// probe, coordinate by coordinate; the choice is cached per (device, n, m,
+// entries of degree > kLowDeg, largest degree, PE code space) for the
+// process.  Every schedule gives the same result; only the time differs.
+constexpr int64_t kTuneMinEntries = 1 << 20;
+double now_wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+struct SchedKey {
+  int dev;
+  int32_t n;
+  int64_t m, m_hi, max_deg;
+  int32_t kc;
+  bool operator==(const SchedKey& o) const {
+    return dev == o.dev && n == o.n && m == o.m && m_hi == o.m_hi && max_deg == o.max_deg && kc == o.kc;
+  }
+};
+struct SchedChoice {
+  int32_t mid_deg;
+  int64_t split_deg;
+};
+std::mutex g_sched_mutex;
+std::vector<std::pair<SchedKey, SchedChoice>> g_sched_cache;
+
+// Device time of the probe, best of two: a full J evaluation and Alg. 4
+// step 1 over the vertices of degree > kLowDeg (per-warp and hub tables),
+// with no vertex locked and the outputs in transient scratch (the
+// rebalancing buffers), on the level's mapping, which is zeroed first on a
+// coarse level (it is set later by projection or the initial mapping).
+double probe_ms(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  struct ProfOff {  // the probe's launches stay out of the kernel-class profile
+    Ctx& c;
+    bool was;
+    explicit ProfOff(Ctx& cc) : c(cc), was(cc.prof) { cc.prof = false; }
+    ~ProfOff() { c.prof = was; }
+  } prof_off(c);
+  if (lvl > 0) GM_CUDA(cudaMemsetAsync(L.pi, 0, (size_t)std::max(1, L.n) * sizeof(int32_t), c.st));
+  GM_CUDA(cudaMemsetAsync(c.sel, 0, (size_t)std::max(1, L.n), c.st));
+  const GroupLayout glay = group_layout(c.topo);
+  const LpFilter flt{0, 1};
+  cudaEvent_t e0, e1;
+  GM_CUDA(cudaEventCreate(&e0));
+  GM_CUDA(cudaEventCreate(&e1));
+  double best = 1e30;
+  for (int rep = 0; rep < 2; rep++) {
+    GM_CUDA(cudaEventRecord(e0, c.st));
+    launch_eval(c, lvl, nullptr, true);
+    if (L.n_hi > L.n_huge) {
+      const size_t sm = mid_table_smem(glay.total);
+      k_lp_gain_mid<<<mid_grid(c, (const void*)k_lp_gain_mid, sm, L.n_hi), kMidThreads, sm, c.st>>>(
+          view(L), L.hi, L.n_hi, L.pi, c.sel, c.dest, c.P64, c.elig, c.topo, glay, flt, c.probe_state);
+      count_launch();
+    }
+    if (L.n_huge) {
+      const LpHubPolicy pol{L.pi, c.sel, c.dest, c.P64, c.elig, c.topo, glay, flt, c.probe_state};
+      launch_hub_tab(c, L, pol, (size_t)glay.total * sizeof(int32_t));
+    }
+    GM_CUDA(cudaEventRecord(e1, c.st));
+    GM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    GM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+}  // namespace
+
+void classify_degrees(Ctx& c, int lvl) {
+  Level& L = c.lv[lvl];
+  const int32_t prev_mid = L.mid_deg;
+  const int64_t prev_split = L.split_req;
+  const bool fixed = c.cfg.mid_deg > 0 || c.cfg.split_deg > 0;
+  SchedChoice ch{c.cfg.mid_deg > 0 ? c.cfg.mid_deg : kMidDeg, c.cfg.split_deg > 0 ? c.cfg.split_deg : kSplitDeg};
+  classify_with(c, L, ch.mid_deg, ch.split_deg);
+  L.tuned = 0;
+  if (!fixed && L.m_hi >= kTuneMinEntries && mid_tables(c)) {
+    const SchedKey key{c.dev, L.n, L.m, L.m_hi, L.max_deg, c.topo.kc};
+    bool hit = false;
+    {
+      std::lock_guard<std::mutex> lock(g_sched_mutex);
+      for (const auto& kv : g_sched_cache)
+        if (kv.first == key) {
+          ch = kv.second;
+          hit = true;
+        }
+    }
+    if (!hit) {
+      const double t0 = now_wall_ms();
+      double best = probe_ms(c, lvl);
+      SchedChoice cur = ch;
+      for (int32_t md : {128, 64}) {
+        classify_with(c, L, md, cur.split_deg);
+        const double t = probe_ms(c, lvl);
+        if (t < best) {
+          best = t;
+          ch = SchedChoice{md, cur.split_deg};
+        }
+      }
+      cur = ch;
+      for (int64_t sd : {(int64_t)2048, (int64_t)16384}) {
+        classify_with(c, L, cur.mid_deg, sd);
+        const double t = probe_ms(c, lvl);
+        if (t < best) {
+          best = t;
+          ch = SchedChoice{cur.mid_deg, sd};
+        }
+      }
+      c.ms_tune += now_wall_ms() - t0;
+      std::lock_guard<std::mutex> lock(g_sched_mutex);
+      g_sched_cache.emplace_back(key, ch);
+    }
+    classify_with(c, L, ch.mid_deg, ch.split_deg);
+    L.tuned = 1;
+  }
+  L.split_req = ch.split_deg;
+  if (L.mid_deg != prev_mid || L.split_req != prev_split) {
+    // kernels captured for the other schedule
+    drop_graph(L);
+    if (L.cgexec) cudaGraphExecDestroy(L.cgexec);
+    L.cgexec = nullptr;
+  }
 }
 
 }  // namespace gm

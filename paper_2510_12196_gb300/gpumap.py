@@ -43,7 +43,8 @@ class MapConfig(C.Structure):
                 ("launch_mode", C.c_int32), ("engine_max_n", C.c_int32),
                 ("grid_engine_max_n", C.c_int32), ("coarsener", C.c_int32),
                 ("match_rounds", C.c_int32), ("initial", C.c_int32), ("lp_relax_num", C.c_int32),
-                ("lp_relax_den", C.c_int32), ("reb_objective", C.c_int32)]
+                ("lp_relax_den", C.c_int32), ("reb_objective", C.c_int32), ("mid_deg", C.c_int32),
+                ("split_deg", C.c_int32)]
 
 
 class MapStats(C.Structure):
@@ -51,7 +52,8 @@ class MapStats(C.Structure):
                 ("J", C.c_int64 * 65), ("iters", C.c_int32 * 65), ("ms_coarsen", C.c_double),
                 ("ms_initial", C.c_double), ("ms_refine", C.c_double), ("ms_project", C.c_double),
                 ("device_bytes", C.c_int64), ("device_bytes_peak", C.c_int64),
-                ("ms_refine_level", C.c_double * 65)]
+                ("ms_refine_level", C.c_double * 65), ("mid_deg", C.c_int32 * 65), ("split_deg", C.c_int32 * 65),
+                ("tuned", C.c_int32 * 65), ("ms_tune", C.c_double)]
 
 
 class MapHmStats(C.Structure):
