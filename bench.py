@@ -668,6 +668,8 @@ def run_probe(args, local):
     cfg.launch_mode = 1  # stream launches: a profiler sees every kernel
     ctx = G.map_create(g.xadj, g.adj, g.adjw, g.vw, g.n, t.hier, t.dist, t.eps, cfg)
     J = G.map_run(ctx)
+    st0 = G.map_stats(ctx)
+    sched0 = {"mid_deg": st0.mid_deg[0], "split_deg": st0.split_deg[0], "autotuned": st0.tuned[0]}
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("probe_coarsen")
     G.map_coarsen(ctx)
@@ -692,7 +694,8 @@ def run_probe(args, local):
     G.map_destroy(ctx)
     print(json.dumps({"probe": "coarsening (range probe_coarsen); lp_step + objective on level 0 after "
                                "map_run (range probe); matching coarsening (range probe_match)", "J_map": J,
-                      "moved": moved, "J_after_step": J2, "n": g.n, "m_dir": g.m_dir, "match_levels": nl}))
+                      "moved": moved, "J_after_step": J2, "n": g.n, "m_dir": g.m_dir, "match_levels": nl,
+                      "level0_schedule": sched0}))
     return 0
 
 

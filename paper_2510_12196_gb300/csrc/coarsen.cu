@@ -102,7 +102,7 @@ constexpr int64_t kValChunk = 64;
 __global__ void __launch_bounds__(kThreads) k_validate_entries(GraphView g, int64_t m, uint32_t* err,
                                                               unsigned long long* sums) {
   uint32_t e_local = 0;
-  unsigned long long sw = 0;
+  unsigned long long sw = 0, n_search = 0, n_other = 0;
   const int64_t chunks = (m + kValChunk - 1) / kValChunk;
   for (int64_t ch = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ch < chunks;
        ch += (int64_t)gridDim.x * blockDim.x) {
@@ -127,23 +127,40 @@ __global__ void __launch_bounds__(kThreads) k_validate_entries(GraphView g, int6
       if (e > beg && g.adj[e - 1] >= u) e_local |= ERR_UNSORTED;
       if (w < 1) e_local |= ERR_WEIGHT;
       else sw += (unsigned long long)w;
-      int64_t l = g.xadj[u], r = g.xadj[u + 1];
+      if (u == v) continue;
+      // symmetry: the entry looks for its twin (u, v) only when row u is the
+      // smaller of the two rows (by degree, then id), so every search runs in
+      // the shorter row; the others are counted.  Rows being strictly
+      // ascending, the twin map from the searching entries to the others is
+      // injective, so equal counts (checked on the host) make it a bijection.
+      const int64_t ub = g.xadj[u], ue = g.xadj[u + 1];
+      const int64_t du = ue - ub, dv = g.xadj[v + 1] - beg;
+      if (!(du < dv || (du == dv && u < v))) {
+        n_other++;
+        continue;
+      }
+      n_search++;
+      int64_t l = ub, r = ue;
       while (l < r) {  // first entry >= v in row u
         const int64_t mid = (l + r) >> 1;
         if (g.adj[mid] < v) l = mid + 1;
         else r = mid;
       }
-      if (l >= g.xadj[u + 1] || g.adj[l] != (int32_t)v || g.adjw[l] != w) e_local |= ERR_ASYM;
+      if (l >= ue || g.adj[l] != (int32_t)v || g.adjw[l] != w) e_local |= ERR_ASYM;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     e_local |= __shfl_xor_sync(0xffffffffu, e_local, o);
     sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    n_search += __shfl_xor_sync(0xffffffffu, n_search, o);
+    n_other += __shfl_xor_sync(0xffffffffu, n_other, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (e_local) atomicOr(err, e_local);
     if (sw) atomicAdd(&sums[1], sw);
+    if (n_search) atomicAdd(&sums[2], n_search);
+    if (n_other) atomicAdd(&sums[3], n_other);
   }
 }
 
@@ -1554,7 +1571,7 @@ void validate_graph(Ctx& c) {
   Level& L = c.lv[0];
   unsigned long long* sums = reinterpret_cast<unsigned long long*>(c.counters);
   GM_CUDA(cudaMemsetAsync(c.errword, 0, sizeof(uint32_t), c.st));
-  GM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), c.st));
+  GM_CUDA(cudaMemsetAsync(sums, 0, 4 * sizeof(int64_t), c.st));  // weights; searching / other entries
   k_validate_rows<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(view(L), L.m, c.errword, sums); count_launch();
   // the entries only once the rows are known to be sound (their search needs a monotone xadj)
   int64_t* hs = c.h_small;
@@ -1570,17 +1587,19 @@ void validate_graph(Ctx& c) {
   GM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int64_t), c.st));
   k_max_i32<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.vw, dmax); count_launch();
   GM_CUDA(cudaGetLastError());
-  // pinned: [0] error flags, [1..2] sums, [3] largest weight
+  // pinned: [0] error flags, [1..2] sums, [3] largest weight, [4..5] searching / other entries
   hs[0] = 0;
   hs[3] = 0;
   GM_CUDA(cudaMemcpyAsync(hs, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(hs + 1, sums, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(hs + 3, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+  GM_CUDA(cudaMemcpyAsync(hs + 4, sums + 2, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaStreamSynchronize(c.st));
-  const uint32_t e = (uint32_t)(hs[0] & 0xffffffffLL);
+  uint32_t e = (uint32_t)(hs[0] & 0xffffffffLL);
+  if (hs[4] != hs[5]) e |= ERR_ASYM;  // an entry without its twin
   const unsigned long long h[2] = {(unsigned long long)hs[1], (unsigned long long)hs[2]};
   const int32_t hmax = (int32_t)(hs[3] & 0xffffffffLL);
-  GM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), c.st));
+  GM_CUDA(cudaMemsetAsync(sums, 0, 4 * sizeof(int64_t), c.st));
   if (e) {
     std::string m = "invalid graph:";
     if (e & ERR_XADJ) m += " xadj not monotone or out of range;";

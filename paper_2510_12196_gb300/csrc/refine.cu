@@ -1422,6 +1422,10 @@ __global__ void __launch_bounds__(kHiThreads) k_hub_tab(GraphView g, HubRows hr,
   __shared__ int64_t sb[32];
   __shared__ int32_t sc[32];
   __shared__ int64_t s_ch;
+  // the rows of the current chunk (kHubChunkRows at most), checked at once
+  __shared__ int32_t s_v[kHubChunkRows];  // the row's vertex; -1: not this chunk's to rate
+  __shared__ uint8_t s_want[kHubChunkRows];
+  __shared__ uint8_t s_split[kHubChunkRows];
   if (!pol.run()) return;
   const int32_t words = pol.words(), kc = pol.topo_kc();
   for (int32_t b = threadIdx.x; b < words; b += blockDim.x) tab[b] = 0;
@@ -1429,15 +1433,33 @@ __global__ void __launch_bounds__(kHiThreads) k_hub_tab(GraphView g, HubRows hr,
   const int64_t m_hub = hr.pre[hr.n_huge];
   for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
     const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
-    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
+    const int32_t r0 = hr.chunk[ch];
+    if (threadIdx.x < kHubChunkRows) {
+      const int32_t r = r0 + (int32_t)threadIdx.x;
+      int32_t v = -1;
+      bool w = false, sp = false;
+      if (r < hr.n_huge && hr.pre[r] < ce) {
+        const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
+        sp = re - rb > split_deg;
+        if (sp || rb >= cb) {  // a row up to split_deg is rated whole by the chunk of its first entry
+          v = hr.hi[hr.huge[r]];
+          w = pol.want(v);
+        }
+      }
+      s_v[threadIdx.x] = v;
+      s_want[threadIdx.x] = w;
+      s_split[threadIdx.x] = sp;
+    }
+    __syncthreads();  // also: every want() has read what skip() writes
+    for (int32_t i = 0; i < kHubChunkRows; i++) {
+      const int32_t r = r0 + i;
+      if (r >= hr.n_huge) break;
       const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
       if (rb >= ce) break;
-      const bool split = re - rb > split_deg;
-      if (!split && rb < cb) continue;  // rated whole by the chunk of its first entry
-      const int32_t v = hr.hi[hr.huge[r]];
-      const bool w = pol.want(v);
-      if (P::kWantBarrier) __syncthreads();  // every thread has read what want() reads before skip() writes it
-      if (!w) {
+      const int32_t v = s_v[i];
+      if (v < 0) continue;
+      const bool split = s_split[i];
+      if (!s_want[i]) {
         if (!split && threadIdx.x == 0) pol.skip(v);
         continue;
       }
