@@ -5,9 +5,15 @@
 // at the lowest unvisited id whenever the queue runs empty, neighbours taken
 // in adjacency order; the vertex with preceding weight s goes to PE
 // floor(s k / c(V)).  That order is produced here without a queue:
-//   1. connected components, each labelled by its smallest id (hooking of the
-//      larger label onto the smaller one along every edge, then pointer
-//      jumping, until no edge joins two labels);
+//   1. connected components, each labelled by its smallest id: hooking of the
+//      larger label onto the smaller one along each vertex's first and then
+//      second edge, with pointer jumping after each pass; then, with the most
+//      frequent label among sampled vertices taken as the giant component's,
+//      hooking along every edge of the vertices outside it, and jumping,
+//      until no such edge joins two labels (an edge between the giant and
+//      another vertex is seen from the other side, so then no edge at all
+//      joins two labels; labels only ever move to smaller ones, so each ends
+//      as its component's smallest id);
 //   2. one level-synchronous search from all component roots at once: the
 //      frontier is kept in order, every unvisited neighbour is claimed by its
 //      earliest frontier vertex, and the children are laid out by a scan over
@@ -39,14 +45,6 @@ int bits_of(int64_t x) {  // smallest b with x < 2^b
   return b;
 }
 
-// source vertex of every CSR entry (one warp per row)
-__global__ void k_src_fill(int32_t n, const int64_t* __restrict__ xadj, int32_t* src) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nw)
-    for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) src[e] = (int32_t)v;
-}
-
 __global__ void k_cc_init(int32_t n, int32_t* lab, int32_t* lev, int32_t* claim) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     lab[v] = (int32_t)v;
@@ -55,19 +53,41 @@ __global__ void k_cc_init(int32_t n, int32_t* lab, int32_t* lev, int32_t* claim)
   }
 }
 
-// every edge with two labels hooks the larger label onto the smaller
-__global__ void k_cc_hook(int64_t m, const int32_t* __restrict__ src, const int32_t* __restrict__ adj, int32_t* lab,
-                          int32_t* changed) {
-  bool any = false;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = src[e], v = adj[e];
-    if (u >= v) continue;  // each undirected edge once
-    const int32_t lu = lab[u], lv = lab[v];
-    if (lu == lv) continue;
-    atomicMin(&lab[max(lu, lv)], min(lu, lv));
-    any = true;
+// hooking along the r-th edge of every vertex (sampling passes)
+__global__ void k_cc_sample(int32_t n, const int64_t* __restrict__ xadj, const int32_t* __restrict__ adj, int32_t* lab,
+                            int32_t r) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = xadj[v] + r;
+    if (e >= xadj[v + 1]) continue;
+    const int32_t lu = lab[v], lv = lab[adj[e]];
+    if (lu != lv) atomicMin(&lab[max(lu, lv)], min(lu, lv));
   }
-  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) *changed = 1;
+}
+
+// hooking along every edge of the vertices whose label is not `giant` (one
+// warp per vertex)
+__global__ void k_cc_hook_rest(int32_t n, const int64_t* __restrict__ xadj, const int32_t* __restrict__ adj,
+                               int32_t* lab, int32_t giant, int32_t* changed) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  bool any = false;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    if (__shfl_sync(0xffffffffu, lab[u], 0) == giant) continue;
+    for (int64_t e = xadj[u] + lane; e < xadj[u + 1]; e += 32) {
+      const int32_t lu = lab[u], lv = lab[adj[e]];
+      if (lu == lv) continue;
+      atomicMin(&lab[max(lu, lv)], min(lu, lv));
+      any = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, any) && lane == 0) *changed = 1;
+}
+
+// the labels of kCcSample spread vertices (to find the giant component's)
+constexpr int kCcSample = 1024;
+__global__ void k_cc_pick(int32_t n, const int32_t* __restrict__ lab, int32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kCcSample) out[i] = lab[(int64_t)(((uint64_t)i * 2654435761ULL) % (uint64_t)n)];
 }
 
 // pointer jumping with path halving: every label becomes the root of its
@@ -229,11 +249,32 @@ bool initial_map_large(Ctx& c) {
   k_cc_init<<<gn, kIThreads, 0, c.st>>>(n, lab, lev, claim); count_launch();
   // 1. components labelled by their smallest id
   if (m > 0) {
-    k_src_fill<<<igrid(c, (int64_t)n * 32), kIThreads, 0, c.st>>>(n, L.xadj, src); count_launch();
+    for (int32_t r = 0; r < 2; r++) {
+      k_cc_sample<<<gn, kIThreads, 0, c.st>>>(n, L.xadj, L.adj, lab, r); count_launch();
+      k_cc_jump<<<gn, kIThreads, 0, c.st>>>(n, lab, c.errword); count_launch();
+    }
+    // the most frequent sampled label: the giant component's, if there is one
+    int32_t* picks = src;
+    k_cc_pick<<<(kCcSample + kIThreads - 1) / kIThreads, kIThreads, 0, c.st>>>(n, lab, picks); count_launch();
+    std::vector<int32_t> h(kCcSample);
+    GM_CUDA(cudaMemcpyAsync(h.data(), picks, kCcSample * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    GM_CUDA(cudaStreamSynchronize(c.st));
+    std::sort(h.begin(), h.end());
+    int32_t giant = h[0], best = 0;
+    for (int i = 0; i < kCcSample;) {
+      int j = i;
+      while (j < kCcSample && h[j] == h[i]) j++;
+      if (j - i > best) {
+        best = j - i;
+        giant = h[i];
+      }
+      i = j;
+    }
     for (int it = 0;; it++) {
       if (it > 64 + 4 * bits_of(n)) return false;  // not settled: the caller takes the one-CTA search
       GM_CUDA(cudaMemsetAsync(changed, 0, sizeof(int64_t), c.st));
-      k_cc_hook<<<igrid(c, m), kIThreads, 0, c.st>>>(m, src, L.adj, lab, changed); count_launch();
+      k_cc_hook_rest<<<igrid(c, (int64_t)n * 32), kIThreads, 0, c.st>>>(n, L.xadj, L.adj, lab, giant, changed);
+      count_launch();
       k_cc_jump<<<gn, kIThreads, 0, c.st>>>(n, lab, c.errword); count_launch();
       if (read_dev(c, c.counters + 6) == 0) break;
     }

@@ -932,27 +932,60 @@ __global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, HubRows 
 }
 
 // Alg. 4 step 3: simultaneous move of M (lock = moved), block weights.
+// Block-weight changes of a simultaneous move.  With a PE code space of at
+// most kApplyCodes codes each CTA sums its changes in shared memory and adds
+// the non-zero ones to W at the end: movers crowd into a few blocks (a hub's
+// neighbourhood moves together on power-law graphs), and one global atomic per
+// mover on the same few words serialises.
+constexpr int32_t kApplyCodes = 4096;
+struct BlockDelta {
+  long long* dW;  // shared, kApplyCodes
+  int64_t* W;
+  bool local;
+  __device__ __forceinline__ void init(int32_t kc) {
+    if (local)
+      for (int32_t b = threadIdx.x; b < kc; b += blockDim.x) dW[b] = 0;
+  }
+  __device__ __forceinline__ void move(int32_t p, int32_t q, int64_t c) {
+    if (local) {
+      atomicAdd((unsigned long long*)&dW[p], (unsigned long long)(-c));
+      atomicAdd((unsigned long long*)&dW[q], (unsigned long long)c);
+    } else {
+      atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
+      atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    }
+  }
+  // after a barrier
+  __device__ __forceinline__ void flush(int32_t kc) {
+    if (local)
+      for (int32_t b = threadIdx.x; b < kc; b += blockDim.x)
+        if (dW[b]) atomicAdd((unsigned long long*)&W[b], (unsigned long long)dW[b]);
+  }
+};
+
 __global__ void __launch_bounds__(kThreads) k_lp_apply(int32_t n, int32_t* __restrict__ pi,
                                                        const int32_t* __restrict__ pp,
                                                        const uint8_t* __restrict__ lock,
-                                                       const int32_t* __restrict__ vw, int64_t* W,
+                                                       const int32_t* __restrict__ vw, int64_t* W, int32_t kc,
                                                        RefineState* st) {
   __shared__ int32_t cnt;
+  __shared__ long long dW[kApplyCodes];
   if (!kind_is(st, 1 << KIND_LP)) return;
+  BlockDelta bd{dW, W, kc <= kApplyCodes};
+  bd.init(kc);
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   int32_t mine = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     if (!lock[v]) continue;
     const int32_t p = pi[v], q = pp[v];
-    const int64_t c = vw[v];
     pi[v] = q;
-    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
-    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    bd.move(p, q, vw[v]);
     mine++;
   }
   if (mine) atomicAdd(&cnt, mine);
   __syncthreads();
+  bd.flush(kc);
   if (threadIdx.x == 0 && cnt) atomicAdd(&st->moved, cnt);
 }
 
@@ -1697,18 +1730,22 @@ __global__ void k_reb_mark_cut(const uint64_t* __restrict__ key, const int32_t* 
 
 __global__ void k_reb_apply_sel(int32_t n, const uint8_t* __restrict__ elig, const uint8_t* __restrict__ sel,
                                 const int32_t* __restrict__ dest, int32_t* pi, const int32_t* __restrict__ vw,
-                                int64_t* W, RefineState* st) {
+                                int64_t* W, int32_t kc, RefineState* st) {
+  __shared__ long long dW[kApplyCodes];
   if (st->kind != KIND_WEAK) return;
+  BlockDelta bd{dW, W, kc <= kApplyCodes};
+  bd.init(kc);
+  __syncthreads();
   int32_t mine = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     if (!elig[v] || !sel[v]) continue;
     const int32_t p = pi[v], q = dest[v];
-    const int64_t c = vw[v];
     pi[v] = q;
-    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
-    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    bd.move(p, q, vw[v]);
     mine++;
   }
+  __syncthreads();
+  bd.flush(kc);
   mine = warp_sum(mine);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&st->moved, mine);
 }
@@ -1766,7 +1803,11 @@ __global__ void k_reb_apply_strong(const uint64_t* __restrict__ key, const int32
                                    int64_t max_n, const uint8_t* __restrict__ acc, const int64_t* __restrict__ sarr,
                                    const int64_t* __restrict__ Rb, int32_t kc, int32_t* pi,
                                    const int32_t* __restrict__ vw, int64_t* W, RefineState* st) {
+  __shared__ long long dW[kApplyCodes];
   const int64_t n = *d_n;
+  BlockDelta bd{dW, W, kc <= kApplyCodes};
+  bd.init(kc);
+  __syncthreads();
   int32_t mine = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < max_n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1790,10 +1831,11 @@ __global__ void k_reb_apply_strong(const uint64_t* __restrict__ key, const int32
     if (q < 0) continue;
     const int32_t p = pi[v];
     pi[v] = q;
-    atomicAdd((unsigned long long*)&W[p], (unsigned long long)(-c));
-    atomicAdd((unsigned long long*)&W[q], (unsigned long long)c);
+    bd.move(p, q, c);
     mine++;
   }
+  __syncthreads();
+  bd.flush(kc);
   mine = warp_sum(mine);  // one update of the shared counter per warp
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&st->moved, mine);
 }
@@ -2108,7 +2150,8 @@ void launch_lp(Ctx& c, int lvl) {
     count_launch();
   }
   launch_delta(c, lvl, LpMoves{c.lock, c.pp}, KIND_LP);
-  k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.state); count_launch();
+  k_lp_apply<<<grid_for(c, kThreads, L.n), kThreads, 0, c.st>>>(L.n, L.pi, c.pp, c.lock, L.vw, c.W, c.topo.kc,
+                                                                 c.state); count_launch();
 }
 
 RebPrepArgs reb_prep_args(const Ctx& c) {
@@ -2177,7 +2220,8 @@ void launch_rebalance(Ctx& c, int lvl, bool prep_done = false) {
     big(c.st, nullptr, nullptr);
   }
   launch_delta(c, lvl, WeakMoves{c.elig, selected, c.dest}, KIND_WEAK);
-  k_reb_apply_sel<<<g, kThreads, 0, c.st>>>(L.n, c.elig, selected, c.dest, L.pi, L.vw, c.W, c.state); count_launch();
+  k_reb_apply_sel<<<g, kThreads, 0, c.st>>>(L.n, c.elig, selected, c.dest, L.pi, L.vw, c.W, c.topo.kc, c.state);
+  count_launch();
 }
 
 __global__ void k_strong_gate(const RefineState* st, int64_t* d_sel) {
