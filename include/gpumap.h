@@ -89,12 +89,12 @@ typedef struct {
   map_free_fn free;
   void* alloc_user;
   int32_t launch_mode;   /* 0: refinement and clustering loops as CUDA graphs (default); 1: stream launches */
-  int32_t engine_max_n;  /* levels with at most this many vertices (and no vertex of degree > 128) are refined
-                            by the fused one-launch engine on one thread-block cluster; 0: library default
-                            (32768); -1: never */
-  int32_t grid_engine_max_n; /* larger levels with at most this many vertices (and no vertex of degree > 128)
-                            run the same engine over all SMs (cooperative launch); 0: library default
-                            (262144); -1: never */
+  int32_t engine_max_n;  /* levels with at most this many vertices are refined by the fused one-launch
+                            engine on one thread-block cluster (rows of degree > 128 by whole CTAs; a level
+                            with such a row needs a PE code space whose connectivity table, conn per code
+                            plus the level group sums, fits in 96 KiB); 0: library default (32768); -1: never */
+  int32_t grid_engine_max_n; /* larger levels with at most this many vertices (same condition) run the same
+                            engine over all SMs (cooperative launch); 0: library default (262144); -1: never */
   int32_t coarsener;     /* 0: label-propagation clustering (default); 1: two-hop matching (heavy-edge rounds
                             with the rating w^2 / (c(u) c(v)), then leaf, twin, relative and isolated pairing
                             while at most 75% of the vertices are matched) */
@@ -379,9 +379,12 @@ GPUMAP_API map_status map_selftest_barrier_timeout(void* stream);
  * batch shape for the rest of the process; autotune = 0 takes `cluster` and
  * `tile_entries` instead (0: a size-based default).
  *
- * Limits: all contexts on the current device, no context twice, and no
- * vertex of degree > 128 on the refined level (MAP_E_INVALID: refine such a
- * job with map_refine).  The batch keeps pointers into the contexts: destroy
+ * Limits: all contexts on the current device, no context twice.  Rows of
+ * degree > 128 are rated by whole CTAs from a connectivity table over the PE
+ * codes in shared memory: a job whose refined level has such a row needs a
+ * code space whose table (conn per code plus the level group sums, 4 bytes
+ * each) fits in 96 KiB, e.g. every hierarchy of at most 8192 PEs
+ * (MAP_E_INVALID otherwise: refine such a job with map_refine).  The batch keeps pointers into the contexts: destroy
  * it before them.  map_coarsen and map_run (which coarsens) may move a job's
  * level buffers: after either ran on a job, map_batch_launch returns
  * MAP_E_STATE; build a new batch.  The launch is asynchronous on the
@@ -424,7 +427,11 @@ GPUMAP_API void map_batch_destroy(map_batch* batch);
  * admitted by device memory; `slots` worker threads, each with its own CUDA
  * stream, run the admitted jobs concurrently, so a request that arrives while
  * others are on the GPU starts as soon as a slot and memory are free and its
- * kernels overlap with theirs (continuous batching).  A job is admissible
+ * kernels overlap with theirs (continuous batching).  The jobs' small levels
+ * are batched across requests: each refinement that the fused engine would
+ * run on one thread-block cluster waits for a free batcher lane, which runs
+ * every waiting refinement in one persistent engine launch (one cluster per
+ * job, largest first), so batches grow with the load.  A job is admissible
  * when the estimated device bytes of the running jobs plus its own
  * (map_job_estimate_bytes) fit in `mem_budget`; a job that alone exceeds the
  * budget starts only when nothing else runs.  Admission examines the oldest
@@ -478,6 +485,11 @@ typedef struct {
   int64_t mem_budget;         /* device bytes for the running jobs; 0: 90% of the free memory at creation */
   map_job_runner runner;      /* NULL: the mapping pipeline */
   void* runner_user;
+  int32_t batch_lanes;        /* small levels of the running jobs (those the fused engine refines on one
+                                 cluster) are refined together, in shared engine launches by this many
+                                 batcher threads; 0: 2; -1: each job launches its own engine */
+  int32_t whole_gpu_levels;   /* 0 (default): jobs whose config leaves grid_engine_max_n at 0 do not use the
+                                 cooperative whole-GPU engine, whose launches hold every SM; 1: as configured */
 } map_server_opts;
 
 typedef struct {
@@ -486,9 +498,12 @@ typedef struct {
   int64_t bytes_in_flight, peak_bytes_in_flight, mem_budget;
   int32_t peak_running;
   double uptime_ms;
+  int64_t engine_launches;    /* launches of the level batcher */
+  int64_t engine_jobs;        /* level refinements they ran */
+  int32_t peak_batch;         /* most level refinements one batch took */
 } map_server_stats_t;
 
-/* slots 8, lookahead 8, mem_budget 0 (automatic), no runner. */
+/* slots 8, lookahead 8, mem_budget 0 (automatic), no runner, batch_lanes 0 (2), whole_gpu_levels 0. */
 GPUMAP_API void map_server_opts_default(map_server_opts* opts);
 /* Device bytes a job's context may hold (an upper estimate for graphs whose
  * coarser levels together hold at most twice the input's CSR entries, which

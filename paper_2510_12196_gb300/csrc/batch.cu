@@ -307,7 +307,9 @@ map_status map_batch_create(map_ctx* const* jobs, int32_t njobs, const map_batch
       Ctx& c = B.jobs[i]->c;
       if (!engine_job_write(c, B.opts.level, B.opts.rounds, hj.data() + jb * r))
         throw ApiError(MAP_E_INVALID, "job " + std::to_string(i) +
-                                          ": the level has a vertex of degree > 128; refine it with map_refine");
+                                          ": the level has a row of degree > 128 and a PE code space whose "
+                                          "connectivity table does not fit in shared memory; refine it with "
+                                          "map_refine");
       const Level& L = c.lv[B.opts.level];
       B.max_n = std::max(B.max_n, L.n);
       B.sum_n += L.n;

@@ -172,6 +172,17 @@ struct HmStats {
   int32_t workers = 0;
 };
 
+struct Ctx;
+// Takes the fused-engine refinements of contexts that run beside each other
+// (a server's jobs) and runs them in shared launches of the engine, one
+// thread-block cluster per job.  refine() returns once the level has been
+// refined, with the job's final Alg. 6 state; the context's earlier work on
+// its own stream is ordered before the launch and its later work after it.
+struct EngineSink {
+  virtual ~EngineSink() = default;
+  virtual void refine(Ctx& c, int lvl, int32_t rounds, int C, RefineState* out) = 0;
+};
+
 struct Ctx {
   cudaStream_t st = nullptr;
   map_config cfg{};
@@ -260,6 +271,9 @@ struct Ctx {
   void* mstate = nullptr;            // two-hop matching state (device)
 
   // fused small-level engine
+  EngineSink* sink = nullptr;  // when set, runs the cluster-engine refinements (with other contexts')
+  bool blocking_wait = false;  // host waits sleep on wait_ev instead of spinning
+  cudaEvent_t wait_ev = nullptr;
   int eng_max_cluster = 0;
   void* eng_job = nullptr;    // device job descriptor
   void* gbar = nullptr;       // device barrier state of the grid-wide engine
@@ -300,6 +314,12 @@ struct Ctx {
 
 // api.cu: error text of the last failed context-free call on this thread
 std::string& last_create_error();
+// api.cu: the host waits for a context's stream.  By default the thread
+// spins (lowest latency); contexts created on a thread that asked for
+// blocking waits (a server's workers) sleep on a blocking-sync event, so that
+// many waiting jobs leave the CPU cores to those with host work to do.
+void host_wait(Ctx& c);
+void set_thread_blocking_wait(bool on);
 
 // refine.cu
 void refine_alloc(Ctx& c);

@@ -131,7 +131,6 @@ struct EvalCtl {
   int use_h;
 };
 __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec);
-__device__ void eval_close(int64_t* Jacc, const EvalCtl& ec);
 
 // True when the J evaluation closing an Alg. 6 iteration has nothing to do:
 // after an LP or weak step the step itself added its exact change of J to the
@@ -155,8 +154,12 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_eval_tile(Grap
   const TileGraph tg{g.n, g.xadj, g.adj, g.adjw};
   if (incremental_j(ec.s, ec.phase)) {
     // after an LP or weak step Jacc already holds J (old J + the exact
-    // change): one block runs the decision, the others leave at once
-    if (blockIdx.x == 0) eval_close(Jacc, ec);
+    // change): the blocks only arrive, and the last one runs the decision.
+    // The decision rewrites the step kind that every block reads on entry,
+    // so it must wait for all of them: a block scheduled late (the SMs
+    // shared with other streams' kernels) would otherwise read the next
+    // step's kind and stream its tiles into the accumulator.
+    eval_finish(Jacc, ec);
     return;
   }
   const int64_t ntiles = ((int64_t)g.n + kTileV - 1) / kTileV;
@@ -454,10 +457,27 @@ __host__ inline GroupLayout group_layout(const Topo& t) {
 
 // Fills conn[0, kc) (already zeroed) with the edge weights of v per neighbour
 // PE and the level group sums after it.  Returns T(P(v)) summed over the block.
-// conn of the CSR entries [e0, e1) added into tab[code] (shared memory).
+// conn of the CSR entries [e0, e1) added into tab[code] (shared memory):
+// four entries per thread at a time, whose adjacency loads and PE gathers
+// are all issued before the first add.
 __device__ __forceinline__ void conn_add(const GraphView& g, int64_t e0, int64_t e1, const int32_t* __restrict__ pi,
                                          int32_t* tab) {
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
+  constexpr int kB = 4;
+  const int64_t step = blockDim.x;
+  int64_t e = e0 + threadIdx.x;
+  for (; e + (kB - 1) * step < e1; e += kB * step) {
+    int32_t u[kB], w[kB];
+#pragma unroll
+    for (int b = 0; b < kB; b++) {
+      u[b] = g.adj[e + b * step];
+      w[b] = g.adjw[e + b * step];
+    }
+#pragma unroll
+    for (int b = 0; b < kB; b++) u[b] = pi[u[b]];
+#pragma unroll
+    for (int b = 0; b < kB; b++) atomicAdd(&tab[u[b]], w[b]);
+  }
+  for (; e < e1; e += step) atomicAdd(&tab[pi[g.adj[e]]], g.adjw[e]);
 }
 
 // The level group sums of a complete conn table (layout of GroupLayout).
@@ -1939,24 +1959,15 @@ __device__ void control_step(RefineState* s, int64_t mx, int64_t J, const CtlArg
   }
 }
 
-// Last block of a fused J evaluation: the Alg. 6 decision on the complete J.
 // Value of the J accumulator for the step just decided: the current J when
 // that step adds its exact change (LP, weak), else 0 (a full evaluation).
 __device__ __forceinline__ int64_t next_j_base(const RefineState* s, int64_t J) {
   return (s->kind == KIND_LP || s->kind == KIND_WEAK) ? J : 0;
 }
 
-// The decision on a J that is already complete in the accumulator (one block).
-__device__ void eval_close(int64_t* Jacc, const EvalCtl& ec) {
-  __shared__ int64_t smax[32];
-  const int64_t mx = block_max_w(ec.W, ec.a.kc, smax);
-  if (threadIdx.x == 0) {
-    const int64_t J = *(volatile int64_t*)Jacc;
-    control_step(ec.s, mx, J, ec.a, ec.phase, ec.h, ec.use_h);
-    *Jacc = next_j_base(ec.s, J);
-  }
-}
-
+// Every block of a J evaluation arrives here once its part of J is in the
+// accumulator; the last one to arrive takes the Alg. 6 decision on the
+// complete J (all blocks have read the step kind by then).
 __device__ void eval_finish(int64_t* Jacc, const EvalCtl& ec) {
   __shared__ unsigned int last;
   __shared__ int64_t smax[32];
@@ -2232,15 +2243,17 @@ __global__ void k_strong_gate(const RefineState* st, int64_t* d_sel) {
 // Fused engine: the whole Alg. 6 run of one small level (or of every graph
 // of a batch, one cluster each) in a single launch of thread-block clusters.
 // The phases of an iteration are separated by cluster barriers instead of
-// kernel boundaries; one thread per vertex walks its row (rows have at most
-// kLowDeg entries here); the serial steps (sorts, cut, strong tail, the
-// controller) run in the cluster's first CTA.  Arrays written inside the
-// launch are read through plain pointers (no read-only path), and the
-// barriers order the phases across the cluster's SMs.
+// kernel boundaries; rows of at most kEngLaneDeg entries are taken by warp
+// tiles (one lane or an 8-lane sub-warp per vertex), larger rows by whole
+// CTAs (dense connectivity tables over the PE codes in shared memory, as the
+// hub kernels of the stream path); the serial steps (sorts, cut, strong
+// tail, the controller) run in the cluster's first CTA.  Arrays written
+// inside the launch are read through plain pointers (no read-only path), and
+// the barriers order the phases across the cluster's SMs.
 // ---------------------------------------------------------------------------
 constexpr int kEngThreads = 1024;
 constexpr int kEngMaxN = 1 << 15;   // default: levels of at most this many vertices use the engine
-constexpr int kEngMaxDeg = 128;     // and no vertex of larger degree
+constexpr int kEngLaneDeg = 128;    // larger rows are taken by whole CTAs
 constexpr int kEngMaxCluster = 16;
 static_assert(kEngThreads == kSmallThreads, "the engine's CTA sorts with the single-CTA sort");
 
@@ -2286,6 +2299,11 @@ struct EngineJob {
   int32_t rounds;
   LpFilter flt;
   int32_t reb_obj;  // rebalancing gains: 0 cut, 1 Eq. 1
+  // rows of degree > kEngLaneDeg: found among the vertices of degree > kLowDeg
+  const int32_t* hi;
+  int32_t n_hi;
+  int32_t has_heavy;  // some row has more than kEngLaneDeg entries
+  GroupLayout gl;     // connectivity table layout of those rows
 };
 
 struct PlainRow {  // neighbour PEs through plain loads (the mapping changes inside the launch)
@@ -2381,6 +2399,8 @@ struct EngSmem {
   int64_t sm[33];
   int32_t sdist[32];
   int64_t smax[32];
+  int64_t hb[32];  // per-warp best scores of a CTA-wide row decision
+  int32_t hc[32];  // and their codes
 };
 
 // Stable LSD radix sort (8-bit digits) of n pairs by one CTA through global
@@ -2557,9 +2577,41 @@ __device__ bool eng_reb_select(const EngineJob& J, int32_t v, int64_t sigma, int
 struct EngGeom {
   int64_t gt, GT;  // thread index and thread count of the cluster
   int64_t gw, GW;  // warp index and warp count of the cluster
+  int cta, ncta;   // CTA index and CTA count of the cluster
   int lane;
   bool lead;  // first CTA of the cluster
 };
+
+// Whether a row of `deg` entries is taken by a whole CTA.
+__device__ __forceinline__ bool eng_heavy(const EngineJob& J, int64_t deg) {
+  return J.has_heavy && deg > kEngLaneDeg;
+}
+
+// Calls f(v, b, e) for every row of more than kEngLaneDeg entries that falls
+// to the calling CTA (rows dealt round-robin over the cluster's CTAs); all
+// threads of the CTA take the same rows.
+template <class F>
+__device__ __forceinline__ void eng_heavy_rows(const EngineJob& J, const EngGeom& eg, F f) {
+  if (!J.has_heavy) return;
+  for (int32_t h = eg.cta; h < J.n_hi; h += eg.ncta) {
+    const int32_t v = J.hi[h];
+    const int64_t b = J.g.xadj[v], e = J.g.xadj[v + 1];
+    if (e - b > kEngLaneDeg) f(v, b, e);
+  }
+}
+
+// Dense connectivity table of one row in shared memory (`total` entries
+// zeroed first): conn per PE code, and with `groups` the level group sums
+// (the layout of GroupLayout).  The mapping is read through plain loads.
+// All threads of the CTA call it; ends with a barrier.
+__device__ __forceinline__ void eng_row_table(const EngineJob& J, int64_t b, int64_t e, int32_t* tab, int32_t total,
+                                              bool groups) {
+  for (int32_t i = threadIdx.x; i < total; i += blockDim.x) tab[i] = 0;
+  __syncthreads();
+  for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) atomicAdd(&tab[J.pi[J.g.adj[x]]], J.g.adjw[x]);
+  __syncthreads();
+  if (groups) conn_groups(J.topo, J.gl, tab);
+}
 
 struct PlainGather {  // neighbour PEs through plain loads (the mapping changes inside the launch)
   const int32_t* pi;
@@ -2569,6 +2621,7 @@ struct PlainGather {  // neighbour PEs through plain loads (the mapping changes 
 // Stages one tile of neighbour PEs and returns T(P(v)) = sum_j w_j D(P(v), c_j)
 // of the lane's vertex; `cand` tells whether a staged row has a neighbour
 // outside P(v) (oversized tiles are left to the global path: cand false).
+// A row of more than kEngLaneDeg entries gives 0 and no candidate here.
 template <int kTE>
 __device__ __forceinline__ TileLane eng_stage(const EngineJob& J, const TileGraph& tg, int64_t tile, int lane,
                                               int32_t* sc, int32_t* sw, const int32_t* sdist, int64_t& Tp,
@@ -2576,7 +2629,7 @@ __device__ __forceinline__ TileLane eng_stage(const EngineJob& J, const TileGrap
   const TileLane t = stage_tile<kTE>(tg, tile * kTileV, lane, sc, sw, PlainGather{J.pi});
   Tp = 0;
   cand = false;
-  if (t.v < tg.n) {
+  if (t.v < tg.n && !eng_heavy(J, t.e - t.b)) {
     const int deg = (int)(t.e - t.b);
     const int32_t p = J.pi[t.v];
     if (t.staged) {
@@ -2703,7 +2756,8 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x, int lane) {
 
 // Exact change of J by the moves of an LP or weak step, added to the J
 // accumulator (the mapping still holds the old values): the movers of each
-// warp tile are served four at a time by 8-lane sub-warps.
+// warp tile are served four at a time by 8-lane sub-warps, the movers with
+// more than kEngLaneDeg entries by whole CTAs.
 template <class Mv>
 __device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const EngGeom& eg, int64_t ntiles) {
   const GraphView& g = J.g;
@@ -2711,7 +2765,8 @@ __device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const En
   int64_t acc = 0;
   for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
     const int64_t v = tile * kTileV + lane;
-    const unsigned work = __ballot_sync(0xffffffffu, v < g.n && mv.moved(v));
+    const unsigned work =
+        __ballot_sync(0xffffffffu, v < g.n && mv.moved(v) && !eng_heavy(J, g.xadj[v + 1] - g.xadj[v]));
     const int rounds = (__popc(work) + 3) / 4;
     for (int r = 0; r < rounds; r++) {
       const int src = tile_worker(work, r, sub);
@@ -2724,6 +2779,12 @@ __device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const En
     }
     __syncwarp();
   }
+  eng_heavy_rows(J, eg, [&](int32_t v, int64_t b, int64_t e) {
+    if (!mv.moved(v)) return;
+    const int32_t ov = J.pi[v], nv = mv.target(v);
+    for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x)
+      acc += delta_entry(mv, J.pi, S.sdist, ov, nv, g.adj[x], g.adjw[x]);
+  });
   acc = block_sum(acc, S.sm);
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
 }
@@ -2855,6 +2916,11 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         }
         __syncwarp();
       }
+      eng_heavy_rows(J, eg, [&](int32_t v, int64_t b, int64_t e) {
+        const int32_t p = J.pi[v];
+        for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x)
+          acc += (int64_t)g.adjw[x] * dcode(S.sdist, p, J.pi[g.adj[x]]);
+      });
       acc = block_sum(acc, S.sm);
       if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)J.Jacc, (unsigned long long)acc);
       sy.sync();
@@ -2892,7 +2958,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         bool cand = cand0;
         if (!reuse) t = eng_stage<kTE>(J, tg, tile, lane, sc, sw, S.sdist, Tp, cand, false);
         int32_t p = -1;
-        if (t.v < n) {
+        if (t.v < n && !eng_heavy(J, t.e - t.b)) {
           p = J.pi[t.v];
           bool written = false;
           if (J.lock[t.v]) {
@@ -2928,11 +2994,31 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         });
         __syncwarp();
       }
+      if (J.has_heavy) {
+        __syncthreads();  // the warps' staging areas are free for the row tables
+        const LpFilter flt = kVar ? J.flt : LpFilter{0, 1};
+        eng_heavy_rows(J, eg, [&](int32_t v, int64_t b, int64_t e) {
+          const int32_t p = J.pi[v];
+          if (J.lock[v]) {
+            __syncthreads();  // every thread has read the lock
+            if (threadIdx.x == 0) {
+              J.lock[v] = 0;
+              J.inx[v] = 0;
+              J.pp[v] = p;
+              J.gain[v] = 0;
+            }
+            return;
+          }
+          eng_row_table(J, b, e, dyn, J.gl.total, true);
+          lp_hub_decide(dyn, J.topo, J.gl, flt, v, p, J.pp, J.gain, J.inx, S.hb, S.hc);
+        });
+      }
       sy.sync();
       // step 2: recomputed gain under ord, one 8-lane sub-warp per candidate
       for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
         const int64_t v = tile * kTileV + lane;
-        const unsigned work = __ballot_sync(0xffffffffu, v < n && J.inx[v]);
+        const unsigned work =
+            __ballot_sync(0xffffffffu, v < n && J.inx[v] && !eng_heavy(J, g.xadj[v + 1] - g.xadj[v]));
         const int sub = lane >> 3, sl = lane & 7;
         const int rounds = (__popc(work) + 3) / 4;
         for (int r = 0; r < rounds; r++) {
@@ -2959,6 +3045,23 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
         }
         __syncwarp();
       }
+      eng_heavy_rows(J, eg, [&](int32_t v, int64_t b, int64_t e) {
+        if (!J.inx[v]) return;
+        const int32_t p = J.pi[v], q = J.pp[v];
+        const int64_t gv = J.gain[v];
+        int64_t sum = 0;
+        for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) {
+          const int32_t u = g.adj[x];
+          int32_t bu = J.pi[u];
+          if (J.inx[u]) {
+            const int64_t gu = J.gain[u];
+            if (gu > gv || (gu == gv && u < v)) bu = J.pp[u];
+          }
+          sum += (int64_t)g.adjw[x] * (dcode(S.sdist, p, bu) - dcode(S.sdist, q, bu));
+        }
+        sum = block_sum(sum, S.sm);
+        if (threadIdx.x == 0 && sum >= 0) J.lock[v] = 1;
+      });
       sy.sync();
       eng_delta(J, LpMoves{J.lock, J.pp}, S, eg, ntiles);
       sy.sync();
@@ -2984,7 +3087,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       const int64_t v = tile * kTileV + lane;
       int32_t A = -1;
       bool cand = false;
-      if (v < n) {
+      if (v < n && !eng_heavy(J, g.xadj[v + 1] - g.xadj[v])) {
         A = J.pi[v];
         const int64_t WA = J.W[A];
         cand = WA > J.lmax && 2 * (int64_t)J.k * g.vw[v] <= 3 * ((int64_t)J.k * WA - J.cV);
@@ -3039,6 +3142,19 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       else
         reb_tile_queue<false>(work, tl, A, sc, sw, J.W, sigma, S.sdist, lane, reb_out);
       __syncwarp();
+    }
+    if (J.has_heavy) {
+      __syncthreads();  // the warps' staging areas are free for the row tables
+      const RebArgs ra{J.W, J.U, J.cnt, J.tab, J.lmax, J.cV, J.k, J.seed, kVar ? J.reb_obj : 0, J.topo};
+      eng_heavy_rows(J, eg, [&](int32_t v, int64_t b, int64_t e) {
+        const int32_t A = J.pi[v];
+        if (!reb_eligible(ra, A, g.vw[v])) {
+          if (threadIdx.x == 0) J.elig[v] = 0;
+          return;
+        }
+        eng_row_table(J, b, e, dyn, ra.obj ? J.gl.total : J.topo.kc, ra.obj != 0);
+        reb_hub_decide(dyn, ra, J.topo.kc, J.gl, v, A, g.vw[v], J.dest, J.bkt, J.elig, s, S.hb, S.hc);
+      });
     }
     sy.sync();
     // the cut bucket of each overloaded block A: the first bucket whose
@@ -3266,6 +3382,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine(const EngineJob* __re
   eg.GT = (int64_t)csize * blockDim.x;
   eg.gw = (int64_t)crank * (blockDim.x >> 5) + warp;
   eg.GW = (int64_t)csize * (blockDim.x >> 5);
+  eg.cta = crank;
+  eg.ncta = csize;
   int32_t* sc = eng_dyn + warp * 2 * kTE;
   int32_t* sw = sc + kTE;
   if (!queue) {  // one job per cluster
@@ -3300,6 +3418,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) k_engine_grid(const EngineJob*
   eg.GT = (int64_t)gridDim.x * blockDim.x;
   eg.gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   eg.GW = (int64_t)gridDim.x * (blockDim.x >> 5);
+  eg.cta = (int)blockIdx.x;
+  eg.ncta = (int)gridDim.x;
   int32_t* sc = eng_dyn + warp * 2 * kTE;
   int32_t* sw = sc + kTE;
   engine_run_job<kTE, kVar>(*job, S, eng_dyn, sc, sw, eg, GridSync{bar, &bar_flag, gridDim.x});
@@ -3433,7 +3553,7 @@ void objective(Ctx& c, int lvl, int64_t* J, int64_t* maxw) {
   int64_t hJ = 0;
   GM_CUDA(cudaMemcpyAsync(&hJ, c.Jacc, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(W.data(), c.W, W.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   if (J) *J = hJ;
   if (maxw) *maxw = W.empty() ? 0 : *std::max_element(W.begin(), W.end());
 }
@@ -3450,7 +3570,7 @@ static void set_state(Ctx& c, int32_t kind, int32_t t, int32_t level) {
 
 static int32_t read_moved(Ctx& c) {
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   return c.h_state->moved;
 }
 
@@ -3488,7 +3608,7 @@ static void refine_stream(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* 
   const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
   while (true) {
     GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-    GM_CUDA(cudaStreamSynchronize(c.st));
+    host_wait(c);
     const RefineState h = *c.h_state;
     if (h.done) break;
     if (h.kind == KIND_LP) {
@@ -3609,7 +3729,7 @@ static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* m
     build_refine_graph(c, lvl, rounds);
   GM_CUDA(cudaGraphLaunch(L.gexec, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   const RefineState h = *c.h_state;
   add_launches(L.g_root + (long long)h.kernels);
   if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
@@ -3619,10 +3739,24 @@ static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* m
   if (iters) *iters = h.t;
 }
 
+// dynamic shared memory: the warps' staging arrays, or the two key / value
+// buffers of the single-CTA sort (used at other times)
+static size_t engine_smem(int te) {
+  return std::max((size_t)(kEngThreads / 32) * 2 * te * sizeof(int32_t),
+                  (size_t)2 * kSmallSort * (sizeof(uint64_t) + sizeof(int32_t)));
+}
+
+// Whether the engine takes every row of a level: the rows of more than
+// kEngLaneDeg entries need their connectivity table (conn per PE code and the
+// level group sums) in the dynamic shared memory of the smallest build.
+static bool engine_rows_fit(const Ctx& c, const Level& L) {
+  return L.max_deg <= kEngLaneDeg || (size_t)group_layout(c.topo).total * sizeof(int32_t) <= engine_smem(256);
+}
+
 // Cluster size of the fused engine for a level (0: not used).
 static int engine_cluster(Ctx& c, const Level& L) {
   const int64_t lim = c.cfg.engine_max_n > 0 ? c.cfg.engine_max_n : (c.cfg.engine_max_n < 0 ? -1 : kEngMaxN);
-  if (!c.use_graphs || c.prof || L.n > lim || L.max_deg > kEngMaxDeg) return 0;
+  if (!c.use_graphs || c.prof || L.n > lim || !engine_rows_fit(c, L)) return 0;
   int C = (L.n + 1023) / 1024;  // about one vertex per thread
   if (C < 1) C = 1;
   if (C > c.eng_max_cluster) C = c.eng_max_cluster;
@@ -3637,13 +3771,6 @@ static EngineKernel engine_kernel(int te, bool var = false) {
 }
 using GridKernel = void (*)(const EngineJob*, GridBar*);
 static GridKernel grid_kernel(bool var) { return var ? k_engine_grid<512, true> : k_engine_grid<512, false>; }
-
-// dynamic shared memory: the warps' staging arrays, or the two key / value
-// buffers of the single-CTA sort (used at other times)
-static size_t engine_smem(int te) {
-  return std::max((size_t)(kEngThreads / 32) * 2 * te * sizeof(int32_t),
-                  (size_t)2 * kSmallSort * (sizeof(uint64_t) + sizeof(int32_t)));
-}
 
 static cudaLaunchConfig_t engine_config(int C, int te, unsigned grid, cudaStream_t st, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg{};
@@ -3753,6 +3880,10 @@ static EngineJob engine_job(Ctx& c, int lvl, int32_t rounds) {
   j.reb_obj = c.cfg.reb_objective;
   j.level = lvl;
   j.rounds = rounds;
+  j.hi = L.hi;
+  j.n_hi = L.n_hi;
+  j.has_heavy = L.max_deg > kEngLaneDeg ? 1 : 0;
+  j.gl = group_layout(c.topo);
   return j;
 }
 
@@ -3761,7 +3892,7 @@ size_t engine_job_bytes() { return sizeof(EngineJob); }
 bool engine_job_write(Ctx& c, int lvl, int32_t rounds, void* dst) {
   engine_setup(c);
   const Level& L = c.lv[lvl];
-  if (L.max_deg > kEngMaxDeg) return false;
+  if (!engine_rows_fit(c, L)) return false;
   *static_cast<EngineJob*>(dst) = engine_job(c, lvl, rounds);
   return true;
 }
@@ -3782,7 +3913,7 @@ static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, in
   GM_CUDA(cudaMemcpyAsync(c.eng_job, c.h_eng_job, sizeof(EngineJob), cudaMemcpyHostToDevice, c.st));
   engine_launch(c.st, c.eng_job, 1, nullptr, C, 512, 1, uses_variants(c.cfg));
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   const RefineState h = *c.h_state;
   if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
   c.last_iters = h.t;
@@ -3796,7 +3927,7 @@ static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, in
 static bool engine_grid_ok(Ctx& c, const Level& L) {
   const int64_t lim =
       c.cfg.grid_engine_max_n > 0 ? c.cfg.grid_engine_max_n : (c.cfg.grid_engine_max_n < 0 ? -1 : (1 << 18));
-  if (!c.use_graphs || c.prof || L.n > lim || L.max_deg > kEngMaxDeg) return false;
+  if (!c.use_graphs || c.prof || L.n > lim || !engine_rows_fit(c, L)) return false;
   static std::atomic<int> cached[64];  // a property of the device: once per process
   if (c.eng_grid_blocks == 0) c.eng_grid_blocks = cached[c.dev & 63].load();
   if (c.eng_grid_blocks == 0) {
@@ -3838,7 +3969,7 @@ static void refine_engine_grid(Ctx& c, int lvl, int32_t rounds, int64_t* J, int6
   count_launch();
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_small, c.gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   if (reinterpret_cast<const GridBar*>(c.h_small)->err)
     throw ApiError(MAP_E_TIMEOUT, "a grid barrier of the refinement engine gave up waiting");
   const RefineState h = *c.h_state;
@@ -3883,7 +4014,15 @@ bool barrier_selftest(cudaStream_t st) {
 void refine(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* maxw, int32_t* iters) {
   engine_setup(c);
   const int C = engine_cluster(c, c.lv[lvl]);
-  if (C > 0) refine_engine(c, lvl, rounds, C, J, maxw, iters);
+  if (C > 0 && c.sink) {
+    RefineState h{};
+    c.sink->refine(c, lvl, rounds, C, &h);
+    if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
+    c.last_iters = h.t;
+    if (J) *J = h.best_J;
+    if (maxw) *maxw = h.best_maxw;
+    if (iters) *iters = h.t;
+  } else if (C > 0) refine_engine(c, lvl, rounds, C, J, maxw, iters);
   else if (engine_grid_ok(c, c.lv[lvl])) refine_engine_grid(c, lvl, rounds, J, maxw, iters);
   else if (c.use_graphs && !c.prof) refine_graph(c, lvl, rounds, J, maxw, iters);
   else refine_stream(c, lvl, rounds, J, maxw, iters);
@@ -3984,7 +4123,7 @@ struct LoadHubDeg {
 // one device value read back through the context's pinned block (slot 5)
 int64_t read_i64_at(Ctx& c, const int64_t* d) {
   GM_CUDA(cudaMemcpyAsync(c.h_small + 5, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   return c.h_small[5];
 }
 
@@ -4060,7 +4199,7 @@ void classify_with(Ctx& c, Level& L, int32_t mid_deg, int64_t split_deg) {
   GM_CUDA(cudaMemcpyAsync(c.h_small, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
                           cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_small + 1, st, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  GM_CUDA(cudaStreamSynchronize(c.st));
+  host_wait(c);
   L.n_hi = (int32_t)(c.h_small[0] & 0xffffffffLL);
   L.n_huge = (int32_t)(c.h_small[0] >> 32);
   L.m_hi = c.h_small[1];

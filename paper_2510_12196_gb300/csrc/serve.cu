@@ -13,6 +13,19 @@
 // and their kernels overlap with the running jobs' on the device.  A job is
 // the ordinary pipeline (map_create, map_run, download of the mapping,
 // map_destroy) on the worker's stream; its result is the one it has alone.
+//
+// Batching across requests: the small levels of the running jobs (those the
+// fused engine refines on one thread-block cluster) are not launched by each
+// job but handed to the server's level batcher, whose `batch_lanes` threads
+// each take every refinement that is waiting when they become free and run
+// them in one persistent launch of the engine, one cluster per job, largest
+// job first; jobs asking for the same cluster size share a launch, the
+// launches of one batch run side by side on the lane's streams.  While a
+// batch runs, newly arriving refinements wait for the next free lane, so the
+// batches grow with the load.  A job's result does not depend on the batch
+// it ran in (the engine keeps each job's buffers), and by default the jobs
+// leave out the cooperative whole-GPU engine, whose launches hold every SM
+// and would stop the other jobs' kernels for their whole duration.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -52,6 +65,217 @@ int64_t code_space(const int32_t* hier, int32_t levels) {
   return bits > 30 ? (int64_t)1 << 30 : (int64_t)1 << bits;
 }
 
+// The server's level batcher (see the file comment).
+class LevelBatcher final : public EngineSink {
+ public:
+  static constexpr int kMaxBatch = 256;
+  static constexpr int kSizes = 5;  // cluster sizes 1, 2, 4, 8, 16
+
+  struct Stats {
+    int64_t launches = 0, jobs = 0;
+    int32_t peak_batch = 0;
+  };
+
+  LevelBatcher(int dev, int lanes) : dev_(dev) {
+    try {
+      for (int i = 0; i < lanes; i++) lanes_.emplace_back(&LevelBatcher::lane, this);
+    } catch (...) {
+      stop();
+      throw;
+    }
+  }
+  ~LevelBatcher() override { stop(); }
+
+  void refine(Ctx& c, int lvl, int32_t rounds, int C, RefineState* out) override {
+    Req r;
+    r.c = &c;
+    r.lvl = lvl;
+    r.rounds = rounds;
+    r.C = C;
+    GM_CUDA(cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming));
+    const cudaError_t e = cudaEventRecord(r.ready, c.st);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(r.ready);
+      GM_CUDA(e);
+    }
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      pending_.push_back(&r);
+    }
+    cv_req_.notify_one();
+    {
+      std::unique_lock<std::mutex> lock(mu_);
+      cv_done_.wait(lock, [&] { return r.done; });
+    }
+    cudaEventDestroy(r.ready);
+    if (r.status != MAP_OK) throw ApiError(r.status, r.err);
+    *out = r.st;
+  }
+
+  Stats stats() {
+    std::lock_guard<std::mutex> lock(mu_);
+    return stats_;
+  }
+
+ private:
+  struct Req {
+    Ctx* c = nullptr;
+    int lvl = 0;
+    int32_t rounds = 0;
+    int C = 1;
+    cudaEvent_t ready = nullptr;
+    bool done = false;
+    map_status status = MAP_OK;
+    std::string err;
+    RefineState st{};
+  };
+
+  void stop() {
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      stopping_ = true;
+    }
+    cv_req_.notify_all();
+    for (auto& t : lanes_)
+      if (t.joinable()) t.join();
+    lanes_.clear();
+  }
+
+  // One batch: the waiting requests grouped by cluster size, each group one
+  // persistent launch on its own stream, largest job first.
+  void run_batch(std::vector<Req*>& batch, cudaStream_t* st, cudaEvent_t* done, void* d_jobs,
+                 unsigned int* d_queue, unsigned char* h_jobs, RefineState* h_states) {
+    const size_t jb = engine_job_bytes();
+    std::vector<Req*> group[kSizes];
+    for (Req* r : batch) {
+      int g = 0;
+      while (g + 1 < kSizes && (1 << g) < r->C) g++;
+      group[g].push_back(r);
+    }
+    size_t off = 0;
+    for (int g = 0; g < kSizes; g++) {
+      std::vector<Req*>& rs = group[g];
+      if (rs.empty()) continue;
+      std::stable_sort(rs.begin(), rs.end(), [](const Req* x, const Req* y) {
+        const Level& a = x->c->lv[x->lvl];
+        const Level& b = y->c->lv[y->lvl];
+        return (int64_t)a.n + a.m > (int64_t)b.n + b.m;
+      });
+      bool var = false;
+      for (size_t i = 0; i < rs.size(); i++) {
+        GM_CUDA(cudaStreamWaitEvent(st[g], rs[i]->ready, 0));
+        if (!engine_job_write(*rs[i]->c, rs[i]->lvl, rs[i]->rounds, h_jobs + jb * (off + i)))
+          throw ApiError(MAP_E_INTERNAL, "a level handed to the batcher does not suit the engine");
+        var = var || uses_variants(rs[i]->c->cfg);
+      }
+      const int C = 1 << g;
+      const int ncl = std::min<int>(engine_max_clusters(C, 512), (int)rs.size());
+      if (ncl < 1) throw ApiError(MAP_E_CUDA, "the refinement engine cannot be launched on this device");
+      unsigned char* dj = static_cast<unsigned char*>(d_jobs) + jb * off;
+      GM_CUDA(cudaMemcpyAsync(dj, h_jobs + jb * off, jb * rs.size(), cudaMemcpyHostToDevice, st[g]));
+      GM_CUDA(cudaMemsetAsync(d_queue + g, 0, sizeof(unsigned int), st[g]));
+      engine_launch(st[g], dj, (int)rs.size(), d_queue + g, C, 512, ncl, var);
+      for (size_t i = 0; i < rs.size(); i++)
+        GM_CUDA(cudaMemcpyAsync(&h_states[off + i], rs[i]->c->state, sizeof(RefineState), cudaMemcpyDeviceToHost,
+                                st[g]));
+      {
+        std::lock_guard<std::mutex> lock(mu_);
+        stats_.launches++;
+      }
+      off += rs.size();
+    }
+    for (int g = 0; g < kSizes; g++) {  // a sleeping wait (see host_wait)
+      GM_CUDA(cudaEventRecord(done[g], st[g]));
+      GM_CUDA(cudaEventSynchronize(done[g]));
+    }
+    off = 0;
+    for (int g = 0; g < kSizes; g++)
+      for (Req* r : group[g]) r->st = h_states[off++];
+  }
+
+  void lane() {
+    cudaStream_t st[kSizes] = {};
+    void* d_jobs = nullptr;
+    unsigned int* d_queue = nullptr;
+    unsigned char* h_jobs = nullptr;
+    RefineState* h_states = nullptr;
+    std::string setup_err;
+    if (cudaSetDevice(dev_) != cudaSuccess) setup_err = "cudaSetDevice failed";
+    cudaEvent_t done[kSizes] = {};
+    for (int g = 0; g < kSizes && setup_err.empty(); g++)
+      if (cudaStreamCreateWithFlags(&st[g], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&done[g], cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess)
+        setup_err = "stream creation failed";
+    if (setup_err.empty() && (cudaMalloc(&d_jobs, engine_job_bytes() * kMaxBatch) != cudaSuccess ||
+                              cudaMalloc(&d_queue, kSizes * sizeof(unsigned int)) != cudaSuccess ||
+                              cudaMallocHost(&h_jobs, engine_job_bytes() * kMaxBatch) != cudaSuccess ||
+                              cudaMallocHost(&h_states, sizeof(RefineState) * kMaxBatch) != cudaSuccess))
+      setup_err = "the level batcher could not allocate its buffers";
+    if (!setup_err.empty()) cudaGetLastError();
+    while (true) {
+      std::vector<Req*> batch;
+      {
+        std::unique_lock<std::mutex> lock(mu_);
+        cv_req_.wait(lock, [&] { return stopping_ || !pending_.empty(); });
+        if (pending_.empty()) break;  // stopping
+        while (!pending_.empty() && (int)batch.size() < kMaxBatch) {
+          batch.push_back(pending_.front());
+          pending_.pop_front();
+        }
+      }
+      map_status status = MAP_OK;
+      std::string err;
+      if (!setup_err.empty()) {
+        status = MAP_E_OOM;
+        err = setup_err;
+      } else {
+        try {
+          run_batch(batch, st, done, d_jobs, d_queue, h_jobs, h_states);
+        } catch (const ApiError& e) {
+          status = e.status;
+          err = e.what();
+        } catch (const CudaError& e) {
+          status = e.code == cudaErrorMemoryAllocation ? MAP_E_OOM : MAP_E_CUDA;
+          err = e.what();
+        } catch (const std::exception& e) {
+          status = MAP_E_INTERNAL;
+          err = e.what();
+        }
+        if (status != MAP_OK)
+          for (int g = 0; g < kSizes; g++) cudaStreamSynchronize(st[g]);
+      }
+      {
+        std::lock_guard<std::mutex> lock(mu_);
+        for (Req* r : batch) {
+          r->status = status;
+          r->err = err;
+          r->done = true;
+        }
+        stats_.jobs += (int64_t)batch.size();
+        stats_.peak_batch = std::max(stats_.peak_batch, (int32_t)batch.size());
+      }
+      cv_done_.notify_all();
+    }
+    for (int g = 0; g < kSizes; g++) {
+      if (st[g]) cudaStreamDestroy(st[g]);
+      if (done[g]) cudaEventDestroy(done[g]);
+    }
+    if (d_jobs) cudaFree(d_jobs);
+    if (d_queue) cudaFree(d_queue);
+    if (h_jobs) cudaFreeHost(h_jobs);
+    if (h_states) cudaFreeHost(h_states);
+    cudaGetLastError();
+  }
+
+  int dev_;
+  std::mutex mu_;
+  std::condition_variable cv_req_, cv_done_;
+  std::deque<Req*> pending_;
+  bool stopping_ = false;
+  Stats stats_;
+  std::vector<std::thread> lanes_;
+};
+
 }  // namespace
 }  // namespace gm
 
@@ -71,6 +295,7 @@ struct map_server {
   bool stopping = false;
   map_server_stats_t stats{};
   std::vector<std::thread> workers;
+  std::unique_ptr<LevelBatcher> batcher;  // null: every job launches its own engine
   std::string err;
 
   double now_ms() const {
@@ -102,15 +327,21 @@ void fill_error(map_job_result& r, map_status st, const char* msg) {
 }
 
 // The mapping pipeline of one job on `stream`.
-void run_pipeline(Job& j, cudaStream_t stream) {
+void run_pipeline(map_server& S, Job& j, cudaStream_t stream) {
   const map_job& d = j.desc;
+  map_config cfg;
+  if (j.has_cfg) cfg = j.cfg;
+  else map_config_default(&cfg);
+  // the whole-GPU engine only where asked for explicitly (see the file comment)
+  if (!S.opts.whole_gpu_levels && cfg.grid_engine_max_n == 0) cfg.grid_engine_max_n = -1;
   map_ctx* ctx = nullptr;
   map_status st = map_create(d.xadj, d.adjncy, d.adjwgt, d.vwgt, d.n, j.hier.data(), j.dist.data(),
-                             (int32_t)j.hier.size(), d.eps, j.has_cfg ? &j.cfg : nullptr, (void*)stream, 0, &ctx);
+                             (int32_t)j.hier.size(), d.eps, &cfg, (void*)stream, 0, &ctx);
   if (st != MAP_OK) {
     fill_error(j.res, st, map_last_error(nullptr));
     return;
   }
+  ctx->c.sink = S.batcher.get();
   int64_t J = 0;
   st = map_run(ctx, d.out_pi, &J);
   if (st != MAP_OK) {
@@ -128,6 +359,8 @@ void run_pipeline(Job& j, cudaStream_t stream) {
 
 void worker(map_server* S) {
   if (cudaSetDevice(S->dev) != cudaSuccess) cudaGetLastError();
+  // the jobs' host waits sleep instead of spinning: many workers wait at once
+  set_thread_blocking_wait(true);
   cudaStream_t stream = nullptr;
   if (!S->opts.runner) {
     if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -154,7 +387,7 @@ void worker(map_server* S) {
       j->res.status = (map_status)S->opts.runner(&j->desc, (void*)stream, S->opts.runner_user, &j->res);
     } else {
       try {
-        run_pipeline(*j, stream);
+        run_pipeline(*S, *j, stream);
       } catch (...) {
         fill_error(j->res, MAP_E_INTERNAL, "unexpected exception in the server worker");
       }
@@ -185,6 +418,8 @@ void map_server_opts_default(map_server_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->slots = 8;
   o->lookahead = 8;
+  o->batch_lanes = 0;
+  o->whole_gpu_levels = 0;
 }
 
 int64_t map_job_estimate_bytes(int32_t n, int64_t m_dir, const int32_t* hier, int32_t levels) {
@@ -209,8 +444,12 @@ map_status map_server_create(const map_server_opts* opts, map_server** out) {
   else map_server_opts_default(&S->opts);
   if (S->opts.slots == 0) S->opts.slots = 8;
   if (S->opts.lookahead == 0) S->opts.lookahead = 8;
-  if (S->opts.slots < 1 || S->opts.slots > 256 || S->opts.lookahead < 1 || S->opts.mem_budget < 0) {
-    last_create_error() = "slots must be in [1, 256], lookahead >= 1, mem_budget >= 0";
+  if (S->opts.batch_lanes == 0) S->opts.batch_lanes = 2;
+  if (S->opts.slots < 1 || S->opts.slots > 256 || S->opts.lookahead < 1 || S->opts.mem_budget < 0 ||
+      S->opts.batch_lanes < -1 || S->opts.batch_lanes > 16 || S->opts.whole_gpu_levels < 0 ||
+      S->opts.whole_gpu_levels > 1) {
+    last_create_error() = "slots must be in [1, 256], lookahead >= 1, mem_budget >= 0, batch_lanes in -1..16, "
+                          "whole_gpu_levels 0 or 1";
     return MAP_E_INVALID;
   }
   if (cudaGetDevice(&S->dev) != cudaSuccess) {
@@ -227,6 +466,14 @@ map_status map_server_create(const map_server_opts* opts, map_server** out) {
     }
   }
   S->t0 = std::chrono::steady_clock::now();
+  if (!S->opts.runner && S->opts.batch_lanes > 0) {
+    try {
+      S->batcher.reset(new LevelBatcher(S->dev, S->opts.batch_lanes));
+    } catch (...) {
+      last_create_error() = "could not start the level batcher";
+      return MAP_E_INTERNAL;
+    }
+  }
   try {
     for (int i = 0; i < S->opts.slots; i++) S->workers.emplace_back(worker, S.get());
   } catch (...) {
@@ -318,6 +565,12 @@ map_status map_server_stats(map_server* S, map_server_stats_t* out) {
   if (!S || !out) return MAP_E_INVALID;
   std::lock_guard<std::mutex> lock(S->mu);
   *out = S->stats;
+  if (S->batcher) {
+    const LevelBatcher::Stats b = S->batcher->stats();
+    out->engine_launches = b.launches;
+    out->engine_jobs = b.jobs;
+    out->peak_batch = b.peak_batch;
+  }
   out->queued = (int64_t)S->queue.size();
   out->mem_budget = S->opts.mem_budget;
   out->uptime_ms = S->now_ms();
@@ -343,6 +596,7 @@ void map_server_destroy(map_server* S) {
   S->cv_work.notify_all();
   S->cv_done.notify_all();
   for (auto& t : S->workers) t.join();
+  S->batcher.reset();  // after the workers: their jobs may still hand it levels
   delete S;
 }
 

@@ -476,14 +476,16 @@ JOB_RUNNER = C.CFUNCTYPE(C.c_int32, C.POINTER(MapJob), C.c_void_p, C.c_void_p, C
 
 class MapServerOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("lookahead", C.c_int32), ("mem_budget", C.c_int64),
-                ("runner", JOB_RUNNER), ("runner_user", C.c_void_p)]
+                ("runner", JOB_RUNNER), ("runner_user", C.c_void_p), ("batch_lanes", C.c_int32),
+                ("whole_gpu_levels", C.c_int32)]
 
 
 class MapServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("queued", C.c_int64), ("running", C.c_int64), ("bytes_in_flight", C.c_int64),
                 ("peak_bytes_in_flight", C.c_int64), ("mem_budget", C.c_int64), ("peak_running", C.c_int32),
-                ("uptime_ms", C.c_double)]
+                ("uptime_ms", C.c_double), ("engine_launches", C.c_int64), ("engine_jobs", C.c_int64),
+                ("peak_batch", C.c_int32)]
 
 
 def map_job_estimate_bytes(n: int, m_dir: int, hier) -> int:
@@ -495,10 +497,12 @@ class MapServer:
     """Request loop over the C server (see include/gpumap.h).  Keeps every
     submitted job's host arrays alive until its result is collected."""
 
-    def __init__(self, slots: int = 8, lookahead: int = 8, mem_budget: int = 0, runner=None):
+    def __init__(self, slots: int = 8, lookahead: int = 8, mem_budget: int = 0, runner=None,
+                 batch_lanes: int = 0, whole_gpu_levels: int = 0):
         o = MapServerOpts()
         lib().map_server_opts_default(C.byref(o))
         o.slots, o.lookahead, o.mem_budget = slots, lookahead, mem_budget
+        o.batch_lanes, o.whole_gpu_levels = batch_lanes, whole_gpu_levels
         self._runner = JOB_RUNNER(runner) if runner is not None else None
         if self._runner is not None:
             o.runner = self._runner

@@ -1,7 +1,8 @@
 """Batched refinement (one persistent launch over many contexts) against the
 CPU oracle: every job of the batch must equal Alg. 6 run on that graph alone,
-for every schedule the autotuner can pick, on graph replays, and on the full
-64-graph batch workload (RGGs of 2^12..2^18 vertices, 10 fixed rounds)."""
+for every schedule the autotuner can pick, on graph replays, on degree-skewed
+jobs (rows above 128 entries rated by whole CTAs), and on the full 64-graph
+batch workload (RGGs of 2^12..2^18 vertices, 10 fixed rounds)."""
 import numpy as np
 import pytest
 
@@ -188,7 +189,9 @@ def test_batch_errors():
     jobs = _jobs([500, 600], seed0=0x5EED1400)
     ctxs = _make(jobs)
     star = I.csr_from_pairs(300, np.zeros(299, np.int64), np.arange(1, 300), name="star300")
-    cs = make_ctx(star, (4, 8), (1, 10))
+    # a row of degree 299 with 2^14 PE codes in binary groups: its table (conn
+    # per code plus the level group sums) does not fit in shared memory
+    cs = make_ctx(star, (2,) * 14, tuple(range(1, 15)))
     try:
         with pytest.raises(G.MapError) as e:
             G.map_batch_create([ctxs[0], ctxs[0]])
@@ -197,7 +200,7 @@ def test_batch_errors():
             G.map_batch_create(ctxs, G.map_batch_opts_default(level=3))
         assert e.value.status == 6
         with pytest.raises(G.MapError) as e:
-            G.map_batch_create([ctxs[1], cs])  # a vertex of degree 299
+            G.map_batch_create([ctxs[1], cs])  # degree 299, 2^14 binary codes
         assert e.value.status == 1
         with pytest.raises(G.MapError) as e:
             G.map_batch_create(ctxs, G.map_batch_opts_default(rounds=0))
@@ -230,3 +233,85 @@ def test_batch_workload_64_rggs_full_size():
     finally:
         for c in ctxs:
             G.map_destroy(c)
+
+
+def _skewed_jobs(seed0=0x5EED1600):
+    """Degree-skewed jobs: R-MAT graphs (hubs of hundreds to thousands of
+    entries, isolated vertices), a star, the degree-mix graph and a dense
+    Erdos-Renyi graph, under hierarchies of two to four levels."""
+    graphs = [I.rmat(10, 8, 0.57, 0.19, 0.19, seed0), I.rmat(12, 16, 0.57, 0.19, 0.19, seed0 + 1),
+              I.csr_from_pairs(300, np.zeros(299, np.int64), np.arange(1, 300), name="star300"),
+              I.degree_mix(), I.erdos_renyi(400, 0.5, seed0 + 2, wmax=9, vwmax=4),
+              I.rmat(13, 16, 0.57, 0.19, 0.19, seed0 + 3), I.rgg2d(5000, I.rgg_radius(5000, 10.0), seed0 + 4, wmax=10)]
+    hiers = ((4, 8), (4, 8, 8), (2, 4, 16, 8), (4, 16, 8))
+    out = []
+    for i, g in enumerate(graphs):
+        hier = hiers[i % len(hiers)]
+        dist = (1, 10, 100, 1000)[:len(hier)]
+        out.append((g, hier, dist, I.random_mapping(g.n, int(np.prod(hier)), seed0 + 16 + i)))
+    return out
+
+
+@pytest.mark.parametrize("rounds", [10, -1])
+def test_batch_degree_skewed_jobs(rounds):
+    """Rows of more than 128 entries are rated by whole CTAs inside the
+    engine (connectivity tables over the PE codes): every job of a batch of
+    power-law, star and dense graphs equals the oracle, whichever number of
+    CTAs per job and staging capacity runs it."""
+    jobs = _skewed_jobs()
+    assert max(int(np.diff(g.xadj).max()) for g, _, _, _ in jobs) > 1000
+    ref = _oracle(jobs, rounds)
+    ctxs = _make(jobs)
+    try:
+        for opts in ({}, dict(autotune=0, cluster=1, tile_entries=512), dict(autotune=0, cluster=16, tile_entries=256)):
+            _reset(ctxs, jobs)
+            J, mw, it, _ = _run_batch(ctxs, rounds=rounds, **opts)
+            _check(ctxs, J, mw, it, ref)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
+def test_batch_degree_skewed_variants():
+    """The same with the refinement variants (relaxed Alg. 4 filter, Eq. 1
+    gains in rebalancing), which the CTA-per-row decisions also take."""
+    jobs = _skewed_jobs(seed0=0x5EED1700)[:5]
+    ref = []
+    for g, hier, dist, pi0 in jobs:
+        L = O.lmax(int(g.vw.sum()), int(np.prod(hier)), 0.03)
+        prm = oracle_params(lp_relax_num=3, lp_relax_den=4, reb_objective=1)
+        opi, oJ, omx, oit, okinds, _, _ = O.refine(g, hier, dist, L, pi0, rounds=12, params=prm)
+        ref.append((opi, oJ, omx, oit, okinds))
+    ctxs = []
+    for g, hier, dist, pi0 in jobs:
+        c = make_ctx(g, hier, dist, lp_relax_num=3, lp_relax_den=4, reb_objective=1)
+        G.map_set_mapping(c, 0, pi0)
+        ctxs.append(c)
+    try:
+        J, mw, it, _ = _run_batch(ctxs, rounds=12)
+        _check(ctxs, J, mw, it, ref)
+    finally:
+        for c in ctxs:
+            G.map_destroy(c)
+
+
+@pytest.mark.parametrize("engine", ["cluster", "grid"])
+def test_engine_power_law_level(engine):
+    """map_refine of an R-MAT scale-16 level (65,536 vertices, hubs of
+    thousands of entries) in the fused engine: on one cluster, or over all
+    SMs (the default for levels above 32,768 vertices); Alg. 6 termination."""
+    g = I.rmat(16, 16, 0.57, 0.19, 0.19, 0x5EED1800)
+    hier, dist = (4, 16, 8), (1, 10, 100)
+    pi0 = I.random_mapping(g.n, 512, 0x5EED1801)
+    L = O.lmax(int(g.vw.sum()), 512, 0.03)
+    opi, oJ, omx, oit, okinds, _, _ = O.refine(g, hier, dist, L, pi0, rounds=-1, params=oracle_params())
+    over = dict(engine_max_n=1 << 17, grid_engine_max_n=-1) if engine == "cluster" else {}
+    c = make_ctx(g, hier, dist, **over)
+    try:
+        G.map_set_mapping(c, 0, pi0)
+        assert G.map_refine(c, 0, -1) == (oJ, omx, oit)
+        assert np.array_equal(G.map_get_mapping(c, 0), opi)
+        kinds, _, _, cnt = G.map_get_refine_trace(c)
+        assert cnt == oit and np.array_equal(kinds, okinds)
+    finally:
+        G.map_destroy(c)

@@ -1,6 +1,7 @@
 """The mapping server on the GPU: jobs of the serving mix (3D grids and RGGs,
-hierarchies up to 4:16:16) give the same J and mapping when they run alone
-and when they overlap with others under memory admission; the admission
+hierarchies up to 4:16:16) and degree-skewed jobs give the same J and mapping
+when they run alone and when they overlap with others under memory admission,
+with their small levels batched across requests or not; the admission
 estimate bounds what each job's context really held."""
 import numpy as np
 import pytest
@@ -105,3 +106,55 @@ def test_estimate_bounds_full_size_jobs():
             G.map_destroy(ctx)
         est = G.map_job_estimate_bytes(g.n, g.m_dir, h)
         assert peak <= est, (g.n, peak, est)
+
+
+def _small_mix():
+    """Twenty small jobs (every level refined by the fused engine): 3D grids,
+    RGGs and R-MAT graphs (rows of hundreds of entries)."""
+    out = []
+    hiers = ((4, 8), (4, 8, 8), (4, 16, 8), (4, 16, 16))
+    for i in range(20):
+        h = hiers[i % 4]
+        d = (1, 10, 100)[:len(h)]
+        if i % 3 == 0:
+            g = I.grid3d(8 << (i % 2), 8, 8 << (i % 3 == 0))
+        elif i % 3 == 1:
+            n = 2000 + 1500 * i
+            g = I.rgg2d(n, I.rgg_radius(n, 12.0), 0x5EED2100 + i, wmax=10)
+        else:
+            g = I.rmat(10 + i % 4, 8, 0.57, 0.19, 0.19, 0x5EED2200 + i)
+        out.append((g, h, d))
+    return out
+
+
+@pytest.mark.parametrize("lanes,whole_gpu", [(1, 0), (2, 0), (-1, 1)])
+def test_batched_small_levels_equal_alone(lanes, whole_gpu):
+    """Small levels of concurrent jobs refined in shared engine launches
+    (one or two batcher lanes), or each job on its own (lanes -1, whole-GPU
+    engine allowed): every result equals the job alone, which equals the
+    oracle on the degree-skewed jobs."""
+    jobs = _small_mix()
+    alone = [_alone(*j) for j in jobs]
+    for k in (2, 5):  # R-MAT jobs against the oracle
+        (g, h, d), (J, pi) = jobs[k], alone[k]
+        opi, oJ, _ = O.map_run(g, h, d, 0.03, oracle_params())
+        assert J == oJ and np.array_equal(pi, opi)
+    srv = G.MapServer(slots=8, lookahead=8, batch_lanes=lanes, whole_gpu_levels=whole_gpu)
+    try:
+        tickets = [srv.submit(g, h, d, user=i) for i, (g, h, d) in enumerate(jobs)]
+        res = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.close()
+    for i, ((r, pi), (J, opi)) in enumerate(zip(res, alone)):
+        assert r.status == 0, r.error
+        assert r.J == J and np.array_equal(pi, opi), i
+    assert st.completed == len(jobs) and st.failed == 0
+    if lanes > 0:
+        # every job's levels went through the batcher; with one lane and
+        # eight jobs in flight, refinements of several requests shared a launch
+        assert st.engine_jobs >= len(jobs) and st.engine_launches >= 1
+        if lanes == 1:
+            assert st.engine_launches < st.engine_jobs and st.peak_batch >= 2
+    else:
+        assert st.engine_launches == 0 and st.engine_jobs == 0
