@@ -108,7 +108,9 @@ def parse():
                     help="length of each Poisson stream (requests = rate x seconds)")
     ap.add_argument("--serve-pool", type=int, default=48,
                     help="distinct requests generated; the stream cycles through them")
-    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-lanes", type=int, default=0,
+                    help="level batcher threads of the server (0: the library default, -1: no batching)")
     ap.add_argument("--probe", action="store_true",
                     help="one map_run, then one label-propagation step and one J evaluation on the input "
                          "graph inside the NVTX range 'probe', the coarsening again inside 'probe_coarsen' and "
@@ -886,16 +888,17 @@ def run_serve(args, ws, rank, local):
     time.sleep(0.3)
     launches0 = G.map_launch_count()
     R = args.serve_requests
-    cap = stream(args.serve_slots, R, None)
-    one = stream(1, max(len(pool), R // 2), None)
+    lanes = args.serve_lanes
+    cap = stream(args.serve_slots, R, None, lanes)
+    one = stream(1, max(len(pool), R // 2), None, lanes)
     loads = {}
     for frac in (0.5, 0.9):
         rate = frac * cap["jobs_per_s"]
         n = max(len(pool), int(round(rate * args.serve_seconds)))
         loads[f"{int(frac * 100)}pct"] = stream(args.serve_slots, n,
-                                                I.poisson_arrivals(n, 1.0 / rate, I.SEED_ITEM + 0x20000))
+                                                I.poisson_arrivals(n, 1.0 / rate, I.SEED_ITEM + 0x20000), lanes)
     n200 = max(len(pool), int(round(200.0 * args.serve_seconds)))
-    cfg200 = stream(args.serve_slots, n200, I.poisson_arrivals(n200, 0.005, I.SEED_ITEM + 0x20000))
+    cfg200 = stream(args.serve_slots, n200, I.poisson_arrivals(n200, 0.005, I.SEED_ITEM + 0x20000), lanes)
     launches = G.map_launch_count() - launches0
     clocks = sampler.stop()
     if rank == 0:
@@ -907,7 +910,7 @@ def run_serve(args, ws, rank, local):
                                        "2^10..2^21 cells, 50% RGGs 2^12..2^20 vertices mean degree 12; H from "
                                        "{4:8, 4:8:8, 4:16:8, 4:16:16}, D prefix of 1:10:100, eps 0.03, full "
                                        "multilevel per request",
-                           "distinct_requests": len(pool), "slots": args.serve_slots,
+                           "distinct_requests": len(pool), "slots": args.serve_slots, "batch_lanes": lanes,
                            "l2": "not flushed (a stream of different graphs)"},
                 "p50_ms": cfg200["p50_ms"], "p99_ms": cfg200["p99_ms"], "edges_per_s": cfg200["edges_per_s"],
                 "capacity": cap, "capacity_one_slot": one,

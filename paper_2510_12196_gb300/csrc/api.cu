@@ -132,22 +132,6 @@ std::string& last_create_error() {
 }
 
 namespace {
-thread_local bool t_blocking_wait = false;
-}  // namespace
-
-void set_thread_blocking_wait(bool on) { t_blocking_wait = on; }
-
-void host_wait(Ctx& c) {
-  if (!c.blocking_wait) {
-    GM_CUDA(cudaStreamSynchronize(c.st));
-    return;
-  }
-  if (!c.wait_ev) GM_CUDA(cudaEventCreateWithFlags(&c.wait_ev, cudaEventBlockingSync | cudaEventDisableTiming));
-  GM_CUDA(cudaEventRecord(c.wait_ev, c.st));
-  GM_CUDA(cudaEventSynchronize(c.wait_ev));
-}
-
-namespace {
 
 void build_topology(Ctx& c, const int32_t* hier, const int32_t* dist, int32_t levels) {
   if (levels < 1 || levels > kMaxLevels) throw ApiError(MAP_E_INVALID, "levels must be in [1, 16]");
@@ -246,7 +230,7 @@ map_status guarded(map_ctx* ctx, F&& f) {
   }
 }
 
-void sync(Ctx& c) { host_wait(c); }
+void sync(Ctx& c) { GM_CUDA(cudaStreamSynchronize(c.st)); }
 
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -330,7 +314,6 @@ map_status map_create(const int64_t* xadj, const int32_t* adjncy, const int32_t*
       throw ApiError(MAP_E_INVALID, "mid_deg must be 0 (autotuned) or in 33..255");
     if (c.cfg.split_deg < 0) throw ApiError(MAP_E_INVALID, "split_deg must be 0 (autotuned) or positive");
     c.st = (cudaStream_t)stream;
-    c.blocking_wait = t_blocking_wait;
     GM_CUDA(cudaGetDevice(&c.dev));
     sort_init();
     GM_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.dev));
@@ -442,7 +425,6 @@ void map_destroy(map_ctx* ctx) {
     pinned_put(ctx->c.h_eng_job);
     pinned_put(ctx->c.h_tables);
     for (cudaEvent_t e : ctx->c.ev_pool) cudaEventDestroy(e);
-    if (ctx->c.wait_ev) cudaEventDestroy(ctx->c.wait_ev);
     for (auto& L : ctx->c.lv) {
       drop_graph(L);
       if (L.cgexec) cudaGraphExecDestroy(L.cgexec);

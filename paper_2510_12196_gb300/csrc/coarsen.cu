@@ -1218,7 +1218,7 @@ struct LoadTableSize {
 // a pageable copy stages through a driver buffer that concurrent contexts share
 int64_t read_i64(Ctx& c, const int64_t* d) {
   GM_CUDA(cudaMemcpyAsync(c.h_small + 6, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   return c.h_small[6];
 }
 
@@ -1231,7 +1231,7 @@ int bits_for(int64_t x) {  // smallest b with x < 2^b
 void check_err(Ctx& c) {
   c.h_small[7] = 0;
   GM_CUDA(cudaMemcpyAsync(c.h_small + 7, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   const uint32_t e = (uint32_t)(c.h_small[7] & 0xffffffffLL);
   if (e & ERR_TIMEOUT) throw ApiError(MAP_E_TIMEOUT, "a bounded device loop gave up");
   if (e) throw ApiError(MAP_E_INTERNAL, "device consistency check failed (flags " + std::to_string(e) + ")");
@@ -1427,7 +1427,7 @@ int32_t cluster_level(Ctx& c, int lvl) {
       launch_subround(c, lvl, 1, wcap);
       k_cl_end<<<1, 1, 0, c.st>>>(cs, n, c.cfg.cluster_iters, 0, 0, 0); count_launch();
       GM_CUDA(cudaMemcpyAsync(c.h_cstate, cs, sizeof(ClusterState), cudaMemcpyDeviceToHost, c.st));
-      host_wait(c);
+      GM_CUDA(cudaStreamSynchronize(c.st));
       if (c.h_cstate->done) break;
     }
   }
@@ -1445,7 +1445,7 @@ int32_t cluster_level(Ctx& c, int lvl) {
   if (!L.M) L.M = c.mem.make<int32_t>((size_t)std::max(1, n));
   k_apply_rank<<<gv, kThreads, 0, c.st>>>(n, c.C, c.rank, L.M); count_launch();
   GM_CUDA(cudaGetLastError());
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   if (graph_ran) add_launches(L.cg_root + (long long)c.h_cstate->kernels);
   const int64_t nc = c.h_small[0];
   const uint32_t e = (uint32_t)(c.h_small[1] & 0xffffffffLL);
@@ -1577,7 +1577,7 @@ void validate_graph(Ctx& c) {
   int64_t* hs = c.h_small;
   hs[0] = 0;
   GM_CUDA(cudaMemcpyAsync(hs, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   if (hs[0] == 0 && L.m > 0) {
     k_validate_entries<<<grid_for(c, kThreads, (L.m + kValChunk - 1) / kValChunk), kThreads, 0, c.st>>>(
         view(L), L.m, c.errword, sums); count_launch();
@@ -1594,7 +1594,7 @@ void validate_graph(Ctx& c) {
   GM_CUDA(cudaMemcpyAsync(hs + 1, sums, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(hs + 3, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(hs + 4, sums + 2, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   uint32_t e = (uint32_t)(hs[0] & 0xffffffffLL);
   if (hs[4] != hs[5]) e |= ERR_ASYM;  // an entry without its twin
   const unsigned long long h[2] = {(unsigned long long)hs[1], (unsigned long long)hs[2]};

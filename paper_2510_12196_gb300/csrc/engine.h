@@ -272,8 +272,6 @@ struct Ctx {
 
   // fused small-level engine
   EngineSink* sink = nullptr;  // when set, runs the cluster-engine refinements (with other contexts')
-  bool blocking_wait = false;  // host waits sleep on wait_ev instead of spinning
-  cudaEvent_t wait_ev = nullptr;
   int eng_max_cluster = 0;
   void* eng_job = nullptr;    // device job descriptor
   void* gbar = nullptr;       // device barrier state of the grid-wide engine
@@ -314,12 +312,6 @@ struct Ctx {
 
 // api.cu: error text of the last failed context-free call on this thread
 std::string& last_create_error();
-// api.cu: the host waits for a context's stream.  By default the thread
-// spins (lowest latency); contexts created on a thread that asked for
-// blocking waits (a server's workers) sleep on a blocking-sync event, so that
-// many waiting jobs leave the CPU cores to those with host work to do.
-void host_wait(Ctx& c);
-void set_thread_blocking_wait(bool on);
 
 // refine.cu
 void refine_alloc(Ctx& c);

@@ -261,11 +261,11 @@ void partition_level(Ctx& c, const Stack& S, int32_t i, int32_t a, int32_t* part
   };
   const int32_t T = std::max(1, std::min(workers, S.cnt));
   if (T == 1) {
-    host_wait(c);
+    GM_CUDA(cudaStreamSynchronize(c.st));
     for (int32_t j = 0; j < S.cnt; j++)
       if (!job(j, c.st)) break;
   } else {
-    host_wait(c);  // the stacked arrays are complete
+    GM_CUDA(cudaStreamSynchronize(c.st));  // the stacked arrays are complete
     std::vector<std::thread> pool;
     for (int32_t t = 0; t < T; t++) {
       pool.emplace_back([&, t]() {
@@ -329,7 +329,7 @@ Stack build_children(Ctx& c, int32_t n, const Stack& S, int32_t i, int32_t a, co
   std::vector<int64_t> hs((size_t)nchild), he((size_t)nchild);
   GM_CUDA(cudaMemcpyAsync(hs.data(), start, (size_t)nchild * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(he.data(), end, (size_t)nchild * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   Stack C;
   C.cnt = (int32_t)nchild;
   C.voff.assign((size_t)nchild + 1, 0);
@@ -354,7 +354,7 @@ Stack build_children(Ctx& c, int32_t n, const Stack& S, int32_t i, int32_t a, co
   std::vector<int64_t> heb((size_t)nchild + 1), hwb((size_t)nchild + 1);
   GM_CUDA(cudaMemcpyAsync(heb.data(), eb, ((size_t)nchild + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(hwb.data(), wb, ((size_t)nchild + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   C.eoff = heb;
   C.weight.assign((size_t)nchild, 0);
   for (int64_t ch = 0; ch < nchild; ch++) C.weight[(size_t)ch] = hwb[(size_t)ch + 1] - hwb[(size_t)ch];
@@ -428,7 +428,7 @@ void hm_run(Ctx& c, int lvl, int32_t workers, HmStats* st) {
       Stack C = build_children(c, n, S, i, a, part);
       free_stack(c, S);
       S = C;
-      host_wait(c);
+      GM_CUDA(cudaStreamSynchronize(c.st));
       if (st) st->ms_build += ms_since(tb);
     }
   } catch (...) {
@@ -436,7 +436,7 @@ void hm_run(Ctx& c, int lvl, int32_t workers, HmStats* st) {
     throw;
   }
   free_stack(c, S);
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   if (st) st->ms_total = ms_since(t0);
 }
 

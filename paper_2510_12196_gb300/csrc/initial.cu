@@ -226,7 +226,7 @@ struct StorePe {
 
 int64_t read_dev(Ctx& c, const int64_t* d) {
   GM_CUDA(cudaMemcpyAsync(c.h_small + 6, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   return c.h_small[6];
 }
 
@@ -258,7 +258,7 @@ bool initial_map_large(Ctx& c) {
     k_cc_pick<<<(kCcSample + kIThreads - 1) / kIThreads, kIThreads, 0, c.st>>>(n, lab, picks); count_launch();
     std::vector<int32_t> h(kCcSample);
     GM_CUDA(cudaMemcpyAsync(h.data(), picks, kCcSample * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
-    host_wait(c);
+    GM_CUDA(cudaStreamSynchronize(c.st));
     std::sort(h.begin(), h.end());
     int32_t giant = h[0], best = 0;
     for (int i = 0; i < kCcSample;) {
@@ -311,7 +311,7 @@ bool initial_map_large(Ctx& c) {
   GM_CUDA(cudaGetLastError());
   c.h_small[7] = 0;
   GM_CUDA(cudaMemcpyAsync(c.h_small + 7, c.errword, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   if (c.h_small[7] & ERR_TIMEOUT) throw ApiError(MAP_E_TIMEOUT, "a bounded device loop gave up");
   return true;
 }

@@ -443,14 +443,14 @@ int32_t match_level(Ctx& c, int lvl) {
     GM_CUDA(cudaGraphLaunch(L.cgexec, c.st));
     GM_CUDA(cudaMemcpyAsync(c.h_small, &s->nc, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
     GM_CUDA(cudaMemcpyAsync(c.h_small + 1, &s->kernels, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-    host_wait(c);
+    GM_CUDA(cudaStreamSynchronize(c.st));
     add_launches(L.cg_root + (long long)c.h_small[1]);
     return (int32_t)c.h_small[0];
   }
   // stream launches: the same kernels, the loop decisions taken on the host
   auto read = [&](const int64_t* d) {
     GM_CUDA(cudaMemcpyAsync(c.h_small, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-    host_wait(c);
+    GM_CUDA(cudaStreamSynchronize(c.st));
     return c.h_small[0];
   };
   GM_CUDA(cudaMemsetAsync(c.C, 0xFF, (size_t)std::max(1, n) * sizeof(int32_t), c.st));

@@ -3553,7 +3553,7 @@ void objective(Ctx& c, int lvl, int64_t* J, int64_t* maxw) {
   int64_t hJ = 0;
   GM_CUDA(cudaMemcpyAsync(&hJ, c.Jacc, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(W.data(), c.W, W.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   if (J) *J = hJ;
   if (maxw) *maxw = W.empty() ? 0 : *std::max_element(W.begin(), W.end());
 }
@@ -3570,7 +3570,7 @@ static void set_state(Ctx& c, int32_t kind, int32_t t, int32_t level) {
 
 static int32_t read_moved(Ctx& c) {
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   return c.h_state->moved;
 }
 
@@ -3608,7 +3608,7 @@ static void refine_stream(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* 
   const unsigned gcopy = grid_for(c, kThreads * 4, L.n);
   while (true) {
     GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-    host_wait(c);
+    GM_CUDA(cudaStreamSynchronize(c.st));
     const RefineState h = *c.h_state;
     if (h.done) break;
     if (h.kind == KIND_LP) {
@@ -3729,7 +3729,7 @@ static void refine_graph(Ctx& c, int lvl, int32_t rounds, int64_t* J, int64_t* m
     build_refine_graph(c, lvl, rounds);
   GM_CUDA(cudaGraphLaunch(L.gexec, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   const RefineState h = *c.h_state;
   add_launches(L.g_root + (long long)h.kernels);
   if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
@@ -3913,7 +3913,7 @@ static void refine_engine(Ctx& c, int lvl, int32_t rounds, int C, int64_t* J, in
   GM_CUDA(cudaMemcpyAsync(c.eng_job, c.h_eng_job, sizeof(EngineJob), cudaMemcpyHostToDevice, c.st));
   engine_launch(c.st, c.eng_job, 1, nullptr, C, 512, 1, uses_variants(c.cfg));
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   const RefineState h = *c.h_state;
   if (h.capped) throw ApiError(MAP_E_TIMEOUT, "refinement stopped at the iteration cap");
   c.last_iters = h.t;
@@ -3969,7 +3969,7 @@ static void refine_engine_grid(Ctx& c, int lvl, int32_t rounds, int64_t* J, int6
   count_launch();
   GM_CUDA(cudaMemcpyAsync(c.h_state, c.state, sizeof(RefineState), cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_small, c.gbar, sizeof(GridBar), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   if (reinterpret_cast<const GridBar*>(c.h_small)->err)
     throw ApiError(MAP_E_TIMEOUT, "a grid barrier of the refinement engine gave up waiting");
   const RefineState h = *c.h_state;
@@ -4123,7 +4123,7 @@ struct LoadHubDeg {
 // one device value read back through the context's pinned block (slot 5)
 int64_t read_i64_at(Ctx& c, const int64_t* d) {
   GM_CUDA(cudaMemcpyAsync(c.h_small + 5, d, sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   return c.h_small[5];
 }
 
@@ -4199,7 +4199,7 @@ void classify_with(Ctx& c, Level& L, int32_t mid_deg, int64_t split_deg) {
   GM_CUDA(cudaMemcpyAsync(c.h_small, c.scan.tile_sums + std::max<int64_t>(1, scan_tiles(L.n)), sizeof(int64_t),
                           cudaMemcpyDeviceToHost, c.st));
   GM_CUDA(cudaMemcpyAsync(c.h_small + 1, st, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, c.st));
-  host_wait(c);
+  GM_CUDA(cudaStreamSynchronize(c.st));
   L.n_hi = (int32_t)(c.h_small[0] & 0xffffffffLL);
   L.n_huge = (int32_t)(c.h_small[0] >> 32);
   L.m_hi = c.h_small[1];

@@ -143,8 +143,8 @@ class LevelBatcher final : public EngineSink {
 
   // One batch: the waiting requests grouped by cluster size, each group one
   // persistent launch on its own stream, largest job first.
-  void run_batch(std::vector<Req*>& batch, cudaStream_t* st, cudaEvent_t* done, void* d_jobs,
-                 unsigned int* d_queue, unsigned char* h_jobs, RefineState* h_states) {
+  void run_batch(std::vector<Req*>& batch, cudaStream_t* st, void* d_jobs, unsigned int* d_queue,
+                 unsigned char* h_jobs, RefineState* h_states) {
     const size_t jb = engine_job_bytes();
     std::vector<Req*> group[kSizes];
     for (Req* r : batch) {
@@ -184,10 +184,7 @@ class LevelBatcher final : public EngineSink {
       }
       off += rs.size();
     }
-    for (int g = 0; g < kSizes; g++) {  // a sleeping wait (see host_wait)
-      GM_CUDA(cudaEventRecord(done[g], st[g]));
-      GM_CUDA(cudaEventSynchronize(done[g]));
-    }
+    for (int g = 0; g < kSizes; g++) GM_CUDA(cudaStreamSynchronize(st[g]));
     off = 0;
     for (int g = 0; g < kSizes; g++)
       for (Req* r : group[g]) r->st = h_states[off++];
@@ -201,11 +198,8 @@ class LevelBatcher final : public EngineSink {
     RefineState* h_states = nullptr;
     std::string setup_err;
     if (cudaSetDevice(dev_) != cudaSuccess) setup_err = "cudaSetDevice failed";
-    cudaEvent_t done[kSizes] = {};
     for (int g = 0; g < kSizes && setup_err.empty(); g++)
-      if (cudaStreamCreateWithFlags(&st[g], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&done[g], cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess)
-        setup_err = "stream creation failed";
+      if (cudaStreamCreateWithFlags(&st[g], cudaStreamNonBlocking) != cudaSuccess) setup_err = "stream creation failed";
     if (setup_err.empty() && (cudaMalloc(&d_jobs, engine_job_bytes() * kMaxBatch) != cudaSuccess ||
                               cudaMalloc(&d_queue, kSizes * sizeof(unsigned int)) != cudaSuccess ||
                               cudaMallocHost(&h_jobs, engine_job_bytes() * kMaxBatch) != cudaSuccess ||
@@ -230,7 +224,7 @@ class LevelBatcher final : public EngineSink {
         err = setup_err;
       } else {
         try {
-          run_batch(batch, st, done, d_jobs, d_queue, h_jobs, h_states);
+          run_batch(batch, st, d_jobs, d_queue, h_jobs, h_states);
         } catch (const ApiError& e) {
           status = e.status;
           err = e.what();
@@ -256,10 +250,8 @@ class LevelBatcher final : public EngineSink {
       }
       cv_done_.notify_all();
     }
-    for (int g = 0; g < kSizes; g++) {
+    for (int g = 0; g < kSizes; g++)
       if (st[g]) cudaStreamDestroy(st[g]);
-      if (done[g]) cudaEventDestroy(done[g]);
-    }
     if (d_jobs) cudaFree(d_jobs);
     if (d_queue) cudaFree(d_queue);
     if (h_jobs) cudaFreeHost(h_jobs);
@@ -359,8 +351,6 @@ void run_pipeline(map_server& S, Job& j, cudaStream_t stream) {
 
 void worker(map_server* S) {
   if (cudaSetDevice(S->dev) != cudaSuccess) cudaGetLastError();
-  // the jobs' host waits sleep instead of spinning: many workers wait at once
-  set_thread_blocking_wait(true);
   cudaStream_t stream = nullptr;
   if (!S->opts.runner) {
     if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
