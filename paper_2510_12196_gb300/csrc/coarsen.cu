@@ -329,6 +329,9 @@ constexpr unsigned long long kEmptySlot = ~0ULL;
 constexpr int64_t kSmemRowDeg = 2047;
 constexpr uint32_t kSmemSlots = 4096;  // >= 2 (kSmemRowDeg + 1)
 static_assert(kSmemSlots >= 2 * (kSmemRowDeg + 1), "shared-memory row table at most half full");
+// rows of one chunk at most: every row there has more than kLowDeg + 1 >= 33 entries
+constexpr int kChunkRows = 64;
+static_assert(kHubChunk / 34 + 2 <= kChunkRows, "a chunk's rows fit the per-chunk row table");
 
 // Inserts from slot h on (`probes` already made).
 __device__ __forceinline__ bool hub_insert_from(unsigned long long* T, uint32_t mask, int32_t t, int32_t w, uint32_t h,
@@ -474,31 +477,58 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRow
                                                              const int64_t* __restrict__ hoff,
                                                              unsigned long long* htab, ClusterArgs a,
                                                              unsigned long long* ctr, uint32_t* err) {
+  static_assert(kHiThreads >= kChunkRows, "one thread per row of a chunk");
   __shared__ unsigned long long stab[kSmemSlots];
   __shared__ HubScratch sx;
   __shared__ int32_t s_bs, s_bt;
   __shared__ uint64_t s_bh;
   __shared__ int64_t s_ch;
+  // the rows of the current chunk, looked up at once (one thread each): a
+  // row's lookup is a chain of dependent loads that would otherwise run
+  // row after row
+  __shared__ int32_t s_v[kChunkRows];  // -1: nothing for this chunk to do
+  __shared__ int32_t s_own[kChunkRows], s_idx[kChunkRows];
+  __shared__ int64_t s_rb[kChunkRows], s_re[kChunkRows], s_x0[kChunkRows];
   for (uint32_t s = threadIdx.x; s < kSmemSlots; s += blockDim.x) stab[s] = kEmptySlot;
   __syncthreads();
   const int64_t m_hub = hr.pre[hr.n_huge];
   for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
     const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
-    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
-      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
-      if (rb >= ce) break;
+    const int32_t r = hr.chunk[ch] + (int32_t)threadIdx.x;
+    bool row = false;
+    if (threadIdx.x < kChunkRows) {
+      int32_t v = -1;
+      int64_t rb = 0, re = 0;
+      if (r < hr.n_huge) {
+        rb = hr.pre[r];
+        re = hr.pre[r + 1];
+        row = rb < ce;
+      }
       const int64_t deg = re - rb;
       const bool first = rb >= cb;  // this chunk holds the row's first entry
       // a row on the shared-memory path belongs to the chunk of its first entry
-      if (deg <= kSmemRowDeg && !first) continue;
-      const int32_t idx = hr.huge[r];
-      const int32_t v = hr.hi[idx];
-      if (!cluster_active(a, v, deg)) {
-        if (first && threadIdx.x == 0) a.req[v] = -1;
-        continue;
+      if (row && (deg > kSmemRowDeg || first)) {
+        const int32_t idx = hr.huge[r];
+        const int32_t u = hr.hi[idx];
+        if (cluster_active(a, u, deg)) {
+          v = u;
+          s_idx[threadIdx.x] = idx;
+          s_own[threadIdx.x] = a.C[u];
+          s_x0[threadIdx.x] = g.xadj[u] - rb;  // CSR position of flat entry f: x0 + f
+        } else if (first) {
+          a.req[u] = -1;
+        }
       }
-      const int32_t own = a.C[v];
-      const int64_t x0 = g.xadj[v] - rb;  // CSR position of flat entry f: x0 + f
+      s_v[threadIdx.x] = v;
+      s_rb[threadIdx.x] = rb;
+      s_re[threadIdx.x] = re;
+    }
+    const int nrows = __syncthreads_count(row);  // the chunk's rows are a prefix
+    for (int i = 0; i < nrows; i++) {
+      const int32_t v = s_v[i];
+      if (v < 0) continue;
+      const int64_t rb = s_rb[i], re = s_re[i], deg = re - rb, x0 = s_x0[i];
+      const int32_t own = s_own[i];
       bool ok = true;
       if (deg <= kSmemRowDeg) {
         uint32_t size = 64;
@@ -511,10 +541,11 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRow
         if (threadIdx.x == 0) cluster_request(a, v, own, s_bt, g.vw[v]);
         continue;
       }
+      const int32_t idx = s_idx[i];
       const int64_t base = hoff[idx];
       const uint32_t mask = (uint32_t)(hoff[idx + 1] - base) - 1u;
       unsigned long long* T = htab + base;
-      if (first && threadIdx.x == 0) ok = hub_insert(T, mask, own, 0);
+      if (rb >= cb && threadIdx.x == 0) ok = hub_insert(T, mask, own, 0);
       ok &= hub_insert_range(g, a.C, x0 + max(rb, cb), x0 + min(re, ce), T, mask);
       if (!ok) atomicOr(err, ERR_CAPACITY);
     }
@@ -532,16 +563,34 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_giant(HubRows hr, const 
   __shared__ int32_t s_bs, s_bt;
   __shared__ uint64_t s_bh;
   __shared__ int64_t s_ch;
+  __shared__ int32_t s_idx[kChunkRows];  // the chunk's active larger rows (-1: none)
+  __shared__ int64_t s_rb[kChunkRows], s_re[kChunkRows];
   const int64_t m_hub = hr.pre[hr.n_huge];
   for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
     const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
-    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
-      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
-      if (rb >= ce) break;
-      const int64_t deg = re - rb;
-      if (deg <= kSmemRowDeg) continue;
-      const int32_t idx = hr.huge[r];
-      if (!cluster_active(a, hr.hi[idx], deg)) continue;
+    const int32_t r = hr.chunk[ch] + (int32_t)threadIdx.x;
+    bool row = false;
+    if (threadIdx.x < kChunkRows) {
+      int32_t idx = -1;
+      int64_t rb = 0, re = 0;
+      if (r < hr.n_huge) {
+        rb = hr.pre[r];
+        re = hr.pre[r + 1];
+        row = rb < ce;
+      }
+      if (row && re - rb > kSmemRowDeg) {
+        const int32_t j = hr.huge[r];
+        if (cluster_active(a, hr.hi[j], re - rb)) idx = j;
+      }
+      s_idx[threadIdx.x] = idx;
+      s_rb[threadIdx.x] = rb;
+      s_re[threadIdx.x] = re;
+    }
+    const int nrows = __syncthreads_count(row);  // the chunk's rows are a prefix
+    for (int i = 0; i < nrows; i++) {
+      const int32_t idx = s_idx[i];
+      if (idx < 0) continue;
+      const int64_t rb = s_rb[i], re = s_re[i], deg = re - rb;
       const int64_t base = hoff[idx];
       const int64_t S = hoff[idx + 1] - base;
       const uint32_t s0 = (uint32_t)(S * (max(rb, cb) - rb) / deg), s1 = (uint32_t)(S * (min(re, ce) - rb) / deg);
@@ -904,7 +953,7 @@ __global__ void k_coarse_vw(int32_t n, const int32_t* __restrict__ M, const int3
 // each lane finds the row of its entry among the 32 row starts.  A first walk
 // counts the warp's valid entries, the block reserves one range for its eight
 // warps with a single atomic, and a second walk (gathers now cached) writes.
-// Rows of degree > kMidDeg are jumped over (k_contract_keys_big takes them),
+// Rows of degree > mid_deg are jumped over (k_contract_keys_hub takes them),
 // so that no warp walks a hub's row alone while the rest of its block waits.
 __device__ __forceinline__ int contract_owner(int64_t x, int64_t b, int last) {
   // largest lane L <= last with row start(L) <= x (starts are non-decreasing)
@@ -1025,38 +1074,69 @@ struct LoadValid32 {
 // Keys of the rows of degree > kMidDeg (one CTA per row; `sel` lists their
 // positions in hi[]): the block counts its row's valid entries, reserves one
 // range with a single atomic, and its warps fill it through a shared cursor.
-__global__ void __launch_bounds__(kThreads) k_contract_keys_big(GraphView g, const int32_t* __restrict__ hi,
-                                                                const int32_t* __restrict__ sel, int32_t n_sel,
-                                                                const int32_t* __restrict__ M, int bits, uint64_t* key,
-                                                                int32_t* val, int64_t* valid) {
+// The rows of degree > mid_deg (flattened, in chunks of kHubChunk entries,
+// kHubChunk / kThreads per thread): the rows of a chunk are looked up at once
+// (one thread each), then every thread keys its entries, the block reserves
+// one output range per chunk with a single atomic and each thread writes its
+// valid entries at its exclusive prefix.
+__global__ void __launch_bounds__(kThreads) k_contract_keys_hub(GraphView g, HubRows hr,
+                                                                const int32_t* __restrict__ M, int bits,
+                                                                uint64_t* key, int32_t* val, int64_t* valid) {
+  constexpr int kPer = (int)(kHubChunk / kThreads);
+  static_assert(kPer * kThreads == kHubChunk && kThreads >= kChunkRows, "chunk layout");
+  __shared__ int64_t s_rb[kChunkRows], s_x0[kChunkRows];
+  __shared__ int32_t s_mo[kChunkRows];
   __shared__ unsigned long long sm[33];
-  __shared__ unsigned long long cursor;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int32_t j = blockIdx.x; j < n_sel; j += gridDim.x) {
-    const int32_t v = hi[sel[j]];
-    const int64_t beg = g.xadj[v], end = g.xadj[v + 1];
-    const int32_t mo = M[v];
-    unsigned long long cnt = 0;
-    for (int64_t x = beg + threadIdx.x; x < end; x += blockDim.x) cnt += M[g.adj[x]] != mo ? 1 : 0;
-    cnt = block_sum(cnt, sm);
-    if (threadIdx.x == 0) cursor = cnt ? atomicAdd((unsigned long long*)valid, cnt) : 0ULL;
-    __syncthreads();
-    for (int64_t x0 = beg; x0 < end; x0 += blockDim.x) {  // same trip count in every warp
-      const int64_t x = x0 + threadIdx.x;
-      const int32_t mu = x < end ? M[g.adj[x]] : mo;
-      const bool ok = mu != mo;
-      const unsigned bal = __ballot_sync(0xffffffffu, ok);
-      unsigned long long p = 0;
-      if (lane == 0 && bal) p = atomicAdd(&cursor, (unsigned long long)__popc(bal));
-      p = __shfl_sync(0xffffffffu, p, 0);
-      if (ok) {
-        const unsigned long long q = p + __popc(bal & lt);
-        key[q] = ((uint64_t)(uint32_t)mo << bits) | (uint32_t)mu;
-        val[q] = g.adjw[x];
+  __shared__ unsigned long long s_base;
+  const int64_t m_hub = hr.pre[hr.n_huge];
+  for (int64_t ch = blockIdx.x; ch < hr.nchunks; ch += gridDim.x) {
+    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
+    const int32_t r = hr.chunk[ch] + (int32_t)threadIdx.x;
+    bool row = false;
+    if (threadIdx.x < kChunkRows && r < hr.n_huge) {
+      const int64_t rb = hr.pre[r];
+      row = rb < ce;
+      if (row) {
+        const int32_t u = hr.hi[hr.huge[r]];
+        s_rb[threadIdx.x] = rb;
+        s_x0[threadIdx.x] = g.xadj[u] - rb;  // CSR position of flat entry f: x0 + f
+        s_mo[threadIdx.x] = M[u];
       }
     }
-    __syncthreads();  // cursor and sm are rewritten for the next row
+    const int nrows = __syncthreads_count(row);  // the chunk's rows are a prefix
+    // entries f = cb + k * kThreads + threadIdx.x (coalesced), rows found by a
+    // forward walk over the row starts
+    int32_t mo[kPer], mu[kPer];
+    int64_t xe[kPer];
+    unsigned long long cnt = 0;
+    int i = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      const int64_t f = cb + (int64_t)k * kThreads + threadIdx.x;
+      mo[k] = 0;
+      mu[k] = 0;
+      xe[k] = -1;
+      if (f < ce) {
+        while (i + 1 < nrows && s_rb[i + 1] <= f) i++;
+        xe[k] = s_x0[i] + f;
+        mo[k] = s_mo[i];
+        mu[k] = M[g.adj[xe[k]]];
+        cnt += mu[k] != mo[k] ? 1 : 0;
+      }
+    }
+    unsigned long long tot;
+    unsigned long long pos = block_exclusive_scan(cnt, sm, &tot);
+    if (threadIdx.x == 0) s_base = tot ? atomicAdd((unsigned long long*)valid, tot) : 0ULL;
+    __syncthreads();
+    pos += s_base;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+      if (xe[k] < 0 || mu[k] == mo[k]) continue;
+      key[pos] = ((uint64_t)(uint32_t)mo[k] << bits) | (uint32_t)mu[k];
+      val[pos] = g.adjw[xe[k]];
+      pos++;
+    }
+    __syncthreads();  // s_base and the row table are rewritten for the next chunk
   }
 }
 
@@ -1497,8 +1577,9 @@ void contract_level(Ctx& c, int lvl, int32_t nc, Level* spare) {
     k_contract_keys<<<grid_for(c, kThreads, F.n), kThreads, 0, c.st>>>(view(F), F.M, bits, c.sort.key[0],
                                                                        c.sort.val[0], d_valid); count_launch();
     if (F.n_huge) {
-      k_contract_keys_big<<<std::max(1, std::min(F.n_huge, c.num_sms * 8)), kThreads, 0, c.st>>>(
-          view(F), F.hi, F.huge, F.n_huge, F.M, bits, c.sort.key[0], c.sort.val[0], d_valid); count_launch();
+      k_contract_keys_hub<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(F.n_hub_chunks, (int64_t)c.num_sms * 8)),
+                            kThreads, 0, c.st>>>(view(F), hub_rows(F), F.M, bits, c.sort.key[0], c.sort.val[0],
+                                                 d_valid); count_launch();
     }
     c.prof_level = lvl;
     cudaEvent_t ev = c.prof_begin();

@@ -20,9 +20,12 @@ constexpr int kMidThreads = kMidWarps * 32;
 constexpr int kMidTableMax = 1536;
 // entries per chunk when the rows of degree > kMidDeg are spread over CTAs
 constexpr int64_t kHubChunk = 2048;
-// rows of one chunk at most: every row there has more than kLowDeg + 1 >= 33 entries
-constexpr int kHubChunkRows = 64;
-static_assert(kHubChunk / 34 + 2 <= kHubChunkRows, "a chunk's rows fit the per-chunk row table");
+// chunks a CTA takes at once in the connectivity-table and exact-change
+// kernels: the rows of such a span are checked in one step, one thread each
+// (a row's check is a chain of dependent loads; per chunk it set the pace)
+constexpr int64_t kSpanChunks = 4;
+constexpr int kSpanRows = 256;  // rows of one span at most (rows there have more than kLowDeg + 1 entries)
+static_assert(kSpanChunks * kHubChunk / 34 + 2 <= kSpanRows, "a span's rows fit the per-span row table");
 // rows rated by one CTA whole (PE-code tables); larger rows sum chunk tables
 constexpr int64_t kSplitDeg = 4096;
 // bound of the per-level partial tables of the larger rows (else rated whole)

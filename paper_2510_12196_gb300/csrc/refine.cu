@@ -787,30 +787,53 @@ __global__ void __launch_bounds__(kHiThreads) k_lp_after_hub(GraphView g, HubRow
                                                              const int64_t* __restrict__ gain,
                                                              const uint8_t* __restrict__ inx, int64_t* acc, Topo topo,
                                                              const RefineState* st, unsigned long long* ctr) {
+  static_assert(kHiThreads == kSpanRows, "one thread per row of a span");
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
   __shared__ int64_t s_ch;
+  // the candidates among the rows of the current span, found at once
+  __shared__ int32_t s_v[kSpanRows];  // -1: not a candidate
+  __shared__ int64_t s_rb[kSpanRows], s_re[kSpanRows];
   if (!kind_is(st, 1 << KIND_LP)) return;
   load_sdist(sdist, topo);
   __syncthreads();
   const int64_t m_hub = hr.pre[hr.n_huge];
-  for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
-    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
-    for (int32_t r = hr.chunk[ch]; r < hr.n_huge; r++) {
-      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
-      if (rb >= ce) break;
-      const int32_t v = hr.hi[hr.huge[r]];
-      if (!inx[v]) continue;
-      const int32_t p = pi[v], q = pp[v];
-      const int64_t gv = gain[v];
-      const int64_t x0 = g.xadj[v] - rb;
+  const int64_t nspans = (hr.nchunks + kSpanChunks - 1) / kSpanChunks;
+  for (int64_t sp = next_chunk(ctr, &s_ch); sp < nspans; sp = next_chunk(ctr, &s_ch)) {
+    const int64_t cb = sp * kSpanChunks * kHubChunk, ce = min(cb + kSpanChunks * kHubChunk, m_hub);
+    const int32_t r0 = hr.chunk[sp * kSpanChunks];
+    const int32_t r = r0 + (int32_t)threadIdx.x;
+    bool row = false;
+    int32_t v = -1;
+    int64_t rb = 0, re = 0;
+    if (r < hr.n_huge) {
+      rb = hr.pre[r];
+      re = hr.pre[r + 1];
+      row = rb < ce;
+    }
+    if (row) {
+      const int32_t u = hr.hi[hr.huge[r]];
+      if (inx[u]) v = u;
+    }
+    s_v[threadIdx.x] = v;
+    s_rb[threadIdx.x] = rb;
+    s_re[threadIdx.x] = re;
+    const int nrows = __syncthreads_count(row);  // the span's rows are a prefix
+    for (int i = 0; i < nrows; i++) {
+      const int32_t w = s_v[i];
+      if (w < 0) continue;
+      const int32_t p = pi[w], q = pp[w];
+      const int64_t gv = gain[w];
+      const int64_t x0 = g.xadj[w] - s_rb[i];
+      const int64_t f1 = min(s_re[i], ce);
       int64_t s = 0;
-      for (int64_t e = x0 + max(rb, cb) + threadIdx.x; e < x0 + min(re, ce); e += blockDim.x) {
-        const int32_t b = future_block(g.adj[e], v, gv, pi, pp, gain, inx);
+      for (int64_t f = max(s_rb[i], cb) + threadIdx.x; f < f1; f += blockDim.x) {
+        const int64_t e = x0 + f;
+        const int32_t b = future_block(g.adj[e], w, gv, pi, pp, gain, inx);
         s += (int64_t)g.adjw[e] * (dcode(sdist, p, b) - dcode(sdist, q, b));
       }
       s = block_sum(s, sm);
-      if (threadIdx.x == 0 && s) atomicAdd((unsigned long long*)&acc[r], (unsigned long long)s);
+      if (threadIdx.x == 0 && s) atomicAdd((unsigned long long*)&acc[r0 + i], (unsigned long long)s);
     }
   }
   leave_chunks(ctr);
@@ -913,39 +936,49 @@ template <class Mv>
 __global__ void __launch_bounds__(kHiThreads) k_delta_high(GraphView g, HubRows hr, const int32_t* __restrict__ pi,
                                                            Mv mv, Topo topo, int64_t* Jacc, const RefineState* st,
                                                            int kind) {
+  static_assert(kHiThreads == kSpanRows, "one thread per row of a span");
   __shared__ int32_t sdist[32];
   __shared__ int64_t sm[33];
+  // the movers among the rows of the current span, found at once
+  __shared__ int32_t s_v[kSpanRows];  // -1: the row stays
+  __shared__ int64_t s_rb[kSpanRows], s_re[kSpanRows];
   if (st->kind != kind) return;
   load_sdist(sdist, topo);
   __syncthreads();
   const int64_t m_hub = hr.pre[hr.n_huge];
+  const int64_t nspans = (hr.nchunks + kSpanChunks - 1) / kSpanChunks;
   int64_t acc = 0;
-  for (int64_t ch = blockIdx.x; ch < hr.nchunks; ch += gridDim.x) {
-    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
-    int32_t r = hr.chunk[ch];
-    int64_t re = hr.pre[r + 1], x0 = 0;
-    int32_t ov = 0, nv = 0;
-    int state = 0;  // 0: row not looked at, 1: a mover, 2: stays
-    for (int64_t f = cb + threadIdx.x; f < ce; f += blockDim.x) {
-      while (f >= re) {
-        r++;
-        re = hr.pre[r + 1];
-        state = 0;
-      }
-      if (state == 0) {
-        const int32_t v = hr.hi[hr.huge[r]];
-        state = 2;
-        if (mv.moved(v)) {
-          state = 1;
-          x0 = g.xadj[v] - hr.pre[r];
-          ov = pi[v];
-          nv = mv.target(v);
-        }
-      }
-      if (state != 1) continue;
-      const int64_t e = x0 + f;
-      acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[e], g.adjw[e]);
+  for (int64_t sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
+    const int64_t cb = sp * kSpanChunks * kHubChunk, ce = min(cb + kSpanChunks * kHubChunk, m_hub);
+    const int32_t r = hr.chunk[sp * kSpanChunks] + (int32_t)threadIdx.x;
+    bool row = false;
+    int32_t v = -1;
+    int64_t rb = 0, re = 0;
+    if (r < hr.n_huge) {
+      rb = hr.pre[r];
+      re = hr.pre[r + 1];
+      row = rb < ce;
     }
+    if (row) {
+      const int32_t u = hr.hi[hr.huge[r]];
+      if (mv.moved(u)) v = u;
+    }
+    s_v[threadIdx.x] = v;
+    s_rb[threadIdx.x] = rb;
+    s_re[threadIdx.x] = re;
+    const int nrows = __syncthreads_count(row);  // the span's rows are a prefix
+    for (int i = 0; i < nrows; i++) {
+      const int32_t w = s_v[i];
+      if (w < 0) continue;
+      const int64_t x0 = g.xadj[w] - s_rb[i];  // CSR position of flat entry f: x0 + f
+      const int32_t ov = pi[w], nv = mv.target(w);
+      const int64_t f1 = min(s_re[i], ce);
+      for (int64_t f = max(s_rb[i], cb) + threadIdx.x; f < f1; f += blockDim.x) {
+        const int64_t e = x0 + f;
+        acc += delta_entry(mv, pi, sdist, ov, nv, g.adj[e], g.adjw[e]);
+      }
+    }
+    __syncthreads();  // the row table is rewritten for the next span
   }
   acc = block_sum(acc, sm);
   if (threadIdx.x == 0 && acc) atomicAdd((unsigned long long*)Jacc, (unsigned long long)acc);
@@ -1471,53 +1504,54 @@ template <class P>
 __global__ void __launch_bounds__(kHiThreads) k_hub_tab(GraphView g, HubRows hr, P pol, int64_t split_deg,
                                                         const int32_t* __restrict__ sidx, int32_t* gtab,
                                                         unsigned long long* ctr) {
+  static_assert(kHiThreads == kSpanRows, "one thread per row of a span");
   extern __shared__ int32_t tab[];
   __shared__ int64_t sb[32];
   __shared__ int32_t sc[32];
   __shared__ int64_t s_ch;
-  // the rows of the current chunk (kHubChunkRows at most), checked at once
-  __shared__ int32_t s_v[kHubChunkRows];  // the row's vertex; -1: not this chunk's to rate
-  __shared__ uint8_t s_want[kHubChunkRows];
-  __shared__ uint8_t s_split[kHubChunkRows];
+  // the rows of the current span, checked at once
+  __shared__ int32_t s_v[kSpanRows];  // the row's vertex; -1: nothing for this span to do
+  __shared__ int64_t s_rb[kSpanRows], s_re[kSpanRows];
+  __shared__ uint8_t s_split[kSpanRows];
   if (!pol.run()) return;
   const int32_t words = pol.words(), kc = pol.topo_kc();
   for (int32_t b = threadIdx.x; b < words; b += blockDim.x) tab[b] = 0;
   __syncthreads();
   const int64_t m_hub = hr.pre[hr.n_huge];
-  for (int64_t ch = next_chunk(ctr, &s_ch); ch < hr.nchunks; ch = next_chunk(ctr, &s_ch)) {
-    const int64_t cb = ch * kHubChunk, ce = min(cb + kHubChunk, m_hub);
-    const int32_t r0 = hr.chunk[ch];
-    if (threadIdx.x < kHubChunkRows) {
-      const int32_t r = r0 + (int32_t)threadIdx.x;
+  const int64_t nspans = (hr.nchunks + kSpanChunks - 1) / kSpanChunks;
+  for (int64_t sp = next_chunk(ctr, &s_ch); sp < nspans; sp = next_chunk(ctr, &s_ch)) {
+    const int64_t cb = sp * kSpanChunks * kHubChunk, ce = min(cb + kSpanChunks * kHubChunk, m_hub);
+    const int32_t r = hr.chunk[sp * kSpanChunks] + (int32_t)threadIdx.x;
+    bool row = false;
+    {
       int32_t v = -1;
-      bool w = false, sp = false;
-      if (r < hr.n_huge && hr.pre[r] < ce) {
-        const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
-        sp = re - rb > split_deg;
-        if (sp || rb >= cb) {  // a row up to split_deg is rated whole by the chunk of its first entry
-          v = hr.hi[hr.huge[r]];
-          w = pol.want(v);
+      bool sp_row = false;
+      int64_t rb = 0, re = 0;
+      if (r < hr.n_huge) {
+        rb = hr.pre[r];
+        re = hr.pre[r + 1];
+        row = rb < ce;
+      }
+      if (row) {
+        sp_row = re - rb > split_deg;
+        if (sp_row || rb >= cb) {  // a row up to split_deg is rated whole by the span of its first entry
+          const int32_t u = hr.hi[hr.huge[r]];
+          if (pol.want(u)) v = u;
+          else if (!sp_row) pol.skip(u);  // (the finishing kernel skips the larger rows)
         }
       }
       s_v[threadIdx.x] = v;
-      s_want[threadIdx.x] = w;
-      s_split[threadIdx.x] = sp;
+      s_rb[threadIdx.x] = rb;
+      s_re[threadIdx.x] = re;
+      s_split[threadIdx.x] = sp_row;
     }
-    __syncthreads();  // also: every want() has read what skip() writes
-    for (int32_t i = 0; i < kHubChunkRows; i++) {
-      const int32_t r = r0 + i;
-      if (r >= hr.n_huge) break;
-      const int64_t rb = hr.pre[r], re = hr.pre[r + 1];
-      if (rb >= ce) break;
+    const int nrows = __syncthreads_count(row);  // the span's rows are a prefix
+    for (int i = 0; i < nrows; i++) {
       const int32_t v = s_v[i];
       if (v < 0) continue;
-      const bool split = s_split[i];
-      if (!s_want[i]) {
-        if (!split && threadIdx.x == 0) pol.skip(v);
-        continue;
-      }
+      const int64_t rb = s_rb[i], re = s_re[i];
       const int64_t x0 = g.xadj[v] - rb;
-      if (!split) {
+      if (!s_split[i]) {
         conn_add(g, x0 + rb, x0 + re, pol.pi, tab);
         __syncthreads();
         if (pol.groups()) conn_groups(pol.topo_of(), pol.gl, tab);
@@ -1525,7 +1559,7 @@ __global__ void __launch_bounds__(kHiThreads) k_hub_tab(GraphView g, HubRows hr,
       } else {
         conn_add(g, x0 + max(rb, cb), x0 + min(re, ce), pol.pi, tab);
         __syncthreads();
-        int32_t* G = gtab + (int64_t)sidx[r] * kc;
+        int32_t* G = gtab + (int64_t)sidx[hr.chunk[sp * kSpanChunks] + i] * kc;
         for (int32_t b = threadIdx.x; b < kc; b += blockDim.x)
           if (tab[b]) atomicAdd(&G[b], tab[b]);
         __syncthreads();
@@ -2050,7 +2084,8 @@ template <class P>
 void launch_hub_tab(Ctx& c, Level& L, const P& pol, size_t smem) {
   const void* f1 = (const void*)k_hub_tab<P>;
   const int64_t r1 = (int64_t)c.num_sms * c.resident_blocks(f1, kHiThreads, smem);
-  k_hub_tab<P><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, r1)), kHiThreads, smem, c.st>>>(
+  const int64_t spans = (L.n_hub_chunks + kSpanChunks - 1) / kSpanChunks;
+  k_hub_tab<P><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(spans, r1)), kHiThreads, smem, c.st>>>(
       view(L), hub_rows(L), pol, L.hub_split_deg, L.hub_sidx, L.hub_gtab, c.hub_ctr);
   count_launch();
   if (L.n_split) {
@@ -2104,7 +2139,8 @@ void launch_delta(Ctx& c, int lvl, Mv mv, int kind) {
         view(L), L.hi, L.n_hi, L.pi, mv, c.topo, c.Jacc, c.state, kind); count_launch();
   }
   if (L.n_huge)
-    k_delta_high<Mv><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, (int64_t)c.num_sms * 8)),
+    k_delta_high<Mv><<<(unsigned)std::max<int64_t>(
+                           1, std::min<int64_t>((L.n_hub_chunks + kSpanChunks - 1) / kSpanChunks, (int64_t)c.num_sms * 8)),
                        kHiThreads, 0, c.st>>>(view(L), hub_rows(L), L.pi, mv, c.topo, c.Jacc, c.state, kind);
   if (L.n_huge) count_launch();
 }
@@ -2153,7 +2189,8 @@ void launch_lp(Ctx& c, int lvl) {
   }
   if (L.n_huge) {
     const int64_t res = (int64_t)c.num_sms * c.resident_blocks((const void*)k_lp_after_hub, kHiThreads, 0);
-    k_lp_after_hub<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(L.n_hub_chunks, res)), kHiThreads, 0, c.st>>>(
+    const int64_t spans = (L.n_hub_chunks + kSpanChunks - 1) / kSpanChunks;
+    k_lp_after_hub<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(spans, res)), kHiThreads, 0, c.st>>>(
         view(L), hub_rows(L), L.pi, c.pp, c.gain, c.inx, L.hub_acc, c.topo, c.state, c.hub_ctr);
     count_launch();
     k_lp_after_hub_finish<<<grid_for(c, kThreads, L.n_huge), kThreads, 0, c.st>>>(hub_rows(L), c.inx, L.hub_acc,
