@@ -57,8 +57,6 @@ L2_FLUSH_BYTES = 512 << 20
 # profiles/k_match_prefer_rgg2e20_level0.md),
 # valid only while the kernel's source hash matches.
 TRAFFIC = {
-    ("rgg2d", "eval_J"): {"kernel": "k_eval_tile", "kernel_hash": "6ae06d04190287ca", "dram_bytes": 116894208,
-               "alg_bytes": 163348488, "dram_per_alg_byte": 116894208 / 163348488},
     ("rgg2d", "lp_gain"): {"kernel": "k_lp_gain_tile", "kernel_hash": "6b701f37fb0860d6", "dram_bytes": 120026880,
                 "alg_bytes": 178028552, "dram_per_alg_byte": 120026880 / 178028552},
     ("rgg2d", "cluster"): {"kernel": "k_cluster_tile", "kernel_hash": "03b2663e5efeed5a", "dram_bytes": 129838592,

@@ -46,8 +46,11 @@ void pinned_put(void* p) {
 // which by default hands freed memory back to the system at every
 // synchronisation, so that the next context maps it again.  Keeping up to
 // kPoolKeepBytes of freed blocks in the pool makes creating and destroying
-// contexts cheap (serving, hierarchical multisection).  Once per device.
-constexpr uint64_t kPoolKeepBytes = 8ULL << 30;
+// contexts cheap (serving, hierarchical multisection, repeated maps of one
+// large graph: a context for R-MAT scale 22 holds more than 8 GB, and with
+// an 8 GB bound every other map_create spent about 50 ms mapping memory
+// back).  Once per device.
+constexpr uint64_t kPoolKeepBytes = 32ULL << 30;
 void keep_pool_memory(int dev) {
   static std::atomic<unsigned long long> done{0};  // one bit per device
   const unsigned long long bit = 1ULL << (dev & 63);

@@ -2623,6 +2623,10 @@ struct EngGeom {
 __device__ __forceinline__ bool eng_heavy(const EngineJob& J, int64_t deg) {
   return J.has_heavy && deg > kEngLaneDeg;
 }
+// The same for vertex v (its row bounds are read only when the level has such rows).
+__device__ __forceinline__ bool eng_heavy_row(const EngineJob& J, int64_t v) {
+  return J.has_heavy && J.g.xadj[v + 1] - J.g.xadj[v] > kEngLaneDeg;
+}
 
 // Calls f(v, b, e) for every row of more than kEngLaneDeg entries that falls
 // to the calling CTA (rows dealt round-robin over the cluster's CTAs); all
@@ -2803,7 +2807,7 @@ __device__ void eng_delta(const EngineJob& J, const Mv& mv, EngSmem& S, const En
   for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
     const int64_t v = tile * kTileV + lane;
     const unsigned work =
-        __ballot_sync(0xffffffffu, v < g.n && mv.moved(v) && !eng_heavy(J, g.xadj[v + 1] - g.xadj[v]));
+        __ballot_sync(0xffffffffu, v < g.n && mv.moved(v) && !eng_heavy_row(J, v));
     const int rounds = (__popc(work) + 3) / 4;
     for (int r = 0; r < rounds; r++) {
       const int src = tile_worker(work, r, sub);
@@ -3055,7 +3059,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       for (int64_t tile = eg.gw; tile < ntiles; tile += eg.GW) {
         const int64_t v = tile * kTileV + lane;
         const unsigned work =
-            __ballot_sync(0xffffffffu, v < n && J.inx[v] && !eng_heavy(J, g.xadj[v + 1] - g.xadj[v]));
+            __ballot_sync(0xffffffffu, v < n && J.inx[v] && !eng_heavy_row(J, v));
         const int sub = lane >> 3, sl = lane & 7;
         const int rounds = (__popc(work) + 3) / 4;
         for (int r = 0; r < rounds; r++) {
@@ -3124,7 +3128,7 @@ __device__ void engine_run_job(const EngineJob& J, EngSmem& S, int32_t* dyn, int
       const int64_t v = tile * kTileV + lane;
       int32_t A = -1;
       bool cand = false;
-      if (v < n && !eng_heavy(J, g.xadj[v + 1] - g.xadj[v])) {
+      if (v < n && !eng_heavy_row(J, v)) {
         A = J.pi[v];
         const int64_t WA = J.W[A];
         cand = WA > J.lmax && 2 * (int64_t)J.k * g.vw[v] <= 3 * ((int64_t)J.k * WA - J.cV);
