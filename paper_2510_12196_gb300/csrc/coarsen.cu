@@ -331,6 +331,12 @@ constexpr uint32_t kSmemSlots = 4096;  // >= 2 (kSmemRowDeg + 1)
 static_assert(kSmemSlots >= 2 * (kSmemRowDeg + 1), "shared-memory row table at most half full");
 // rows of one chunk at most: every row there has more than kLowDeg + 1 >= 33 entries
 constexpr int kChunkRows = 64;
+// rows of at most kGroupRowDeg entries are rated by kRowGroups thread groups
+// of a CTA side by side, each with its share of the shared-memory table
+constexpr int kRowGroups = 2;
+constexpr int64_t kGroupRowDeg = kSmemSlots / kRowGroups / 2 - 1;
+static_assert(kSmemSlots / kRowGroups >= 2 * (kGroupRowDeg + 1), "a group's table at most half full");
+static_assert(kRowGroups <= 2, "named barriers 1 and 2 serve the row groups");
 static_assert(kHubChunk / 34 + 2 <= kChunkRows, "a chunk's rows fit the per-chunk row table");
 
 // Inserts from slot h on (`probes` already made).
@@ -355,21 +361,39 @@ __device__ __forceinline__ bool hub_insert(unsigned long long* T, uint32_t mask,
 // entries a thread keeps in flight
 constexpr int kHubBatch = 4;
 
-// Inserts the CSR entries [e0, e1) of a row (labels gathered from C) with
-// stride blockDim.x: per thread kHubBatch entries at a time, whose loads,
+// The threads that rate one row together: the whole CTA (barrier 0), or one
+// of the groups of consecutive warps that rate rows side by side, each with
+// its own named barrier.
+struct RowGroup {
+  int tid, size;    // thread index in the group, group size (a multiple of 32)
+  int warp0, warps; // the group's warps within the CTA
+  int bar;          // 0: the CTA barrier; else a named barrier of `size` threads
+  __device__ __forceinline__ void sync() const {  // (immediate barrier ids: the kernel reserves three)
+    if (bar == 0) __syncthreads();
+    else if (bar == 1) asm volatile("bar.sync 1, %0;" ::"r"(size) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"r"(size) : "memory");
+  }
+};
+__device__ __forceinline__ RowGroup cta_group() {
+  return RowGroup{(int)threadIdx.x, (int)blockDim.x, 0, (int)(blockDim.x >> 5), 0};
+}
+
+// Inserts the CSR entries [e0, e1) of a row (labels gathered from C) by the
+// threads of group gr: per thread kHubBatch entries at a time, whose loads,
 // label gathers and first compare-and-swaps are each issued before any
 // result is used; only collisions with another label probe on.  Returns
 // false if a table overflowed.
 __device__ __forceinline__ bool hub_insert_range(const GraphView& g, const int32_t* __restrict__ C, int64_t e0,
-                                                 int64_t e1, unsigned long long* T, uint32_t mask) {
+                                                 int64_t e1, unsigned long long* T, uint32_t mask,
+                                                 const RowGroup& gr) {
   bool ok = true;
-  for (int64_t f0 = e0; f0 < e1; f0 += (int64_t)blockDim.x * kHubBatch) {
+  for (int64_t f0 = e0; f0 < e1; f0 += (int64_t)gr.size * kHubBatch) {
     int32_t t[kHubBatch], w[kHubBatch];
     uint32_t h[kHubBatch];
     unsigned long long prev[kHubBatch];
 #pragma unroll
     for (int b = 0; b < kHubBatch; b++) {
-      const int64_t e = f0 + (int64_t)b * blockDim.x + threadIdx.x;
+      const int64_t e = f0 + (int64_t)b * gr.size + gr.tid;
       t[b] = e < e1 ? g.adj[e] : -1;
       w[b] = e < e1 ? g.adjw[e] : 0;
     }
@@ -404,27 +428,29 @@ struct HubScratch {
 // L2, where other CTAs' atomics were performed): the largest weight, then
 // the smaller tie-hash, then the smaller label, in two passes so that only
 // labels of the largest weight are hashed; every slot is put back to empty.
-// All threads of the CTA call it; thread 0 receives the result (bs = -1 for
-// no label); ends with a barrier.
+// All threads of group gr call it; the group's thread 0 receives the result
+// (bs = -1 for no label); ends with the group's barrier.
 template <bool kGlobal>
 __device__ __forceinline__ void table_best(unsigned long long* T, uint32_t s0, uint32_t s1, const ClusterArgs& a,
-                                           HubScratch& sx, int32_t& out_bs, uint64_t& out_bh, int32_t& out_bt) {
+                                           HubScratch& sx, const RowGroup& gr, int32_t& out_bs, uint64_t& out_bh,
+                                           int32_t& out_bt) {
+  const int warp = (int)(threadIdx.x >> 5);
   int32_t bs = -1;
 #pragma unroll 4
-  for (uint32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+  for (uint32_t s = s0 + gr.tid; s < s1; s += gr.size) {
     const unsigned long long x = kGlobal ? __ldcg(T + s) : T[s];
     if (x != kEmptySlot) bs = max(bs, (int32_t)(uint32_t)x);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) bs = max(bs, __shfl_xor_sync(0xffffffffu, bs, o));
-  if ((threadIdx.x & 31) == 0) sx.bs[threadIdx.x >> 5] = bs;
-  __syncthreads();
-  bs = sx.bs[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); w++) bs = max(bs, sx.bs[w]);
+  if ((threadIdx.x & 31) == 0) sx.bs[warp] = bs;
+  gr.sync();
+  bs = sx.bs[gr.warp0];
+  for (int w = 1; w < gr.warps; w++) bs = max(bs, sx.bs[gr.warp0 + w]);
   uint64_t bh = ~0ULL;
   int32_t bt = INT32_MAX;
 #pragma unroll 4
-  for (uint32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+  for (uint32_t s = s0 + gr.tid; s < s1; s += gr.size) {
     const unsigned long long x = kGlobal ? __ldcg(T + s) : T[s];
     if (x == kEmptySlot) continue;
     T[s] = kEmptySlot;
@@ -446,21 +472,24 @@ __device__ __forceinline__ void table_best(unsigned long long* T, uint32_t s0, u
     }
   }
   if ((threadIdx.x & 31) == 0) {
-    sx.bh[threadIdx.x >> 5] = bh;
-    sx.bt[threadIdx.x >> 5] = bt;
+    sx.bh[warp] = bh;
+    sx.bt[warp] = bt;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-      if (sx.bh[w] < bh || (sx.bh[w] == bh && sx.bt[w] < bt)) {
-        bh = sx.bh[w];
-        bt = sx.bt[w];
+  gr.sync();
+  if (gr.tid == 0) {
+    for (int w = 1; w < gr.warps; w++) {
+      const uint64_t h = sx.bh[gr.warp0 + w];
+      const int32_t t = sx.bt[gr.warp0 + w];
+      if (h < bh || (h == bh && t < bt)) {
+        bh = h;
+        bt = t;
       }
+    }
     out_bs = bs;
     out_bh = bh;
     out_bt = bt;
   }
-  __syncthreads();
+  gr.sync();
 }
 
 // The larger rows' slice results: per chunk two slots (0: the large row
@@ -473,15 +502,16 @@ __device__ __forceinline__ int64_t part_slot(int64_t ch, int64_t rb) {
 
 // Sub-round step 1 for the rows of degree > kMidDeg: the rows on the
 // shared-memory path are rated and decided here; the larger rows only insert.
-__global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRows hr,
+__global__ void __launch_bounds__(kHiThreads, 5) k_cluster_high(GraphView g, HubRows hr,
                                                              const int64_t* __restrict__ hoff,
                                                              unsigned long long* htab, ClusterArgs a,
                                                              unsigned long long* ctr, uint32_t* err) {
   static_assert(kHiThreads >= kChunkRows, "one thread per row of a chunk");
-  __shared__ unsigned long long stab[kSmemSlots];
+  static_assert(kHiThreads % (32 * kRowGroups) == 0, "whole warps per row group");
+  __shared__ unsigned long long stab[kSmemSlots];  // the groups' tables side by side, or one CTA table
   __shared__ HubScratch sx;
-  __shared__ int32_t s_bs, s_bt;
-  __shared__ uint64_t s_bh;
+  __shared__ int32_t s_bs[kRowGroups], s_bt[kRowGroups];
+  __shared__ uint64_t s_bh[kRowGroups];
   __shared__ int64_t s_ch;
   // the rows of the current chunk, looked up at once (one thread each): a
   // row's lookup is a chain of dependent loads that would otherwise run
@@ -524,21 +554,47 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRow
       s_re[threadIdx.x] = re;
     }
     const int nrows = __syncthreads_count(row);  // the chunk's rows are a prefix
+    {
+      // rows of at most kGroupRowDeg entries: the row groups side by side,
+      // row i to group i mod kRowGroups, each with its part of the table
+      constexpr int kG = kHiThreads / kRowGroups;
+      const int gi = (int)threadIdx.x / kG;
+      const RowGroup gr{(int)threadIdx.x % kG, kG, gi * (kG / 32), kG / 32, 1 + gi};
+      unsigned long long* gtab = stab + gi * (kSmemSlots / kRowGroups);
+      for (int i = gi; i < nrows; i += kRowGroups) {
+        const int32_t v = s_v[i];
+        const int64_t deg = s_re[i] - s_rb[i];
+        if (v < 0 || deg > kGroupRowDeg) continue;
+        const int32_t own = s_own[i];
+        uint32_t size = 64;
+        while (size < 2 * (uint32_t)(deg + 1)) size <<= 1;
+        bool ok = true;
+        if (gr.tid == 0) ok = hub_insert(gtab, size - 1, own, 0);
+        ok &= hub_insert_range(g, a.C, s_x0[i] + s_rb[i], s_x0[i] + s_re[i], gtab, size - 1, gr);
+        if (!ok) atomicOr(err, ERR_CAPACITY);
+        gr.sync();
+        table_best<false>(gtab, 0, size, a, sx, gr, s_bs[gi], s_bh[gi], s_bt[gi]);
+        if (gr.tid == 0) cluster_request(a, v, own, s_bt[gi], g.vw[v]);
+      }
+    }
+    __syncthreads();  // the groups' tables are empty again: the whole table is the CTA's
+    const RowGroup cta = cta_group();
     for (int i = 0; i < nrows; i++) {
       const int32_t v = s_v[i];
       if (v < 0) continue;
       const int64_t rb = s_rb[i], re = s_re[i], deg = re - rb, x0 = s_x0[i];
+      if (deg <= kGroupRowDeg) continue;  // rated by a row group above
       const int32_t own = s_own[i];
       bool ok = true;
       if (deg <= kSmemRowDeg) {
         uint32_t size = 64;
         while (size < 2 * (uint32_t)(deg + 1)) size <<= 1;
         if (threadIdx.x == 0) ok = hub_insert(stab, size - 1, own, 0);
-        ok &= hub_insert_range(g, a.C, x0 + rb, x0 + re, stab, size - 1);
+        ok &= hub_insert_range(g, a.C, x0 + rb, x0 + re, stab, size - 1, cta);
         if (!ok) atomicOr(err, ERR_CAPACITY);
         __syncthreads();
-        table_best<false>(stab, 0, size, a, sx, s_bs, s_bh, s_bt);
-        if (threadIdx.x == 0) cluster_request(a, v, own, s_bt, g.vw[v]);
+        table_best<false>(stab, 0, size, a, sx, cta, s_bs[0], s_bh[0], s_bt[0]);
+        if (threadIdx.x == 0) cluster_request(a, v, own, s_bt[0], g.vw[v]);
         continue;
       }
       const int32_t idx = s_idx[i];
@@ -546,7 +602,7 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_high(GraphView g, HubRow
       const uint32_t mask = (uint32_t)(hoff[idx + 1] - base) - 1u;
       unsigned long long* T = htab + base;
       if (rb >= cb && threadIdx.x == 0) ok = hub_insert(T, mask, own, 0);
-      ok &= hub_insert_range(g, a.C, x0 + max(rb, cb), x0 + min(re, ce), T, mask);
+      ok &= hub_insert_range(g, a.C, x0 + max(rb, cb), x0 + min(re, ce), T, mask, cta);
       if (!ok) atomicOr(err, ERR_CAPACITY);
     }
   }
@@ -594,7 +650,7 @@ __global__ void __launch_bounds__(kHiThreads) k_cluster_giant(HubRows hr, const 
       const int64_t base = hoff[idx];
       const int64_t S = hoff[idx + 1] - base;
       const uint32_t s0 = (uint32_t)(S * (max(rb, cb) - rb) / deg), s1 = (uint32_t)(S * (min(re, ce) - rb) / deg);
-      table_best<true>(htab + base, s0, s1, a, sx, s_bs, s_bh, s_bt);
+      table_best<true>(htab + base, s0, s1, a, sx, cta_group(), s_bs, s_bh, s_bt);
       if (threadIdx.x == 0) {
         const int64_t p = part_slot(ch, rb);
         part[p] = ((unsigned long long)(uint32_t)s_bs << 32) | (uint32_t)s_bt;
