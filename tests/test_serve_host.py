@@ -218,6 +218,12 @@ def test_wait_timeout_poll_and_cancel():
 def test_invalid_options_and_jobs():
     with pytest.raises(G.MapError):
         G.MapServer(slots=-1)
+    # batcher lanes in -1..16 (0: the default), whole_gpu_levels 0 or 1
+    for bad_opts in (dict(batch_lanes=-2), dict(batch_lanes=17), dict(whole_gpu_levels=2),
+                     dict(whole_gpu_levels=-1)):
+        with pytest.raises(G.MapError) as e:
+            G.MapServer(runner=lambda *a: 0, **bad_opts)
+        assert e.value.status == 1, bad_opts
     h = Harness(slots=1)
     try:
         bad = I.Graph(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32),
@@ -225,5 +231,20 @@ def test_invalid_options_and_jobs():
         with pytest.raises(G.MapError) as e:
             h.srv.submit(bad, HIER, DIST)
         assert e.value.status == 1
+    finally:
+        h.close()
+
+
+def test_runner_servers_have_no_level_batcher():
+    """With a stand-in runner there is no GPU pipeline, so no level batcher
+    runs (its counters stay zero), whatever batch_lanes asks for."""
+    h = Harness(slots=2, batch_lanes=4)
+    try:
+        t = h.submit(0, 100)
+        h.let_go(0)
+        r, _ = h.srv.wait(t)
+        assert r.status == 0
+        st = h.srv.stats()
+        assert (st.engine_launches, st.engine_jobs, st.peak_batch) == (0, 0, 0)
     finally:
         h.close()
