@@ -540,6 +540,8 @@ def run_ours(args, ws, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": config_of(w, {"levels": levels, "level_n": [st.n[i] for i in range(levels)],
                                         "refine_rounds": [st.iters[i] for i in range(levels)],
+                                        "refine_kinds_lp_weak_strong": [[st.lp_iters[i], st.weak_iters[i],
+                                                                         st.strong_iters[i]] for i in range(levels)],
                                         "schedule": {"mid_deg": [st.mid_deg[i] for i in range(levels)],
                                                      "split_deg": [st.split_deg[i] for i in range(levels)],
                                                      "autotuned": [st.tuned[i] for i in range(levels)],

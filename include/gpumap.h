@@ -134,6 +134,9 @@ typedef struct {
   int32_t split_deg[65];   /* hub split bound in force on each level (INT32_MAX: every hub row rated whole) */
   int32_t tuned[65];       /* 1: chosen by the autotuner; 0: defaults or the config's */
   double ms_tune;          /* host wall time the autotuner has spent on this context */
+  int32_t lp_iters[65];    /* of iters[]: label-propagation, weak and strong rebalancing iterations per */
+  int32_t weak_iters[65];  /* level (map_run; counted over the first 4096 iterations of a level) */
+  int32_t strong_iters[65];
 } map_stats_t;
 
 /* Fills *cfg with the defaults listed above (seed 0x5EED0000, no allocator). */

@@ -641,6 +641,17 @@ map_status map_run(map_ctx* ctx, int32_t* out_pi, int64_t* out_J) {
         c.iters[l] = it;
         c.Jlev[l] = J;
         c.ms_level[l] = dt;
+        // the kinds of the level's iterations (the trace holds the first trace_cap)
+        const int32_t cnt = std::min(it, c.trace_cap);
+        c.kinds[l][0] = c.kinds[l][1] = c.kinds[l][2] = 0;
+        if (cnt > 0) {
+          std::vector<int32_t> tk((size_t)cnt);
+          GM_CUDA(cudaMemcpyAsync(tk.data(), c.trace_kind, (size_t)cnt * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  c.st));
+          sync(c);
+          for (int32_t k : tk)
+            if (k >= KIND_LP && k <= KIND_STRONG) c.kinds[l][k]++;
+        }
       }
     }
     if (out_pi) {
@@ -705,6 +716,9 @@ map_status map_stats(map_ctx* ctx, map_stats_t* out) {
       out->mid_deg[l] = c.lv[l].mid_deg;
       out->split_deg[l] = (int32_t)std::min<int64_t>(c.lv[l].hub_split_deg, INT32_MAX);
       out->tuned[l] = c.lv[l].tuned;
+      out->lp_iters[l] = c.kinds[l][KIND_LP];
+      out->weak_iters[l] = c.kinds[l][KIND_WEAK];
+      out->strong_iters[l] = c.kinds[l][KIND_STRONG];
     }
     out->ms_tune = c.ms_tune;
     out->ms_coarsen = c.ms_coarsen;

@@ -306,6 +306,7 @@ struct Ctx {
   double ms_tune = 0;             // host wall time the schedule autotuner spent
   RefineState* probe_state = nullptr;  // kind = LP, for the autotuner's timing probe
   int32_t iters[65] = {0};
+  int32_t kinds[65][3] = {};  // map_run: LP, weak and strong iterations per level (from the trace)
   int64_t Jlev[65] = {0};
   double ms_level[65] = {0};
 };

@@ -53,7 +53,8 @@ class MapStats(C.Structure):
                 ("ms_initial", C.c_double), ("ms_refine", C.c_double), ("ms_project", C.c_double),
                 ("device_bytes", C.c_int64), ("device_bytes_peak", C.c_int64),
                 ("ms_refine_level", C.c_double * 65), ("mid_deg", C.c_int32 * 65), ("split_deg", C.c_int32 * 65),
-                ("tuned", C.c_int32 * 65), ("ms_tune", C.c_double)]
+                ("tuned", C.c_int32 * 65), ("ms_tune", C.c_double), ("lp_iters", C.c_int32 * 65),
+                ("weak_iters", C.c_int32 * 65), ("strong_iters", C.c_int32 * 65)]
 
 
 class MapHmStats(C.Structure):

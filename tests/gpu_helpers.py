@@ -63,6 +63,8 @@ def map_run_compare(g, hier, dist, eps=0.03, seed=0x5EED0000, **over):
     assert [st.n[i] for i in range(st.levels)] == [ost.n[i] for i in range(ost.levels)]
     assert [st.iters[i] for i in range(st.levels)] == [ost.iters[i] for i in range(ost.levels)]
     assert [st.J[i] for i in range(st.levels)] == [ost.J[i] for i in range(ost.levels)]
+    for i in range(st.levels):  # the per-level split of the iterations into LP, weak and strong steps
+        assert st.lp_iters[i] + st.weak_iters[i] + st.strong_iters[i] == min(st.iters[i], 4096), i
     assert J == oJ
     assert np.array_equal(pi, opi)
     return J
